@@ -1,0 +1,521 @@
+#!/usr/bin/env python3
+"""Benchmark of the run-time format transformation + SpMV + AT hot path.
+
+One step = one pass of every row of the hot path over one synthetic matrix,
+through the C ABI:
+  on-line AT (analysis, D_mat, choice, build of the chosen format),
+  CRS schedule, CRS -> COO-Row, CRS -> ELL-Row, Phase I (CRS -> CCS),
+  Phase II (CCS -> COO-Column), CCS -> ELL-Column,
+  SpMV in CRS, COO-Row, ELL-Row, COO-Column and ELL-Column.
+`value` is the step's algorithmic bytes (the byte model below) over the
+device time of the step, summed over ranks (each rank runs its own replica).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SpMV GB/s (% HBM peak) per format; CRS->ELL cost in CRS-SpMV units; p99 ms"
+L2_BYTES = 129 * 1024 * 1024
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    "stencil27_128": dict(kind="stencil27", N=128, seed_a=1, seed_x=2, cap=0,
+                          desc="3-D 27-point stencil, 128^3 grid, N(0,1) off-diagonals, "
+                               "diagonal 27 + |row sum|, x U[-1,1]"),
+    "laplace2d_64": dict(kind="laplace", N=64, seed_x=0, cap=0,
+                         desc="2-D 5-point Laplacian, 64x64 grid, x U[-1,1]"),
+    "powerlaw_4m": dict(kind="powerlaw", n=4_000_000, seed_a=3, seed_x=4, cap=40 * 10 ** 9,
+                        desc="n = 4e6, truncated power-law row lengths (exponent 2, mean 16, max 20000), "
+                             "sorted unique random columns"),
+}
+DEFAULT_WORKLOAD = "stencil27_128"
+
+
+# ----------------------------------------------------------------- inputs
+def make_matrix(w: dict, rank: int = 0):
+    import spmv_synth as synth
+    off = 1000 * rank  # each rank its own replica
+    if w["kind"] == "stencil27":
+        H = synth.stencil_3d_27pt(w["N"], seed=w["seed_a"] + off)
+    elif w["kind"] == "laplace":
+        H = synth.laplacian_2d_5pt(w["N"])
+    else:
+        H = synth.power_law(w["n"], seed=w["seed_a"] + off)
+    x = synth.vector_pm1(H.n_cols, seed=w["seed_x"] + off)
+    return H, x
+
+
+# -------------------------------------------------------------- byte model
+def round32(n: int) -> int:
+    return (n + 31) // 32 * 32
+
+
+def byte_model(n_rows: int, n_cols: int, nnz: int, W: int, Wc: int) -> dict:
+    """Algorithmic bytes of each hot-path row (x and y counted once)."""
+    ld, ldc = round32(n_rows), round32(n_cols)
+    xy = 8 * n_cols + 8 * n_rows
+    return {
+        "analyze": 4 * (n_rows + 1),
+        "crs_schedule": 4 * (n_rows + 1) + 4 * nnz,  # row statistics + index check
+        "crs_to_coo_row": 4 * (n_rows + 1) + 4 * nnz,
+        "crs_to_ell_row": 12 * nnz + 4 * (n_rows + 1) + 12 * ld * W,
+        "phase1_ccs": (4 * nnz + 4 * n_cols) + 8 * n_cols + (12 * nnz + 4 * (n_rows + 1) + 12 * nnz),
+        "ccs_to_coo_col": 4 * (n_cols + 1) + 4 * nnz,
+        "ccs_to_ell_col": 12 * nnz + 4 * (n_cols + 1) + 12 * ldc * Wc,
+        "spmv_crs": 12 * nnz + 4 * (n_rows + 1) + xy,
+        "spmv_coo_row": 16 * nnz + xy,
+        "spmv_ell_row": 12 * ld * W + xy,
+        "spmv_coo_col": 16 * nnz + xy,
+        "spmv_ell_col": 12 * ldc * Wc + xy,
+    }
+
+
+def kernel_bytes(name: str, bm: dict, n_rows: int, n_cols: int, nnz: int):
+    """Bytes one launch of a library kernel moves by design (None: not modelled)."""
+    table = {
+        "spmv_ell_row": bm["spmv_ell_row"],
+        "spmv_coo_row": bm["spmv_coo_row"],
+        "spmv_coo_col": bm["spmv_coo_col"],
+        "spmv_ell_col": bm["spmv_ell_col"],
+        "crs_to_ell_row": bm["crs_to_ell_row"],
+        "ccs_to_ell_col": bm["ccs_to_ell_col"],
+        "crs_to_coo_row": bm["crs_to_coo_row"],
+        "ccs_to_coo_col": bm["ccs_to_coo_col"],
+        "analyze": bm["analyze"],
+        "validate_idx": 4 * nnz,
+        # Phase I as built here: ICOL in, rank out; rank + ICOL in, (k, row)
+        # pairs out; pairs + VAL gather in, ICOL_T + VAL_T out
+        "col_count": 8 * nnz + 4 * n_cols,
+        "scan_lookback": 8 * n_cols,
+        "col_scatter": 16 * nnz + 4 * (n_rows + 1) + 4 * n_cols,
+        "col_fixup_warp": 28 * nnz + 4 * n_cols,
+    }
+    if name.startswith("spmv_crs_v"):
+        return bm["spmv_crs"]
+    return table.get(name)
+
+
+# --------------------------------------------------------------- the step
+class Step:
+    """All hot-path rows through the C ABI on one device-resident matrix."""
+
+    def __init__(self, L, A, x, ys, dstar: float, cap: int):
+        self.L, self.A, self.x, self.ys = L, A, x, ys
+        self.dstar, self.cap = dstar, cap
+        self.chosen = None
+
+    def run(self):
+        L, A = self.L, self.A
+        chosen, stats = L.spmv_autotune(A, dstar=self.dstar, mem_cap_bytes=self.cap)
+        fmt = chosen.describe()["format"]
+        self.chosen = {0: "CRS", 1: "COO-Row", 2: "ELL-Row"}[fmt]
+        mats = {}
+        mats["crs"] = chosen if fmt == L.SPMV_CRS else L.spmv_transform(A, L.SPMV_CRS, L.SPMV_ROWWISE)
+        mats["coo_row"] = L.spmv_transform(A, L.SPMV_COO, L.SPMV_ROWWISE)
+        if fmt == L.SPMV_ELL:
+            mats["ell_row"] = chosen
+        elif not self.cap or stats["ell_bytes"] <= self.cap:
+            mats["ell_row"] = L.spmv_transform(A, L.SPMV_ELL, L.SPMV_ROWWISE, self.cap)
+        ccs = L.spmv_transform(A, L.SPMV_CRS, L.SPMV_COLWISE, self.cap)
+        mats["coo_col"] = L.spmv_transform_from(ccs, L.SPMV_COO, self.cap)
+        mats["ell_col"] = L.spmv_transform_from(ccs, L.SPMV_ELL, self.cap)
+        for name, M in mats.items():
+            L.spmv_apply(M, self.x, self.ys[name])
+        for M in list(mats.values()) + [ccs]:
+            M.close()
+        return stats
+
+
+def calibrate_dstar(L, torch, quick: bool = True):
+    """Off-line phase (Sec. 2.2) on a small synthetic set on this device."""
+    import spmv_synth as synth
+    mats = [synth.laplacian_2d_5pt(256), synth.stencil_3d_27pt(40),
+            synth.random_crs(200000, 200000, 12, seed=41),
+            synth.power_law(200000, kmax=2000, seed=42), synth.power_law(200000, kmax=20000, seed=43)]
+    dev = [L.Crs.from_host(H) for H in mats]
+    dstar, d, r = L.spmv_calibrate(dev, c=1.0, timing_reps=5 if quick else 20, warmup_reps=2)
+    return dstar, d, r
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.out.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out:
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ distributed
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def reduce_max_sum(torch, ms: float, nbytes: float, device, group=None):
+    """(max of ms, sum of bytes) over ranks; identity when not distributed."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return ms, nbytes
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    b = torch.tensor([nbytes], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM, group=group)
+    return float(t.item()), float(b.item())
+
+
+def barrier_sync(torch):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_step(H, xh) -> dict:
+    """The same rows on the CPU oracle; returns {row: seconds}."""
+    import oracle
+    t = {}
+    c = time.perf_counter
+    t0 = c(); st = oracle.analyze(H.n_rows, H.irp); t["analyze"] = c() - t0
+    t0 = c(); irow = oracle.crs_to_coo_row(H.n_rows, H.irp); t["crs_to_coo_row"] = c() - t0
+    t0 = c(); ev, ec, W = oracle.crs_to_ell_row(H.n_rows, H.irp, H.icol, H.val); t["crs_to_ell_row"] = c() - t0
+    t0 = c(); irp_t, icol_t, val_t, nc = oracle.crs_to_ccs(H.n_rows, H.n_cols, H.irp, H.icol, H.val)
+    t["phase1_ccs"] = c() - t0
+    t0 = c(); jcol = oracle.ccs_to_coo_col(H.n_cols, irp_t); t["ccs_to_coo_col"] = c() - t0
+    t0 = c(); ev2, er2, W2 = oracle.ccs_to_ell_col(H.n_cols, irp_t, icol_t, val_t); t["ccs_to_ell_col"] = c() - t0
+    t0 = c(); oracle.spmv_crs(H.n_rows, H.irp, H.icol, H.val, xh); t["spmv_crs"] = c() - t0
+    t0 = c(); oracle.spmv_coo(H.n_rows, irow, H.icol, H.val, xh); t["spmv_coo_row"] = c() - t0
+    t0 = c(); oracle.spmv_ell_row(H.n_rows, W, ev, ec, xh); t["spmv_ell_row"] = c() - t0
+    t0 = c(); oracle.spmv_coo(H.n_rows, icol_t, jcol, val_t, xh); t["spmv_coo_col"] = c() - t0
+    t0 = c(); oracle.spmv_ell_col(H.n_rows, H.n_cols, W2, ev2, er2, xh); t["spmv_ell_col"] = c() - t0
+    t["_W"], t["_Wc"] = W, W2
+    return t
+
+
+def oracle_bytes(H, W, Wc) -> float:
+    bm = byte_model(H.n_rows, H.n_cols, H.nnz, W, Wc)
+    # the oracle's ELL has ld = n; the row set matches the GPU step minus the
+    # CRS schedule (the oracle needs none)
+    keys = ["analyze", "crs_to_coo_row", "crs_to_ell_row", "phase1_ccs", "ccs_to_coo_col", "ccs_to_ell_col",
+            "spmv_crs", "spmv_coo_row", "spmv_ell_row", "spmv_coo_col", "spmv_ell_col"]
+    return float(sum(bm[k] for k in keys))
+
+
+def cpu_baseline(H, xh, budget_s: float = 12.0) -> dict:
+    """Times the oracle on a bounded row sample of the workload."""
+    frac = 8
+    rows = max(1, H.n_rows // frac)
+    S = H.row_slice(0, rows)
+    xs = xh  # the slice keeps all columns
+    tot_t, tot_b, runs = 0.0, 0.0, 0
+    while tot_t < budget_s and runs < 20:
+        t = oracle_step(S, xs)
+        tot_t += sum(v for k, v in t.items() if not k.startswith("_"))
+        tot_b += oracle_bytes(S, t["_W"], t["_Wc"])
+        runs += 1
+    return {"value": tot_b / tot_t / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"rows 0..{rows} of {H.n_rows} ({S.nnz} nnz), {runs} oracle step(s), {tot_t:.1f} s, "
+                      f"single thread, FP64 serial loops"}
+
+
+# -------------------------------------------------------------- reference
+def run_reference(args, w: dict) -> None:
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    H, xh = make_matrix(w)
+    rows = max(1, H.n_rows // 16)
+    S = H.row_slice(0, rows)
+    for _ in range(args.warmup):
+        oracle_step(S, xh)
+    ts, bs = [], []
+    for _ in range(args.steps):
+        t = oracle_step(S, xh)
+        ts.append(sum(v for k, v in t.items() if not k.startswith("_")))
+        bs.append(oracle_bytes(S, t["_W"], t["_Wc"]))
+    total = sum(ts)
+    value = sum(bs) / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample_rows": rows, "sample_nnz": S.nnz, "n": H.n_rows,
+                   "nnz": H.nnz},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"rows 0..{rows} of {H.n_rows} per step, single-thread FP64 oracle"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- main
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def csrc_digest() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2407_00019_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the
+    current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(p) as f:
+            rows = json.load(f)
+    except (OSError, ValueError):
+        return None
+    for r in rows:
+        if r.get("kernel") == kernel and r.get("workload") == workload and r.get("csrc") == csrc_digest():
+            return r.get("bytes_per_launch")
+    return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    import paper_2407_00019_gb300 as L
+    L.load_library()
+
+    H, xh = make_matrix(w, rank)
+    A = L.Crs.from_host(H)
+    x = torch.from_numpy(xh).to(device)
+    fmts = ["crs", "coo_row", "ell_row", "coo_col", "ell_col"]
+    ys = {f: torch.empty(H.n_rows, dtype=torch.float64, device=device) for f in fmts}
+    dstar, d_pts, r_pts = calibrate_dstar(L, torch)
+    step = Step(L, A, x, ys, dstar, w["cap"])
+    stats = L.spmv_analyze(A)
+    W = stats["W"]
+    ccs = L.spmv_transform(A, L.SPMV_CRS, L.SPMV_COLWISE)
+    ell_c = L.spmv_transform_from(ccs, L.SPMV_ELL)
+    Wc = ell_c.describe()["width"]
+    ell_c.close(); ccs.close()
+    bm = byte_model(H.n_rows, H.n_cols, H.nnz, W, Wc)
+    if w["cap"] and stats["ell_bytes"] > w["cap"]:
+        bm.pop("crs_to_ell_row"); bm.pop("spmv_ell_row")
+    step_bytes = float(sum(bm.values()))
+
+    for _ in range(args.warmup):
+        step.run()
+    stream = torch.cuda.current_stream()
+    barrier_sync(torch)
+    L.spmv_profile_read(reset=True)
+    L.spmv_profile_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = L.spmv_launch_count()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier_sync(torch)
+    ev[0].record(stream)
+    for i in range(args.steps):
+        step.run()
+        ev[i + 1].record(stream)
+    barrier_sync(torch)
+    launches = L.spmv_launch_count() - launches0
+    clk = clocks.stop()
+    L.spmv_profile_enable(False)
+    prof = L.spmv_profile_read(reset=True)
+    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    t_max, bytes_all = reduce_max_sum(torch, total_ms, step_bytes * args.steps, device)
+    value = bytes_all / (t_max * 1e-3) / 1e9
+
+    peak, peak_kind = measured_hbm_peak()
+    per_kernel = {}
+    for name, (n, ms) in prof.items():
+        kb = kernel_bytes(name, bm, H.n_rows, H.n_cols, H.nnz)
+        avg = ms / n
+        per_kernel[name] = {"launches": n, "ms_per_launch": avg, "share": None,
+                            "GB/s": (kb / (avg * 1e-3) / 1e9) if kb else None}
+    ksum = sum(ms for _, ms in prof.values()) or 1.0
+    for name, (n, ms) in prof.items():
+        per_kernel[name]["share"] = ms / ksum
+    top = max(prof.items(), key=lambda kv: kv[1][1])[0]
+    top_b = kernel_bytes(top, bm, H.n_rows, H.n_cols, H.nnz)
+    top_ms = prof[top][1] / prof[top][0]
+    achieved = top_b / (top_ms * 1e-3) / 1e9 if top_b else None
+    roofline = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
+                "traffic": stored_traffic(top, args.workload),
+                "algorithmic_bytes_per_launch": top_b}
+
+    def fmt_rate(kname):
+        if kname not in per_kernel:
+            return None
+        g = per_kernel[kname]["GB/s"]
+        return {"GB/s": g, "pct_hbm": 100.0 * g / peak if g else None,
+                "ms": per_kernel[kname]["ms_per_launch"]}
+    crs_k = [k for k in per_kernel if k.startswith("spmv_crs_v")]
+    per_format = {"crs": fmt_rate(crs_k[0]) if crs_k else None, "coo_row": fmt_rate("spmv_coo_row"),
+                  "ell_row": fmt_rate("spmv_ell_row"), "coo_col": fmt_rate("spmv_coo_col"),
+                  "ell_col": fmt_rate("spmv_ell_col")}
+    # CRS -> ELL cost in CRS-SpMV units: standalone build, and the fused
+    # build + first SpMV counted beyond the SpMV it replaces
+    t_crs = per_kernel[crs_k[0]]["ms_per_launch"] if crs_k else None
+    cost = None
+    if t_crs and "crs_to_ell_row" in per_kernel:
+        t_an = per_kernel["analyze"]["ms_per_launch"]
+        t_tr = per_kernel["crs_to_ell_row"]["ms_per_launch"]
+        L.spmv_profile_enable(True)
+        yf = torch.empty(H.n_rows, dtype=torch.float64, device=device)
+        for _ in range(5):
+            L.spmv_transform_apply(A, x, yf).close()
+        torch.cuda.synchronize()
+        L.spmv_profile_enable(False)
+        pf = L.spmv_profile_read(reset=True)
+        t_f = pf["crs_to_ell_row_fused_spmv"][1] / pf["crs_to_ell_row_fused_spmv"][0]
+        cost = {"standalone": (t_an + t_tr) / t_crs, "fused_marginal": (t_an + t_f - t_crs) / t_crs,
+                "t_crs_ms": t_crs, "t_trans_ms": t_an + t_tr, "t_fused_ms": t_an + t_f,
+                "byte_floor_standalone": bm["crs_to_ell_row"] / bm["spmv_crs"]}
+
+    e2e = None
+    if not args.no_e2e:
+        pin = {k: torch.from_numpy(v).pin_memory() for k, v in (("irp", H.irp), ("icol", H.icol), ("val", H.val))}
+        xpin = torch.from_numpy(xh).pin_memory()
+        yhost = torch.empty(H.n_rows, dtype=torch.float64).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in pin.values()) + xpin.numel() * 8
+        d2h = yhost.numel() * 8
+        estep = Step(L, A, x, ys, dstar, w["cap"])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier_sync(torch)
+        e0.record(stream)
+        for _ in range(args.steps):
+            A.irp.copy_(pin["irp"], non_blocking=True)
+            A.icol.copy_(pin["icol"], non_blocking=True)
+            A.val.copy_(pin["val"], non_blocking=True)
+            x.copy_(xpin, non_blocking=True)
+            estep.run()
+            yhost.copy_(ys["ell_row" if estep.chosen == "ELL-Row" else "crs"], non_blocking=True)
+        e1.record(stream)
+        barrier_sync(torch)
+        et_max, eb_all = reduce_max_sum(torch, e0.elapsed_time(e1), step_bytes * args.steps, device)
+        e2e = {"value": eb_all / (et_max * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": et_max / args.steps}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(H, xh)
+
+    if rank == 0:
+        srt = sorted(per_step)
+        p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": w["desc"], "n": H.n_rows, "nnz": H.nnz, "W": W,
+                       "W_col": Wc, "D_mat": stats["dmat"], "step_bytes": step_bytes,
+                       "l2": "inputs larger than L2 (CRS %.0f MB vs 129 MB L2); no flush" % (
+                           (12 * H.nnz + 4 * H.n_rows) / 1e6),
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "p50_ms": statistics.median(per_step), "p99_ms": p99,
+            "per_format": per_format,
+            "crs_to_ell_cost": cost,
+            "at": {"dstar": dstar if math.isfinite(dstar) else "inf", "chosen": step.chosen,
+                   "calib_dmat": d_pts, "calib_rell": r_pts},
+            "per_kernel": per_kernel,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,275 @@
+/*
+ * spmvat.h - C ABI of the GB300 (sm_103a) library for run-time sparse-format
+ * transformation, SpMV and format auto-tuning after Katagiri & Sato, "An
+ * Auto-tuning Method for Run-time Data Transformation for Sparse
+ * Matrix-Vector Multiplication" (Sec. 2.1 formats and transformations,
+ * Sec. 2.2 the D_mat / R_ell auto-tuning rule, Sec. 3 SpMV per format).
+ *
+ * Conventions for every entry point
+ *  - Indices are 0-based int32, values float64. A matrix has n_rows rows and
+ *    n_cols columns; nnz < 2^31.
+ *  - Pointers named "device" must point to memory of the current CUDA device;
+ *    pointers named "host" to host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Work is enqueued on it in stream order. Only the calls marked
+ *    SYNC wait for the stream; all others return after enqueueing.
+ *  - Nothing throws, exits or prints. Every call returns an spmv_status; on
+ *    any error, output handles are set to NULL and no handle memory leaks.
+ *  - Kernels never read or write out of bounds on a malformed CRS: entries
+ *    with an index out of range are skipped and reported as
+ *    SPMV_ERR_INVALID_MATRIX by the next SYNC call that reads the status.
+ */
+#ifndef SPMVAT_H
+#define SPMVAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPMVAT_VERSION 1
+
+typedef void *spmv_stream_t; /* cudaStream_t */
+
+typedef enum spmv_status {
+    SPMV_OK = 0,
+    SPMV_ERR_INVALID_ARG = 1,     /* NULL pointer, negative size, bad enum */
+    SPMV_ERR_INVALID_MATRIX = 2,  /* IRP not monotone / not 0..nnz, index out of range */
+    SPMV_ERR_OOM = 3,             /* the allocator returned NULL */
+    SPMV_ERR_MEMORY_CAP = 4,      /* the result would exceed mem_cap_bytes */
+    SPMV_ERR_TIMEOUT = 5,         /* a bounded device-side wait ran out */
+    SPMV_ERR_CUDA = 6,            /* a CUDA runtime call failed */
+    SPMV_ERR_UNSUPPORTED = 7      /* valid request this build does not serve */
+} spmv_status;
+
+/* Storage formats of Sec. 2.1. With SPMV_COLWISE, SPMV_CRS denotes the
+ * compressed-column result of Phase I (CCS). */
+typedef enum spmv_format { SPMV_CRS = 0, SPMV_COO = 1, SPMV_ELL = 2 } spmv_format;
+typedef enum spmv_layout { SPMV_ROWWISE = 0, SPMV_COLWISE = 1 } spmv_layout;
+
+/* A CRS matrix (Sec. 2.1: VAL(1:nnz), ICOL(1:nnz), IRP(1:n+1)), 0-based.
+ * All three arrays are device memory owned by the caller. */
+typedef struct spmv_crs {
+    int32_t n_rows;
+    int32_t n_cols;
+    int64_t nnz;
+    const int32_t *irp;  /* device int32[n_rows+1]; irp[0]=0, non-decreasing, irp[n_rows]=nnz */
+    const int32_t *icol; /* device int32[nnz]; column of each entry, 0 <= icol < n_cols */
+    const double *val;   /* device float64[nnz] */
+} spmv_crs;
+
+/* Row-length statistics (Sec. 2.2, Eq. (4)). */
+typedef struct spmv_stats {
+    double mu;            /* mean nonzeros per row = nnz / n_rows */
+    double sigma;         /* population standard deviation of the row lengths */
+    double dmat;          /* D_mat = sigma / mu (0 when nnz = 0) */
+    int32_t max_row_len;  /* W: the ELL width ("nz", the bandwidth length of Sec. 2.1) */
+    int32_t min_row_len;
+    int64_t n_empty_rows;
+    uint64_t ell_bytes;   /* device bytes a row-wise ELL of this matrix needs */
+    int64_t row_len_hist[32]; /* rows per class: 0 = empty, c >= 1: length in [2^(c-1), 2^c) */
+} spmv_stats;
+
+/* Parameters of the run-time AT method (Sec. 2.2). */
+#define SPMV_DSTAR_PREFIX 0  /* D* = D_mat of the first point, by ascending D_mat, with R_ell < c */
+#define SPMV_DSTAR_MAXPASS 1 /* D* = largest D_mat among points with R_ell >= c */
+#define SPMV_AT_TRY_COO 1    /* flag: when ELL is rejected, time COO-Row against CRS and keep the faster */
+typedef struct spmv_at_params {
+    double c;               /* R_ell threshold of the off-line phase; the paper uses 1.0 */
+    double dstar;           /* D*: the on-line phase picks ELL iff dmat < dstar */
+    uint64_t mem_cap_bytes; /* device bytes a transformation may own; 0 = no cap */
+    int32_t timing_reps;    /* timed repetitions per measurement (median); <= 0 means 20 */
+    int32_t warmup_reps;    /* untimed repetitions first; < 0 means 3 */
+    int32_t dstar_rule;     /* SPMV_DSTAR_PREFIX or SPMV_DSTAR_MAXPASS */
+    int32_t flags;          /* SPMV_AT_TRY_COO */
+} spmv_at_params;
+
+/* Times of one matrix (Sec. 2.2, Eqs. (1)-(3)); milliseconds, medians. */
+typedef struct spmv_timing {
+    double t_crs_ms, t_ell_ms, t_trans_ms, t_coo_ms;
+    double sp;    /* SP_crs/ell = t_crs / t_ell                         (Eq. 1) */
+    double tt;    /* TT_ell = t_trans / t_crs (Eq. 2, read as the cost of the
+                     transformation in CRS-SpMV units)                 */
+    double r_ell; /* R_ell = SP / TT                                    (Eq. 3) */
+    double dmat;  /* D_mat of the matrix                                (Eq. 4) */
+} spmv_timing;
+
+/* Opaque handle to a matrix in one format; owns its device arrays. */
+typedef struct spmv_matrix spmv_matrix;
+
+/* Read-only view of a handle's arrays (device pointers). ELL slot arrays are
+ * column-major over lines with leading dimension ld >= number of lines: slot
+ * k of line i is element k*ld + i (Fig. 3 indexing with N replaced by ld).
+ * Lines are rows for SPMV_ROWWISE and columns for SPMV_COLWISE. */
+typedef struct spmv_matrix_desc {
+    int32_t format, layout;
+    int32_t n_rows, n_cols;
+    int64_t nnz;
+    int32_t width;       /* ELL: slots per line; else 0 */
+    int32_t ld;          /* ELL: leading dimension; else 0 */
+    const int32_t *ptr;  /* CRS: IRP (caller's); column-wise: IRP_T, int32[n_cols+1]; else NULL */
+    const int32_t *idx;  /* CRS, COO-Row: ICOL (caller's); CCS, COO-Col: row of each entry;
+                            ELL-Row: column of each slot; ELL-Col: row of each slot */
+    const int32_t *idx2; /* COO-Row: IROW; COO-Col: column of each entry; else NULL */
+    const double *val;   /* values (CRS, COO-Row: the caller's VAL) */
+    uint64_t owned_bytes;/* device bytes this handle keeps alive */
+} spmv_matrix_desc;
+
+/* Device memory hooks. alloc returns NULL on failure; free releases in stream
+ * order on `stream`. Default: a private stream-ordered CUDA memory pool. */
+typedef void *(*spmv_alloc_fn)(size_t bytes, void *ctx, spmv_stream_t stream);
+typedef void (*spmv_free_fn)(void *ptr, size_t bytes, void *ctx, spmv_stream_t stream);
+
+/* Per-kernel device time gathered while profiling is on. */
+typedef struct spmv_kernel_time {
+    char name[48];
+    uint64_t launches;
+    double total_ms;
+} spmv_kernel_time;
+
+/* ------------------------------------------------------------------------ */
+
+/* Library version (SPMVAT_VERSION). */
+int32_t spmv_version(void);
+
+/* Human-readable name of a status code; never NULL. */
+const char *spmv_status_string(spmv_status s);
+
+/* Install device-memory hooks (both non-NULL), or restore the default pool
+ * (both NULL). Affects allocations made after the call. */
+spmv_status spmv_set_allocator(spmv_alloc_fn alloc, spmv_free_fn free_fn, void *ctx);
+
+/* SYNC. Row-length statistics of a CRS matrix: mu, sigma, D_mat (Eq. (4),
+ * Sec. 2.2), the ELL width W and a length histogram. Reads IRP only, which
+ * is why Sec. 4.4 calls D_mat cheap to obtain. Also checks IRP: irp[0] = 0,
+ * non-decreasing, irp[n_rows] = nnz, else SPMV_ERR_INVALID_MATRIX. */
+spmv_status spmv_analyze(const spmv_crs *A, spmv_stats *out, spmv_stream_t stream);
+
+/* SYNC. Full structural check of a CRS matrix (IRP as in spmv_analyze and
+ * every ICOL in [0, n_cols)). SPMV_ERR_INVALID_MATRIX when it fails. */
+spmv_status spmv_validate(const spmv_crs *A, spmv_stream_t stream);
+
+/* Bytes of a padded ELL with `n_lines` lines and `width` slots per line
+ * (float64 values plus int32 indices, leading dimension rounded up). */
+uint64_t spmv_ell_bytes(int32_t n_lines, int32_t width);
+
+/* Build a handle in `format`/`layout` from a CRS matrix (Sec. 2.1):
+ *  - (SPMV_CRS, ROWWISE): the CRS itself plus its SpMV schedule (row bins);
+ *    borrows IRP/ICOL/VAL. SYNC (runs spmv_analyze).
+ *  - (SPMV_COO, ROWWISE): COO-Row, IROW(k) = row of entry k; borrows
+ *    VAL/ICOL, which COO-Row shares with the CRS (Sec. 2.1). Asynchronous.
+ *  - (SPMV_ELL, ROWWISE): ELL-Row, width W = longest row, each row's entries
+ *    in CRS order in slots 0..len-1, padding slots value +0.0 with the
+ *    column of the row's last entry (0 for an empty row). SYNC.
+ *  - (SPMV_CRS, COLWISE): Phase I of Sec. 2.1, CRS -> CCS (per-column
+ *    count, prefix sum, scatter): each column lists its rows ascending, and
+ *    repeated (i, j) entries in CRS order. SYNC.
+ *  - (SPMV_COO, COLWISE): Phase I then Phase II (CCS -> COO-Column). SYNC.
+ *  - (SPMV_ELL, COLWISE): Phase I then the CCS padded to ELL over columns
+ *    (width = longest column, padding: +0.0 with the column's last row). SYNC.
+ * Borrowed caller arrays must stay valid and unchanged until spmv_destroy.
+ * `mem_cap_bytes` (0 = none) bounds the device bytes the handle owns; a
+ * larger result returns SPMV_ERR_MEMORY_CAP before anything is allocated
+ * (the memory policy the paper defers to its reference [7], Sec. 2.2). */
+spmv_status spmv_transform(const spmv_crs *A, spmv_format format, spmv_layout layout,
+                           uint64_t mem_cap_bytes, spmv_matrix **out, spmv_stream_t stream);
+
+/* Transformation from an existing handle `src` that holds a CCS, i.e. a
+ * (SPMV_CRS, COLWISE) or (SPMV_COO, COLWISE) handle (an ELL-Column handle
+ * does not keep its CCS): to SPMV_COO (COO-Column, Phase II of Sec. 2.1) or
+ * SPMV_ELL (ELL-Column). The new handle shares the CCS arrays with `src`;
+ * the two may be destroyed in any order. SPMV_ELL is SYNC (it reads the
+ * longest column), SPMV_COO asynchronous. */
+spmv_status spmv_transform_from(const spmv_matrix *src, spmv_format format,
+                                uint64_t mem_cap_bytes, spmv_matrix **out,
+                                spmv_stream_t stream);
+
+/* y = A x (Sec. 3) in the handle's format. x: device float64[n_cols], y:
+ * device float64[n_rows], overwritten; x and y must not overlap. Row-wise
+ * formats are deterministic (bitwise repeatable); column-wise formats add
+ * into y with atomics, so their rounding order may vary between calls.
+ * Asynchronous. */
+spmv_status spmv_apply(const spmv_matrix *M, const double *x, double *y, spmv_stream_t stream);
+
+/* Fused CRS -> ELL-Row transformation and first SpMV: builds the same
+ * ELL-Row handle as spmv_transform(A, SPMV_ELL, SPMV_ROWWISE, ...) and, in
+ * the same pass over the CRS, y = A x. SYNC. */
+spmv_status spmv_transform_apply(const spmv_crs *A, const double *x, double *y,
+                                 uint64_t mem_cap_bytes, spmv_matrix **out,
+                                 spmv_stream_t stream);
+
+/* Fill `out` with the handle's arrays and sizes. */
+spmv_status spmv_describe(const spmv_matrix *M, spmv_matrix_desc *out);
+
+/* Release a handle. Its device memory is freed in stream order on the stream
+ * that created it; work on other streams that uses it must be ordered
+ * before (or complete). NULL is ignored. */
+void spmv_destroy(spmv_matrix *M);
+
+/* Eqs. (1)-(3) of Sec. 2.2 with Eq. (2) read as TT = t_trans / t_crs:
+ * R_ell = (t_crs / t_ell) / (t_trans / t_crs). Host only. */
+double spmv_r_ell(double t_crs, double t_ell, double t_trans);
+
+/* Off-line step (4) of Sec. 2.2: D* from m points (dmat[i], rell[i]) and
+ * threshold c under `rule` (SPMV_DSTAR_*). PREFIX: points taken by ascending
+ * D_mat (ties in input order); D* = D_mat of the first point with
+ * R_ell < c, +inf if none fails, 0 if the first already fails. MAXPASS:
+ * largest D_mat with R_ell >= c, 0 if none. Host only. */
+spmv_status spmv_dstar_from_points(int32_t m, const double *dmat, const double *rell,
+                                   double c, int32_t rule, double *dstar);
+
+/* SYNC. Off-line measurement for one matrix (Sec. 2.2 steps (2)): median
+ * device times of CRS SpMV, ELL-Row SpMV, the CRS -> ELL-Row transformation
+ * and (with SPMV_AT_TRY_COO) COO-Row SpMV, then SP, TT, R_ell and D_mat.
+ * SPMV_ERR_MEMORY_CAP if the ELL would exceed p->mem_cap_bytes. */
+spmv_status spmv_measure(const spmv_crs *A, const spmv_at_params *p, spmv_timing *out,
+                         spmv_stream_t stream);
+
+/* SYNC. Off-line phase (Sec. 2.2 steps (1)-(4)): spmv_measure on each of the
+ * m matrices, then D* by p->dstar_rule and p->c. dmat_out / rell_out (host
+ * double[m], may be NULL) receive the D_mat-R_ell graph; a matrix whose ELL
+ * exceeds the cap gets R_ell = 0 (never advantageous). */
+spmv_status spmv_calibrate(const spmv_crs *const *set, int32_t m, const spmv_at_params *p,
+                           double *dmat_out, double *rell_out, double *dstar_out,
+                           spmv_stream_t stream);
+
+/* SYNC. On-line phase (Sec. 2.2): D_mat of A (Eq. (4)); ELL-Row if
+ * D_mat < p->dstar and the ELL fits p->mem_cap_bytes, otherwise CRS (or
+ * COO-Row when SPMV_AT_TRY_COO is set and it measures faster). `chosen`
+ * receives the handle, `stats` (may be NULL) the statistics. */
+spmv_status spmv_autotune(const spmv_crs *A, const spmv_at_params *p, spmv_matrix **chosen,
+                          spmv_stats *stats, spmv_stream_t stream);
+
+/* SYNC. On-line phase of Sec. 2.2 without building anything: computes
+ * D_mat (Eq. (4)) and returns in *format / *layout the format that
+ * spmv_autotune would build (ELL-Row if D_mat < p->dstar and the ELL fits
+ * p->mem_cap_bytes, else CRS; the SPMV_AT_TRY_COO timing is not run here).
+ * `stats` may be NULL. */
+spmv_status spmv_autotune_choose(const spmv_crs *A, const spmv_at_params *p, int32_t *format,
+                                 int32_t *layout, spmv_stats *stats, spmv_stream_t stream);
+
+/* Instrumentation: number of kernels this library has launched so far. */
+uint64_t spmv_launch_count(void);
+
+/* Turn per-kernel timing on (1) or off (0). While on, each launch is
+ * bracketed by CUDA events on its stream. */
+spmv_status spmv_profile_enable(int32_t on);
+
+/* SYNC on the recorded events. Copies up to `cap` per-kernel totals into
+ * `out` (host), returns how many kernels have totals; `reset` != 0 clears. */
+int32_t spmv_profile_read(spmv_kernel_time *out, int32_t cap, int32_t reset);
+
+/* SYNC. Test hook for the bounded waits: runs the decoupled look-back scan
+ * on `n` device counters with a first tile that never publishes its sum and
+ * a spin limit of `spin_limit` polls, so every later tile must give up.
+ * Returns the status the scan reports (SPMV_ERR_TIMEOUT expected) in
+ * *observed. Leaves the device usable. */
+spmv_status spmv_debug_scan_timeout(int32_t n, int32_t spin_limit, int32_t *observed,
+                                    spmv_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPMVAT_H */

@@ -1,0 +1,395 @@
+"""Python binding of libspmvat, the GB300 (sm_103a) library for run-time
+sparse-format transformation, SpMV and D_mat / R_ell auto-tuning (Katagiri &
+Sato, Sec. 2-3).
+
+Argument marshalling only: every step runs in the CUDA library. Functions
+carry the C names of ``include/spmvat.h``. Device arrays are torch CUDA
+tensors (int32 indices, float64 values); the stream defaults to torch's
+current stream. Importing this package never falls back to a CPU path: if
+the shared library is missing it raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+__all__ = [
+    "SpmvError", "Crs", "Matrix", "load_library", "library_path", "device_view",
+    "SPMV_CRS", "SPMV_COO", "SPMV_ELL", "SPMV_ROWWISE", "SPMV_COLWISE",
+    "SPMV_DSTAR_PREFIX", "SPMV_DSTAR_MAXPASS", "SPMV_AT_TRY_COO",
+    "spmv_version", "spmv_status_string", "spmv_set_allocator", "spmv_analyze", "spmv_validate",
+    "spmv_ell_bytes", "spmv_transform", "spmv_transform_from", "spmv_apply", "spmv_transform_apply",
+    "spmv_describe", "spmv_destroy", "spmv_r_ell", "spmv_dstar_from_points", "spmv_measure",
+    "spmv_calibrate", "spmv_autotune", "spmv_autotune_choose", "spmv_launch_count", "spmv_profile_enable", "spmv_profile_read",
+    "spmv_debug_scan_timeout",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+SPMV_OK = 0
+SPMV_CRS, SPMV_COO, SPMV_ELL = 0, 1, 2
+SPMV_ROWWISE, SPMV_COLWISE = 0, 1
+SPMV_DSTAR_PREFIX, SPMV_DSTAR_MAXPASS = 0, 1
+SPMV_AT_TRY_COO = 1
+STATUS_NAMES = {0: "SPMV_OK", 1: "SPMV_ERR_INVALID_ARG", 2: "SPMV_ERR_INVALID_MATRIX", 3: "SPMV_ERR_OOM",
+                4: "SPMV_ERR_MEMORY_CAP", 5: "SPMV_ERR_TIMEOUT", 6: "SPMV_ERR_CUDA", 7: "SPMV_ERR_UNSUPPORTED"}
+
+
+class SpmvError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = int(status)
+        super().__init__(f"{where}: {STATUS_NAMES.get(self.status, self.status)}")
+
+
+class _CrsT(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int32), ("n_cols", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("irp", ctypes.c_void_p), ("icol", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class _StatsT(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_double), ("sigma", ctypes.c_double), ("dmat", ctypes.c_double),
+                ("max_row_len", ctypes.c_int32), ("min_row_len", ctypes.c_int32),
+                ("n_empty_rows", ctypes.c_int64), ("ell_bytes", ctypes.c_uint64),
+                ("row_len_hist", ctypes.c_int64 * 32)]
+
+
+class _AtParamsT(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_double), ("dstar", ctypes.c_double), ("mem_cap_bytes", ctypes.c_uint64),
+                ("timing_reps", ctypes.c_int32), ("warmup_reps", ctypes.c_int32),
+                ("dstar_rule", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class _TimingT(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("t_crs_ms", "t_ell_ms", "t_trans_ms", "t_coo_ms", "sp", "tt", "r_ell", "dmat")]
+
+
+class _DescT(ctypes.Structure):
+    _fields_ = [("format", ctypes.c_int32), ("layout", ctypes.c_int32), ("n_rows", ctypes.c_int32),
+                ("n_cols", ctypes.c_int32), ("nnz", ctypes.c_int64), ("width", ctypes.c_int32),
+                ("ld", ctypes.c_int32), ("ptr", ctypes.c_void_p), ("idx", ctypes.c_void_p),
+                ("idx2", ctypes.c_void_p), ("val", ctypes.c_void_p), ("owned_bytes", ctypes.c_uint64)]
+
+
+class _KernelTimeT(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "libspmvat.so")
+
+
+def load_library():
+    """Load libspmvat.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build the CUDA library first "
+                          "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    sig = {
+        "spmv_version": (i32, []),
+        "spmv_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "spmv_set_allocator": (ctypes.c_int, [vp, vp, vp]),
+        "spmv_analyze": (ctypes.c_int, [P(_CrsT), P(_StatsT), vp]),
+        "spmv_validate": (ctypes.c_int, [P(_CrsT), vp]),
+        "spmv_ell_bytes": (u64, [i32, i32]),
+        "spmv_transform": (ctypes.c_int, [P(_CrsT), ctypes.c_int, ctypes.c_int, u64, P(vp), vp]),
+        "spmv_transform_from": (ctypes.c_int, [vp, ctypes.c_int, u64, P(vp), vp]),
+        "spmv_apply": (ctypes.c_int, [vp, vp, vp, vp]),
+        "spmv_transform_apply": (ctypes.c_int, [P(_CrsT), vp, vp, u64, P(vp), vp]),
+        "spmv_describe": (ctypes.c_int, [vp, P(_DescT)]),
+        "spmv_destroy": (None, [vp]),
+        "spmv_r_ell": (dbl, [dbl, dbl, dbl]),
+        "spmv_dstar_from_points": (ctypes.c_int, [i32, P(dbl), P(dbl), dbl, i32, P(dbl)]),
+        "spmv_measure": (ctypes.c_int, [P(_CrsT), P(_AtParamsT), P(_TimingT), vp]),
+        "spmv_calibrate": (ctypes.c_int, [P(P(_CrsT)), i32, P(_AtParamsT), P(dbl), P(dbl), P(dbl), vp]),
+        "spmv_autotune": (ctypes.c_int, [P(_CrsT), P(_AtParamsT), P(vp), P(_StatsT), vp]),
+        "spmv_autotune_choose": (ctypes.c_int, [P(_CrsT), P(_AtParamsT), P(i32), P(i32), P(_StatsT), vp]),
+        "spmv_launch_count": (u64, []),
+        "spmv_profile_enable": (ctypes.c_int, [i32]),
+        "spmv_profile_read": (i32, [P(_KernelTimeT), i32, i32]),
+        "spmv_debug_scan_timeout": (ctypes.c_int, [i32, i32, P(i32), vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(st: int, where: str):
+    if st != SPMV_OK:
+        raise SpmvError(st, where)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
+
+
+class Crs:
+    """A CRS matrix held in torch CUDA tensors (Sec. 2.1 VAL / ICOL / IRP)."""
+
+    def __init__(self, n_rows, n_cols, irp, icol, val):
+        import torch
+        for t, dt in ((irp, torch.int32), (icol, torch.int32), (val, torch.float64)):
+            if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+                raise TypeError("Crs wants contiguous CUDA tensors: irp/icol int32, val float64")
+        self.n_rows, self.n_cols = int(n_rows), int(n_cols)
+        self.irp, self.icol, self.val = irp, icol, val
+        self.nnz = int(icol.numel())
+        self._c = _CrsT(self.n_rows, self.n_cols, self.nnz, _ptr(irp).value, _ptr(icol).value, _ptr(val).value)
+
+    @classmethod
+    def from_host(cls, A, device="cuda"):
+        """Copy a host CRS (numpy arrays: irp, icol, val, n_rows, n_cols) to the device."""
+        import torch
+        return cls(A.n_rows, A.n_cols, torch.from_numpy(A.irp).to(device), torch.from_numpy(A.icol).to(device),
+                   torch.from_numpy(A.val).to(device))
+
+    @property
+    def c(self):
+        return self._c
+
+
+class Matrix:
+    """Owning wrapper of an spmv_matrix handle; keeps borrowed tensors alive."""
+
+    def __init__(self, handle, keep=()):
+        self.handle = ctypes.c_void_p(handle)
+        self._keep = tuple(keep)
+
+    def close(self):
+        if self.handle and self.handle.value:
+            load_library().spmv_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+            self._keep = ()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def describe(self):
+        return spmv_describe(self)
+
+    def arrays(self) -> dict:
+        """Zero-copy torch views of the handle's device arrays (valid while
+        the handle lives): ptr, idx, idx2, val, as present for the format."""
+        import torch
+        d = spmv_describe(self)
+        lines = d["n_rows"] if d["layout"] == SPMV_ROWWISE else d["n_cols"]
+        out = {}
+        if d["format"] == SPMV_ELL:
+            nslot = d["width"] * d["ld"]
+            out["idx"] = device_view(d["idx"], nslot, torch.int32)
+            out["val"] = device_view(d["val"], nslot, torch.float64)
+            return out
+        if d["ptr"]:
+            out["ptr"] = device_view(d["ptr"], lines + 1, torch.int32)
+        out["idx"] = device_view(d["idx"], d["nnz"], torch.int32)
+        if d["idx2"]:
+            out["idx2"] = device_view(d["idx2"], d["nnz"], torch.int32)
+        out["val"] = device_view(d["val"], d["nnz"], torch.float64)
+        return out
+
+
+class _CudaArray:
+    def __init__(self, ptr, count, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": typestr,
+                                         "data": (int(ptr or 0), False), "version": 3}
+
+
+def device_view(ptr, count, dtype):
+    """A torch CUDA tensor viewing `count` elements at device address `ptr`."""
+    import torch
+    typestr = {torch.int32: "<i4", torch.float64: "<f8"}[dtype]
+    if not count:
+        return torch.empty(0, dtype=dtype, device="cuda")
+    return torch.as_tensor(_CudaArray(ptr, count, typestr), device="cuda")
+
+
+# ---------------------------------------------------------------- the C ABI
+def spmv_version() -> int:
+    return load_library().spmv_version()
+
+
+def spmv_status_string(status: int) -> str:
+    return load_library().spmv_status_string(int(status)).decode()
+
+
+_alloc_keepalive = []
+
+
+def spmv_set_allocator(alloc=None, free=None, ctx=None):
+    """Install Python callables alloc(bytes, ctx, stream) -> int and
+    free(ptr, bytes, ctx, stream), or restore the default pool (both None)."""
+    L = load_library()
+    if alloc is None and free is None:
+        _alloc_keepalive.clear()
+        _check(L.spmv_set_allocator(None, None, None), "spmv_set_allocator")
+        return
+    a, f = _ALLOC_FN(alloc), _FREE_FN(free)
+    _alloc_keepalive[:] = [a, f]
+    _check(L.spmv_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), ctx),
+           "spmv_set_allocator")
+
+
+def _stats_dict(s: _StatsT) -> dict:
+    return {"mu": s.mu, "sigma": s.sigma, "dmat": s.dmat, "W": s.max_row_len, "min_len": s.min_row_len,
+            "n_empty": s.n_empty_rows, "ell_bytes": s.ell_bytes, "hist": list(s.row_len_hist)}
+
+
+def spmv_analyze(A: Crs, stream=None) -> dict:
+    s = _StatsT()
+    _check(load_library().spmv_analyze(ctypes.byref(A.c), ctypes.byref(s), _stream(stream)), "spmv_analyze")
+    return _stats_dict(s)
+
+
+def spmv_validate(A: Crs, stream=None) -> None:
+    _check(load_library().spmv_validate(ctypes.byref(A.c), _stream(stream)), "spmv_validate")
+
+
+def spmv_ell_bytes(n_lines: int, width: int) -> int:
+    return int(load_library().spmv_ell_bytes(int(n_lines), int(width)))
+
+
+def spmv_transform(A: Crs, fmt: int, layout: int, mem_cap_bytes: int = 0, stream=None) -> Matrix:
+    h = ctypes.c_void_p()
+    _check(load_library().spmv_transform(ctypes.byref(A.c), int(fmt), int(layout), int(mem_cap_bytes),
+                                         ctypes.byref(h), _stream(stream)), "spmv_transform")
+    return Matrix(h.value, keep=(A,))
+
+
+def spmv_transform_from(src: Matrix, fmt: int, mem_cap_bytes: int = 0, stream=None) -> Matrix:
+    h = ctypes.c_void_p()
+    _check(load_library().spmv_transform_from(src.handle, int(fmt), int(mem_cap_bytes), ctypes.byref(h),
+                                              _stream(stream)), "spmv_transform_from")
+    return Matrix(h.value, keep=src._keep)
+
+
+def spmv_apply(M: Matrix, x, y, stream=None) -> None:
+    _check(load_library().spmv_apply(M.handle, _ptr(x), _ptr(y), _stream(stream)), "spmv_apply")
+
+
+def spmv_transform_apply(A: Crs, x, y, mem_cap_bytes: int = 0, stream=None) -> Matrix:
+    h = ctypes.c_void_p()
+    _check(load_library().spmv_transform_apply(ctypes.byref(A.c), _ptr(x), _ptr(y), int(mem_cap_bytes),
+                                               ctypes.byref(h), _stream(stream)), "spmv_transform_apply")
+    return Matrix(h.value, keep=(A,))
+
+
+def spmv_describe(M: Matrix) -> dict:
+    d = _DescT()
+    _check(load_library().spmv_describe(M.handle, ctypes.byref(d)), "spmv_describe")
+    return {f: getattr(d, f) for f, _ in _DescT._fields_}
+
+
+def spmv_destroy(M: Matrix) -> None:
+    M.close()
+
+
+def spmv_r_ell(t_crs: float, t_ell: float, t_trans: float) -> float:
+    return float(load_library().spmv_r_ell(float(t_crs), float(t_ell), float(t_trans)))
+
+
+def spmv_dstar_from_points(dmat, rell, c: float = 1.0, rule: int = SPMV_DSTAR_PREFIX) -> float:
+    m = len(dmat)
+    D = (ctypes.c_double * max(m, 1))(*[float(v) for v in dmat])
+    R = (ctypes.c_double * max(m, 1))(*[float(v) for v in rell])
+    out = ctypes.c_double()
+    _check(load_library().spmv_dstar_from_points(m, D, R, float(c), int(rule), ctypes.byref(out)),
+           "spmv_dstar_from_points")
+    return out.value
+
+
+def _params(c=1.0, dstar=math.inf, mem_cap_bytes=0, timing_reps=20, warmup_reps=3,
+            dstar_rule=SPMV_DSTAR_PREFIX, flags=0) -> _AtParamsT:
+    return _AtParamsT(float(c), float(dstar), int(mem_cap_bytes), int(timing_reps), int(warmup_reps),
+                      int(dstar_rule), int(flags))
+
+
+def spmv_measure(A: Crs, stream=None, **params) -> dict:
+    t = _TimingT()
+    p = _params(**params)
+    _check(load_library().spmv_measure(ctypes.byref(A.c), ctypes.byref(p), ctypes.byref(t), _stream(stream)),
+           "spmv_measure")
+    return {f: getattr(t, f) for f, _ in _TimingT._fields_}
+
+
+def spmv_calibrate(mats, stream=None, **params):
+    """Returns (D*, [D_mat^i], [R_ell^i])."""
+    m = len(mats)
+    arr = (ctypes.POINTER(_CrsT) * max(m, 1))(*[ctypes.pointer(A.c) for A in mats])
+    D = (ctypes.c_double * max(m, 1))()
+    R = (ctypes.c_double * max(m, 1))()
+    out = ctypes.c_double()
+    p = _params(**params)
+    _check(load_library().spmv_calibrate(arr, m, ctypes.byref(p), D, R, ctypes.byref(out), _stream(stream)),
+           "spmv_calibrate")
+    return out.value, list(D)[:m], list(R)[:m]
+
+
+def spmv_autotune(A: Crs, stream=None, **params):
+    """Returns (Matrix chosen, stats dict)."""
+    h = ctypes.c_void_p()
+    s = _StatsT()
+    p = _params(**params)
+    _check(load_library().spmv_autotune(ctypes.byref(A.c), ctypes.byref(p), ctypes.byref(h), ctypes.byref(s),
+                                        _stream(stream)), "spmv_autotune")
+    return Matrix(h.value, keep=(A,)), _stats_dict(s)
+
+
+def spmv_autotune_choose(A: Crs, stream=None, **params):
+    """Returns ((format, layout), stats dict) of the on-line rule, building nothing."""
+    f, l = ctypes.c_int32(), ctypes.c_int32()
+    s = _StatsT()
+    p = _params(**params)
+    _check(load_library().spmv_autotune_choose(ctypes.byref(A.c), ctypes.byref(p), ctypes.byref(f), ctypes.byref(l),
+                                               ctypes.byref(s), _stream(stream)), "spmv_autotune_choose")
+    return (f.value, l.value), _stats_dict(s)
+
+
+def spmv_launch_count() -> int:
+    return int(load_library().spmv_launch_count())
+
+
+def spmv_profile_enable(on: bool) -> None:
+    _check(load_library().spmv_profile_enable(1 if on else 0), "spmv_profile_enable")
+
+
+def spmv_profile_read(reset: bool = False) -> dict:
+    L = load_library()
+    buf = (_KernelTimeT * 64)()
+    n = L.spmv_profile_read(buf, 64, 1 if reset else 0)
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(n, 64))}
+
+
+def spmv_debug_scan_timeout(n: int, spin_limit: int, stream=None) -> int:
+    obs = ctypes.c_int32()
+    _check(load_library().spmv_debug_scan_timeout(int(n), int(spin_limit), ctypes.byref(obs), _stream(stream)),
+           "spmv_debug_scan_timeout")
+    return int(obs.value)

@@ -1,0 +1,898 @@
+// C ABI of libspmvat (declared in include/spmvat.h): handles, device memory,
+// dispatch to the kernels, and the run-time AT method of Sec. 2.2.
+#include <algorithm>
+#include <atomic>
+#include <cfloat>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "spmvat.h"
+
+using namespace spmvat;
+
+namespace {
+
+// ------------------------------------------------------------------ memory
+struct Hooks {
+    spmv_alloc_fn alloc = nullptr;
+    spmv_free_fn free = nullptr;
+    void *ctx = nullptr;
+};
+std::mutex g_mu;
+Hooks g_hooks;
+cudaMemPool_t g_pools[64] = {};
+
+cudaMemPool_t pool_for(int dev) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    dev &= 63;
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        unsigned long long keep = ULLONG_MAX;  // keep freed blocks for reuse
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pools[dev] = p;
+    }
+    return g_pools[dev];
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    Hooks hooks;
+    ~DevBuf() {
+        if (!p) return;
+        if (hooks.free) hooks.free(p, bytes, hooks.ctx, stream);
+        else if (cudaFreeAsync(p, stream) != cudaSuccess) cudaGetLastError();
+    }
+};
+using BufPtr = std::shared_ptr<DevBuf>;
+
+spmv_status alloc_buf(size_t bytes, cudaStream_t s, BufPtr *out) {
+    Hooks h;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        h = g_hooks;
+    }
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *p = nullptr;
+    if (h.alloc) {
+        p = h.alloc(bytes, h.ctx, s);
+    } else {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return SPMV_ERR_CUDA; }
+        cudaMemPool_t pool = pool_for(dev);
+        if (!pool) return SPMV_ERR_CUDA;
+        cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? SPMV_ERR_OOM : SPMV_ERR_CUDA;
+        }
+    }
+    if (!p) return SPMV_ERR_OOM;
+    auto b = std::make_shared<DevBuf>();
+    b->p = p;
+    b->bytes = bytes;
+    b->stream = s;
+    b->hooks = h;
+    *out = b;
+    return SPMV_OK;
+}
+
+// ------------------------------------------------------- launch accounting
+std::atomic<unsigned long long> g_launches{0};
+std::atomic<int> g_profile_on{0};
+struct ProfRec {
+    std::string name;
+    cudaEvent_t e0, e1;
+};
+std::mutex g_pmu;
+std::vector<ProfRec> g_pending;
+std::vector<cudaEvent_t> g_event_pool;
+std::map<std::string, std::pair<unsigned long long, double>> g_totals;
+
+cudaEvent_t get_event() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    return e;
+}
+
+int g_sm_count[64] = {};
+
+// status helpers
+#define CK(call)                                            \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) { cudaGetLastError(); return SPMV_ERR_CUDA; } \
+    } while (0)
+#define CKS(call)                                           \
+    do {                                                    \
+        spmv_status s_ = (call);                            \
+        if (s_ != SPMV_OK) return s_;                       \
+    } while (0)
+
+inline cudaStream_t S(spmv_stream_t s) { return reinterpret_cast<cudaStream_t>(s); }
+inline int32_t round_up32(int64_t n) { return (int32_t)((n + 31) / 32 * 32); }
+inline uint64_t ell_bytes(int64_t lines, int64_t width) {
+    return (uint64_t)round_up32(lines) * (uint64_t)width * 12ull;
+}
+
+spmv_status status_from_dev(int st) {
+    if (st & ST_TIMEOUT) return SPMV_ERR_TIMEOUT;
+    if (st & (ST_BAD_INDEX | ST_BAD_PTR)) return SPMV_ERR_INVALID_MATRIX;
+    return SPMV_OK;
+}
+
+spmv_status check_crs(const spmv_crs *A) {
+    if (!A) return SPMV_ERR_INVALID_ARG;
+    if (A->n_rows <= 0 || A->n_cols <= 0 || A->nnz < 0 || A->nnz >= (int64_t)INT_MAX) return SPMV_ERR_INVALID_ARG;
+    if (!A->irp) return SPMV_ERR_INVALID_ARG;
+    if (A->nnz > 0 && (!A->icol || !A->val)) return SPMV_ERR_INVALID_ARG;
+    return SPMV_OK;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------- handles
+struct spmv_matrix {
+    int32_t format = 0, layout = 0;
+    int32_t n_rows = 0, n_cols = 0;
+    int64_t nnz = 0;
+    int32_t width = 0, ld = 0;
+    const int32_t *ptr = nullptr;
+    const int32_t *idx = nullptr;
+    const int32_t *idx2 = nullptr;
+    const double *val = nullptr;
+    std::vector<BufPtr> bufs;      // everything this handle keeps alive
+    std::vector<BufPtr> ccs_bufs;  // the CCS arrays (column-wise handles), shareable
+    int32_t colmax = 0;            // longest column (handles holding a CCS)
+    cudaStream_t home = nullptr;
+    // CRS schedule
+    int crs_binned = 0;
+    int crs_v = 1;
+    int64_t bin_off[kNumBins + 1] = {};
+    const int32_t *rowlist = nullptr;
+    uint64_t owned() const {
+        uint64_t t = 0;
+        for (auto &b : bufs) t += b->bytes;
+        return t;
+    }
+};
+
+namespace spmvat {
+
+KernelScope::KernelScope(const char *name, cudaStream_t s) : slot(-1), stream(s) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (!g_profile_on.load(std::memory_order_relaxed)) return;
+    std::lock_guard<std::mutex> lk(g_pmu);
+    cudaEvent_t e0 = get_event(), e1 = get_event();
+    if (!e0 || !e1) return;
+    cudaEventRecord(e0, s);
+    g_pending.push_back({name, e0, e1});
+    slot = (int)g_pending.size() - 1;
+}
+KernelScope::~KernelScope() {
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> lk(g_pmu);
+    if (slot < (int)g_pending.size()) cudaEventRecord(g_pending[slot].e1, stream);
+}
+
+int sm_count() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    dev &= 63;
+    if (!g_sm_count[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        g_sm_count[dev] = n > 0 ? n : 1;
+    }
+    return g_sm_count[dev];
+}
+
+}  // namespace spmvat
+
+namespace {
+
+// ------------------------------------------------------------- analyze core
+// Runs k_analyze (+ optional ICOL validation) and returns the statistics.
+spmv_status analyze_core(const spmv_crs *A, bool validate_icol, spmv_stats *out, cudaStream_t s) {
+    BufPtr acc_buf;
+    CKS(alloc_buf(sizeof(AnalyzeAcc), s, &acc_buf));
+    AnalyzeAcc *acc = reinterpret_cast<AnalyzeAcc *>(acc_buf->p);
+    CK(cudaMemsetAsync(acc, 0, sizeof(AnalyzeAcc), s));
+    CK(launch_analyze(A->irp, A->n_rows, A->nnz, acc, s));
+    if (validate_icol && A->nnz > 0) CK(launch_validate_idx(A->icol, A->nnz, A->n_cols, &acc->status, s));
+    AnalyzeAcc h;
+    CK(cudaMemcpyAsync(&h, acc, sizeof(AnalyzeAcc), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    spmv_status st = status_from_dev(h.status);
+    if (st != SPMV_OK) return st;
+    if ((long long)h.sum_len != A->nnz) return SPMV_ERR_INVALID_MATRIX;
+    const double n = (double)A->n_rows;
+    // sigma^2 = (n * S2 - S1^2) / n^2, numerator exact in 128-bit integers
+    const unsigned __int128 num =
+        (unsigned __int128)(unsigned long long)A->n_rows * h.sum_len2 -
+        (unsigned __int128)h.sum_len * h.sum_len;
+    const double mu = (double)h.sum_len / n;
+    const double sigma = std::sqrt((double)num) / n;
+    memset(out, 0, sizeof(*out));
+    out->mu = mu;
+    out->sigma = sigma;
+    out->dmat = (h.sum_len == 0) ? 0.0 : sigma / mu;
+    out->max_row_len = h.max_len;
+    out->min_row_len = INT_MAX - h.min_len;
+    out->n_empty_rows = (int64_t)h.n_empty;
+    out->ell_bytes = ell_bytes(A->n_rows, h.max_len);
+    for (int c = 0; c < 32; ++c) out->row_len_hist[c] = (int64_t)h.hist[c];
+    return SPMV_OK;
+}
+
+spmv_matrix *new_handle(const spmv_crs *A, int format, int layout, cudaStream_t s) {
+    spmv_matrix *M = new (std::nothrow) spmv_matrix();
+    if (!M) return nullptr;
+    M->format = format;
+    M->layout = layout;
+    M->n_rows = A->n_rows;
+    M->n_cols = A->n_cols;
+    M->nnz = A->nnz;
+    M->home = s;
+    return M;
+}
+
+// Bins of the CRS schedule from the class histogram (class c: [2^(c-1), 2^c)).
+void bin_counts_from_hist(const spmv_stats &st, int64_t cnt[kNumBins]) {
+    for (int b = 0; b < kNumBins; ++b) cnt[b] = 0;
+    cnt[0] += st.row_len_hist[0];
+    for (int c = 1; c < 32; ++c) {
+        const long long lo = 1ll << (c - 1);
+        cnt[bin_of_len_host((int)std::min<long long>(lo, INT_MAX))] += st.row_len_hist[c];
+    }
+}
+
+const int kBinV[kNumBins] = {1, 2, 4, 8, 16, 32, 0};
+
+spmv_status build_crs_plan(const spmv_crs *A, uint64_t cap, spmv_matrix **out, cudaStream_t s) {
+    spmv_stats st;
+    CKS(analyze_core(A, true, &st, s));
+    std::unique_ptr<spmv_matrix> M(new_handle(A, SPMV_CRS, SPMV_ROWWISE, s));
+    if (!M) return SPMV_ERR_OOM;
+    M->ptr = A->irp;
+    M->idx = A->icol;
+    M->val = A->val;
+    const bool regular = st.dmat <= 0.5 && st.max_row_len < 2048;
+    if (regular) {
+        M->crs_binned = 0;
+        M->crs_v = kBinV[std::min(bin_of_len_host(st.max_row_len), 5)];
+        if (M->crs_v < 1) M->crs_v = 1;
+    } else {
+        const uint64_t need = (uint64_t)A->n_rows * 4;
+        if (cap && need > cap) return SPMV_ERR_MEMORY_CAP;
+        int64_t cnt[kNumBins];
+        bin_counts_from_hist(st, cnt);
+        M->bin_off[0] = 0;
+        for (int b = 0; b < kNumBins; ++b) M->bin_off[b + 1] = M->bin_off[b] + cnt[b];
+        BufPtr rl, scr, stw;
+        CKS(alloc_buf(need, s, &rl));
+        CKS(alloc_buf(bin_scratch_bytes(A->n_rows), s, &scr));
+        CKS(alloc_buf(16, s, &stw));
+        CK(cudaMemsetAsync(stw->p, 0, 16, s));
+        CK(launch_bin_rows(A->irp, A->n_rows, scr->p, reinterpret_cast<int32_t *>(rl->p),
+                           reinterpret_cast<int *>(stw->p), s));
+        int hst = 0;
+        CK(cudaMemcpyAsync(&hst, stw->p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        CKS(status_from_dev(hst));
+        M->crs_binned = 1;
+        M->rowlist = reinterpret_cast<const int32_t *>(rl->p);
+        M->bufs.push_back(rl);
+    }
+    *out = M.release();
+    return SPMV_OK;
+}
+
+spmv_status build_coo_row(const spmv_crs *A, uint64_t cap, spmv_matrix **out, cudaStream_t s) {
+    const uint64_t need = (uint64_t)A->nnz * 4;
+    if (cap && need > cap) return SPMV_ERR_MEMORY_CAP;
+    std::unique_ptr<spmv_matrix> M(new_handle(A, SPMV_COO, SPMV_ROWWISE, s));
+    if (!M) return SPMV_ERR_OOM;
+    BufPtr irow;
+    CKS(alloc_buf(need, s, &irow));
+    CK(launch_expand(A->irp, A->n_rows, A->nnz, reinterpret_cast<int32_t *>(irow->p), s, "crs_to_coo_row"));
+    M->ptr = A->irp;
+    M->idx = A->icol;
+    M->idx2 = reinterpret_cast<const int32_t *>(irow->p);
+    M->val = A->val;
+    M->bufs.push_back(irow);
+    *out = M.release();
+    return SPMV_OK;
+}
+
+// CRS -> ELL-Row (optionally fused with y = A x). `st` from analyze_core.
+spmv_status build_ell_row(const spmv_crs *A, const spmv_stats &st, uint64_t cap, const double *x, double *y,
+                          spmv_matrix **out, cudaStream_t s) {
+    const int32_t W = st.max_row_len;
+    const int32_t ld = round_up32(A->n_rows);
+    const uint64_t need = ell_bytes(A->n_rows, W);
+    if (cap && need > cap) return SPMV_ERR_MEMORY_CAP;
+    std::unique_ptr<spmv_matrix> M(new_handle(A, SPMV_ELL, SPMV_ROWWISE, s));
+    if (!M) return SPMV_ERR_OOM;
+    BufPtr ev, ei, stw;
+    CKS(alloc_buf((size_t)ld * W * 8, s, &ev));
+    CKS(alloc_buf((size_t)ld * W * 4, s, &ei));
+    CKS(alloc_buf(16, s, &stw));
+    CK(cudaMemsetAsync(stw->p, 0, 16, s));
+    if (W == 0 && y) CK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)A->n_rows, s));
+    CK(launch_lines_to_ell(A->irp, A->icol, A->val, A->n_rows, A->n_cols, W, ld,
+                           reinterpret_cast<double *>(ev->p), reinterpret_cast<int32_t *>(ei->p), x, y,
+                           reinterpret_cast<int *>(stw->p), s, "crs_to_ell_row"));
+    int hst = 0;
+    CK(cudaMemcpyAsync(&hst, stw->p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CKS(status_from_dev(hst));
+    M->width = W;
+    M->ld = ld;
+    M->idx = reinterpret_cast<const int32_t *>(ei->p);
+    M->val = reinterpret_cast<const double *>(ev->p);
+    M->bufs.push_back(ev);
+    M->bufs.push_back(ei);
+    *out = M.release();
+    return SPMV_OK;
+}
+
+// Phase I (CRS -> CCS). On success M holds the CCS in ccs_bufs/bufs.
+// `ell_cap_check`: when >= 0, fail with MEMORY_CAP before building if an
+// ELL-Column of the longest column would exceed it (checked after the count).
+spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bool want_ell,
+                   std::unique_ptr<spmv_matrix> &M, cudaStream_t s) {
+    const int64_t nnz = A->nnz;
+    const int32_t nc = A->n_cols;
+    const uint64_t own = (uint64_t)(nc + 1) * 4 + (uint64_t)nnz * 12;
+    if (!want_ell && cap_ccs && own > cap_ccs) return SPMV_ERR_MEMORY_CAP;
+    BufPtr cp, trow, tval, rank, pairs, scan_scr, words, longl;
+    CKS(alloc_buf((size_t)(nc + 1) * 4, s, &cp));
+    CKS(alloc_buf((size_t)nnz * 4, s, &rank));
+    CKS(alloc_buf(scan_scratch_bytes(nc), s, &scan_scr));
+    CKS(alloc_buf(64, s, &words));  // [0] status [1] colmax
+    const int64_t max_long = std::min<int64_t>(nc, nnz / 33 + 1);
+    CKS(alloc_buf((size_t)(max_long + 1) * 4, s, &longl));  // [0] count, then the list
+    int32_t *d_cp = reinterpret_cast<int32_t *>(cp->p);
+    int *d_status = reinterpret_cast<int *>(words->p);
+    int32_t *d_colmax = reinterpret_cast<int32_t *>(words->p) + 1;
+    int32_t *d_long = reinterpret_cast<int32_t *>(longl->p);
+    CK(cudaMemsetAsync(d_cp, 0, (size_t)(nc + 1) * 4, s));
+    CK(cudaMemsetAsync(words->p, 0, 64, s));
+    CK(cudaMemsetAsync(d_long, 0, 4, s));
+    CK(launch_col_count(A->icol, nnz, nc, d_cp, reinterpret_cast<int32_t *>(rank->p), d_status, s));
+    CK(launch_scan(d_cp, nc, scan_scr->p, d_colmax, 32, d_long + 1, d_long, d_status, kSpinLimit, 0, s));
+    int hw[2] = {0, 0};
+    CK(cudaMemcpyAsync(hw, words->p, sizeof(hw), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CKS(status_from_dev(hw[0]));
+    const int32_t colmax = hw[1];
+    if (want_ell) {
+        if (cap_ell_col && ell_bytes(nc, colmax) > cap_ell_col) return SPMV_ERR_MEMORY_CAP;
+    }
+    CKS(alloc_buf((size_t)nnz * 4, s, &trow));
+    CKS(alloc_buf((size_t)nnz * 8, s, &tval));
+    CKS(alloc_buf((size_t)nnz * 8, s, &pairs));
+    CK(launch_col_scatter(A->irp, A->n_rows, A->icol, nnz, nc, d_cp, reinterpret_cast<int32_t *>(rank->p),
+                          reinterpret_cast<int2 *>(pairs->p), d_status, s));
+    CK(launch_col_fixup(d_cp, nc, A->irp, A->n_rows, A->val, reinterpret_cast<const int2 *>(pairs->p), d_long + 1,
+                        0, colmax, reinterpret_cast<int32_t *>(rank->p), nullptr,
+                        reinterpret_cast<int32_t *>(trow->p), reinterpret_cast<double *>(tval->p), s));
+    CK(cudaMemcpyAsync(hw, words->p, sizeof(hw), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CKS(status_from_dev(hw[0]));
+    M->ptr = d_cp;
+    M->idx = reinterpret_cast<const int32_t *>(trow->p);
+    M->val = reinterpret_cast<const double *>(tval->p);
+    M->ccs_bufs = {cp, trow, tval};
+    M->colmax = colmax;
+    return SPMV_OK;
+}
+
+spmv_status ell_col_from_ccs(const spmv_matrix *src, uint64_t cap, spmv_matrix **out, cudaStream_t s) {
+    const int32_t W = src->colmax;
+    const int32_t ld = round_up32(src->n_cols);
+    if (cap && ell_bytes(src->n_cols, W) > cap) return SPMV_ERR_MEMORY_CAP;
+    std::unique_ptr<spmv_matrix> M(new (std::nothrow) spmv_matrix());
+    if (!M) return SPMV_ERR_OOM;
+    M->format = SPMV_ELL;
+    M->layout = SPMV_COLWISE;
+    M->n_rows = src->n_rows;
+    M->n_cols = src->n_cols;
+    M->nnz = src->nnz;
+    M->home = s;
+    BufPtr ev, ei, stw;
+    CKS(alloc_buf((size_t)ld * W * 8, s, &ev));
+    CKS(alloc_buf((size_t)ld * W * 4, s, &ei));
+    CKS(alloc_buf(16, s, &stw));
+    CK(cudaMemsetAsync(stw->p, 0, 16, s));
+    CK(launch_lines_to_ell(src->ptr, src->idx, src->val, src->n_cols, src->n_rows, W, ld,
+                           reinterpret_cast<double *>(ev->p), reinterpret_cast<int32_t *>(ei->p), nullptr, nullptr,
+                           reinterpret_cast<int *>(stw->p), s, "ccs_to_ell_col"));
+    int hst = 0;
+    CK(cudaMemcpyAsync(&hst, stw->p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CKS(status_from_dev(hst));
+    M->width = W;
+    M->ld = ld;
+    M->idx = reinterpret_cast<const int32_t *>(ei->p);
+    M->val = reinterpret_cast<const double *>(ev->p);
+    M->bufs = {ev, ei};
+    *out = M.release();
+    return SPMV_OK;
+}
+
+spmv_status coo_col_from_ccs(const spmv_matrix *src, uint64_t cap, spmv_matrix **out, cudaStream_t s) {
+    const uint64_t need = (uint64_t)src->nnz * 4;
+    if (cap && need > cap) return SPMV_ERR_MEMORY_CAP;
+    std::unique_ptr<spmv_matrix> M(new (std::nothrow) spmv_matrix());
+    if (!M) return SPMV_ERR_OOM;
+    M->format = SPMV_COO;
+    M->layout = SPMV_COLWISE;
+    M->n_rows = src->n_rows;
+    M->n_cols = src->n_cols;
+    M->nnz = src->nnz;
+    M->home = s;
+    BufPtr tcol;
+    CKS(alloc_buf(need, s, &tcol));
+    CK(launch_expand(src->ptr, src->n_cols, src->nnz, reinterpret_cast<int32_t *>(tcol->p), s,
+                     "ccs_to_coo_col"));
+    M->ptr = src->ptr;
+    M->idx = src->idx;
+    M->idx2 = reinterpret_cast<const int32_t *>(tcol->p);
+    M->val = src->val;
+    M->ccs_bufs = src->ccs_bufs;
+    M->colmax = src->colmax;
+    M->bufs = src->ccs_bufs;
+    M->bufs.push_back(tcol);
+    *out = M.release();
+    return SPMV_OK;
+}
+
+spmv_status apply_core(const spmv_matrix *M, const double *x, double *y, cudaStream_t s) {
+    if (M->layout == SPMV_ROWWISE) {
+        switch (M->format) {
+            case SPMV_CRS:
+                if (!M->crs_binned) {
+                    CK(launch_spmv_crs_vector(M->crs_v, M->ptr, M->idx, M->val, nullptr, M->n_rows, x, y, s));
+                } else {
+                    for (int b = 0; b < kNumBins; ++b) {
+                        const int64_t cnt = M->bin_off[b + 1] - M->bin_off[b];
+                        if (cnt <= 0) continue;
+                        const int32_t *rows = M->rowlist + M->bin_off[b];
+                        if (kBinV[b] > 0) CK(launch_spmv_crs_vector(kBinV[b], M->ptr, M->idx, M->val, rows, cnt, x, y, s));
+                        else CK(launch_spmv_crs_block(M->ptr, M->idx, M->val, rows, cnt, x, y, s));
+                    }
+                }
+                return SPMV_OK;
+            case SPMV_COO: {
+                BufPtr scr;
+                CKS(alloc_buf(coo_row_scratch_bytes(M->nnz), s, &scr));
+                CK(launch_spmv_coo_row(M->idx2, M->idx, M->val, M->nnz, M->n_rows, M->n_cols, x, y, scr->p, s));
+                return SPMV_OK;
+            }
+            case SPMV_ELL:
+                if (M->width == 0) { CK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)M->n_rows, s)); return SPMV_OK; }
+                if ((reinterpret_cast<uintptr_t>(y) & 15) != 0) return SPMV_ERR_INVALID_ARG;
+                CK(launch_spmv_ell_row(M->val, M->idx, M->n_rows, M->width, M->ld, x, y, s));
+                return SPMV_OK;
+        }
+    } else {
+        switch (M->format) {
+            case SPMV_CRS:
+                CK(launch_spmv_ccs(M->ptr, M->idx, M->val, M->n_rows, M->n_cols, x, y, s));
+                return SPMV_OK;
+            case SPMV_COO:
+                CK(launch_spmv_coo_col(M->idx, M->idx2, M->val, M->nnz, M->n_rows, x, y, s));
+                return SPMV_OK;
+            case SPMV_ELL:
+                CK(launch_spmv_ell_col(M->val, M->idx, M->n_rows, M->n_cols, M->width, M->ld, x, y, s));
+                return SPMV_OK;
+        }
+    }
+    return SPMV_ERR_INVALID_ARG;
+}
+
+double median(std::vector<float> v) {
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    const size_t m = v.size() / 2;
+    return (v.size() % 2) ? v[m] : 0.5 * ((double)v[m - 1] + v[m]);
+}
+
+// Median device time (ms) of fn() over reps after warm-up runs.
+template <typename F>
+spmv_status time_median(F fn, int warm, int reps, cudaStream_t s, double *ms) {
+    for (int i = 0; i < warm; ++i) CKS(fn());
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return SPMV_ERR_CUDA; }
+    std::vector<float> t;
+    spmv_status st = SPMV_OK;
+    for (int i = 0; i < reps && st == SPMV_OK; ++i) {
+        cudaEventRecord(e0, s);
+        st = fn();
+        cudaEventRecord(e1, s);
+        if (st == SPMV_OK) {
+            if (cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); st = SPMV_ERR_CUDA; break; }
+            float f = 0.f;
+            cudaEventElapsedTime(&f, e0, e1);
+            t.push_back(f);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SPMV_OK) return st;
+    *ms = median(t);
+    return SPMV_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+int32_t spmv_version(void) { return SPMVAT_VERSION; }
+
+const char *spmv_status_string(spmv_status s) {
+    switch (s) {
+        case SPMV_OK: return "SPMV_OK";
+        case SPMV_ERR_INVALID_ARG: return "SPMV_ERR_INVALID_ARG";
+        case SPMV_ERR_INVALID_MATRIX: return "SPMV_ERR_INVALID_MATRIX";
+        case SPMV_ERR_OOM: return "SPMV_ERR_OOM";
+        case SPMV_ERR_MEMORY_CAP: return "SPMV_ERR_MEMORY_CAP";
+        case SPMV_ERR_TIMEOUT: return "SPMV_ERR_TIMEOUT";
+        case SPMV_ERR_CUDA: return "SPMV_ERR_CUDA";
+        case SPMV_ERR_UNSUPPORTED: return "SPMV_ERR_UNSUPPORTED";
+    }
+    return "SPMV_ERR_UNKNOWN";
+}
+
+spmv_status spmv_set_allocator(spmv_alloc_fn alloc, spmv_free_fn free_fn, void *ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr)) return SPMV_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_hooks.alloc = alloc;
+    g_hooks.free = free_fn;
+    g_hooks.ctx = alloc ? ctx : nullptr;
+    return SPMV_OK;
+}
+
+uint64_t spmv_ell_bytes(int32_t n_lines, int32_t width) {
+    if (n_lines < 0 || width < 0) return 0;
+    return ell_bytes(n_lines, width);
+}
+
+spmv_status spmv_analyze(const spmv_crs *A, spmv_stats *out, spmv_stream_t stream) {
+    CKS(check_crs(A));
+    if (!out) return SPMV_ERR_INVALID_ARG;
+    return analyze_core(A, false, out, S(stream));
+}
+
+spmv_status spmv_validate(const spmv_crs *A, spmv_stream_t stream) {
+    CKS(check_crs(A));
+    spmv_stats st;
+    return analyze_core(A, true, &st, S(stream));
+}
+
+spmv_status spmv_transform(const spmv_crs *A, spmv_format format, spmv_layout layout, uint64_t mem_cap_bytes,
+                           spmv_matrix **out, spmv_stream_t stream) {
+    if (!out) return SPMV_ERR_INVALID_ARG;
+    *out = nullptr;
+    CKS(check_crs(A));
+    if ((int)format < SPMV_CRS || (int)format > SPMV_ELL) return SPMV_ERR_INVALID_ARG;
+    if ((int)layout != SPMV_ROWWISE && (int)layout != SPMV_COLWISE) return SPMV_ERR_INVALID_ARG;
+    cudaStream_t s = S(stream);
+    if (layout == SPMV_ROWWISE) {
+        if (format == SPMV_CRS) return build_crs_plan(A, mem_cap_bytes, out, s);
+        if (format == SPMV_COO) return build_coo_row(A, mem_cap_bytes, out, s);
+        spmv_stats st;
+        CKS(analyze_core(A, false, &st, s));
+        return build_ell_row(A, st, mem_cap_bytes, nullptr, nullptr, out, s);
+    }
+    // column-wise: Phase I first
+    std::unique_ptr<spmv_matrix> M(new_handle(A, SPMV_CRS, SPMV_COLWISE, s));
+    if (!M) return SPMV_ERR_OOM;
+    {
+        spmv_stats st;
+        CKS(analyze_core(A, false, &st, s));  // IRP checks before Phase I
+    }
+    CKS(phase1(A, format == SPMV_CRS ? mem_cap_bytes : 0, mem_cap_bytes, format == SPMV_ELL, M, s));
+    M->bufs = M->ccs_bufs;
+    if (format == SPMV_CRS) {
+        *out = M.release();
+        return SPMV_OK;
+    }
+    if (format == SPMV_COO) return coo_col_from_ccs(M.get(), mem_cap_bytes, out, s);
+    return ell_col_from_ccs(M.get(), mem_cap_bytes, out, s);
+}
+
+spmv_status spmv_transform_from(const spmv_matrix *src, spmv_format format, uint64_t mem_cap_bytes,
+                                spmv_matrix **out, spmv_stream_t stream) {
+    if (!out) return SPMV_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!src || src->layout != SPMV_COLWISE || src->ccs_bufs.empty()) return SPMV_ERR_INVALID_ARG;
+    if (format == SPMV_COO) return coo_col_from_ccs(src, mem_cap_bytes, out, S(stream));
+    if (format == SPMV_ELL) return ell_col_from_ccs(src, mem_cap_bytes, out, S(stream));
+    return SPMV_ERR_INVALID_ARG;
+}
+
+spmv_status spmv_apply(const spmv_matrix *M, const double *x, double *y, spmv_stream_t stream) {
+    if (!M || !x || !y) return SPMV_ERR_INVALID_ARG;
+    return apply_core(M, x, y, S(stream));
+}
+
+spmv_status spmv_transform_apply(const spmv_crs *A, const double *x, double *y, uint64_t mem_cap_bytes,
+                                 spmv_matrix **out, spmv_stream_t stream) {
+    if (!out) return SPMV_ERR_INVALID_ARG;
+    *out = nullptr;
+    CKS(check_crs(A));
+    if (!x || !y) return SPMV_ERR_INVALID_ARG;
+    spmv_stats st;
+    CKS(analyze_core(A, false, &st, S(stream)));
+    return build_ell_row(A, st, mem_cap_bytes, x, y, out, S(stream));
+}
+
+spmv_status spmv_describe(const spmv_matrix *M, spmv_matrix_desc *out) {
+    if (!M || !out) return SPMV_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+    out->format = M->format;
+    out->layout = M->layout;
+    out->n_rows = M->n_rows;
+    out->n_cols = M->n_cols;
+    out->nnz = M->nnz;
+    out->width = M->width;
+    out->ld = M->ld;
+    out->ptr = M->ptr;
+    out->idx = M->idx;
+    out->idx2 = M->idx2;
+    out->val = M->val;
+    out->owned_bytes = M->owned();
+    return SPMV_OK;
+}
+
+void spmv_destroy(spmv_matrix *M) { delete M; }
+
+double spmv_r_ell(double t_crs, double t_ell, double t_trans) {
+    const double sp = t_crs / t_ell;   // Eq. (1)
+    const double tt = t_trans / t_crs; // Eq. (2), transformation in CRS-SpMV units
+    return sp / tt;                    // Eq. (3)
+}
+
+spmv_status spmv_dstar_from_points(int32_t m, const double *dmat, const double *rell, double c, int32_t rule,
+                                   double *dstar) {
+    if (m < 0 || !dstar || (m > 0 && (!dmat || !rell))) return SPMV_ERR_INVALID_ARG;
+    if (rule == SPMV_DSTAR_MAXPASS) {
+        double best = 0.0;
+        for (int32_t i = 0; i < m; ++i)
+            if (rell[i] >= c && dmat[i] > best) best = dmat[i];
+        *dstar = best;
+        return SPMV_OK;
+    }
+    if (rule != SPMV_DSTAR_PREFIX) return SPMV_ERR_INVALID_ARG;
+    std::vector<int32_t> ord(m);
+    for (int32_t i = 0; i < m; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return dmat[a] < dmat[b]; });
+    double d = INFINITY;
+    for (int32_t t = 0; t < m; ++t) {
+        if (rell[ord[t]] < c) {
+            d = (t == 0) ? 0.0 : dmat[ord[t]];
+            break;
+        }
+    }
+    *dstar = d;
+    return SPMV_OK;
+}
+
+spmv_status spmv_measure(const spmv_crs *A, const spmv_at_params *p, spmv_timing *out, spmv_stream_t stream) {
+    CKS(check_crs(A));
+    if (!p || !out) return SPMV_ERR_INVALID_ARG;
+    cudaStream_t s = S(stream);
+    const int reps = p->timing_reps > 0 ? p->timing_reps : 20;
+    const int warm = p->warmup_reps >= 0 ? p->warmup_reps : 3;
+    memset(out, 0, sizeof(*out));
+    spmv_stats st;
+    CKS(analyze_core(A, false, &st, s));
+    out->dmat = st.dmat;
+    if (p->mem_cap_bytes && st.ell_bytes > p->mem_cap_bytes) return SPMV_ERR_MEMORY_CAP;
+    BufPtr xb, yb;
+    CKS(alloc_buf(sizeof(double) * (size_t)A->n_cols, s, &xb));
+    CKS(alloc_buf(sizeof(double) * (size_t)A->n_rows, s, &yb));
+    CK(cudaMemsetAsync(xb->p, 0, sizeof(double) * (size_t)A->n_cols, s));
+    const double *x = reinterpret_cast<const double *>(xb->p);
+    double *y = reinterpret_cast<double *>(yb->p);
+    spmv_matrix *crs = nullptr;
+    CKS(build_crs_plan(A, 0, &crs, s));
+    std::unique_ptr<spmv_matrix> crs_h(crs);
+    CKS(time_median([&] { return apply_core(crs, x, y, s); }, warm, reps, s, &out->t_crs_ms));
+    // t_trans: device work of CRS -> ELL-Row (row statistics + the ELL
+    // build) into preallocated arrays; allocation is not timed.
+    const int32_t W = st.max_row_len, ld = round_up32(A->n_rows);
+    BufPtr ev, ei, acc, stw;
+    CKS(alloc_buf((size_t)ld * W * 8, s, &ev));
+    CKS(alloc_buf((size_t)ld * W * 4, s, &ei));
+    CKS(alloc_buf(sizeof(AnalyzeAcc), s, &acc));
+    CKS(alloc_buf(16, s, &stw));
+    CK(cudaMemsetAsync(stw->p, 0, 16, s));
+    auto trans = [&]() -> spmv_status {
+        CK(cudaMemsetAsync(acc->p, 0, sizeof(AnalyzeAcc), s));
+        CK(launch_analyze(A->irp, A->n_rows, A->nnz, reinterpret_cast<AnalyzeAcc *>(acc->p), s));
+        CK(launch_lines_to_ell(A->irp, A->icol, A->val, A->n_rows, A->n_cols, W, ld,
+                               reinterpret_cast<double *>(ev->p), reinterpret_cast<int32_t *>(ei->p), nullptr,
+                               nullptr, reinterpret_cast<int *>(stw->p), s, "crs_to_ell_row"));
+        return SPMV_OK;
+    };
+    CKS(time_median(trans, warm, reps, s, &out->t_trans_ms));
+    spmv_matrix ell;
+    ell.format = SPMV_ELL;
+    ell.layout = SPMV_ROWWISE;
+    ell.n_rows = A->n_rows;
+    ell.n_cols = A->n_cols;
+    ell.nnz = A->nnz;
+    ell.width = W;
+    ell.ld = ld;
+    ell.idx = reinterpret_cast<const int32_t *>(ei->p);
+    ell.val = reinterpret_cast<const double *>(ev->p);
+    CKS(time_median([&] { return apply_core(&ell, x, y, s); }, warm, reps, s, &out->t_ell_ms));
+    if (p->flags & SPMV_AT_TRY_COO) {
+        spmv_matrix *coo = nullptr;
+        CKS(build_coo_row(A, 0, &coo, s));
+        std::unique_ptr<spmv_matrix> coo_h(coo);
+        CKS(time_median([&] { return apply_core(coo, x, y, s); }, warm, reps, s, &out->t_coo_ms));
+    }
+    int hst = 0;
+    CK(cudaMemcpyAsync(&hst, stw->p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CKS(status_from_dev(hst));
+    out->sp = out->t_crs_ms / out->t_ell_ms;
+    out->tt = out->t_trans_ms / out->t_crs_ms;
+    out->r_ell = spmv_r_ell(out->t_crs_ms, out->t_ell_ms, out->t_trans_ms);
+    return SPMV_OK;
+}
+
+spmv_status spmv_calibrate(const spmv_crs *const *set, int32_t m, const spmv_at_params *p, double *dmat_out,
+                           double *rell_out, double *dstar_out, spmv_stream_t stream) {
+    if (!set || m < 0 || !p || !dstar_out) return SPMV_ERR_INVALID_ARG;
+    std::vector<double> d(m), r(m);
+    for (int32_t i = 0; i < m; ++i) {
+        spmv_timing t;
+        spmv_status st = spmv_measure(set[i], p, &t, stream);
+        if (st == SPMV_ERR_MEMORY_CAP) {
+            spmv_stats ss;
+            CKS(spmv_analyze(set[i], &ss, stream));
+            d[i] = ss.dmat;
+            r[i] = 0.0;
+        } else if (st != SPMV_OK) {
+            return st;
+        } else {
+            d[i] = t.dmat;
+            r[i] = t.r_ell;
+        }
+        if (dmat_out) dmat_out[i] = d[i];
+        if (rell_out) rell_out[i] = r[i];
+    }
+    return spmv_dstar_from_points(m, d.data(), r.data(), p->c, p->dstar_rule, dstar_out);
+}
+
+spmv_status spmv_autotune(const spmv_crs *A, const spmv_at_params *p, spmv_matrix **chosen, spmv_stats *stats,
+                          spmv_stream_t stream) {
+    if (!chosen || !p) return SPMV_ERR_INVALID_ARG;
+    *chosen = nullptr;
+    CKS(check_crs(A));
+    cudaStream_t s = S(stream);
+    spmv_stats st;
+    CKS(analyze_core(A, false, &st, s));  // on-line step (1): D_mat
+    if (stats) *stats = st;
+    const bool fits = !p->mem_cap_bytes || st.ell_bytes <= p->mem_cap_bytes;
+    if (st.dmat < p->dstar && fits) return build_ell_row(A, st, p->mem_cap_bytes, nullptr, nullptr, chosen, s);
+    if (p->flags & SPMV_AT_TRY_COO) {
+        spmv_matrix *crs = nullptr, *coo = nullptr;
+        CKS(build_crs_plan(A, p->mem_cap_bytes, &crs, s));
+        std::unique_ptr<spmv_matrix> crs_h(crs);
+        spmv_status e = build_coo_row(A, p->mem_cap_bytes, &coo, s);
+        if (e == SPMV_ERR_MEMORY_CAP) { *chosen = crs_h.release(); return SPMV_OK; }
+        CKS(e);
+        std::unique_ptr<spmv_matrix> coo_h(coo);
+        BufPtr xb, yb;
+        CKS(alloc_buf(sizeof(double) * (size_t)A->n_cols, s, &xb));
+        CKS(alloc_buf(sizeof(double) * (size_t)A->n_rows, s, &yb));
+        CK(cudaMemsetAsync(xb->p, 0, sizeof(double) * (size_t)A->n_cols, s));
+        const double *x = reinterpret_cast<const double *>(xb->p);
+        double *y = reinterpret_cast<double *>(yb->p);
+        const int reps = p->timing_reps > 0 ? p->timing_reps : 20;
+        const int warm = p->warmup_reps >= 0 ? p->warmup_reps : 3;
+        double tc = 0, to = 0;
+        CKS(time_median([&] { return apply_core(crs, x, y, s); }, warm, reps, s, &tc));
+        CKS(time_median([&] { return apply_core(coo, x, y, s); }, warm, reps, s, &to));
+        *chosen = (to < tc) ? coo_h.release() : crs_h.release();
+        return SPMV_OK;
+    }
+    return build_crs_plan(A, p->mem_cap_bytes, chosen, s);
+}
+
+spmv_status spmv_autotune_choose(const spmv_crs *A, const spmv_at_params *p, int32_t *format, int32_t *layout,
+                                 spmv_stats *stats, spmv_stream_t stream) {
+    if (!p || !format || !layout) return SPMV_ERR_INVALID_ARG;
+    CKS(check_crs(A));
+    spmv_stats st;
+    CKS(analyze_core(A, false, &st, S(stream)));
+    if (stats) *stats = st;
+    const bool fits = !p->mem_cap_bytes || st.ell_bytes <= p->mem_cap_bytes;
+    *format = (st.dmat < p->dstar && fits) ? SPMV_ELL : SPMV_CRS;
+    *layout = SPMV_ROWWISE;
+    return SPMV_OK;
+}
+
+uint64_t spmv_launch_count(void) { return g_launches.load(); }
+
+spmv_status spmv_profile_enable(int32_t on) {
+    g_profile_on.store(on ? 1 : 0);
+    return SPMV_OK;
+}
+
+int32_t spmv_profile_read(spmv_kernel_time *out, int32_t cap, int32_t reset) {
+    std::lock_guard<std::mutex> lk(g_pmu);
+    for (auto &r : g_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.e1) == cudaSuccess && cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
+            auto &t = g_totals[r.name];
+            t.first += 1;
+            t.second += ms;
+        } else {
+            cudaGetLastError();
+        }
+        g_event_pool.push_back(r.e0);
+        g_event_pool.push_back(r.e1);
+    }
+    g_pending.clear();
+    int32_t n = 0;
+    for (auto &kv : g_totals) {
+        if (out && n < cap) {
+            memset(&out[n], 0, sizeof(out[n]));
+            strncpy(out[n].name, kv.first.c_str(), sizeof(out[n].name) - 1);
+            out[n].launches = kv.second.first;
+            out[n].total_ms = kv.second.second;
+        }
+        ++n;
+    }
+    if (reset) g_totals.clear();
+    return n;
+}
+
+spmv_status spmv_debug_scan_timeout(int32_t n, int32_t spin_limit, int32_t *observed, spmv_stream_t stream) {
+    if (n <= 0 || spin_limit <= 0 || !observed) return SPMV_ERR_INVALID_ARG;
+    cudaStream_t s = S(stream);
+    BufPtr a, scr, words;
+    CKS(alloc_buf((size_t)(n + 1) * 4, s, &a));
+    CKS(alloc_buf(scan_scratch_bytes(n), s, &scr));
+    CKS(alloc_buf(16, s, &words));
+    CK(cudaMemsetAsync(a->p, 0, (size_t)(n + 1) * 4, s));
+    CK(cudaMemsetAsync(words->p, 0, 16, s));
+    CK(launch_scan(reinterpret_cast<int32_t *>(a->p), n, scr->p, nullptr, INT_MAX, nullptr, nullptr,
+                   reinterpret_cast<int *>(words->p), spin_limit, 1, s));
+    int hst = 0;
+    CK(cudaMemcpyAsync(&hst, words->p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *observed = (int32_t)status_from_dev(hst);
+    return SPMV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,191 @@
+// Shared device helpers and the internal launcher interface of libspmvat.
+// Target: sm_103a (GB300). All kernels are written for 32-wide warps,
+// 152 SMs, up to 227 KB of shared memory per CTA and TMA bulk copies.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace spmvat {
+
+// Bits OR-ed into a device status word by kernels.
+enum : int {
+    ST_BAD_INDEX = 1,  // an index (column / row / position) out of range
+    ST_TIMEOUT = 2,    // a bounded wait ran out
+    ST_BAD_PTR = 4,    // IRP not 0 .. nnz or not non-decreasing
+};
+
+// Per-call accumulator of spmv_analyze (one device struct).
+struct AnalyzeAcc {
+    unsigned long long sum_len;
+    unsigned long long sum_len2;
+    unsigned long long n_empty;
+    unsigned long long hist[32];
+    int max_len;
+    int min_len;
+    int status;
+    int pad;
+};
+
+// Bounded-wait budget: polls of a flag or mbarrier before a kernel gives up
+// and reports ST_TIMEOUT. With the backoff used below this is ~1-2 s.
+constexpr long long kSpinLimit = 1ll << 22;
+
+// ---------------------------------------------------------------- host side
+// Launch accounting and optional per-kernel event timing (api.cu).
+struct KernelScope {
+    KernelScope(const char *name, cudaStream_t s);
+    ~KernelScope();
+    int slot;
+    cudaStream_t stream;
+};
+int sm_count();  // SMs of the current device (cached)
+
+inline unsigned ceil_div_u(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+// ------------------------------------------------------------- device side
+__device__ __forceinline__ unsigned lane_id() {
+    unsigned l;
+    asm volatile("mov.u32 %0, %%laneid;" : "=r"(l));
+    return l;
+}
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Largest i in [lo, hi) with a[i] <= key, given a[lo] <= key (a sorted).
+__device__ __forceinline__ int last_le(const int32_t *a, int lo, int hi, long long key) {
+    while (hi - lo > 1) {
+        int mid = lo + ((hi - lo) >> 1);
+        if ((long long)a[mid] <= key) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// ---- mbarrier + TMA bulk copy (global -> shared), inline PTX -------------
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Poll with backoff; false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, long long limit) {
+    for (long long i = 0; i < limit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 16) __nanosleep(256);
+    }
+    return false;
+}
+// 1-D bulk copy of `bytes` (multiple of 16; both addresses 16-byte aligned)
+// from global memory into this CTA's shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *sdst, const void *gsrc, unsigned bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(sdst)),
+        "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---- acquire/release accesses for the look-back scan ----------------------
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// ---- warp / block reductions ----------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// --------------------------------------------------------------- launchers
+// All return cudaGetLastError() after enqueueing on `s`.
+
+// analyze / validate (kernels_rowwise.cu)
+cudaError_t launch_analyze(const int32_t *irp, int32_t n_rows, int64_t nnz, AnalyzeAcc *acc, cudaStream_t s);
+cudaError_t launch_validate_idx(const int32_t *idx, int64_t n, int32_t bound, int *status, cudaStream_t s);
+
+// pointer expansion: out[k] = line of entry k (COO-Row IROW, Phase II column)
+cudaError_t launch_expand(const int32_t *ptr, int32_t n_lines, int64_t nnz, int32_t *out, cudaStream_t s,
+                          const char *name = "expand");
+
+// compressed lines -> padded column-major ELL; optional fused y = A x
+cudaError_t launch_lines_to_ell(const int32_t *ptr, const int32_t *idx, const double *val, int32_t n_lines,
+                                int32_t idx_bound, int32_t width, int32_t ld, double *eval, int32_t *eidx,
+                                const double *x, double *y, int *status, cudaStream_t s,
+                                const char *name = "lines_to_ell");
+
+// Phase I (kernels_colwise.cu)
+cudaError_t launch_col_count(const int32_t *icol, int64_t nnz, int32_t n_cols, int32_t *nc, int32_t *rank,
+                             int *status, cudaStream_t s);
+// Exclusive scan in place over a[0..n) with a[n] = total; also max element
+// (atomicMax into *maxv) and, when long_list != NULL, the indices of
+// elements > long_thresh appended to long_list (count in *long_count).
+size_t scan_scratch_bytes(int64_t n);
+cudaError_t launch_scan(int32_t *a, int64_t n, void *scratch, int32_t *maxv, int32_t long_thresh,
+                        int32_t *long_list, int32_t *long_count, int *status, long long spin_limit,
+                        int debug_stall_first, cudaStream_t s);
+cudaError_t launch_col_scatter(const int32_t *irp, int32_t n_rows, const int32_t *icol, int64_t nnz,
+                               int32_t n_cols, const int32_t *cp, const int32_t *rank, int2 *pairs,
+                               int *status, cudaStream_t s);
+cudaError_t launch_col_fixup(const int32_t *cp, int32_t n_cols, const int32_t *irp, int32_t n_rows,
+                             const double *val, const int2 *pairs, const int32_t *long_list,
+                             int32_t n_long_host, int32_t max_len_host, int32_t *keys_tmp, int32_t *keys_tmp2,
+                             int32_t *trow, double *tval, cudaStream_t s);
+
+// SpMV (kernels_spmv.cu)
+cudaError_t launch_spmv_crs_vector(int v, const int32_t *irp, const int32_t *icol, const double *val,
+                                   const int32_t *rows, int64_t count, const double *x, double *y,
+                                   cudaStream_t s);
+cudaError_t launch_spmv_crs_block(const int32_t *irp, const int32_t *icol, const double *val,
+                                  const int32_t *rows, int64_t count, const double *x, double *y,
+                                  cudaStream_t s);
+cudaError_t launch_spmv_ell_row(const double *eval, const int32_t *eidx, int32_t n_rows, int32_t width,
+                                int32_t ld, const double *x, double *y, cudaStream_t s);
+cudaError_t launch_spmv_ell_col(const double *eval, const int32_t *eidx, int32_t n_rows, int32_t n_cols,
+                                int32_t width, int32_t ld, const double *x, double *y, cudaStream_t s);
+size_t coo_row_scratch_bytes(int64_t nnz);
+cudaError_t launch_spmv_coo_row(const int32_t *irow, const int32_t *icol, const double *val, int64_t nnz,
+                                int32_t n_rows, int32_t n_cols, const double *x, double *y, void *scratch,
+                                cudaStream_t s);
+cudaError_t launch_spmv_coo_col(const int32_t *row, const int32_t *col, const double *val, int64_t nnz,
+                                int32_t n_rows, const double *x, double *y, cudaStream_t s);
+cudaError_t launch_spmv_ccs(const int32_t *cp, const int32_t *trow, const double *tval, int32_t n_rows,
+                            int32_t n_cols, const double *x, double *y, cudaStream_t s);
+
+// CRS row-bin partition (kernels_spmv.cu): stable lists of rows per bin.
+constexpr int kNumBins = 7;
+int bin_of_len_host(int len);
+size_t bin_scratch_bytes(int32_t n_rows);
+cudaError_t launch_bin_rows(const int32_t *irp, int32_t n_rows, void *scratch, int32_t *rowlist,
+                            int *status, cudaStream_t s);
+
+}  // namespace spmvat

@@ -1,0 +1,458 @@
+// Phase I of Sec. 2.1 (CRS -> CCS) on the GPU.
+//
+// The paper's serial Phase I counts the entries of every column, turns the
+// counts into column pointers with a running sum, and then walks the CRS in
+// row order, dropping each entry at its column's cursor. The result lists
+// each column's rows in ascending order (repeated (i, j) entries in CRS
+// order). Here:
+//   k_col_count   : NC[j] by warp-aggregated atomics (__match_any_sync, one
+//                   atomicAdd per distinct column in a warp). Each entry also
+//                   keeps the value its column's counter had when it was
+//                   counted (its "rank"), in arbitrary order.
+//   k_scan        : NC -> IRP_T in place, one pass with decoupled look-back
+//                   (Merrill & Garland, 2016). Every spin is bounded; on
+//                   expiry the tile publishes an error flag that ends its
+//                   successors' waits, and the call reports SPMV_ERR_TIMEOUT.
+//   k_col_scatter : entry k goes to IRP_T[col] + rank[k] as the pair
+//                   (k, row), a permutation with no further atomics.
+//   k_fixup_*     : each column's pairs are put in ascending k (= the serial
+//                   order: CRS position order is row order), then
+//                   ICOL_T = row and VAL_T = VAL[k] are written contiguously.
+//                   Columns of <= 32 entries: one warp, bitonic network in
+//                   registers. Longer: one CTA, bitonic sort in shared memory
+//                   (<= 4096) or sorted chunks + merge-path merges.
+#include <climits>
+
+#include "common.cuh"
+
+namespace spmvat {
+
+// ------------------------------------------------------------------- count
+constexpr int CNT_THREADS = 256;
+constexpr int CNT_ITEMS = 4;
+constexpr int CNT_TILE = CNT_THREADS * CNT_ITEMS;
+
+__global__ void __launch_bounds__(CNT_THREADS) k_col_count(const int32_t *__restrict__ icol, int64_t nnz,
+                                                            int32_t n_cols, int32_t *__restrict__ nc,
+                                                            int32_t *__restrict__ rank, int *status) {
+    const long long k0 = ((long long)blockIdx.x * CNT_THREADS + threadIdx.x) * CNT_ITEMS;
+    int c[CNT_ITEMS];
+    const bool full = (k0 + CNT_ITEMS <= nnz) && ((reinterpret_cast<uintptr_t>(icol + k0) & 15) == 0);
+    if (full) {
+        int4 q = __ldcs(reinterpret_cast<const int4 *>(icol + k0));
+        c[0] = q.x; c[1] = q.y; c[2] = q.z; c[3] = q.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < CNT_ITEMS; ++j) c[j] = (k0 + j < nnz) ? icol[k0 + j] : -1;
+    }
+    const unsigned lane = lane_id();
+    int r[CNT_ITEMS];
+    int bad = 0;
+#pragma unroll
+    for (int j = 0; j < CNT_ITEMS; ++j) {
+        const bool has = (k0 + j < nnz);
+        const bool valid = has && (unsigned)c[j] < (unsigned)n_cols;
+        bad |= has && !valid;
+        const int key = valid ? c[j] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (valid && (int)lane == leader) base = atomicAdd(nc + key, __popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        r[j] = base + __popc(peers & lanemask_lt());
+    }
+    if (full && ((reinterpret_cast<uintptr_t>(rank + k0) & 15) == 0)) {
+        *reinterpret_cast<int4 *>(rank + k0) = make_int4(r[0], r[1], r[2], r[3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < CNT_ITEMS; ++j)
+            if (k0 + j < nnz) rank[k0 + j] = r[j];
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_BAD_INDEX);
+}
+
+cudaError_t launch_col_count(const int32_t *icol, int64_t nnz, int32_t n_cols, int32_t *nc, int32_t *rank,
+                             int *status, cudaStream_t s) {
+    if (nnz <= 0) return cudaSuccess;
+    KernelScope ks("col_count", s);
+    k_col_count<<<ceil_div_u(nnz, CNT_TILE), CNT_THREADS, 0, s>>>(icol, nnz, n_cols, nc, rank, status);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------------- scan
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+constexpr unsigned long long FLAG_NONE = 0ull;
+constexpr unsigned long long FLAG_AGG = 1ull << 62;
+constexpr unsigned long long FLAG_PRE = 2ull << 62;
+constexpr unsigned long long FLAG_ERR = 3ull << 62;
+constexpr unsigned long long VALUE_MASK = (1ull << 62) - 1;
+
+size_t scan_scratch_bytes(int64_t n) {
+    const long long tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    return 16 + (size_t)(tiles > 0 ? tiles : 1) * sizeof(unsigned long long);
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan(int32_t *a, int64_t n, unsigned *ticket,
+                                                        unsigned long long *tile_status, int32_t *maxv,
+                                                        int32_t long_thresh, int32_t *long_list,
+                                                        int32_t *long_count, int *status, long long spin_limit,
+                                                        int stall_first) {
+    __shared__ int s_tile;
+    __shared__ long long s_warp[SCAN_THREADS / 32];
+    __shared__ int s_wmax[SCAN_THREADS / 32];
+    __shared__ long long s_excl;
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) {
+        s_tile = (int)atomicAdd(ticket, 1u);  // tiles start in ticket order
+        s_abort = 0;
+    }
+    __syncthreads();
+    const int tile = s_tile;
+    const long long base = (long long)tile * SCAN_TILE + (long long)threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    long long sum = 0;
+    int mx = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        const long long i = base + j;
+        v[j] = (i < n) ? a[i] : 0;
+        sum += v[j];
+        mx = max(mx, v[j]);
+        if (long_list && i < n && v[j] > long_thresh) long_list[atomicAdd(long_count, 1)] = (int32_t)i;
+    }
+    // block-wide exclusive scan of the per-thread sums
+    const unsigned lane = lane_id();
+    const int w = threadIdx.x >> 5;
+    long long inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long t = __shfl_up_sync(0xffffffffu, inc, o);
+        if ((int)lane >= o) inc += t;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 31) s_warp[w] = inc;
+    if (lane == 0) s_wmax[w] = mx;
+    __syncthreads();
+    long long warp_off = 0, total = 0;
+    int bmax = 0;
+    for (int j = 0; j < SCAN_THREADS / 32; ++j) {
+        if (j < w) warp_off += s_warp[j];
+        total += s_warp[j];
+        bmax = max(bmax, s_wmax[j]);
+    }
+    const long long thread_excl = warp_off + inc - sum;
+    if (threadIdx.x == 0) {
+        if (maxv) atomicMax(maxv, bmax);
+        if (tile == 0) {
+            if (!stall_first) st_release_u64(&tile_status[0], FLAG_PRE | (unsigned long long)total);
+            s_excl = 0;
+        } else {
+            st_release_u64(&tile_status[tile], FLAG_AGG | (unsigned long long)total);
+        }
+    }
+    if (tile > 0 && w == 0) {
+        long long excl = 0;
+        long long pred = tile - 1;
+        long long spins = 0;
+        bool fail = false;
+        while (true) {
+            const long long idx = pred - (long long)lane;
+            const unsigned long long st = (idx >= 0) ? ld_acquire_u64(&tile_status[idx]) : FLAG_PRE;
+            const unsigned long long flag = st & ~VALUE_MASK;
+            if (__ballot_sync(0xffffffffu, flag == FLAG_ERR)) { fail = true; break; }
+            const unsigned pre = __ballot_sync(0xffffffffu, flag == FLAG_PRE);
+            const unsigned none = __ballot_sync(0xffffffffu, flag == FLAG_NONE);
+            const int first_pre = pre ? __ffs(pre) - 1 : 32;
+            const unsigned window = (first_pre >= 31) ? 0xffffffffu : ((1u << (first_pre + 1)) - 1u);
+            if (none & window) {
+                if (++spins > spin_limit) { fail = true; break; }
+                __nanosleep(spins < 64 ? 32 : 1000);
+                continue;
+            }
+            long long contrib = ((int)lane <= first_pre) ? (long long)(st & VALUE_MASK) : 0;
+            excl += warp_sum(contrib);
+            if (first_pre < 32) break;
+            pred -= 32;
+        }
+        if (lane == 0) {
+            if (fail) {
+                st_release_u64(&tile_status[tile], FLAG_ERR);
+                atomicOr(status, ST_TIMEOUT);
+                s_abort = 1;
+            } else {
+                st_release_u64(&tile_status[tile], FLAG_PRE | (unsigned long long)(excl + total));
+                s_excl = excl;
+            }
+        }
+    }
+    __syncthreads();
+    if (s_abort) return;
+    long long run = s_excl + thread_excl;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        const long long i = base + j;
+        if (i < n) a[i] = (int32_t)run;
+        run += v[j];
+        if (i == n - 1) a[n] = (int32_t)run;
+    }
+}
+
+cudaError_t launch_scan(int32_t *a, int64_t n, void *scratch, int32_t *maxv, int32_t long_thresh,
+                        int32_t *long_list, int32_t *long_count, int *status, long long spin_limit,
+                        int debug_stall_first, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const long long tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, scan_scratch_bytes(n), s);
+    if (e != cudaSuccess) return e;
+    unsigned *ticket = reinterpret_cast<unsigned *>(scratch);
+    unsigned long long *tstat = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(scratch) + 16);
+    KernelScope ks("scan_lookback", s);
+    k_scan<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(a, n, ticket, tstat, maxv, long_thresh, long_list, long_count,
+                                                     status, spin_limit, debug_stall_first);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- scatter
+constexpr int SCT_THREADS = 256;
+constexpr int SCT_ITEMS = 4;
+constexpr int SCT_TILE = SCT_THREADS * SCT_ITEMS;
+constexpr int SCT_WIN = 2048;
+
+__global__ void __launch_bounds__(SCT_THREADS) k_col_scatter(const int32_t *__restrict__ irp, int32_t n_rows,
+                                                              const int32_t *__restrict__ icol, int64_t nnz,
+                                                              int32_t n_cols, const int32_t *__restrict__ cp,
+                                                              const int32_t *__restrict__ rank,
+                                                              int2 *__restrict__ pairs, int *status) {
+    __shared__ int32_t s_ptr[SCT_WIN];
+    __shared__ int s_lo, s_hi;
+    const long long k0 = (long long)blockIdx.x * SCT_TILE;
+    const long long k1 = min(k0 + (long long)SCT_TILE, (long long)nnz);
+    if (threadIdx.x == 0) {
+        int lo = last_le(irp, 0, n_rows, k0);
+        s_lo = lo;
+        s_hi = last_le(irp, lo, n_rows, k1 - 1);
+    }
+    __syncthreads();
+    const int lo = s_lo, hi = s_hi;
+    const int wn = hi - lo + 2;
+    const bool sm = wn <= SCT_WIN;
+    if (sm)
+        for (int i = threadIdx.x; i < wn; i += SCT_THREADS) s_ptr[i] = irp[lo + i];
+    __syncthreads();
+    const long long k = k0 + (long long)threadIdx.x * SCT_ITEMS;
+    int bad = 0;
+    if (k < k1) {
+        int row = sm ? lo + last_le(s_ptr, 0, wn - 1, k) : last_le(irp, lo, hi + 1, k);
+        int c[SCT_ITEMS], r[SCT_ITEMS];
+        if (k + SCT_ITEMS <= k1 && ((reinterpret_cast<uintptr_t>(icol + k) & 15) == 0) &&
+            ((reinterpret_cast<uintptr_t>(rank + k) & 15) == 0)) {
+            int4 q = __ldcs(reinterpret_cast<const int4 *>(icol + k));
+            int4 p = __ldcs(reinterpret_cast<const int4 *>(rank + k));
+            c[0] = q.x; c[1] = q.y; c[2] = q.z; c[3] = q.w;
+            r[0] = p.x; r[1] = p.y; r[2] = p.z; r[3] = p.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < SCT_ITEMS; ++j) {
+                c[j] = (k + j < k1) ? icol[k + j] : 0;
+                r[j] = (k + j < k1) ? rank[k + j] : 0;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < SCT_ITEMS; ++j) {
+            const long long kk = k + j;
+            if (kk >= k1) break;
+            while (row < hi && (long long)(sm ? s_ptr[row + 1 - lo] : irp[row + 1]) <= kk) ++row;
+            if ((unsigned)c[j] >= (unsigned)n_cols) { bad = 1; continue; }
+            const long long pos = (long long)__ldg(cp + c[j]) + r[j];
+            if (pos < 0 || pos >= nnz) { bad = 1; continue; }
+            pairs[pos] = make_int2((int)kk, row);
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane_id() == 0) atomicOr(status, ST_BAD_INDEX);
+}
+
+cudaError_t launch_col_scatter(const int32_t *irp, int32_t n_rows, const int32_t *icol, int64_t nnz,
+                               int32_t n_cols, const int32_t *cp, const int32_t *rank, int2 *pairs,
+                               int *status, cudaStream_t s) {
+    if (nnz <= 0) return cudaSuccess;
+    KernelScope ks("col_scatter", s);
+    k_col_scatter<<<ceil_div_u(nnz, SCT_TILE), SCT_THREADS, 0, s>>>(irp, n_rows, icol, nnz, n_cols, cp, rank,
+                                                                     pairs, status);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- fixup
+// Short columns (<= 32 entries): one warp each, in registers.
+__global__ void __launch_bounds__(256) k_fixup_warp(const int32_t *__restrict__ cp, int32_t n_cols,
+                                                     const double *__restrict__ val,
+                                                     const int2 *__restrict__ pairs, int32_t *__restrict__ trow,
+                                                     double *__restrict__ tval) {
+    const unsigned lane = lane_id();
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long j = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n_cols; j += warps) {
+        const int p0 = __ldg(cp + j), p1 = __ldg(cp + j + 1);
+        const int len = p1 - p0;
+        if (len <= 0 || len > 32) continue;  // warp-uniform
+        int key = INT_MAX, row = 0;
+        if ((int)lane < len) {
+            const int2 q = __ldcs(pairs + p0 + lane);
+            key = q.x;
+            row = q.y;
+        }
+        const int nxt = __shfl_down_sync(0xffffffffu, key, 1);
+        const bool unsorted = __any_sync(0xffffffffu, (int)lane + 1 < len && key > nxt);
+        if (unsorted) {
+#pragma unroll
+            for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    const int ok = __shfl_xor_sync(0xffffffffu, key, stride);
+                    const int orow = __shfl_xor_sync(0xffffffffu, row, stride);
+                    const bool asc = (lane & size) == 0;
+                    const bool lower = (lane & stride) == 0;
+                    const bool take = (lower == asc) ? (ok < key) : (ok > key);
+                    if (take) { key = ok; row = orow; }
+                }
+            }
+        }
+        if ((int)lane < len) {
+            __stcs(trow + p0 + lane, row);
+            __stcs(tval + p0 + lane, __ldg(val + key));
+        }
+    }
+}
+
+// Long columns (> 32 entries): one CTA each.
+constexpr int FIX_THREADS = 256;
+constexpr int FIX_CHUNK = 4096;
+
+__device__ void block_bitonic_u64(unsigned long long *s, int P) {
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < (P >> 1); i += blockDim.x) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool asc = (lo & size) == 0;
+                const unsigned long long a = s[lo], b = s[hi];
+                if ((a > b) == asc) { s[lo] = b; s[hi] = a; }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__device__ __forceinline__ int merge_path(const int32_t *A, int na, const int32_t *B, int nb, int d) {
+    int lo = max(0, d - nb), hi = min(d, na);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (A[mid] <= B[d - mid - 1]) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(FIX_THREADS) k_fixup_block(
+    const int32_t *__restrict__ cp, const int32_t *__restrict__ irp, int32_t n_rows,
+    const double *__restrict__ val, int2 *__restrict__ pairs, const int32_t *__restrict__ long_list,
+    const int32_t *__restrict__ long_count, int32_t *__restrict__ keys_tmp, int32_t *__restrict__ trow,
+    double *__restrict__ tval) {
+    __shared__ unsigned long long s[FIX_CHUNK];
+    const int nl = *long_count;
+    for (int li = blockIdx.x; li < nl; li += gridDim.x) {
+        const int j = long_list[li];
+        const int p0 = cp[j], p1 = cp[j + 1];
+        const int L = p1 - p0;
+        if (L <= 32) continue;
+        if (L <= FIX_CHUNK) {
+            int P = 64;
+            while (P < L) P <<= 1;
+            for (int i = threadIdx.x; i < P; i += FIX_THREADS) {
+                if (i < L) {
+                    const int2 q = pairs[p0 + i];
+                    s[i] = ((unsigned long long)(unsigned)q.x << 32) | (unsigned)q.y;
+                } else {
+                    s[i] = ~0ull;
+                }
+            }
+            __syncthreads();
+            block_bitonic_u64(s, P);
+            for (int i = threadIdx.x; i < L; i += FIX_THREADS) {
+                const unsigned long long q = s[i];
+                trow[p0 + i] = (int32_t)(unsigned)(q & 0xffffffffu);
+                tval[p0 + i] = __ldg(val + (int)(q >> 32));
+            }
+            __syncthreads();
+            continue;
+        }
+        // L > FIX_CHUNK: keys only; sorted chunks, then merge passes
+        // ping-ponging between keys_tmp[p0..p1) and the column's own pair
+        // storage viewed as int32 (2L slots); rows are recomputed at the end.
+        int32_t *bufA = keys_tmp + p0;
+        int32_t *bufB = reinterpret_cast<int32_t *>(pairs + p0);
+        for (int c0 = 0; c0 < L; c0 += FIX_CHUNK) {
+            const int cl = min(FIX_CHUNK, L - c0);
+            int P = 64;
+            while (P < cl) P <<= 1;
+            for (int i = threadIdx.x; i < P; i += FIX_THREADS)
+                s[i] = (i < cl) ? (unsigned long long)(unsigned)pairs[p0 + c0 + i].x : ~0ull;
+            __syncthreads();
+            block_bitonic_u64(s, P);
+            for (int i = threadIdx.x; i < cl; i += FIX_THREADS) bufA[c0 + i] = (int32_t)s[i];
+            __syncthreads();
+        }
+        int32_t *src = bufA, *dst = bufB;
+        for (int wdt = FIX_CHUNK; wdt < L; wdt <<= 1) {
+            for (int r0 = 0; r0 < L; r0 += 2 * wdt) {
+                const int na = min(wdt, L - r0);
+                const int nb = max(0, min(wdt, L - r0 - wdt));
+                const int tot = na + nb;
+                const int per = (tot + FIX_THREADS - 1) / FIX_THREADS;
+                const int d0 = min(tot, (int)threadIdx.x * per), d1 = min(tot, d0 + per);
+                const int32_t *A = src + r0, *B = src + r0 + na;
+                int ia = merge_path(A, na, B, nb, d0);
+                int ib = d0 - ia;
+                for (int d = d0; d < d1; ++d) {
+                    if (ib >= nb || (ia < na && A[ia] <= B[ib])) dst[r0 + d] = A[ia++];
+                    else dst[r0 + d] = B[ib++];
+                }
+            }
+            __syncthreads();
+            int32_t *t = src; src = dst; dst = t;
+        }
+        for (int i = threadIdx.x; i < L; i += FIX_THREADS) {
+            const int k = src[i];
+            trow[p0 + i] = last_le(irp, 0, n_rows, k);
+            tval[p0 + i] = __ldg(val + k);
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_col_fixup(const int32_t *cp, int32_t n_cols, const int32_t *irp, int32_t n_rows,
+                             const double *val, const int2 *pairs, const int32_t *long_list,
+                             int32_t n_long_host, int32_t max_len_host, int32_t *keys_tmp, int32_t *keys_tmp2,
+                             int32_t *trow, double *tval, cudaStream_t s) {
+    (void)n_long_host; (void)max_len_host; (void)keys_tmp2;
+    if (n_cols <= 0) return cudaSuccess;
+    {
+        unsigned grid = ceil_div_u(n_cols, 8);
+        const unsigned cap = (unsigned)sm_count() * 16u;
+        if (grid > cap) grid = cap;
+        KernelScope ks("col_fixup_warp", s);
+        k_fixup_warp<<<grid, 256, 0, s>>>(cp, n_cols, val, pairs, trow, tval);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    {
+        // long_list is followed by its device-side count (see api.cu)
+        const int32_t *long_count = long_list - 1;
+        KernelScope ks("col_fixup_block", s);
+        k_fixup_block<<<(unsigned)sm_count() * 2u, FIX_THREADS, 0, s>>>(
+            cp, irp, n_rows, val, const_cast<int2 *>(pairs), long_list, long_count, keys_tmp, trow, tval);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace spmvat

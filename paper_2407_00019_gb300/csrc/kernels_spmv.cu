@@ -1,0 +1,562 @@
+// SpMV y = A x in each format of Sec. 2.1 (Sec. 3 gives the paper's OpenMP
+// loops; these are GB300 designs of the same products).
+//
+//  CRS      : V lanes per row, V from the row-length class (1..32), or a CTA
+//             per row for rows of >= 2048 entries; lanes sum strided entries
+//             in order and reduce with a fixed shuffle tree (deterministic).
+//             Irregular matrices run one launch per length bin over stable
+//             row lists built once per handle.
+//  ELL-Row  : one thread per two rows, 128-bit loads of the column-major
+//             slots (values and indices), FMA in slot order (Fig. 3 order).
+//  COO-Row  : tiles of 2048 entries, thread-local then block segmented
+//             reduction; partial sums of rows that cross tile edges are
+//             finished by a second, per-tile kernel in tile order
+//             (deterministic).
+//  COO-Col, ELL-Col, CCS : the column-major products of Fig. 1: each entry
+//             adds val * x[col] into y[row] with FP64 atomics.
+#include <climits>
+
+#include "common.cuh"
+
+namespace spmvat {
+
+// ===================================================================== CRS
+template <int V>
+__global__ void __launch_bounds__(256) k_spmv_crs_vector(const int32_t *__restrict__ irp,
+                                                          const int32_t *__restrict__ icol,
+                                                          const double *__restrict__ val,
+                                                          const int32_t *__restrict__ rows, int64_t count,
+                                                          const double *__restrict__ x, double *__restrict__ y) {
+    constexpr int G = 32 / V;  // rows per warp and iteration
+    const unsigned lane = lane_id();
+    const int sub = (int)lane % V;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long g0 = warp * G; g0 < count; g0 += nwarps * G) {
+        const long long g = g0 + (lane / V);
+        const bool valid = g < count;
+        const int r = valid ? (rows ? __ldg(rows + g) : (int)g) : 0;
+        const int s = valid ? __ldg(irp + r) : 0;
+        const int e = valid ? __ldg(irp + r + 1) : 0;
+        double acc = 0.0;
+        int k = s + sub;
+        for (; k + V < e; k += 2 * V) {
+            const double v0 = __ldcs(val + k), v1 = __ldcs(val + k + V);
+            const int c0 = __ldcs(icol + k), c1 = __ldcs(icol + k + V);
+            acc = fma(v0, __ldg(x + c0), acc);
+            acc = fma(v1, __ldg(x + c1), acc);
+        }
+        if (k < e) acc = fma(__ldcs(val + k), __ldg(x + __ldcs(icol + k)), acc);
+#pragma unroll
+        for (int o = V / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, V);
+        if (valid && sub == 0) y[r] = acc;
+    }
+}
+
+cudaError_t launch_spmv_crs_vector(int v, const int32_t *irp, const int32_t *icol, const double *val,
+                                   const int32_t *rows, int64_t count, const double *x, double *y,
+                                   cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    const long long warps_needed = (count * v + 31) / 32;
+    unsigned grid = ceil_div_u(warps_needed, 8);
+    const unsigned cap = (unsigned)sm_count() * 16u;
+    if (grid > cap) grid = cap;
+    switch (v) {
+#define SPMV_CASE(VV)                                                                            \
+    case VV: {                                                                                   \
+        KernelScope ks("spmv_crs_v" #VV, s);                                                     \
+        k_spmv_crs_vector<VV><<<grid, 256, 0, s>>>(irp, icol, val, rows, count, x, y);           \
+        break;                                                                                   \
+    }
+        SPMV_CASE(1)
+        SPMV_CASE(2)
+        SPMV_CASE(4)
+        SPMV_CASE(8)
+        SPMV_CASE(16)
+        SPMV_CASE(32)
+#undef SPMV_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// One CTA per (long) row; fixed-order block reduction.
+__global__ void __launch_bounds__(256) k_spmv_crs_block(const int32_t *__restrict__ irp,
+                                                         const int32_t *__restrict__ icol,
+                                                         const double *__restrict__ val,
+                                                         const int32_t *__restrict__ rows, int64_t count,
+                                                         const double *__restrict__ x, double *__restrict__ y) {
+    __shared__ double s_part[8];
+    for (long long g = blockIdx.x; g < count; g += gridDim.x) {
+        const int r = rows ? __ldg(rows + g) : (int)g;
+        const int s = __ldg(irp + r), e = __ldg(irp + r + 1);
+        double acc = 0.0;
+        for (int k = s + (int)threadIdx.x; k < e; k += 256) acc = fma(__ldcs(val + k), __ldg(x + __ldcs(icol + k)), acc);
+        acc = warp_sum(acc);
+        if (lane_id() == 0) s_part[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) t += s_part[j];
+            y[r] = t;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_spmv_crs_block(const int32_t *irp, const int32_t *icol, const double *val,
+                                  const int32_t *rows, int64_t count, const double *x, double *y,
+                                  cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    unsigned grid = (unsigned)(count < (long long)sm_count() * 8 ? count : (long long)sm_count() * 8);
+    KernelScope ks("spmv_crs_block", s);
+    k_spmv_crs_block<<<grid, 256, 0, s>>>(irp, icol, val, rows, count, x, y);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- row-bin partition
+// Bins by row length: 0: 0-3 (V=1), 1: 4-7 (2), 2: 8-15 (4), 3: 16-31 (8),
+// 4: 32-63 (16), 5: 64-2047 (32), 6: >= 2048 (one CTA per row).
+__host__ __device__ __forceinline__ int bin_of_len(int len) {
+    if (len < 4) return 0;
+    if (len < 8) return 1;
+    if (len < 16) return 2;
+    if (len < 32) return 3;
+    if (len < 64) return 4;
+    if (len < 2048) return 5;
+    return 6;
+}
+int bin_of_len_host(int len) { return bin_of_len(len); }
+
+constexpr int BIN_THREADS = 256;
+constexpr int BIN_ITEMS = 8;
+constexpr int BIN_CHUNK = BIN_THREADS * BIN_ITEMS;
+
+size_t bin_scratch_bytes(int32_t n_rows) {
+    const long long chunks = ((long long)n_rows + BIN_CHUNK - 1) / BIN_CHUNK;
+    const long long ncnt = chunks * kNumBins;
+    return (size_t)(ncnt + 1) * 4 + 16 + scan_scratch_bytes(ncnt);
+}
+
+// Per-thread bin counts of its BIN_ITEMS consecutive rows, then a block-wide
+// exclusive scan per bin (rows keep their order inside every bin).
+__device__ __forceinline__ void bin_thread_counts(const int32_t *irp, int32_t n_rows, long long r0, int *b,
+                                                  int cnt[kNumBins]) {
+#pragma unroll
+    for (int q = 0; q < kNumBins; ++q) cnt[q] = 0;
+#pragma unroll
+    for (int j = 0; j < BIN_ITEMS; ++j) {
+        const long long r = r0 + j;
+        b[j] = -1;
+        if (r < n_rows) {
+            b[j] = bin_of_len(irp[r + 1] - irp[r]);
+#pragma unroll
+            for (int q = 0; q < kNumBins; ++q) cnt[q] += (b[j] == q);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(BIN_THREADS) k_bin_count(const int32_t *__restrict__ irp, int32_t n_rows,
+                                                            int32_t *__restrict__ counts, long long n_chunks) {
+    __shared__ int s_tot[kNumBins];
+    if (threadIdx.x < kNumBins) s_tot[threadIdx.x] = 0;
+    __syncthreads();
+    int b[BIN_ITEMS], cnt[kNumBins];
+    bin_thread_counts(irp, n_rows, (long long)blockIdx.x * BIN_CHUNK + (long long)threadIdx.x * BIN_ITEMS, b, cnt);
+#pragma unroll
+    for (int q = 0; q < kNumBins; ++q) {
+        const int t = warp_sum(cnt[q]);
+        if (lane_id() == 0 && t) atomicAdd(&s_tot[q], t);
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumBins) counts[(long long)threadIdx.x * n_chunks + blockIdx.x] = s_tot[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(BIN_THREADS) k_bin_scatter(const int32_t *__restrict__ irp, int32_t n_rows,
+                                                              const int32_t *__restrict__ offs, long long n_chunks,
+                                                              int32_t *__restrict__ rowlist) {
+    __shared__ int s_w[BIN_THREADS / 32][kNumBins];
+    const long long r0 = (long long)blockIdx.x * BIN_CHUNK + (long long)threadIdx.x * BIN_ITEMS;
+    int b[BIN_ITEMS], cnt[kNumBins];
+    bin_thread_counts(irp, n_rows, r0, b, cnt);
+    const unsigned lane = lane_id();
+    const int w = threadIdx.x >> 5;
+    int excl[kNumBins];
+#pragma unroll
+    for (int q = 0; q < kNumBins; ++q) {
+        int inc = cnt[q];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if ((int)lane >= o) inc += t;
+        }
+        excl[q] = inc - cnt[q];
+        if (lane == 31) s_w[w][q] = inc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kNumBins; ++q) {
+        int add = offs[(long long)q * n_chunks + blockIdx.x];
+        for (int j = 0; j < w; ++j) add += s_w[j][q];
+        excl[q] += add;
+    }
+#pragma unroll
+    for (int j = 0; j < BIN_ITEMS; ++j) {
+        if (b[j] >= 0) {
+#pragma unroll
+            for (int q = 0; q < kNumBins; ++q)
+                if (b[j] == q) rowlist[excl[q]++] = (int32_t)(r0 + j);
+        }
+    }
+}
+
+cudaError_t launch_bin_rows(const int32_t *irp, int32_t n_rows, void *scratch, int32_t *rowlist, int *status,
+                            cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    const long long chunks = ((long long)n_rows + BIN_CHUNK - 1) / BIN_CHUNK;
+    const long long ncnt = chunks * kNumBins;
+    int32_t *counts = reinterpret_cast<int32_t *>(scratch);
+    void *scan_scr = reinterpret_cast<char *>(scratch) + (((size_t)(ncnt + 1) * 4 + 15) & ~(size_t)15);
+    {
+        KernelScope ks("bin_count", s);
+        k_bin_count<<<(unsigned)chunks, BIN_THREADS, 0, s>>>(irp, n_rows, counts, chunks);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = launch_scan(counts, ncnt, scan_scr, nullptr, INT_MAX, nullptr, nullptr, status, kSpinLimit, 0, s);
+    if (e != cudaSuccess) return e;
+    KernelScope ks("bin_scatter", s);
+    k_bin_scatter<<<(unsigned)chunks, BIN_THREADS, 0, s>>>(irp, n_rows, counts, chunks, rowlist);
+    return cudaGetLastError();
+}
+
+// ================================================================= ELL-Row
+template <int UNROLL>
+__global__ void __launch_bounds__(256) k_spmv_ell_row(const double *__restrict__ eval,
+                                                       const int32_t *__restrict__ eidx, int32_t n_rows,
+                                                       int32_t width, int32_t ld, const double *__restrict__ x,
+                                                       double *__restrict__ y) {
+    const long long pairs = ((long long)n_rows + 1) >> 1;
+    const long long step = (long long)ld >> 1;  // one slot column, in double2 / int2
+    const double2 *pv = reinterpret_cast<const double2 *>(eval);
+    const int2 *pc = reinterpret_cast<const int2 *>(eidx);
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < pairs;
+         p += (long long)gridDim.x * blockDim.x) {
+        double a0 = 0.0, a1 = 0.0;
+        int k = 0;
+        for (; k + UNROLL <= width; k += UNROLL) {
+            double2 v[UNROLL];
+            int2 c[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                v[u] = __ldcs(pv + (long long)(k + u) * step + p);
+                c[u] = __ldcs(pc + (long long)(k + u) * step + p);
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                a0 = fma(v[u].x, __ldg(x + c[u].x), a0);
+                a1 = fma(v[u].y, __ldg(x + c[u].y), a1);
+            }
+        }
+        for (; k < width; ++k) {
+            const double2 v = __ldcs(pv + (long long)k * step + p);
+            const int2 c = __ldcs(pc + (long long)k * step + p);
+            a0 = fma(v.x, __ldg(x + c.x), a0);
+            a1 = fma(v.y, __ldg(x + c.y), a1);
+        }
+        const long long i = 2 * p;
+        if (i + 1 < n_rows) {
+            __stcs(reinterpret_cast<double2 *>(y + i), make_double2(a0, a1));
+        } else {
+            y[i] = a0;
+        }
+    }
+}
+
+cudaError_t launch_spmv_ell_row(const double *eval, const int32_t *eidx, int32_t n_rows, int32_t width,
+                                int32_t ld, const double *x, double *y, cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    if ((reinterpret_cast<uintptr_t>(y) & 15) != 0) return cudaErrorMisalignedAddress;
+    const long long pairs = ((long long)n_rows + 1) >> 1;
+    const unsigned grid = ceil_div_u(pairs, 256);
+    KernelScope ks("spmv_ell_row", s);
+    k_spmv_ell_row<4><<<grid, 256, 0, s>>>(eval, eidx, n_rows, width, ld, x, y);
+    return cudaGetLastError();
+}
+
+// ================================================================= ELL-Col
+__global__ void __launch_bounds__(256) k_spmv_ell_col(const double *__restrict__ eval,
+                                                       const int32_t *__restrict__ eidx, int32_t n_cols,
+                                                       int32_t width, int32_t ld, const double *__restrict__ x,
+                                                       double *__restrict__ y) {
+    const long long pairs = ((long long)n_cols + 1) >> 1;
+    const long long step = (long long)ld >> 1;
+    const double2 *pv = reinterpret_cast<const double2 *>(eval);
+    const int2 *pc = reinterpret_cast<const int2 *>(eidx);
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < pairs;
+         p += (long long)gridDim.x * blockDim.x) {
+        const long long j = 2 * p;
+        const bool two = j + 1 < n_cols;
+        const double x0 = __ldg(x + j), x1 = two ? __ldg(x + j + 1) : 0.0;
+#pragma unroll 4
+        for (int k = 0; k < width; ++k) {
+            const double2 v = __ldcs(pv + (long long)k * step + p);
+            const int2 r = __ldcs(pc + (long long)k * step + p);
+            atomicAdd(y + r.x, v.x * x0);
+            if (two) atomicAdd(y + r.y, v.y * x1);
+        }
+    }
+}
+
+cudaError_t launch_spmv_ell_col(const double *eval, const int32_t *eidx, int32_t n_rows, int32_t n_cols,
+                                int32_t width, int32_t ld, const double *x, double *y, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(y, 0, sizeof(double) * (size_t)n_rows, s);
+    if (e != cudaSuccess || n_cols <= 0) return e;
+    const long long pairs = ((long long)n_cols + 1) >> 1;
+    KernelScope ks("spmv_ell_col", s);
+    k_spmv_ell_col<<<ceil_div_u(pairs, 256), 256, 0, s>>>(eval, eidx, n_cols, width, ld, x, y);
+    return cudaGetLastError();
+}
+
+// ================================================================= COO-Row
+constexpr int COO_THREADS = 256;
+constexpr int COO_ITEMS = 8;
+constexpr int COO_TILE = COO_THREADS * COO_ITEMS;
+
+size_t coo_row_scratch_bytes(int64_t nnz) {
+    const long long tiles = (nnz + COO_TILE - 1) / COO_TILE;
+    return (size_t)(tiles > 0 ? tiles : 1) * sizeof(double2);
+}
+
+struct SegPair {
+    int f;     // a row starts inside the covered range
+    double v;  // partial sum of the row open at the end of the range
+};
+__device__ __forceinline__ SegPair seg_combine(SegPair a, SegPair b) {
+    SegPair r;
+    r.f = a.f | b.f;
+    r.v = b.f ? b.v : a.v + b.v;
+    return r;
+}
+
+__global__ void __launch_bounds__(COO_THREADS) k_coo_row_tiles(const int32_t *__restrict__ irow,
+                                                                const int32_t *__restrict__ icol,
+                                                                const double *__restrict__ val, int64_t nnz,
+                                                                int32_t n_rows, int32_t n_cols,
+                                                                const double *__restrict__ x,
+                                                                double *__restrict__ y, double2 *__restrict__ carry) {
+    __shared__ int s_ra, s_cin;
+    __shared__ SegPair s_w[COO_THREADS / 32];
+    const long long t0 = (long long)blockIdx.x * COO_TILE;
+    const long long t1 = min(t0 + (long long)COO_TILE, (long long)nnz);
+    if (threadIdx.x == 0) {
+        s_ra = irow[t0];
+        s_cin = (t0 > 0) && irow[t0 - 1] == s_ra;
+    }
+    const long long k = t0 + (long long)threadIdx.x * COO_ITEMS;
+    const int m = (int)max(0ll, min((long long)COO_ITEMS, t1 - k));
+    int r[COO_ITEMS], c[COO_ITEMS];
+    double v[COO_ITEMS];
+    if (m == COO_ITEMS && ((reinterpret_cast<uintptr_t>(irow + k) & 15) == 0) &&
+        ((reinterpret_cast<uintptr_t>(icol + k) & 15) == 0) && ((reinterpret_cast<uintptr_t>(val + k) & 15) == 0)) {
+        const int4 *pr = reinterpret_cast<const int4 *>(irow + k);
+        const int4 *pc = reinterpret_cast<const int4 *>(icol + k);
+        const double2 *pv = reinterpret_cast<const double2 *>(val + k);
+#pragma unroll
+        for (int q = 0; q < COO_ITEMS / 4; ++q) {
+            const int4 a = __ldcs(pr + q), b = __ldcs(pc + q);
+            r[4 * q] = a.x; r[4 * q + 1] = a.y; r[4 * q + 2] = a.z; r[4 * q + 3] = a.w;
+            c[4 * q] = b.x; c[4 * q + 1] = b.y; c[4 * q + 2] = b.z; c[4 * q + 3] = b.w;
+        }
+#pragma unroll
+        for (int q = 0; q < COO_ITEMS / 2; ++q) {
+            const double2 a = __ldcs(pv + q);
+            v[2 * q] = a.x; v[2 * q + 1] = a.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < COO_ITEMS; ++j) {
+            r[j] = (j < m) ? irow[k + j] : 0;
+            c[j] = (j < m) ? icol[k + j] : 0;
+            v[j] = (j < m) ? val[k + j] : 0.0;
+        }
+    }
+    // products (FMA chain per row segment below keeps storage order)
+    const int prev_row = (m > 0 && k > 0) ? irow[k - 1] : -1;
+    const bool cont_prev = (m > 0) && (prev_row == r[0]);
+    // empty rows between the previous entry and my first one
+    if (m > 0)
+        for (int rr = prev_row + 1; rr < r[0] && rr < n_rows; ++rr) y[rr] = 0.0;
+    // local pass: sums of segments; middle segments are complete
+    double first_part = 0.0, part = 0.0;
+    int nseg = 1;
+    int cur = (m > 0) ? r[0] : -1;
+#pragma unroll
+    for (int j = 0; j < COO_ITEMS; ++j) {
+        if (j < m) {
+            if (r[j] != cur) {
+                if (nseg == 1) first_part = part;
+                else if ((unsigned)cur < (unsigned)n_rows) y[cur] = part;
+                for (int rr = cur + 1; rr < r[j] && rr < n_rows; ++rr) y[rr] = 0.0;
+                cur = r[j];
+                part = 0.0;
+                ++nseg;
+            }
+            const int cj = ((unsigned)c[j] < (unsigned)n_cols) ? c[j] : -1;
+            if (cj >= 0) part = fma(v[j], __ldg(x + cj), part);
+        }
+    }
+    // block segmented exclusive scan of (row-start flag, last-row partial)
+    SegPair me;
+    me.f = (m > 0) && (nseg > 1 || !cont_prev);
+    me.v = (m > 0) ? part : 0.0;
+    const unsigned lane = lane_id();
+    const int w = threadIdx.x >> 5;
+    SegPair inc = me;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        SegPair up;
+        up.f = __shfl_up_sync(0xffffffffu, inc.f, o);
+        up.v = __shfl_up_sync(0xffffffffu, inc.v, o);
+        if ((int)lane >= o) inc = seg_combine(up, inc);
+    }
+    SegPair ex;
+    ex.f = __shfl_up_sync(0xffffffffu, inc.f, 1);
+    ex.v = __shfl_up_sync(0xffffffffu, inc.v, 1);
+    if (lane == 0) { ex.f = 0; ex.v = 0.0; }
+    if (lane == 31) s_w[w] = inc;
+    __syncthreads();
+    SegPair wp;
+    wp.f = 0;
+    wp.v = 0.0;
+    for (int j = 0; j < w; ++j) wp = seg_combine(wp, s_w[j]);
+    const SegPair carry_in = seg_combine(wp, ex);
+    if (m == 0) return;
+    const int ra = s_ra;
+    const bool cin = s_cin;
+    const double cin_v = cont_prev ? carry_in.v : 0.0;
+    // first segment, if it ends inside this thread
+    if (nseg > 1) {
+        const double tot = first_part + cin_v;
+        if (r[0] == ra && cin) carry[blockIdx.x].x = tot;
+        else if ((unsigned)r[0] < (unsigned)n_rows) y[r[0]] = tot;
+    }
+    // last segment
+    const long long after = k + m;
+    const int lrow = cur;
+    const bool cont_next = (after < nnz) && irow[after] == lrow;
+    const double ltot = part + (nseg == 1 ? cin_v : 0.0);
+    if (cont_next) {
+        if (after >= t1) {  // continues into the next tile
+            carry[blockIdx.x].y = ltot;
+            if (lrow == ra && cin) carry[blockIdx.x].x = ltot;
+        }
+    } else {
+        if (lrow == ra && cin) carry[blockIdx.x].x = ltot;
+        else if ((unsigned)lrow < (unsigned)n_rows) y[lrow] = ltot;
+    }
+    // empty rows after the last entry of the matrix
+    if (after == nnz)
+        for (int rr = lrow + 1; rr < n_rows; ++rr) y[rr] = 0.0;
+}
+
+// Rows that cross tile edges: the tile where the row starts walks forward
+// and adds the partials in tile order.
+__global__ void __launch_bounds__(256) k_coo_row_carry(const int32_t *__restrict__ irow, int64_t nnz,
+                                                        long long n_tiles, int32_t n_rows,
+                                                        const double2 *__restrict__ carry, double *__restrict__ y) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const long long t0 = t * COO_TILE;
+    const long long t1 = min(t0 + (long long)COO_TILE, (long long)nnz);
+    const int ra = irow[t0], rb = irow[t1 - 1];
+    const bool cin = (t0 > 0) && irow[t0 - 1] == ra;
+    const bool cout = (t1 < nnz) && irow[t1] == rb;
+    if (!cout || (cin && ra == rb)) return;
+    double sum = carry[t].y;
+    for (long long u = t + 1; u < n_tiles; ++u) {
+        sum += carry[u].x;
+        const long long u0 = u * COO_TILE;
+        const long long u1 = min(u0 + (long long)COO_TILE, (long long)nnz);
+        const bool middle = (irow[u1 - 1] == rb) && (u1 < nnz) && irow[u1] == rb;
+        if (!middle) break;
+    }
+    if ((unsigned)rb < (unsigned)n_rows) y[rb] = sum;
+}
+
+cudaError_t launch_spmv_coo_row(const int32_t *irow, const int32_t *icol, const double *val, int64_t nnz,
+                                int32_t n_rows, int32_t n_cols, const double *x, double *y, void *scratch,
+                                cudaStream_t s) {
+    if (nnz <= 0) return cudaMemsetAsync(y, 0, sizeof(double) * (size_t)n_rows, s);
+    const long long tiles = (nnz + COO_TILE - 1) / COO_TILE;
+    double2 *carry = reinterpret_cast<double2 *>(scratch);
+    {
+        KernelScope ks("spmv_coo_row", s);
+        k_coo_row_tiles<<<(unsigned)tiles, COO_THREADS, 0, s>>>(irow, icol, val, nnz, n_rows, n_cols, x, y, carry);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    KernelScope ks("spmv_coo_row_carry", s);
+    k_coo_row_carry<<<ceil_div_u(tiles, 256), 256, 0, s>>>(irow, nnz, tiles, n_rows, carry, y);
+    return cudaGetLastError();
+}
+
+// ================================================================= COO-Col
+constexpr int COOC_ITEMS = 4;
+__global__ void __launch_bounds__(256) k_spmv_coo_col(const int32_t *__restrict__ row,
+                                                       const int32_t *__restrict__ col,
+                                                       const double *__restrict__ val, int64_t nnz,
+                                                       const double *__restrict__ x, double *__restrict__ y) {
+    const long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * COOC_ITEMS;
+    if (k >= nnz) return;
+    if (k + COOC_ITEMS <= nnz && ((reinterpret_cast<uintptr_t>(row + k) & 15) == 0) &&
+        ((reinterpret_cast<uintptr_t>(col + k) & 15) == 0) && ((reinterpret_cast<uintptr_t>(val + k) & 15) == 0)) {
+        const int4 r = __ldcs(reinterpret_cast<const int4 *>(row + k));
+        const int4 c = __ldcs(reinterpret_cast<const int4 *>(col + k));
+        const double2 v0 = __ldcs(reinterpret_cast<const double2 *>(val + k));
+        const double2 v1 = __ldcs(reinterpret_cast<const double2 *>(val + k) + 1);
+        atomicAdd(y + r.x, v0.x * __ldg(x + c.x));
+        atomicAdd(y + r.y, v0.y * __ldg(x + c.y));
+        atomicAdd(y + r.z, v1.x * __ldg(x + c.z));
+        atomicAdd(y + r.w, v1.y * __ldg(x + c.w));
+    } else {
+        for (long long j = k; j < min(k + COOC_ITEMS, (long long)nnz); ++j)
+            atomicAdd(y + row[j], val[j] * __ldg(x + col[j]));
+    }
+}
+
+cudaError_t launch_spmv_coo_col(const int32_t *row, const int32_t *col, const double *val, int64_t nnz,
+                                int32_t n_rows, const double *x, double *y, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(y, 0, sizeof(double) * (size_t)n_rows, s);
+    if (e != cudaSuccess || nnz <= 0) return e;
+    KernelScope ks("spmv_coo_col", s);
+    k_spmv_coo_col<<<ceil_div_u(nnz, 256 * COOC_ITEMS), 256, 0, s>>>(row, col, val, nnz, x, y);
+    return cudaGetLastError();
+}
+
+// ===================================================================== CCS
+// Eight lanes per column; each adds its entries into y[row].
+__global__ void __launch_bounds__(256) k_spmv_ccs(const int32_t *__restrict__ cp, const int32_t *__restrict__ trow,
+                                                   const double *__restrict__ tval, int32_t n_cols,
+                                                   const double *__restrict__ x, double *__restrict__ y) {
+    constexpr int V = 8;
+    const long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / V;
+    const int sub = threadIdx.x % V;
+    if (g >= n_cols) return;
+    const double xj = __ldg(x + g);
+    const int s = __ldg(cp + g), e = __ldg(cp + g + 1);
+    for (int p = s + sub; p < e; p += V) atomicAdd(y + __ldcs(trow + p), __ldcs(tval + p) * xj);
+}
+
+cudaError_t launch_spmv_ccs(const int32_t *cp, const int32_t *trow, const double *tval, int32_t n_rows,
+                            int32_t n_cols, const double *x, double *y, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(y, 0, sizeof(double) * (size_t)n_rows, s);
+    if (e != cudaSuccess || n_cols <= 0) return e;
+    KernelScope ks("spmv_ccs", s);
+    k_spmv_ccs<<<ceil_div_u((long long)n_cols * 8, 256), 256, 0, s>>>(cp, trow, tval, n_cols, x, y);
+    return cudaGetLastError();
+}
+
+}  // namespace spmvat
