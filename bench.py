@@ -38,6 +38,8 @@ WORKLOADS = {
     "stencil27_128": dict(kind="stencil27", N=128, seed_a=1, seed_x=2, cap=0,
                           desc="3-D 27-point stencil, 128^3 grid, N(0,1) off-diagonals, "
                                "diagonal 27 + |row sum|, x U[-1,1]"),
+    "stencil27_80": dict(kind="stencil27", N=80, seed_a=1, seed_x=2, cap=0,
+                         desc="3-D 27-point stencil, 80^3 grid (small case for profiling; CRS 162 MB > L2)"),
     "laplace2d_64": dict(kind="laplace", N=64, seed_x=0, cap=0,
                          desc="2-D 5-point Laplacian, 64x64 grid, x U[-1,1]"),
     "powerlaw_4m": dict(kind="powerlaw", n=4_000_000, seed_a=3, seed_x=4, cap=40 * 10 ** 9,
@@ -352,6 +354,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dstar", type=float, default=None,
+                    help="use this D* instead of the off-line calibration (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = WORKLOADS[args.workload]
@@ -374,7 +378,10 @@ def main():
     x = torch.from_numpy(xh).to(device)
     fmts = ["crs", "coo_row", "ell_row", "coo_col", "ell_col"]
     ys = {f: torch.empty(H.n_rows, dtype=torch.float64, device=device) for f in fmts}
-    dstar, d_pts, r_pts = calibrate_dstar(L, torch)
+    if args.dstar is None:
+        dstar, d_pts, r_pts = calibrate_dstar(L, torch)
+    else:
+        dstar, d_pts, r_pts = args.dstar, [], []
     step = Step(L, A, x, ys, dstar, w["cap"])
     stats = L.spmv_analyze(A)
     W = stats["W"]

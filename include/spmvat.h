@@ -200,6 +200,11 @@ spmv_status spmv_transform_apply(const spmv_crs *A, const double *x, double *y,
                                  uint64_t mem_cap_bytes, spmv_matrix **out,
                                  spmv_stream_t stream);
 
+/* SYNC. Reports whether any bounded device wait inside spmv_apply on this
+ * handle has run out since the handle was built (SPMV_ERR_TIMEOUT), else
+ * SPMV_OK. spmv_apply itself does not wait for the stream. */
+spmv_status spmv_matrix_status(const spmv_matrix *M, spmv_stream_t stream);
+
 /* Fill `out` with the handle's arrays and sizes. */
 spmv_status spmv_describe(const spmv_matrix *M, spmv_matrix_desc *out);
 

@@ -21,7 +21,7 @@ __all__ = [
     "SPMV_DSTAR_PREFIX", "SPMV_DSTAR_MAXPASS", "SPMV_AT_TRY_COO",
     "spmv_version", "spmv_status_string", "spmv_set_allocator", "spmv_analyze", "spmv_validate",
     "spmv_ell_bytes", "spmv_transform", "spmv_transform_from", "spmv_apply", "spmv_transform_apply",
-    "spmv_describe", "spmv_destroy", "spmv_r_ell", "spmv_dstar_from_points", "spmv_measure",
+    "spmv_describe", "spmv_matrix_status", "spmv_destroy", "spmv_r_ell", "spmv_dstar_from_points", "spmv_measure",
     "spmv_calibrate", "spmv_autotune", "spmv_autotune_choose", "spmv_launch_count", "spmv_profile_enable", "spmv_profile_read",
     "spmv_debug_scan_timeout",
 ]
@@ -111,6 +111,7 @@ def load_library():
         "spmv_apply": (ctypes.c_int, [vp, vp, vp, vp]),
         "spmv_transform_apply": (ctypes.c_int, [P(_CrsT), vp, vp, u64, P(vp), vp]),
         "spmv_describe": (ctypes.c_int, [vp, P(_DescT)]),
+        "spmv_matrix_status": (ctypes.c_int, [vp, vp]),
         "spmv_destroy": (None, [vp]),
         "spmv_r_ell": (dbl, [dbl, dbl, dbl]),
         "spmv_dstar_from_points": (ctypes.c_int, [i32, P(dbl), P(dbl), dbl, i32, P(dbl)]),
@@ -306,6 +307,10 @@ def spmv_describe(M: Matrix) -> dict:
     d = _DescT()
     _check(load_library().spmv_describe(M.handle, ctypes.byref(d)), "spmv_describe")
     return {f: getattr(d, f) for f, _ in _DescT._fields_}
+
+
+def spmv_matrix_status(M: Matrix, stream=None) -> None:
+    _check(load_library().spmv_matrix_status(M.handle, _stream(stream)), "spmv_matrix_status")
 
 
 def spmv_destroy(M: Matrix) -> None:

@@ -5,6 +5,7 @@
 #include <cfloat>
 #include <climits>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -167,6 +168,9 @@ struct spmv_matrix {
     // CRS schedule
     int crs_binned = 0;
     int crs_v = 1;
+    int crs_tile_s = 0;            // > 0: row-tile kernel with S lanes per row
+    int crs_stream_s = 0;          // > 0: TMA-staged stream kernel with S lanes per row
+    int *status = nullptr;         // device status word of bounded waits in apply
     int64_t bin_off[kNumBins + 1] = {};
     const int32_t *rowlist = nullptr;
     uint64_t owned() const {
@@ -281,6 +285,25 @@ spmv_status build_crs_plan(const spmv_crs *A, uint64_t cap, spmv_matrix **out, c
         M->crs_binned = 0;
         M->crs_v = kBinV[std::min(bin_of_len_host(st.max_row_len), 5)];
         if (M->crs_v < 1) M->crs_v = 1;
+        // Regular rows: the tile kernel, S lanes per row chosen so that a tile
+        // of 256/S rows always fits shared memory. SPMVAT_CRS_KERNEL
+        // (tile | stream | vector) and SPMVAT_CRS_S override the choice for
+        // schedule sweeps.
+        const char *kv = getenv("SPMVAT_CRS_KERNEL");
+        const std::string kind = kv ? kv : "tile";
+        int S = crs_tile_lanes(st.max_row_len);
+        if (const char *ev = getenv("SPMVAT_CRS_S")) S = atoi(ev);
+        const bool s_ok = S == 1 || S == 2 || S == 4 || S == 8;
+        if (kind == "tile" && s_ok && crs_tile_lanes(st.max_row_len) > 0) {
+            M->crs_tile_s = S;
+        } else if (kind == "stream" && s_ok && (int64_t)(256 / S) * st.max_row_len <= 4096) {
+            BufPtr sw;
+            CKS(alloc_buf(16, s, &sw));
+            CK(cudaMemsetAsync(sw->p, 0, 16, s));
+            M->crs_stream_s = S;
+            M->status = reinterpret_cast<int *>(sw->p);
+            M->bufs.push_back(sw);
+        }
     } else {
         const uint64_t need = (uint64_t)A->n_rows * 4;
         if (cap && need > cap) return SPMV_ERR_MEMORY_CAP;
@@ -312,9 +335,11 @@ spmv_status build_coo_row(const spmv_crs *A, uint64_t cap, spmv_matrix **out, cu
     if (cap && need > cap) return SPMV_ERR_MEMORY_CAP;
     std::unique_ptr<spmv_matrix> M(new_handle(A, SPMV_COO, SPMV_ROWWISE, s));
     if (!M) return SPMV_ERR_OOM;
-    BufPtr irow;
+    BufPtr irow, scr;
     CKS(alloc_buf(need, s, &irow));
-    CK(launch_expand(A->irp, A->n_rows, A->nnz, reinterpret_cast<int32_t *>(irow->p), s, "crs_to_coo_row"));
+    CKS(alloc_buf(expand_scratch_bytes(A->nnz), s, &scr));
+    CK(launch_expand(A->irp, A->n_rows, A->nnz, reinterpret_cast<int32_t *>(irow->p),
+                     reinterpret_cast<int32_t *>(scr->p), s, "crs_to_coo_row"));
     M->ptr = A->irp;
     M->idx = A->icol;
     M->idx2 = reinterpret_cast<const int32_t *>(irow->p);
@@ -389,14 +414,16 @@ spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bo
     if (want_ell) {
         if (cap_ell_col && ell_bytes(nc, colmax) > cap_ell_col) return SPMV_ERR_MEMORY_CAP;
     }
+    BufPtr sct;
     CKS(alloc_buf((size_t)nnz * 4, s, &trow));
     CKS(alloc_buf((size_t)nnz * 8, s, &tval));
-    CKS(alloc_buf((size_t)nnz * 8, s, &pairs));
+    CKS(alloc_buf((size_t)nnz * 8 + 16, s, &pairs));  // slack: staged copies round the end up
+    CKS(alloc_buf(col_scatter_scratch_bytes(nnz), s, &sct));
     CK(launch_col_scatter(A->irp, A->n_rows, A->icol, nnz, nc, d_cp, reinterpret_cast<int32_t *>(rank->p),
-                          reinterpret_cast<int2 *>(pairs->p), d_status, s));
-    CK(launch_col_fixup(d_cp, nc, A->irp, A->n_rows, A->val, reinterpret_cast<const int2 *>(pairs->p), d_long + 1,
-                        0, colmax, reinterpret_cast<int32_t *>(rank->p), nullptr,
-                        reinterpret_cast<int32_t *>(trow->p), reinterpret_cast<double *>(tval->p), s));
+                          reinterpret_cast<int2 *>(pairs->p), reinterpret_cast<int32_t *>(sct->p), d_status, s));
+    CK(launch_col_fixup(d_cp, nc, A->irp, A->n_rows, A->val, reinterpret_cast<int2 *>(pairs->p), d_long + 1,
+                        reinterpret_cast<int32_t *>(rank->p), reinterpret_cast<int32_t *>(trow->p),
+                        reinterpret_cast<double *>(tval->p), d_status, s));
     CK(cudaMemcpyAsync(hw, words->p, sizeof(hw), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     CKS(status_from_dev(hw[0]));
@@ -452,10 +479,11 @@ spmv_status coo_col_from_ccs(const spmv_matrix *src, uint64_t cap, spmv_matrix *
     M->n_cols = src->n_cols;
     M->nnz = src->nnz;
     M->home = s;
-    BufPtr tcol;
+    BufPtr tcol, scr;
     CKS(alloc_buf(need, s, &tcol));
-    CK(launch_expand(src->ptr, src->n_cols, src->nnz, reinterpret_cast<int32_t *>(tcol->p), s,
-                     "ccs_to_coo_col"));
+    CKS(alloc_buf(expand_scratch_bytes(src->nnz), s, &scr));
+    CK(launch_expand(src->ptr, src->n_cols, src->nnz, reinterpret_cast<int32_t *>(tcol->p),
+                     reinterpret_cast<int32_t *>(scr->p), s, "ccs_to_coo_col"));
     M->ptr = src->ptr;
     M->idx = src->idx;
     M->idx2 = reinterpret_cast<const int32_t *>(tcol->p);
@@ -472,7 +500,11 @@ spmv_status apply_core(const spmv_matrix *M, const double *x, double *y, cudaStr
     if (M->layout == SPMV_ROWWISE) {
         switch (M->format) {
             case SPMV_CRS:
-                if (!M->crs_binned) {
+                if (M->crs_tile_s > 0) {
+                    CK(launch_spmv_crs_tile(M->crs_tile_s, M->ptr, M->idx, M->val, M->n_rows, x, y, s));
+                } else if (M->crs_stream_s > 0) {
+                    CK(launch_spmv_crs_stream(M->crs_stream_s, M->ptr, M->idx, M->val, M->n_rows, x, y, M->status, s));
+                } else if (!M->crs_binned) {
                     CK(launch_spmv_crs_vector(M->crs_v, M->ptr, M->idx, M->val, nullptr, M->n_rows, x, y, s));
                 } else {
                     for (int b = 0; b < kNumBins; ++b) {
@@ -839,6 +871,15 @@ spmv_status spmv_autotune_choose(const spmv_crs *A, const spmv_at_params *p, int
     *format = (st.dmat < p->dstar && fits) ? SPMV_ELL : SPMV_CRS;
     *layout = SPMV_ROWWISE;
     return SPMV_OK;
+}
+
+spmv_status spmv_matrix_status(const spmv_matrix *M, spmv_stream_t stream) {
+    if (!M) return SPMV_ERR_INVALID_ARG;
+    if (!M->status) return SPMV_OK;
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, M->status, sizeof(int), cudaMemcpyDeviceToHost, S(stream)));
+    CK(cudaStreamSynchronize(S(stream)));
+    return status_from_dev(h);
 }
 
 uint64_t spmv_launch_count(void) { return g_launches.load(); }

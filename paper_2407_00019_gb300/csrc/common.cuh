@@ -43,6 +43,13 @@ int sm_count();  // SMs of the current device (cached)
 
 inline unsigned ceil_div_u(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
+// Raise a kernel's dynamic shared-memory limit (cheap host call; made before
+// every launch so that each device and each instantiation gets it).
+template <class K>
+cudaError_t set_smem_attr(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 // ------------------------------------------------------------- device side
 __device__ __forceinline__ unsigned lane_id() {
     unsigned l;
@@ -133,9 +140,15 @@ __device__ __forceinline__ T warp_sum(T v) {
 cudaError_t launch_analyze(const int32_t *irp, int32_t n_rows, int64_t nnz, AnalyzeAcc *acc, cudaStream_t s);
 cudaError_t launch_validate_idx(const int32_t *idx, int64_t n, int32_t bound, int *status, cudaStream_t s);
 
+// tile_lines: out[t] = line holding entry t*tile, t < ceil(nnz/tile)
+size_t tile_lines_bytes(int64_t nnz, int tile);
+cudaError_t launch_tile_lines(const int32_t *ptr, int32_t n_lines, int64_t nnz, int tile, int32_t *out,
+                              cudaStream_t s);
+
 // pointer expansion: out[k] = line of entry k (COO-Row IROW, Phase II column)
-cudaError_t launch_expand(const int32_t *ptr, int32_t n_lines, int64_t nnz, int32_t *out, cudaStream_t s,
-                          const char *name = "expand");
+size_t expand_scratch_bytes(int64_t nnz);
+cudaError_t launch_expand(const int32_t *ptr, int32_t n_lines, int64_t nnz, int32_t *out, int32_t *scratch,
+                          cudaStream_t s, const char *name = "expand");
 
 // compressed lines -> padded column-major ELL; optional fused y = A x
 cudaError_t launch_lines_to_ell(const int32_t *ptr, const int32_t *idx, const double *val, int32_t n_lines,
@@ -153,18 +166,26 @@ size_t scan_scratch_bytes(int64_t n);
 cudaError_t launch_scan(int32_t *a, int64_t n, void *scratch, int32_t *maxv, int32_t long_thresh,
                         int32_t *long_list, int32_t *long_count, int *status, long long spin_limit,
                         int debug_stall_first, cudaStream_t s);
+size_t col_scatter_scratch_bytes(int64_t nnz);
 cudaError_t launch_col_scatter(const int32_t *irp, int32_t n_rows, const int32_t *icol, int64_t nnz,
                                int32_t n_cols, const int32_t *cp, const int32_t *rank, int2 *pairs,
-                               int *status, cudaStream_t s);
+                               int32_t *scratch, int *status, cudaStream_t s);
+// `pairs` must have 16 bytes of slack after its nnz elements.
+// `long_list` is preceded by its device-side count.
 cudaError_t launch_col_fixup(const int32_t *cp, int32_t n_cols, const int32_t *irp, int32_t n_rows,
-                             const double *val, const int2 *pairs, const int32_t *long_list,
-                             int32_t n_long_host, int32_t max_len_host, int32_t *keys_tmp, int32_t *keys_tmp2,
-                             int32_t *trow, double *tval, cudaStream_t s);
+                             const double *val, int2 *pairs, const int32_t *long_list, int32_t *keys_tmp,
+                             int32_t *trow, double *tval, int *status, cudaStream_t s);
 
 // SpMV (kernels_spmv.cu)
 cudaError_t launch_spmv_crs_vector(int v, const int32_t *irp, const int32_t *icol, const double *val,
                                    const int32_t *rows, int64_t count, const double *x, double *y,
                                    cudaStream_t s);
+int crs_tile_lanes(int max_row_len);
+cudaError_t launch_spmv_crs_tile(int S, const int32_t *irp, const int32_t *icol, const double *val,
+                                 int32_t n_rows, const double *x, double *y, cudaStream_t s);
+size_t crs_stream_smem_bytes();
+cudaError_t launch_spmv_crs_stream(int S, const int32_t *irp, const int32_t *icol, const double *val,
+                                   int32_t n_rows, const double *x, double *y, int *status, cudaStream_t s);
 cudaError_t launch_spmv_crs_block(const int32_t *irp, const int32_t *icol, const double *val,
                                   const int32_t *rows, int64_t count, const double *x, double *y,
                                   cudaStream_t s);

@@ -5,10 +5,12 @@
 // row order, dropping each entry at its column's cursor. The result lists
 // each column's rows in ascending order (repeated (i, j) entries in CRS
 // order). Here:
-//   k_col_count   : NC[j] by warp-aggregated atomics (__match_any_sync, one
-//                   atomicAdd per distinct column in a warp). Each entry also
-//                   keeps the value its column's counter had when it was
-//                   counted (its "rank"), in arbitrary order.
+//   k_col_count   : NC[j] by one atomicAdd per entry (warp aggregation with
+//                   __match_any_sync was measured slower: on banded matrices a
+//                   warp rarely holds two entries of one column, and the match
+//                   instruction saturates the MIO pipe). Each entry also keeps
+//                   the value its column's counter had when it was counted
+//                   (its "rank"), in arbitrary order.
 //   k_scan        : NC -> IRP_T in place, one pass with decoupled look-back
 //                   (Merrill & Garland, 2016). Every spin is bounded; on
 //                   expiry the tile publishes an error flag that ends its
@@ -28,47 +30,34 @@
 namespace spmvat {
 
 // ------------------------------------------------------------------- count
+// Thread-striped tiles: item u of thread t is entry k0 + u*256 + t, so one
+// instruction of a warp covers 32 consecutive entries and the CTA issues its
+// atomics in (nearly) ascending k. Ranks then mostly come out in the serial
+// order and the fix-up rarely has to sort.
 constexpr int CNT_THREADS = 256;
-constexpr int CNT_ITEMS = 4;
+constexpr int CNT_ITEMS = 8;
 constexpr int CNT_TILE = CNT_THREADS * CNT_ITEMS;
 
 __global__ void __launch_bounds__(CNT_THREADS) k_col_count(const int32_t *__restrict__ icol, int64_t nnz,
                                                             int32_t n_cols, int32_t *__restrict__ nc,
                                                             int32_t *__restrict__ rank, int *status) {
-    const long long k0 = ((long long)blockIdx.x * CNT_THREADS + threadIdx.x) * CNT_ITEMS;
+    const long long k0 = (long long)blockIdx.x * CNT_TILE + threadIdx.x;
     int c[CNT_ITEMS];
-    const bool full = (k0 + CNT_ITEMS <= nnz) && ((reinterpret_cast<uintptr_t>(icol + k0) & 15) == 0);
-    if (full) {
-        int4 q = __ldcs(reinterpret_cast<const int4 *>(icol + k0));
-        c[0] = q.x; c[1] = q.y; c[2] = q.z; c[3] = q.w;
-    } else {
 #pragma unroll
-        for (int j = 0; j < CNT_ITEMS; ++j) c[j] = (k0 + j < nnz) ? icol[k0 + j] : -1;
+    for (int u = 0; u < CNT_ITEMS; ++u) {
+        const long long k = k0 + (long long)u * CNT_THREADS;
+        c[u] = (k < nnz) ? __ldcs(icol + k) : -1;
     }
-    const unsigned lane = lane_id();
-    int r[CNT_ITEMS];
     int bad = 0;
 #pragma unroll
-    for (int j = 0; j < CNT_ITEMS; ++j) {
-        const bool has = (k0 + j < nnz);
-        const bool valid = has && (unsigned)c[j] < (unsigned)n_cols;
-        bad |= has && !valid;
-        const int key = valid ? c[j] : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        const int leader = __ffs(peers) - 1;
-        int base = 0;
-        if (valid && (int)lane == leader) base = atomicAdd(nc + key, __popc(peers));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        r[j] = base + __popc(peers & lanemask_lt());
+    for (int u = 0; u < CNT_ITEMS; ++u) {
+        const long long k = k0 + (long long)u * CNT_THREADS;
+        const bool valid = (k < nnz) && (unsigned)c[u] < (unsigned)n_cols;
+        bad |= (k < nnz) && !valid;
+        const int r = valid ? atomicAdd(nc + c[u], 1) : 0;
+        if (k < nnz) __stcs(rank + k, r);
     }
-    if (full && ((reinterpret_cast<uintptr_t>(rank + k0) & 15) == 0)) {
-        *reinterpret_cast<int4 *>(rank + k0) = make_int4(r[0], r[1], r[2], r[3]);
-    } else {
-#pragma unroll
-        for (int j = 0; j < CNT_ITEMS; ++j)
-            if (k0 + j < nnz) rank[k0 + j] = r[j];
-    }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_BAD_INDEX);
+    if (__any_sync(0xffffffffu, bad) && lane_id() == 0) atomicOr(status, ST_BAD_INDEX);
 }
 
 cudaError_t launch_col_count(const int32_t *icol, int64_t nnz, int32_t n_cols, int32_t *nc, int32_t *rank,
@@ -216,8 +205,10 @@ cudaError_t launch_scan(int32_t *a, int64_t n, void *scratch, int32_t *maxv, int
 }
 
 // ----------------------------------------------------------------- scatter
+// Entry loads (ICOL, rank) are issued before the tile's row window is
+// fetched, so the two round trips overlap.
 constexpr int SCT_THREADS = 256;
-constexpr int SCT_ITEMS = 4;
+constexpr int SCT_ITEMS = 8;
 constexpr int SCT_TILE = SCT_THREADS * SCT_ITEMS;
 constexpr int SCT_WIN = 2048;
 
@@ -225,102 +216,165 @@ __global__ void __launch_bounds__(SCT_THREADS) k_col_scatter(const int32_t *__re
                                                               const int32_t *__restrict__ icol, int64_t nnz,
                                                               int32_t n_cols, const int32_t *__restrict__ cp,
                                                               const int32_t *__restrict__ rank,
+                                                              const int32_t *__restrict__ tl, long long n_tiles,
                                                               int2 *__restrict__ pairs, int *status) {
     __shared__ int32_t s_ptr[SCT_WIN];
-    __shared__ int s_lo, s_hi;
     const long long k0 = (long long)blockIdx.x * SCT_TILE;
     const long long k1 = min(k0 + (long long)SCT_TILE, (long long)nnz);
-    if (threadIdx.x == 0) {
-        int lo = last_le(irp, 0, n_rows, k0);
-        s_lo = lo;
-        s_hi = last_le(irp, lo, n_rows, k1 - 1);
+    const long long k = k0 + (long long)threadIdx.x * SCT_ITEMS;
+    int c[SCT_ITEMS], r[SCT_ITEMS];
+    if (k + SCT_ITEMS <= k1 && ((reinterpret_cast<uintptr_t>(icol + k) & 15) == 0) &&
+        ((reinterpret_cast<uintptr_t>(rank + k) & 15) == 0)) {
+#pragma unroll
+        for (int h = 0; h < SCT_ITEMS / 4; ++h) {
+            const int4 q = __ldcs(reinterpret_cast<const int4 *>(icol + k) + h);
+            const int4 p = __ldcs(reinterpret_cast<const int4 *>(rank + k) + h);
+            c[4 * h] = q.x; c[4 * h + 1] = q.y; c[4 * h + 2] = q.z; c[4 * h + 3] = q.w;
+            r[4 * h] = p.x; r[4 * h + 1] = p.y; r[4 * h + 2] = p.z; r[4 * h + 3] = p.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < SCT_ITEMS; ++j) {
+            c[j] = (k + j < k1) ? icol[k + j] : 0;
+            r[j] = (k + j < k1) ? rank[k + j] : 0;
+        }
     }
-    __syncthreads();
-    const int lo = s_lo, hi = s_hi;
+    long long pos[SCT_ITEMS];
+    int bad = 0;
+#pragma unroll
+    for (int j = 0; j < SCT_ITEMS; ++j) {
+        const bool ok = (k + j < k1) && (unsigned)c[j] < (unsigned)n_cols;
+        bad |= (k + j < k1) && !ok;
+        pos[j] = ok ? (long long)__ldg(cp + c[j]) + r[j] : -1;
+    }
+    const int lo = tl[blockIdx.x];
+    const int hi = (blockIdx.x + 1 < n_tiles) ? tl[blockIdx.x + 1] : n_rows - 1;
     const int wn = hi - lo + 2;
     const bool sm = wn <= SCT_WIN;
     if (sm)
         for (int i = threadIdx.x; i < wn; i += SCT_THREADS) s_ptr[i] = irp[lo + i];
     __syncthreads();
-    const long long k = k0 + (long long)threadIdx.x * SCT_ITEMS;
-    int bad = 0;
     if (k < k1) {
         int row = sm ? lo + last_le(s_ptr, 0, wn - 1, k) : last_le(irp, lo, hi + 1, k);
-        int c[SCT_ITEMS], r[SCT_ITEMS];
-        if (k + SCT_ITEMS <= k1 && ((reinterpret_cast<uintptr_t>(icol + k) & 15) == 0) &&
-            ((reinterpret_cast<uintptr_t>(rank + k) & 15) == 0)) {
-            int4 q = __ldcs(reinterpret_cast<const int4 *>(icol + k));
-            int4 p = __ldcs(reinterpret_cast<const int4 *>(rank + k));
-            c[0] = q.x; c[1] = q.y; c[2] = q.z; c[3] = q.w;
-            r[0] = p.x; r[1] = p.y; r[2] = p.z; r[3] = p.w;
-        } else {
-#pragma unroll
-            for (int j = 0; j < SCT_ITEMS; ++j) {
-                c[j] = (k + j < k1) ? icol[k + j] : 0;
-                r[j] = (k + j < k1) ? rank[k + j] : 0;
-            }
-        }
 #pragma unroll
         for (int j = 0; j < SCT_ITEMS; ++j) {
             const long long kk = k + j;
             if (kk >= k1) break;
             while (row < hi && (long long)(sm ? s_ptr[row + 1 - lo] : irp[row + 1]) <= kk) ++row;
-            if ((unsigned)c[j] >= (unsigned)n_cols) { bad = 1; continue; }
-            const long long pos = (long long)__ldg(cp + c[j]) + r[j];
-            if (pos < 0 || pos >= nnz) { bad = 1; continue; }
-            pairs[pos] = make_int2((int)kk, row);
+            if (pos[j] < 0) continue;
+            if (pos[j] >= nnz) { bad = 1; continue; }
+            pairs[pos[j]] = make_int2((int)kk, row);
         }
     }
     if (__any_sync(0xffffffffu, bad) && lane_id() == 0) atomicOr(status, ST_BAD_INDEX);
 }
 
+size_t col_scatter_scratch_bytes(int64_t nnz) { return tile_lines_bytes(nnz, SCT_TILE); }
+
 cudaError_t launch_col_scatter(const int32_t *irp, int32_t n_rows, const int32_t *icol, int64_t nnz,
                                int32_t n_cols, const int32_t *cp, const int32_t *rank, int2 *pairs,
-                               int *status, cudaStream_t s) {
+                               int32_t *scratch, int *status, cudaStream_t s) {
     if (nnz <= 0) return cudaSuccess;
+    cudaError_t e = launch_tile_lines(irp, n_rows, nnz, SCT_TILE, scratch, s);
+    if (e != cudaSuccess) return e;
+    const long long n_tiles = (nnz + SCT_TILE - 1) / SCT_TILE;
     KernelScope ks("col_scatter", s);
-    k_col_scatter<<<ceil_div_u(nnz, SCT_TILE), SCT_THREADS, 0, s>>>(irp, n_rows, icol, nnz, n_cols, cp, rank,
-                                                                     pairs, status);
+    k_col_scatter<<<(unsigned)n_tiles, SCT_THREADS, 0, s>>>(irp, n_rows, icol, nnz, n_cols, cp, rank, scratch,
+                                                             n_tiles, pairs, status);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------- fixup
-// Short columns (<= 32 entries): one warp each, in registers.
-__global__ void __launch_bounds__(256) k_fixup_warp(const int32_t *__restrict__ cp, int32_t n_cols,
-                                                     const double *__restrict__ val,
-                                                     const int2 *__restrict__ pairs, int32_t *__restrict__ trow,
-                                                     double *__restrict__ tval) {
+// Short columns (<= 32 entries), one CTA per tile of FT_COLS consecutive
+// columns, many CTAs per SM. The tile's (k, row) pairs are loaded into shared
+// memory with coalesced loads; pass 1: warp w orders the columns it owns with
+// a bitonic network in registers when they are out of order and writes them
+// back; pass 2: all threads stride over the tile and write ICOL_T = row and
+// VAL_T = VAL[k] contiguously, four independent VAL gathers in flight per
+// thread. Columns longer than 32 are marked and left to k_fixup_block. A tile
+// whose pairs exceed FT_CAP is handled column by column from global memory.
+constexpr int FT_THREADS = 256;
+constexpr int FT_COLS = 64;
+constexpr int FT_CAP = 2048;  // pairs per tile in shared memory (16 KB)
+
+__device__ __forceinline__ void warp_sort_pairs(int &key, int &row) {
     const unsigned lane = lane_id();
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long j = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n_cols; j += warps) {
-        const int p0 = __ldg(cp + j), p1 = __ldg(cp + j + 1);
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const int ok = __shfl_xor_sync(0xffffffffu, key, stride);
+            const int orow = __shfl_xor_sync(0xffffffffu, row, stride);
+            const bool asc = (lane & size) == 0;
+            const bool lower = (lane & stride) == 0;
+            const bool take = (lower == asc) ? (ok < key) : (ok > key);
+            if (take) { key = ok; row = orow; }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(FT_THREADS) k_fixup_tiles(const int32_t *__restrict__ cp, int32_t n_cols,
+                                                             const double *__restrict__ val,
+                                                             const int2 *__restrict__ pairs,
+                                                             int32_t *__restrict__ trow, double *__restrict__ tval) {
+    __shared__ int2 s_pr[FT_CAP];
+    __shared__ int32_t s_cp[FT_COLS + 1];
+    const unsigned lane = lane_id();
+    const int w = threadIdx.x >> 5;
+    const long long c0 = (long long)blockIdx.x * FT_COLS;
+    const int nc = (int)min((long long)FT_COLS, (long long)n_cols - c0);
+    for (int i = threadIdx.x; i <= nc; i += FT_THREADS) s_cp[i] = cp[c0 + i];
+    __syncthreads();
+    const int e0 = s_cp[0], e1 = s_cp[nc];
+    const bool staged = (e1 - e0) <= FT_CAP;
+    if (staged)
+        for (int q = e0 + (int)threadIdx.x; q < e1; q += FT_THREADS) s_pr[q - e0] = __ldcs(pairs + q);
+    __syncthreads();
+    for (int j = w; j < nc; j += FT_THREADS / 32) {
+        const int p0 = s_cp[j], p1 = s_cp[j + 1];
         const int len = p1 - p0;
-        if (len <= 0 || len > 32) continue;  // warp-uniform
+        if (len <= 0) continue;
+        if (len > 32) {
+            if (staged)
+                for (int q = p0 + (int)lane; q < p1; q += 32) s_pr[q - e0].x = -1;
+            continue;
+        }
         int key = INT_MAX, row = 0;
         if ((int)lane < len) {
-            const int2 q = __ldcs(pairs + p0 + lane);
+            const int2 q = staged ? s_pr[p0 - e0 + lane] : pairs[p0 + lane];
             key = q.x;
             row = q.y;
         }
         const int nxt = __shfl_down_sync(0xffffffffu, key, 1);
-        const bool unsorted = __any_sync(0xffffffffu, (int)lane + 1 < len && key > nxt);
-        if (unsorted) {
-#pragma unroll
-            for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-                for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    const int ok = __shfl_xor_sync(0xffffffffu, key, stride);
-                    const int orow = __shfl_xor_sync(0xffffffffu, row, stride);
-                    const bool asc = (lane & size) == 0;
-                    const bool lower = (lane & stride) == 0;
-                    const bool take = (lower == asc) ? (ok < key) : (ok > key);
-                    if (take) { key = ok; row = orow; }
-                }
+        if (__any_sync(0xffffffffu, (int)lane + 1 < len && key > nxt)) warp_sort_pairs(key, row);
+        if ((int)lane < len) {
+            if (staged) {
+                s_pr[p0 - e0 + lane] = make_int2(key, row);
+            } else {
+                __stcs(trow + p0 + lane, row);
+                __stcs(tval + p0 + lane, __ldg(val + key));
             }
         }
-        if ((int)lane < len) {
-            __stcs(trow + p0 + lane, row);
-            __stcs(tval + p0 + lane, __ldg(val + key));
+    }
+    __syncthreads();
+    if (!staged) return;
+    for (int q0 = e0 + (int)threadIdx.x; q0 < e1; q0 += 4 * FT_THREADS) {
+        int2 pr[4];
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * FT_THREADS;
+            pr[u] = (q < e1) ? s_pr[q - e0] : make_int2(-1, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = (pr[u].x >= 0) ? __ldg(val + pr[u].x) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * FT_THREADS;
+            if (pr[u].x >= 0) {
+                __stcs(trow + q, pr[u].y);
+                __stcs(tval + q, v[u]);
+            }
         }
     }
 }
@@ -431,26 +485,21 @@ __global__ void __launch_bounds__(FIX_THREADS) k_fixup_block(
 }
 
 cudaError_t launch_col_fixup(const int32_t *cp, int32_t n_cols, const int32_t *irp, int32_t n_rows,
-                             const double *val, const int2 *pairs, const int32_t *long_list,
-                             int32_t n_long_host, int32_t max_len_host, int32_t *keys_tmp, int32_t *keys_tmp2,
-                             int32_t *trow, double *tval, cudaStream_t s) {
-    (void)n_long_host; (void)max_len_host; (void)keys_tmp2;
+                             const double *val, int2 *pairs, const int32_t *long_list, int32_t *keys_tmp,
+                             int32_t *trow, double *tval, int *status, cudaStream_t s) {
+    (void)status;
     if (n_cols <= 0) return cudaSuccess;
     {
-        unsigned grid = ceil_div_u(n_cols, 8);
-        const unsigned cap = (unsigned)sm_count() * 16u;
-        if (grid > cap) grid = cap;
-        KernelScope ks("col_fixup_warp", s);
-        k_fixup_warp<<<grid, 256, 0, s>>>(cp, n_cols, val, pairs, trow, tval);
+        KernelScope ks("col_fixup_tiles", s);
+        k_fixup_tiles<<<ceil_div_u(n_cols, FT_COLS), FT_THREADS, 0, s>>>(cp, n_cols, val, pairs, trow, tval);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     {
-        // long_list is followed by its device-side count (see api.cu)
         const int32_t *long_count = long_list - 1;
         KernelScope ks("col_fixup_block", s);
-        k_fixup_block<<<(unsigned)sm_count() * 2u, FIX_THREADS, 0, s>>>(
-            cp, irp, n_rows, val, const_cast<int2 *>(pairs), long_list, long_count, keys_tmp, trow, tval);
+        k_fixup_block<<<(unsigned)sm_count() * 2u, FIX_THREADS, 0, s>>>(cp, irp, n_rows, val, pairs, long_list,
+                                                                         long_count, keys_tmp, trow, tval);
     }
     return cudaGetLastError();
 }

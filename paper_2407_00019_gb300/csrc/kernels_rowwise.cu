@@ -12,11 +12,15 @@
 #include <climits>
 
 #include "common.cuh"
+#include "stage_pipe.cuh"
 
 namespace spmvat {
 
 // ---------------------------------------------------------------- analyze
+// One pass: each thread takes AN_ITEMS consecutive rows (one 16-byte load of
+// IRP plus the next pointer), so all loads of a warp are in flight at once.
 constexpr int AN_THREADS = 256;
+constexpr int AN_ITEMS = 4;
 
 __global__ void __launch_bounds__(AN_THREADS) k_analyze(const int32_t *__restrict__ irp, int32_t n, int64_t nnz,
                                                          AnalyzeAcc *acc) {
@@ -25,25 +29,40 @@ __global__ void __launch_bounds__(AN_THREADS) k_analyze(const int32_t *__restric
     __shared__ int s_mm[AN_THREADS / 32][3];
     if (threadIdx.x < 32) s_hist[threadIdx.x] = 0ull;
     __syncthreads();
+    const long long i0 = ((long long)blockIdx.x * AN_THREADS + threadIdx.x) * AN_ITEMS;
+    int p[AN_ITEMS + 1];
+    if (i0 + AN_ITEMS <= n && ((reinterpret_cast<uintptr_t>(irp + i0) & 15) == 0)) {
+        const int4 q = *reinterpret_cast<const int4 *>(irp + i0);
+        p[0] = q.x; p[1] = q.y; p[2] = q.z; p[3] = q.w;
+        p[4] = irp[i0 + 4];
+    } else {
+#pragma unroll
+        for (int j = 0; j <= AN_ITEMS; ++j) p[j] = (i0 + j <= n) ? irp[i0 + j] : 0;
+    }
     unsigned long long sl = 0, sl2 = 0, ne = 0;
     int mx = 0, inv_mn = 0, bad = 0;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        int a = irp[i], b = irp[i + 1];
-        int len = b - a;
-        if (len < 0 || a < 0 || (long long)b > nnz) { bad = 1; len = len < 0 ? 0 : len; }
-        if (i == 0 && a != 0) bad = 1;
-        if (i == n - 1 && (long long)b != nnz) bad = 1;
-        sl += (unsigned)len;
-        sl2 += (unsigned long long)len * (unsigned long long)len;
-        ne += (len == 0);
-        mx = max(mx, len);
-        inv_mn = max(inv_mn, INT_MAX - len);
-        int cls = (len == 0) ? 0 : 32 - __clz(len);
-        unsigned act = __activemask();
-        unsigned peers = __match_any_sync(act, cls);
-        if ((lanemask_lt() & peers) == 0) atomicAdd(&s_hist[cls], (unsigned long long)__popc(peers));
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int j = 0; j < AN_ITEMS; ++j) {
+        const long long i = i0 + j;
+        const bool has = i < n;
+        int len = 0;
+        if (has) {
+            len = p[j + 1] - p[j];
+            if (len < 0 || p[j] < 0 || (long long)p[j + 1] > nnz) { bad = 1; len = len < 0 ? 0 : len; }
+            if (i == 0 && p[0] != 0) bad = 1;
+            if (i == n - 1 && (long long)p[j + 1] != nnz) bad = 1;
+            sl += (unsigned)len;
+            sl2 += (unsigned long long)len * (unsigned long long)len;
+            ne += (len == 0);
+            mx = max(mx, len);
+            inv_mn = max(inv_mn, INT_MAX - len);
+        }
+        const int cls = has ? ((len == 0) ? 0 : 32 - __clz(len)) : 32;
+        const unsigned peers = __match_any_sync(0xffffffffu, cls);
+        if (has && (lanemask_lt() & peers) == 0) atomicAdd(&s_hist[cls], (unsigned long long)__popc(peers));
     }
+    (void)lane;
     sl = warp_sum(sl);
     sl2 = warp_sum(sl2);
     ne = warp_sum(ne);
@@ -75,10 +94,7 @@ __global__ void __launch_bounds__(AN_THREADS) k_analyze(const int32_t *__restric
 }
 
 cudaError_t launch_analyze(const int32_t *irp, int32_t n_rows, int64_t nnz, AnalyzeAcc *acc, cudaStream_t s) {
-    unsigned grid = ceil_div_u(n_rows, AN_THREADS);
-    unsigned cap = (unsigned)sm_count() * 8u;
-    if (grid > cap) grid = cap;
-    if (grid == 0) grid = 1;
+    const unsigned grid = ceil_div_u(n_rows, (long long)AN_THREADS * AN_ITEMS);
     KernelScope ks("analyze", s);
     k_analyze<<<grid, AN_THREADS, 0, s>>>(irp, n_rows, nnz, acc);
     return cudaGetLastError();
@@ -104,29 +120,45 @@ cudaError_t launch_validate_idx(const int32_t *idx, int64_t n, int32_t bound, in
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------- tile lines
+// out[t] = the line holding entry t*tile (largest i with ptr[i] <= t*tile),
+// one thread per tile: the searches run in parallel instead of serially at
+// the start of every CTA of the consumer.
+__global__ void __launch_bounds__(256) k_tile_lines(const int32_t *__restrict__ ptr, int32_t n_lines, int tile,
+                                                     long long n_tiles, int32_t *__restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_tiles) out[t] = last_le(ptr, 0, n_lines, t * (long long)tile);
+}
+
+size_t tile_lines_bytes(int64_t nnz, int tile) { return (size_t)((nnz + tile - 1) / tile + 1) * 4; }
+
+cudaError_t launch_tile_lines(const int32_t *ptr, int32_t n_lines, int64_t nnz, int tile, int32_t *out,
+                              cudaStream_t s) {
+    const long long n_tiles = (nnz + tile - 1) / tile;
+    if (n_tiles <= 0) return cudaSuccess;
+    KernelScope ks("tile_lines", s);
+    k_tile_lines<<<ceil_div_u(n_tiles, 256), 256, 0, s>>>(ptr, n_lines, tile, n_tiles, out);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ expand
 // Tile of EXP_TILE consecutive entries; each thread writes EXP_ITEMS of them
 // with one 16-byte store. The pointers of the lines that cover the tile are
-// staged in shared memory when they fit, and each thread finds its first
-// line by binary search there, then walks forward.
+// staged in shared memory when they fit; each thread finds its first line by
+// binary search there and walks forward.
 constexpr int EXP_THREADS = 256;
 constexpr int EXP_ITEMS = 4;
 constexpr int EXP_TILE = EXP_THREADS * EXP_ITEMS;
 constexpr int EXP_WIN = 2048;
 
 __global__ void __launch_bounds__(EXP_THREADS) k_expand(const int32_t *__restrict__ ptr, int32_t n_lines, int64_t nnz,
+                                                         const int32_t *__restrict__ tl, long long n_tiles,
                                                          int32_t *__restrict__ out) {
     __shared__ int32_t s_ptr[EXP_WIN];
-    __shared__ int s_lo, s_hi;
     const long long k0 = (long long)blockIdx.x * EXP_TILE;
     const long long k1 = min(k0 + (long long)EXP_TILE, (long long)nnz);
-    if (threadIdx.x == 0) {
-        int lo = last_le(ptr, 0, n_lines, k0);
-        s_lo = lo;
-        s_hi = last_le(ptr, lo, n_lines, k1 - 1);
-    }
-    __syncthreads();
-    const int lo = s_lo, hi = s_hi;
+    const int lo = tl[blockIdx.x];
+    const int hi = (blockIdx.x + 1 < n_tiles) ? tl[blockIdx.x + 1] : n_lines - 1;
     const int wn = hi - lo + 2;  // ptr[lo .. hi+1]
     const bool sm = wn <= EXP_WIN;
     if (sm)
@@ -145,7 +177,7 @@ __global__ void __launch_bounds__(EXP_THREADS) k_expand(const int32_t *__restric
         v[j] = line;
     }
     if (k + EXP_ITEMS <= k1 && ((reinterpret_cast<uintptr_t>(out + k) & 15) == 0)) {
-        *reinterpret_cast<int4 *>(out + k) = make_int4(v[0], v[1], v[2], v[3]);
+        __stcs(reinterpret_cast<int4 *>(out + k), make_int4(v[0], v[1], v[2], v[3]));
     } else {
 #pragma unroll
         for (int j = 0; j < EXP_ITEMS; ++j)
@@ -153,34 +185,30 @@ __global__ void __launch_bounds__(EXP_THREADS) k_expand(const int32_t *__restric
     }
 }
 
-cudaError_t launch_expand(const int32_t *ptr, int32_t n_lines, int64_t nnz, int32_t *out, cudaStream_t s,
-                          const char *name) {
+size_t expand_scratch_bytes(int64_t nnz) { return tile_lines_bytes(nnz, EXP_TILE); }
+
+cudaError_t launch_expand(const int32_t *ptr, int32_t n_lines, int64_t nnz, int32_t *out, int32_t *scratch,
+                          cudaStream_t s, const char *name) {
     if (nnz <= 0) return cudaSuccess;
+    cudaError_t e = launch_tile_lines(ptr, n_lines, nnz, EXP_TILE, scratch, s);
+    if (e != cudaSuccess) return e;
+    const long long n_tiles = (nnz + EXP_TILE - 1) / EXP_TILE;
     KernelScope ks(name, s);
-    k_expand<<<ceil_div_u(nnz, EXP_TILE), EXP_THREADS, 0, s>>>(ptr, n_lines, nnz, out);
+    k_expand<<<(unsigned)n_tiles, EXP_THREADS, 0, s>>>(ptr, n_lines, nnz, scratch, n_tiles, out);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ lines -> ELL
-// Persistent CTAs walk tiles of ELL_LINES consecutive lines. For each tile
-// one thread issues two TMA bulk copies (values and indices of the tile's
-// entries, the 16-byte-aligned interior of the range) into one of two shared
-// stages, so the copy of tile t+grid overlaps the write-out of tile t. The
-// write-out stores slot k of line i at k*ld + i: for a fixed k a warp writes
-// 32 consecutive lines (fully coalesced). Entries outside the staged interior
-// (at most one value and three indices per tile edge), and whole tiles whose
-// entries exceed a stage, are read from global memory instead.
+// Persistent CTAs walk tiles of ELL_LINES consecutive lines through the
+// two-stage TMA pipeline (stage_pipe.cuh): the tile's values and indices
+// arrive in shared memory while the previous tile is written out. Slot k of
+// line i goes to k*ld + i: for a fixed k a warp writes 32 consecutive lines
+// (coalesced, streaming stores). Two threads per line take alternate slots.
 constexpr int ELL_LINES = 128;
-constexpr int ELL_SPLIT = 2;  // threads per line (they take alternate slots)
+constexpr int ELL_SPLIT = 2;
 constexpr int ELL_THREADS = ELL_LINES * ELL_SPLIT;
 constexpr int ELL_STAGE_CAP = 4096;  // entries per stage (48 KB)
-constexpr size_t ELL_SMEM = 128 + 2 * (size_t)ELL_STAGE_CAP * 12;
-
-struct EllMeta {
-    long long a0v, b0v, a0i, b0i;
-    int staged;
-    int pad;
-};
+using EllPipe = StagePipe<ELL_STAGE_CAP, true>;
 
 template <bool FUSED>
 __global__ void __launch_bounds__(ELL_THREADS) k_lines_to_ell(
@@ -189,78 +217,20 @@ __global__ void __launch_bounds__(ELL_THREADS) k_lines_to_ell(
     double *__restrict__ eval, int32_t *__restrict__ eidx, const double *__restrict__ x, double *__restrict__ y,
     int *status) {
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    EllMeta *meta = reinterpret_cast<EllMeta *>(smem + 16);
-    double *sval0 = reinterpret_cast<double *>(smem + 128);
-    int32_t *sidx0 = reinterpret_cast<int32_t *>(smem + 128 + (size_t)ELL_STAGE_CAP * 8);
-    double *sval1 = reinterpret_cast<double *>(smem + 128 + (size_t)ELL_STAGE_CAP * 12);
-    int32_t *sidx1 = reinterpret_cast<int32_t *>(smem + 128 + (size_t)ELL_STAGE_CAP * 20);
     __shared__ double s_acc[ELL_LINES];
-
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-
-    auto issue = [&](int tile, int st) {
-        const long long l0 = (long long)tile * ELL_LINES;
-        EllMeta m;
-        long long e0 = 0, e1 = 0;
-        if (l0 < n_lines) {
-            const long long l1 = min(l0 + (long long)ELL_LINES, (long long)n_lines);
-            e0 = ptr[l0];
-            e1 = ptr[l1];
-            if (e1 < e0) e1 = e0;
-        }
-        m.a0v = e0 & ~1ll;
-        m.b0v = max(m.a0v, e1 & ~1ll);
-        m.a0i = e0 & ~3ll;
-        m.b0i = max(m.a0i, e1 & ~3ll);
-        const unsigned bv = (unsigned)((m.b0v - m.a0v) * 8), bi = (unsigned)((m.b0i - m.a0i) * 4);
-        m.staged = can_stage && (m.b0v - m.a0v) <= ELL_STAGE_CAP && (m.b0i - m.a0i) <= ELL_STAGE_CAP &&
-                   (bv + bi) > 0;
-        m.pad = 0;
-        meta[st] = m;
-        if (m.staged) {
-            mbar_arrive_expect_tx(&bar[st], bv + bi);
-            if (bv) bulk_g2s(st ? (void *)sval1 : (void *)sval0, val + m.a0v, bv, &bar[st]);
-            if (bi) bulk_g2s(st ? (void *)sidx1 : (void *)sidx0, idx + m.a0i, bi, &bar[st]);
-        } else {
-            mbar_arrive_expect_tx(&bar[st], 0);
-        }
-    };
-
-    int it = 0;
-    if (threadIdx.x == 0 && (int)blockIdx.x < n_tiles) issue(blockIdx.x, 0);
+    EllPipe P;
+    P.setup(smem);
     const int lt = threadIdx.x % ELL_LINES;
     const int part = threadIdx.x / ELL_LINES;
     int bad = 0;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
-        const int st = it & 1;
-        const int next = tile + gridDim.x;
-        if (threadIdx.x == 0 && next < n_tiles) issue(next, st ^ 1);
-        const bool ok = mbar_wait_bounded(&bar[st], (unsigned)((it >> 1) & 1), kSpinLimit);
-        if (__syncthreads_or(!ok)) {
-            // Give up, but do not leave a copy in flight into the shared
-            // memory of an exiting CTA: wait (bounded) for both stages.
-            if (threadIdx.x == 0) {
-                atomicOr(status, ST_TIMEOUT);
-                mbar_wait_bounded(&bar[st], (unsigned)((it >> 1) & 1), kSpinLimit);
-                if (next < n_tiles) mbar_wait_bounded(&bar[st ^ 1], (unsigned)(((it + 1) >> 1) & 1), kSpinLimit);
-            }
-            break;
-        }
-        const EllMeta m = meta[st];
-        const double *sv = st ? sval1 : sval0;
-        const int32_t *si = st ? sidx1 : sidx0;
-        auto VAL = [&](long long k) -> double {
-            return (m.staged && k >= m.a0v && k < m.b0v) ? sv[k - m.a0v] : val[k];
-        };
-        auto IDX = [&](long long k) -> int32_t {
-            return (m.staged && k >= m.a0i && k < m.b0i) ? si[k - m.a0i] : idx[k];
-        };
+    auto range = [&](int tile, long long *e0, long long *e1) {
+        const long long l0 = (long long)tile * ELL_LINES;
+        if (l0 >= n_lines) { *e0 = *e1 = 0; return; }
+        const long long l1 = min(l0 + (long long)ELL_LINES, (long long)n_lines);
+        *e0 = ptr[l0];
+        *e1 = ptr[l1];
+    };
+    auto body = [&](int tile, int st, const StageMeta &m) {
         const long long l = (long long)tile * ELL_LINES + lt;
         double acc = 0.0;
         if (l < ld) {
@@ -268,14 +238,14 @@ __global__ void __launch_bounds__(ELL_THREADS) k_lines_to_ell(
                 const long long s = ptr[l], e = ptr[l + 1];
                 int len = (int)(e - s);
                 if (len < 0 || len > width) { bad = 1; len = len < 0 ? 0 : width; }
-                int last = len > 0 ? IDX(s + len - 1) : 0;
+                int last = len > 0 ? P.idx_at(m, st, idx, s + len - 1) : 0;
                 if ((unsigned)last >= (unsigned)idx_bound) { bad = 1; last = 0; }
                 for (int k = part; k < width; k += ELL_SPLIT) {
                     double v;
                     int32_t c;
                     if (k < len) {
-                        v = VAL(s + k);
-                        c = IDX(s + k);
+                        v = P.val_at(m, st, val, s + k);
+                        c = P.idx_at(m, st, idx, s + k);
                         if ((unsigned)c >= (unsigned)idx_bound) { bad = 1; c = 0; }
                         if (FUSED) acc = fma(v, __ldg(x + c), acc);
                     } else {
@@ -297,8 +267,8 @@ __global__ void __launch_bounds__(ELL_THREADS) k_lines_to_ell(
             __syncthreads();
             if (part == 0 && l < n_lines) y[l] = acc + s_acc[lt];
         }
-        __syncthreads();
-    }
+    };
+    pipe_tiles(P, n_tiles, val, idx, can_stage != 0, status, range, body);
     if (bad) atomicOr(status, ST_BAD_INDEX);
 }
 
@@ -309,30 +279,20 @@ cudaError_t launch_lines_to_ell(const int32_t *ptr, const int32_t *idx, const do
     const int n_tiles = (int)ceil_div_u(ld, ELL_LINES);
     const int can_stage = ((reinterpret_cast<uintptr_t>(val) & 15) == 0) &&
                           ((reinterpret_cast<uintptr_t>(idx) & 15) == 0);
-    static bool attr_set[64][2];
-    int dev = 0;
-    cudaGetDevice(&dev);
-    dev &= 63;
     const bool fused = (y != nullptr);
-    if (!attr_set[dev][fused]) {
-        cudaError_t e = fused ? cudaFuncSetAttribute(k_lines_to_ell<true>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ELL_SMEM)
-                              : cudaFuncSetAttribute(k_lines_to_ell<false>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ELL_SMEM);
-        if (e != cudaSuccess) return e;
-        attr_set[dev][fused] = true;
-    }
+    cudaError_t e = fused ? set_smem_attr(k_lines_to_ell<true>, EllPipe::kSmem)
+                          : set_smem_attr(k_lines_to_ell<false>, EllPipe::kSmem);
+    if (e != cudaSuccess) return e;
     int grid = sm_count() * 2;
     if (grid > n_tiles) grid = n_tiles;
     if (fused) {
         KernelScope ks("crs_to_ell_row_fused_spmv", s);
-        k_lines_to_ell<true><<<grid, ELL_THREADS, ELL_SMEM, s>>>(ptr, idx, val, n_lines, idx_bound, width, ld,
-                                                                 n_tiles, can_stage, eval, eidx, x, y, status);
+        k_lines_to_ell<true><<<grid, ELL_THREADS, EllPipe::kSmem, s>>>(
+            ptr, idx, val, n_lines, idx_bound, width, ld, n_tiles, can_stage, eval, eidx, x, y, status);
     } else {
         KernelScope ks(name, s);
-        k_lines_to_ell<false><<<grid, ELL_THREADS, ELL_SMEM, s>>>(ptr, idx, val, n_lines, idx_bound, width, ld,
-                                                                  n_tiles, can_stage, eval, eidx, nullptr,
-                                                                  nullptr, status);
+        k_lines_to_ell<false><<<grid, ELL_THREADS, EllPipe::kSmem, s>>>(
+            ptr, idx, val, n_lines, idx_bound, width, ld, n_tiles, can_stage, eval, eidx, nullptr, nullptr, status);
     }
     return cudaGetLastError();
 }

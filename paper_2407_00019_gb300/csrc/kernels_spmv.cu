@@ -17,6 +17,7 @@
 #include <climits>
 
 #include "common.cuh"
+#include "stage_pipe.cuh"
 
 namespace spmvat {
 
@@ -75,6 +76,174 @@ cudaError_t launch_spmv_crs_vector(int v, const int32_t *irp, const int32_t *ico
         SPMV_CASE(16)
         SPMV_CASE(32)
 #undef SPMV_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// Rows staged by TMA: persistent CTAs take tiles of LINES consecutive rows;
+// the tile's VAL / ICOL range arrives in shared memory through the two-stage
+// bulk-copy pipeline while the previous tile is multiplied. S lanes per row
+// sum strided entries in order; a fixed shuffle tree combines them.
+constexpr int CRS_STAGE_CAP = 4096;
+using CrsPipe = StagePipe<CRS_STAGE_CAP, true>;
+
+template <int S>
+__global__ void __launch_bounds__(256) k_spmv_crs_stream(const int32_t *__restrict__ irp,
+                                                          const int32_t *__restrict__ icol,
+                                                          const double *__restrict__ val, int32_t n_rows,
+                                                          int n_tiles, int can_stage, const double *__restrict__ x,
+                                                          double *__restrict__ y, int *status) {
+    constexpr int LINES = 256 / S;
+    extern __shared__ __align__(128) unsigned char smem[];
+    CrsPipe P;
+    P.setup(smem);
+    const int lt = threadIdx.x / S, sub = threadIdx.x % S;
+    auto range = [&](int tile, long long *e0, long long *e1) {
+        const long long r0 = (long long)tile * LINES;
+        const long long r1 = min(r0 + LINES, (long long)n_rows);
+        *e0 = irp[r0];
+        *e1 = irp[r1];
+    };
+    auto body = [&](int tile, int st, const StageMeta &m) {
+        const long long r = (long long)tile * LINES + lt;
+        double acc = 0.0;
+        if (r < n_rows) {
+            const int s = irp[r], e = irp[r + 1];
+            if (m.staged && s >= m.a0v && e <= m.b0v && s >= m.a0i && e <= m.b0i) {
+                const double *sv = P.sval(st);
+                const int32_t *si = P.sidx(st);
+                const int ov = (int)(s - m.a0v), oi = (int)(s - m.a0i);
+                const int len = e - s;
+                for (int k = sub; k < len; k += S) acc = fma(sv[ov + k], __ldg(x + si[oi + k]), acc);
+            } else {
+                for (int k = s + sub; k < e; k += S)
+                    acc = fma(P.val_at(m, st, val, k), __ldg(x + P.idx_at(m, st, icol, k)), acc);
+            }
+        }
+#pragma unroll
+        for (int o = S / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, S);
+        if (sub == 0 && r < n_rows) y[r] = acc;
+    };
+    pipe_tiles(P, n_tiles, val, icol, can_stage != 0, status, range, body);
+}
+
+size_t crs_stream_smem_bytes() { return CrsPipe::kSmem; }
+
+cudaError_t launch_spmv_crs_stream(int S, const int32_t *irp, const int32_t *icol, const double *val,
+                                   int32_t n_rows, const double *x, double *y, int *status, cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    const int lines = 256 / S;
+    const int n_tiles = (int)ceil_div_u(n_rows, lines);
+    const int can_stage = ((reinterpret_cast<uintptr_t>(val) & 15) == 0) &&
+                          ((reinterpret_cast<uintptr_t>(icol) & 15) == 0);
+    int grid = sm_count() * 2;
+    if (grid > n_tiles) grid = n_tiles;
+    switch (S) {
+#define STREAM_CASE(SS)                                                                                  \
+    case SS: {                                                                                           \
+        cudaError_t e = set_smem_attr(k_spmv_crs_stream<SS>, CrsPipe::kSmem);                            \
+        if (e != cudaSuccess) return e;                                                                  \
+        KernelScope ks("spmv_crs_stream_s" #SS, s);                                                      \
+        k_spmv_crs_stream<SS><<<grid, 256, CrsPipe::kSmem, s>>>(irp, icol, val, n_rows, n_tiles, can_stage, x, \
+                                                                 y, status);                            \
+        break;                                                                                           \
+    }
+        STREAM_CASE(1)
+        STREAM_CASE(2)
+        STREAM_CASE(4)
+        STREAM_CASE(8)
+#undef STREAM_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// Rows in tiles, many CTAs per SM: a CTA takes 256/S consecutive rows. Phase
+// A: all threads stride over the tile's entries with coalesced loads of VAL
+// and ICOL and gather x, eight entries in flight per thread, into shared
+// memory. Phase B: S lanes per row accumulate VAL * x with FMA in storage
+// order (lane-strided), and a fixed shuffle tree combines them. The product
+// needs one FP64 FMA per entry, as the row-wise loop does.
+constexpr int CRS_TILE_CAP = 2048;
+
+template <int S>
+__global__ void __launch_bounds__(256) k_spmv_crs_tile(const int32_t *__restrict__ irp,
+                                                        const int32_t *__restrict__ icol,
+                                                        const double *__restrict__ val, int32_t n_rows,
+                                                        const double *__restrict__ x, double *__restrict__ y) {
+    constexpr int ROWS = 256 / S;
+    __shared__ double s_v[CRS_TILE_CAP];
+    __shared__ double s_x[CRS_TILE_CAP];
+    __shared__ int32_t s_ptr[ROWS + 1];
+    const long long r0 = (long long)blockIdx.x * ROWS;
+    const int nr = (int)min((long long)ROWS, (long long)n_rows - r0);
+    // the tile's entry range, read by every thread (broadcast), so the entry
+    // loads start without waiting for the row window below
+    const int e0 = __ldg(irp + r0), e1 = __ldg(irp + r0 + nr);
+    const int n = e1 - e0;
+    const bool staged = n <= CRS_TILE_CAP;
+    for (int i = threadIdx.x; i <= nr; i += 256) s_ptr[i] = irp[r0 + i];
+    if (staged) {
+        for (int q0 = threadIdx.x; q0 < n; q0 += 8 * 256) {
+            double v[8];
+            int c[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int q = q0 + u * 256;
+                v[u] = (q < n) ? __ldcs(val + e0 + q) : 0.0;
+                c[u] = (q < n) ? __ldcs(icol + e0 + q) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int q = q0 + u * 256;
+                if (q < n) {
+                    s_v[q] = v[u];
+                    s_x[q] = __ldg(x + c[u]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int lt = threadIdx.x / S, sub = threadIdx.x % S;
+    double acc = 0.0;
+    if (lt < nr) {
+        const int s = s_ptr[lt] - e0, e = s_ptr[lt + 1] - e0;
+        if (staged) {
+            for (int q = s + sub; q < e; q += S) acc = fma(s_v[q], s_x[q], acc);
+        } else {
+            for (int k = e0 + s + sub; k < e0 + e; k += S) acc = fma(__ldcs(val + k), __ldg(x + __ldcs(icol + k)), acc);
+        }
+    }
+#pragma unroll
+    for (int o = S / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, S);
+    if (sub == 0 && lt < nr) y[r0 + lt] = acc;
+}
+
+int crs_tile_lanes(int max_row_len) {
+    for (int S = 1; S <= 8; S <<= 1)
+        if ((long long)(256 / S) * max_row_len <= CRS_TILE_CAP) return S;
+    return 0;  // a tile of 32 rows would not fit: use another schedule
+}
+
+cudaError_t launch_spmv_crs_tile(int S, const int32_t *irp, const int32_t *icol, const double *val,
+                                 int32_t n_rows, const double *x, double *y, cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    const unsigned grid = ceil_div_u(n_rows, 256 / S);
+    switch (S) {
+#define TILE_CASE(SS)                                                                \
+    case SS: {                                                                       \
+        KernelScope ks("spmv_crs_tile_s" #SS, s);                                    \
+        k_spmv_crs_tile<SS><<<grid, 256, 0, s>>>(irp, icol, val, n_rows, x, y);      \
+        break;                                                                       \
+    }
+        TILE_CASE(1)
+        TILE_CASE(2)
+        TILE_CASE(4)
+        TILE_CASE(8)
+#undef TILE_CASE
         default:
             return cudaErrorInvalidValue;
     }
@@ -341,71 +510,79 @@ __device__ __forceinline__ SegPair seg_combine(SegPair a, SegPair b) {
     return r;
 }
 
+// Phase A: striped, coalesced loads of IROW / ICOL / VAL and the x gathers,
+// eight in flight per thread, into shared memory padded by one slot per
+// COO_ITEMS (blocked reads below are then bank-conflict free). Phase B: each
+// thread reduces its COO_ITEMS consecutive entries with an FMA chain per row
+// segment; a block segmented scan carries partial rows between threads.
+__device__ __forceinline__ int coo_pad(int q) { return q + q / COO_ITEMS; }
+
 __global__ void __launch_bounds__(COO_THREADS) k_coo_row_tiles(const int32_t *__restrict__ irow,
                                                                 const int32_t *__restrict__ icol,
                                                                 const double *__restrict__ val, int64_t nnz,
                                                                 int32_t n_rows, int32_t n_cols,
                                                                 const double *__restrict__ x,
                                                                 double *__restrict__ y, double2 *__restrict__ carry) {
-    __shared__ int s_ra, s_cin;
+    constexpr int PADDED = COO_TILE + COO_TILE / COO_ITEMS;
+    __shared__ double s_v[PADDED];
+    __shared__ double s_x[PADDED];
+    __shared__ int32_t s_r[PADDED];
     __shared__ SegPair s_w[COO_THREADS / 32];
     const long long t0 = (long long)blockIdx.x * COO_TILE;
     const long long t1 = min(t0 + (long long)COO_TILE, (long long)nnz);
-    if (threadIdx.x == 0) {
-        s_ra = irow[t0];
-        s_cin = (t0 > 0) && irow[t0 - 1] == s_ra;
-    }
-    const long long k = t0 + (long long)threadIdx.x * COO_ITEMS;
-    const int m = (int)max(0ll, min((long long)COO_ITEMS, t1 - k));
-    int r[COO_ITEMS], c[COO_ITEMS];
-    double v[COO_ITEMS];
-    if (m == COO_ITEMS && ((reinterpret_cast<uintptr_t>(irow + k) & 15) == 0) &&
-        ((reinterpret_cast<uintptr_t>(icol + k) & 15) == 0) && ((reinterpret_cast<uintptr_t>(val + k) & 15) == 0)) {
-        const int4 *pr = reinterpret_cast<const int4 *>(irow + k);
-        const int4 *pc = reinterpret_cast<const int4 *>(icol + k);
-        const double2 *pv = reinterpret_cast<const double2 *>(val + k);
+    const int nt = (int)(t1 - t0);
+    // tile edges: the row of the entry before and after the tile
+    const int ra = __ldg(irow + t0);
+    const bool cin = (t0 > 0) && __ldg(irow + t0 - 1) == ra;
+    {
+        int r[COO_ITEMS], c[COO_ITEMS];
+        double v[COO_ITEMS];
 #pragma unroll
-        for (int q = 0; q < COO_ITEMS / 4; ++q) {
-            const int4 a = __ldcs(pr + q), b = __ldcs(pc + q);
-            r[4 * q] = a.x; r[4 * q + 1] = a.y; r[4 * q + 2] = a.z; r[4 * q + 3] = a.w;
-            c[4 * q] = b.x; c[4 * q + 1] = b.y; c[4 * q + 2] = b.z; c[4 * q + 3] = b.w;
+        for (int u = 0; u < COO_ITEMS; ++u) {
+            const int q = u * COO_THREADS + threadIdx.x;
+            const bool h = q < nt;
+            r[u] = h ? __ldcs(irow + t0 + q) : 0;
+            c[u] = h ? __ldcs(icol + t0 + q) : 0;
+            v[u] = h ? __ldcs(val + t0 + q) : 0.0;
         }
 #pragma unroll
-        for (int q = 0; q < COO_ITEMS / 2; ++q) {
-            const double2 a = __ldcs(pv + q);
-            v[2 * q] = a.x; v[2 * q + 1] = a.y;
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < COO_ITEMS; ++j) {
-            r[j] = (j < m) ? irow[k + j] : 0;
-            c[j] = (j < m) ? icol[k + j] : 0;
-            v[j] = (j < m) ? val[k + j] : 0.0;
+        for (int u = 0; u < COO_ITEMS; ++u) {
+            const int q = u * COO_THREADS + threadIdx.x;
+            if (q < nt) {
+                const bool okc = (unsigned)c[u] < (unsigned)n_cols;
+                s_r[coo_pad(q)] = r[u];
+                s_v[coo_pad(q)] = okc ? v[u] : 0.0;
+                s_x[coo_pad(q)] = okc ? __ldg(x + c[u]) : 0.0;
+            }
         }
     }
-    // products (FMA chain per row segment below keeps storage order)
-    const int prev_row = (m > 0 && k > 0) ? irow[k - 1] : -1;
-    const bool cont_prev = (m > 0) && (prev_row == r[0]);
-    // empty rows between the previous entry and my first one
+    __syncthreads();
+    const int qb = (int)threadIdx.x * COO_ITEMS;
+    const int m = max(0, min(COO_ITEMS, nt - qb));
+    const long long k = t0 + qb;
+    const int prev_row = (m > 0) ? ((qb > 0) ? s_r[coo_pad(qb - 1)] : (k > 0 ? __ldg(irow + k - 1) : -1)) : -1;
+    const long long after = k + m;
+    const int next_row = (m > 0 && after < nnz) ? ((after < t1) ? s_r[coo_pad(qb + m)] : __ldg(irow + after)) : -1;
+    const int r0 = (m > 0) ? s_r[coo_pad(qb)] : -1;
+    const bool cont_prev = (m > 0) && (prev_row == r0);
     if (m > 0)
-        for (int rr = prev_row + 1; rr < r[0] && rr < n_rows; ++rr) y[rr] = 0.0;
-    // local pass: sums of segments; middle segments are complete
+        for (int rr = prev_row + 1; rr < r0 && rr < n_rows; ++rr) y[rr] = 0.0;
     double first_part = 0.0, part = 0.0;
     int nseg = 1;
-    int cur = (m > 0) ? r[0] : -1;
+    int cur = r0;
 #pragma unroll
     for (int j = 0; j < COO_ITEMS; ++j) {
         if (j < m) {
-            if (r[j] != cur) {
+            const int rj = s_r[coo_pad(qb + j)];
+            if (rj != cur) {
                 if (nseg == 1) first_part = part;
                 else if ((unsigned)cur < (unsigned)n_rows) y[cur] = part;
-                for (int rr = cur + 1; rr < r[j] && rr < n_rows; ++rr) y[rr] = 0.0;
-                cur = r[j];
+                for (int rr = cur + 1; rr < rj && rr < n_rows; ++rr) y[rr] = 0.0;
+                cur = rj;
                 part = 0.0;
                 ++nseg;
             }
-            const int cj = ((unsigned)c[j] < (unsigned)n_cols) ? c[j] : -1;
-            if (cj >= 0) part = fma(v[j], __ldg(x + cj), part);
+            part = fma(s_v[coo_pad(qb + j)], s_x[coo_pad(qb + j)], part);
         }
     }
     // block segmented exclusive scan of (row-start flag, last-row partial)
@@ -434,19 +611,16 @@ __global__ void __launch_bounds__(COO_THREADS) k_coo_row_tiles(const int32_t *__
     for (int j = 0; j < w; ++j) wp = seg_combine(wp, s_w[j]);
     const SegPair carry_in = seg_combine(wp, ex);
     if (m == 0) return;
-    const int ra = s_ra;
-    const bool cin = s_cin;
     const double cin_v = cont_prev ? carry_in.v : 0.0;
     // first segment, if it ends inside this thread
     if (nseg > 1) {
         const double tot = first_part + cin_v;
-        if (r[0] == ra && cin) carry[blockIdx.x].x = tot;
-        else if ((unsigned)r[0] < (unsigned)n_rows) y[r[0]] = tot;
+        if (r0 == ra && cin) carry[blockIdx.x].x = tot;
+        else if ((unsigned)r0 < (unsigned)n_rows) y[r0] = tot;
     }
     // last segment
-    const long long after = k + m;
     const int lrow = cur;
-    const bool cont_next = (after < nnz) && irow[after] == lrow;
+    const bool cont_next = (after < nnz) && next_row == lrow;
     const double ltot = part + (nseg == 1 ? cin_v : 0.0);
     if (cont_next) {
         if (after >= t1) {  // continues into the next tile

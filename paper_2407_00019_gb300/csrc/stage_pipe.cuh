@@ -1,0 +1,125 @@
+// Two-stage TMA pipeline that copies a contiguous range of a float64 array
+// (and optionally the same range of an int32 array) into shared memory.
+//
+// One thread issues, for stage `st`, two 1-D bulk copies (cp.async.bulk) of
+// the 16-byte-aligned interior of the entry range [e0, e1); the few entries
+// outside it (at most one value and three indices per edge) and whole ranges
+// larger than a stage are read from global memory by the consumers. Stage
+// completion is an mbarrier with expected transaction bytes; every wait is
+// bounded. A CTA alternates stages, so the copy for its next tile runs while
+// it consumes the current one.
+#pragma once
+
+#include "common.cuh"
+
+namespace spmvat {
+
+struct StageMeta {
+    long long e0, e1;    // the entry range of the tile
+    long long a0v, b0v;  // staged value range [a0v, b0v)
+    long long a0i, b0i;  // staged index range [a0i, b0i)
+    int staged;
+    int pad;
+};
+
+template <int CAP, bool WITH_IDX>
+struct StagePipe {
+    static constexpr size_t kHeader = 128;
+    static constexpr size_t kStage = (size_t)CAP * 8 + (WITH_IDX ? (size_t)CAP * 4 : 0);
+    static constexpr size_t kSmem = kHeader + 2 * kStage;
+    static_assert(CAP % 4 == 0, "stage capacity must keep 16-byte alignment");
+
+    uint64_t *bar;
+    StageMeta *meta;
+    unsigned char *base;
+
+    __device__ void setup(unsigned char *smem) {
+        bar = reinterpret_cast<uint64_t *>(smem);
+        meta = reinterpret_cast<StageMeta *>(smem + 16);
+        base = smem + kHeader;
+        if (threadIdx.x == 0) {
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+    }
+    __device__ double *sval(int st) const { return reinterpret_cast<double *>(base + st * kStage); }
+    __device__ int32_t *sidx(int st) const {
+        return reinterpret_cast<int32_t *>(base + st * kStage + (size_t)CAP * 8);
+    }
+
+    // Thread 0 only. `can_stage`: both base pointers are 16-byte aligned.
+    __device__ void issue(int st, long long e0, long long e1, const double *val, const int32_t *idx,
+                          bool can_stage) {
+        StageMeta m;
+        if (e1 < e0) e1 = e0;
+        m.e0 = e0;
+        m.e1 = e1;
+        m.a0v = e0 & ~1ll;
+        m.b0v = max(m.a0v, e1 & ~1ll);
+        m.a0i = e0 & ~3ll;
+        m.b0i = WITH_IDX ? max(m.a0i, e1 & ~3ll) : m.a0i;
+        const unsigned bv = (unsigned)((m.b0v - m.a0v) * 8);
+        const unsigned bi = (unsigned)((m.b0i - m.a0i) * 4);
+        m.staged = can_stage && (m.b0v - m.a0v) <= CAP && (m.b0i - m.a0i) <= CAP && (bv + bi) > 0;
+        m.pad = 0;
+        meta[st] = m;
+        if (m.staged) {
+            mbar_arrive_expect_tx(&bar[st], bv + bi);
+            if (bv) bulk_g2s(sval(st), val + m.a0v, bv, &bar[st]);
+            if (WITH_IDX && bi) bulk_g2s(sidx(st), idx + m.a0i, bi, &bar[st]);
+        } else {
+            mbar_arrive_expect_tx(&bar[st], 0);
+        }
+    }
+
+    // All threads. `use` counts the previous waits on this stage.
+    __device__ bool wait(int st, int use) { return mbar_wait_bounded(&bar[st], (unsigned)(use & 1), kSpinLimit); }
+
+    __device__ __forceinline__ double val_at(const StageMeta &m, int st, const double *val, long long k) const {
+        return (m.staged && k >= m.a0v && k < m.b0v) ? sval(st)[k - m.a0v] : val[k];
+    }
+    __device__ __forceinline__ int32_t idx_at(const StageMeta &m, int st, const int32_t *idx, long long k) const {
+        return (m.staged && k >= m.a0i && k < m.b0i) ? sidx(st)[k - m.a0i] : idx[k];
+    }
+};
+
+// Standard loop over tiles with the pipeline. `range(tile, &e0, &e1)` gives
+// a tile's entry range, `body(tile, st, meta)` consumes it; all threads call.
+// On a wait that runs out, sets ST_TIMEOUT, waits (bounded) for the copies in
+// flight and returns false.
+template <class Pipe, class RangeF, class BodyF>
+__device__ bool pipe_tiles(Pipe &P, int n_tiles, const double *val, const int32_t *idx, bool can_stage,
+                           int *status, RangeF range, BodyF body) {
+    int it = 0;
+    if (threadIdx.x == 0 && (int)blockIdx.x < n_tiles) {
+        long long e0, e1;
+        range((int)blockIdx.x, &e0, &e1);
+        P.issue(0, e0, e1, val, idx, can_stage);
+    }
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+        const int st = it & 1;
+        const int next = tile + gridDim.x;
+        if (threadIdx.x == 0 && next < n_tiles) {
+            long long e0, e1;
+            range(next, &e0, &e1);
+            P.issue(st ^ 1, e0, e1, val, idx, can_stage);
+        }
+        const bool ok = P.wait(st, it >> 1);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicOr(status, ST_TIMEOUT);
+                P.wait(st, it >> 1);
+                if (next < n_tiles) P.wait(st ^ 1, (it + 1) >> 1);
+            }
+            return false;
+        }
+        const StageMeta m = P.meta[st];
+        body(tile, st, m);
+        __syncthreads();
+    }
+    return true;
+}
+
+}  // namespace spmvat

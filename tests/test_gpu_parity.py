@@ -198,3 +198,47 @@ def test_crs_schedule_binned_and_regular_agree():
     M = L.spmv_transform(A, L.SPMV_CRS, L.SPMV_ROWWISE)
     assert_spmv_close(run_apply(M, torch.from_numpy(xh).cuda(), H.n_rows), H, xh, what="binned")
     M.close()
+
+
+def test_unaligned_caller_arrays_take_the_global_path():
+    """VAL / ICOL not 16-byte aligned: the TMA-staged kernels fall back to
+    plain loads and give the same bits."""
+    import torch
+    L = lib()
+    H = synth.stencil_3d_27pt(16)
+    icol = torch.empty(H.nnz + 1, dtype=torch.int32, device="cuda")[1:]
+    val = torch.empty(H.nnz + 1, dtype=torch.float64, device="cuda")[1:]
+    icol.copy_(torch.from_numpy(H.icol))
+    val.copy_(torch.from_numpy(H.val))
+    assert icol.data_ptr() % 16 and val.data_ptr() % 16
+    A = L.Crs(H.n_rows, H.n_cols, torch.from_numpy(H.irp).cuda(), icol, val)
+    xh = xvec(H.n_cols, seed=6)
+    x = torch.from_numpy(xh).cuda()
+    M = L.spmv_transform(A, L.SPMV_ELL, L.SPMV_ROWWISE)
+    W, ld, ev, ei = ell_from_gpu(M, H.n_rows)
+    rv, ri, rW = oracle.crs_to_ell_row(H.n_rows, H.irp, H.icol, H.val)
+    assert np.array_equal(bits(ev[:, :H.n_rows]), bits(rv.reshape(W, H.n_rows)))
+    assert np.array_equal(ei[:, :H.n_rows], ri.reshape(W, H.n_rows))
+    M.close()
+    for fmt, lay in ((L.SPMV_CRS, L.SPMV_ROWWISE), (L.SPMV_COO, L.SPMV_COLWISE)):
+        M = L.spmv_transform(A, fmt, lay)
+        assert_spmv_close(run_apply(M, x, H.n_rows), H, xh, what=f"unaligned {fmt}/{lay}")
+        M.close()
+
+
+@pytest.mark.parametrize("kernel,S", [("tile", 1), ("tile", 2), ("tile", 4), ("tile", 8), ("stream", 1),
+                                      ("stream", 2), ("stream", 4), ("stream", 8), ("vector", 0)])
+def test_crs_kernel_variants(monkeypatch, kernel, S):
+    """Every CRS schedule the plan can pick gives results inside the tolerance."""
+    import torch
+    L = lib()
+    monkeypatch.setenv("SPMVAT_CRS_KERNEL", kernel)
+    if S:
+        monkeypatch.setenv("SPMVAT_CRS_S", str(S))
+    for name in ("laplace37x23", "stencil27_24"):
+        H = case(name)
+        xh = xvec(H.n_cols, seed=7)
+        M = L.spmv_transform(dev(H), L.SPMV_CRS, L.SPMV_ROWWISE)
+        assert_spmv_close(run_apply(M, torch.from_numpy(xh).cuda(), H.n_rows), H, xh, what=f"{name}/{kernel}{S}")
+        L.spmv_matrix_status(M)
+        M.close()
