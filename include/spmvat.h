@@ -255,6 +255,30 @@ spmv_status spmv_autotune(const spmv_crs *A, const spmv_at_params *p, spmv_matri
 spmv_status spmv_autotune_choose(const spmv_crs *A, const spmv_at_params *p, int32_t *format,
                                  int32_t *layout, spmv_stats *stats, spmv_stream_t stream);
 
+/* COO-Row SpMV that allocates no device memory. The paper has no
+ * counterpart: this is for callers that cannot allocate device memory while
+ * they multiply, such as solvers that reserve all of their memory up front
+ * from a fixed arena, or latency-critical loops where an allocation could
+ * block or fail between iterations.
+ * Computes y = A x like spmv_apply on a COO-Row handle, from caller-owned
+ * device arrays: irow, icol (int32[nnz], irow non-decreasing, every index in
+ * range), val (float64[nnz]), x (float64[n_cols]), y (float64[n_rows],
+ * overwritten). Asynchronous; deterministic like spmv_apply.
+ * Its temporary data (partial sums of rows that cross tile boundaries) lives
+ * in one fixed device array of SPMV_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading the library holds until the process exits; the call allocates and
+ * frees nothing. nnz above SPMV_NOALLOC_COO_MAX_NNZ returns
+ * SPMV_ERR_UNSUPPORTED before touching the device. All calls share the
+ * array: calls whose work overlaps on one device (several streams or host
+ * threads) race on it and must be ordered by the caller. The first call on a
+ * device looks up the array's device address (a CUDA runtime query, no
+ * allocation); make that first call before any stream capture. */
+#define SPMV_NOALLOC_SCRATCH_BYTES (1u << 20)
+#define SPMV_NOALLOC_COO_MAX_NNZ 134217728ll /* 2048-entry tiles x 16 bytes of scratch each */
+spmv_status spmv_apply_coo_row_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *irow,
+                                       const int32_t *icol, const double *val, const double *x, double *y,
+                                       spmv_stream_t stream);
+
 /* Instrumentation: number of kernels this library has launched so far. */
 uint64_t spmv_launch_count(void);
 

@@ -22,7 +22,7 @@ __all__ = [
     "spmv_version", "spmv_status_string", "spmv_set_allocator", "spmv_analyze", "spmv_validate",
     "spmv_ell_bytes", "spmv_transform", "spmv_transform_from", "spmv_apply", "spmv_transform_apply",
     "spmv_describe", "spmv_matrix_status", "spmv_destroy", "spmv_r_ell", "spmv_dstar_from_points", "spmv_measure",
-    "spmv_calibrate", "spmv_autotune", "spmv_autotune_choose", "spmv_launch_count", "spmv_profile_enable", "spmv_profile_read",
+    "spmv_calibrate", "spmv_autotune", "spmv_autotune_choose", "spmv_apply_coo_row_noalloc", "spmv_launch_count", "spmv_profile_enable", "spmv_profile_read",
     "spmv_debug_scan_timeout",
 ]
 
@@ -119,6 +119,7 @@ def load_library():
         "spmv_calibrate": (ctypes.c_int, [P(P(_CrsT)), i32, P(_AtParamsT), P(dbl), P(dbl), P(dbl), vp]),
         "spmv_autotune": (ctypes.c_int, [P(_CrsT), P(_AtParamsT), P(vp), P(_StatsT), vp]),
         "spmv_autotune_choose": (ctypes.c_int, [P(_CrsT), P(_AtParamsT), P(i32), P(i32), P(_StatsT), vp]),
+        "spmv_apply_coo_row_noalloc": (ctypes.c_int, [i32, i32, i64, vp, vp, vp, vp, vp, vp]),
         "spmv_launch_count": (u64, []),
         "spmv_profile_enable": (ctypes.c_int, [i32]),
         "spmv_profile_read": (i32, [P(_KernelTimeT), i32, i32]),
@@ -376,6 +377,18 @@ def spmv_autotune_choose(A: Crs, stream=None, **params):
     _check(load_library().spmv_autotune_choose(ctypes.byref(A.c), ctypes.byref(p), ctypes.byref(f), ctypes.byref(l),
                                                ctypes.byref(s), _stream(stream)), "spmv_autotune_choose")
     return (f.value, l.value), _stats_dict(s)
+
+
+SPMV_NOALLOC_SCRATCH_BYTES = 1 << 20
+SPMV_NOALLOC_COO_MAX_NNZ = 134217728
+
+
+def spmv_apply_coo_row_noalloc(n_rows: int, n_cols: int, irow, icol, val, x, y, stream=None) -> None:
+    """COO-Row SpMV from caller-owned device tensors, with no device allocation
+    (temporaries in a fixed device array shared by all calls)."""
+    _check(load_library().spmv_apply_coo_row_noalloc(int(n_rows), int(n_cols), int(icol.numel()), _ptr(irow),
+                                                     _ptr(icol), _ptr(val), _ptr(x), _ptr(y), _stream(stream)),
+           "spmv_apply_coo_row_noalloc")
 
 
 def spmv_launch_count() -> int:
