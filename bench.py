@@ -106,9 +106,13 @@ def kernel_bytes(name: str, bm: dict, n_rows: int, n_cols: int, nnz: int):
         "col_count": 8 * nnz + 4 * n_cols,
         "scan_lookback": 8 * n_cols,
         "col_scatter": 16 * nnz + 4 * (n_rows + 1) + 4 * n_cols,
-        "col_fixup_warp": 28 * nnz + 4 * n_cols,
+        "col_fixup_tiles": 28 * nnz + 4 * n_cols,
+        "tile_lines": 4 * (nnz // 2048 + 1),
+        "spmv_coo_row_carry": 16 * (nnz // 2048 + 1),
+        "col_fixup_block": 0,
+        "crs_to_ell_row_fused_spmv": bm["crs_to_ell_row"] + 8 * n_cols + 8 * n_rows,
     }
-    if name.startswith("spmv_crs_v"):
+    if name.startswith("spmv_crs_"):
         return bm["spmv_crs"]
     return table.get(name)
 

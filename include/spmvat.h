@@ -273,8 +273,8 @@ spmv_status spmv_autotune_choose(const spmv_crs *A, const spmv_at_params *p, int
  * threads) race on it and must be ordered by the caller. The first call on a
  * device looks up the array's device address (a CUDA runtime query, no
  * allocation); make that first call before any stream capture. */
-#define SPMV_NOALLOC_SCRATCH_BYTES (1u << 20)
-#define SPMV_NOALLOC_COO_MAX_NNZ 134217728ll /* 2048-entry tiles x 16 bytes of scratch each */
+#define SPMV_NOALLOC_SCRATCH_BYTES ((1u << 20) + 256u)
+#define SPMV_NOALLOC_COO_MAX_NNZ 134217728ll /* 65536 tiles of 2048 entries, 16 bytes of scratch each */
 spmv_status spmv_apply_coo_row_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *irow,
                                        const int32_t *icol, const double *val, const double *x, double *y,
                                        spmv_stream_t stream);

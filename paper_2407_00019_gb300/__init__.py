@@ -379,7 +379,7 @@ def spmv_autotune_choose(A: Crs, stream=None, **params):
     return (f.value, l.value), _stats_dict(s)
 
 
-SPMV_NOALLOC_SCRATCH_BYTES = 1 << 20
+SPMV_NOALLOC_SCRATCH_BYTES = (1 << 20) + 256
 SPMV_NOALLOC_COO_MAX_NNZ = 134217728
 
 

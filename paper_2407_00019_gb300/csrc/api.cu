@@ -168,8 +168,11 @@ struct spmv_matrix {
     // CRS schedule
     int crs_binned = 0;
     int crs_v = 1;
+    int crs_rows_split = 0;        // > 0: ELL-order row-tile kernel, threads per row
+    int crs_rows_cap = 0;          //      and its shared-memory capacity (entries)
     int crs_tile_s = 0;            // > 0: row-tile kernel with S lanes per row
     int crs_stream_s = 0;          // > 0: TMA-staged stream kernel with S lanes per row
+    int crs_stream_r = 0;          //      and R rows per tile
     int *status = nullptr;         // device status word of bounded waits in apply
     int64_t bin_off[kNumBins + 1] = {};
     const int32_t *rowlist = nullptr;
@@ -290,17 +293,26 @@ spmv_status build_crs_plan(const spmv_crs *A, uint64_t cap, spmv_matrix **out, c
         // (tile | stream | vector) and SPMVAT_CRS_S override the choice for
         // schedule sweeps.
         const char *kv = getenv("SPMVAT_CRS_KERNEL");
-        const std::string kind = kv ? kv : "tile";
+        const std::string kind = kv ? kv : "rows";
         int S = crs_tile_lanes(st.max_row_len);
         if (const char *ev = getenv("SPMVAT_CRS_S")) S = atoi(ev);
         const bool s_ok = S == 1 || S == 2 || S == 4 || S == 8;
-        if (kind == "tile" && s_ok && crs_tile_lanes(st.max_row_len) > 0) {
+        if (kind == "rows" && crs_rows_cap(st.max_row_len) > 0) {
+            int split = st.mu <= 8.0 ? 2 : 4;
+            if (const char *ev = getenv("SPMVAT_CRS_S")) split = atoi(ev);
+            if (split == 1 || split == 2 || split == 4 || split == 8) {
+                M->crs_rows_split = split;
+                M->crs_rows_cap = crs_rows_cap(st.max_row_len);
+            }
+        } else if (kind == "tile" && s_ok && crs_tile_lanes(st.max_row_len) > 0) {
             M->crs_tile_s = S;
-        } else if (kind == "stream" && s_ok && (int64_t)(256 / S) * st.max_row_len <= 4096) {
+        } else if (kind == "stream" && s_ok && crs_stream_rows(S, st.max_row_len) > 0) {
             BufPtr sw;
             CKS(alloc_buf(16, s, &sw));
             CK(cudaMemsetAsync(sw->p, 0, 16, s));
             M->crs_stream_s = S;
+            M->crs_stream_r = crs_stream_rows(S, st.max_row_len);
+            if (const char *rv = getenv("SPMVAT_CRS_R")) M->crs_stream_r = std::min(M->crs_stream_r, atoi(rv));
             M->status = reinterpret_cast<int *>(sw->p);
             M->bufs.push_back(sw);
         }
@@ -340,6 +352,11 @@ spmv_status build_coo_row(const spmv_crs *A, uint64_t cap, spmv_matrix **out, cu
     CKS(alloc_buf(expand_scratch_bytes(A->nnz), s, &scr));
     CK(launch_expand(A->irp, A->n_rows, A->nnz, reinterpret_cast<int32_t *>(irow->p),
                      reinterpret_cast<int32_t *>(scr->p), s, "crs_to_coo_row"));
+    BufPtr sw;
+    CKS(alloc_buf(16, s, &sw));
+    CK(cudaMemsetAsync(sw->p, 0, 16, s));
+    M->status = reinterpret_cast<int *>(sw->p);
+    M->bufs.push_back(sw);
     M->ptr = A->irp;
     M->idx = A->icol;
     M->idx2 = reinterpret_cast<const int32_t *>(irow->p);
@@ -407,12 +424,12 @@ spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bo
     CK(launch_col_count(A->icol, nnz, nc, d_cp, reinterpret_cast<int32_t *>(rank->p), d_status, s));
     CK(launch_scan(d_cp, nc, scan_scr->p, d_colmax, 32, d_long + 1, d_long, d_status, kSpinLimit, 0, s));
     int hw[2] = {0, 0};
-    CK(cudaMemcpyAsync(hw, words->p, sizeof(hw), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    CKS(status_from_dev(hw[0]));
-    const int32_t colmax = hw[1];
     if (want_ell) {
-        if (cap_ell_col && ell_bytes(nc, colmax) > cap_ell_col) return SPMV_ERR_MEMORY_CAP;
+        // the ELL-Column width decides the cap check before anything else is built
+        CK(cudaMemcpyAsync(hw, words->p, sizeof(hw), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        CKS(status_from_dev(hw[0]));
+        if (cap_ell_col && ell_bytes(nc, hw[1]) > cap_ell_col) return SPMV_ERR_MEMORY_CAP;
     }
     BufPtr sct;
     CKS(alloc_buf((size_t)nnz * 4, s, &trow));
@@ -427,6 +444,7 @@ spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bo
     CK(cudaMemcpyAsync(hw, words->p, sizeof(hw), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     CKS(status_from_dev(hw[0]));
+    const int32_t colmax = hw[1];
     M->ptr = d_cp;
     M->idx = reinterpret_cast<const int32_t *>(trow->p);
     M->val = reinterpret_cast<const double *>(tval->p);
@@ -500,10 +518,14 @@ spmv_status apply_core(const spmv_matrix *M, const double *x, double *y, cudaStr
     if (M->layout == SPMV_ROWWISE) {
         switch (M->format) {
             case SPMV_CRS:
-                if (M->crs_tile_s > 0) {
+                if (M->crs_rows_split > 0) {
+                    CK(launch_spmv_crs_rows(M->crs_rows_split, M->crs_rows_cap, M->ptr, M->idx, M->val, M->n_rows,
+                                            x, y, s));
+                } else if (M->crs_tile_s > 0) {
                     CK(launch_spmv_crs_tile(M->crs_tile_s, M->ptr, M->idx, M->val, M->n_rows, x, y, s));
                 } else if (M->crs_stream_s > 0) {
-                    CK(launch_spmv_crs_stream(M->crs_stream_s, M->ptr, M->idx, M->val, M->n_rows, x, y, M->status, s));
+                    CK(launch_spmv_crs_stream(M->crs_stream_s, M->crs_stream_r, M->ptr, M->idx, M->val, M->n_rows, x,
+                                              y, M->status, s));
                 } else if (!M->crs_binned) {
                     CK(launch_spmv_crs_vector(M->crs_v, M->ptr, M->idx, M->val, nullptr, M->n_rows, x, y, s));
                 } else {
@@ -519,7 +541,8 @@ spmv_status apply_core(const spmv_matrix *M, const double *x, double *y, cudaStr
             case SPMV_COO: {
                 BufPtr scr;
                 CKS(alloc_buf(coo_row_scratch_bytes(M->nnz), s, &scr));
-                CK(launch_spmv_coo_row(M->idx2, M->idx, M->val, M->nnz, M->n_rows, M->n_cols, x, y, scr->p, s));
+                CK(launch_spmv_coo_row(M->idx2, M->idx, M->val, M->nnz, M->n_rows, M->n_cols, x, y, scr->p,
+                                       M->status, s));
                 return SPMV_OK;
             }
             case SPMV_ELL:

@@ -180,11 +180,15 @@ cudaError_t launch_col_fixup(const int32_t *cp, int32_t n_cols, const int32_t *i
 cudaError_t launch_spmv_crs_vector(int v, const int32_t *irp, const int32_t *icol, const double *val,
                                    const int32_t *rows, int64_t count, const double *x, double *y,
                                    cudaStream_t s);
+int crs_rows_cap(int max_row_len);
+cudaError_t launch_spmv_crs_rows(int split, int cap, const int32_t *irp, const int32_t *icol, const double *val,
+                                 int32_t n_rows, const double *x, double *y, cudaStream_t s);
 int crs_tile_lanes(int max_row_len);
 cudaError_t launch_spmv_crs_tile(int S, const int32_t *irp, const int32_t *icol, const double *val,
                                  int32_t n_rows, const double *x, double *y, cudaStream_t s);
 size_t crs_stream_smem_bytes();
-cudaError_t launch_spmv_crs_stream(int S, const int32_t *irp, const int32_t *icol, const double *val,
+int crs_stream_rows(int S, int max_row_len);
+cudaError_t launch_spmv_crs_stream(int S, int R, const int32_t *irp, const int32_t *icol, const double *val,
                                    int32_t n_rows, const double *x, double *y, int *status, cudaStream_t s);
 cudaError_t launch_spmv_crs_block(const int32_t *irp, const int32_t *icol, const double *val,
                                   const int32_t *rows, int64_t count, const double *x, double *y,
@@ -194,9 +198,11 @@ cudaError_t launch_spmv_ell_row(const double *eval, const int32_t *eidx, int32_t
 cudaError_t launch_spmv_ell_col(const double *eval, const int32_t *eidx, int32_t n_rows, int32_t n_cols,
                                 int32_t width, int32_t ld, const double *x, double *y, cudaStream_t s);
 size_t coo_row_scratch_bytes(int64_t nnz);
+// `scratch`: coo_row_scratch_bytes(nnz); `status` may be NULL (then a word
+// inside the scratch is used).
 cudaError_t launch_spmv_coo_row(const int32_t *irow, const int32_t *icol, const double *val, int64_t nnz,
                                 int32_t n_rows, int32_t n_cols, const double *x, double *y, void *scratch,
-                                cudaStream_t s);
+                                int *status, cudaStream_t s);
 cudaError_t launch_spmv_coo_col(const int32_t *row, const int32_t *col, const double *val, int64_t nnz,
                                 int32_t n_rows, const double *x, double *y, cudaStream_t s);
 cudaError_t launch_spmv_ccs(const int32_t *cp, const int32_t *trow, const double *tval, int32_t n_rows,

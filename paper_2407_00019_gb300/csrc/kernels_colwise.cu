@@ -313,6 +313,20 @@ __device__ __forceinline__ void warp_sort_pairs(int &key, int &row) {
     }
 }
 
+__device__ __forceinline__ void warp_sort_u32(unsigned &key) {
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const unsigned ok = __shfl_xor_sync(0xffffffffu, key, stride);
+            const bool asc = (lane & size) == 0;
+            const bool lower = (lane & stride) == 0;
+            key = ((lower == asc) == (ok < key)) ? ok : key;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(FT_THREADS) k_fixup_tiles(const int32_t *__restrict__ cp, int32_t n_cols,
                                                              const double *__restrict__ val,
                                                              const int2 *__restrict__ pairs,
@@ -346,7 +360,26 @@ __global__ void __launch_bounds__(FT_THREADS) k_fixup_tiles(const int32_t *__res
             row = q.y;
         }
         const int nxt = __shfl_down_sync(0xffffffffu, key, 1);
-        if (__any_sync(0xffffffffu, (int)lane + 1 < len && key > nxt)) warp_sort_pairs(key, row);
+        if (__any_sync(0xffffffffu, (int)lane + 1 < len && key > nxt)) {
+            // Keys within 2^26 of the first one: sort 32-bit words
+            // ((k - k0 + 2^26) << 5 | lane), one shuffle per network step,
+            // then fetch each row from the lane it came from.
+            const int k0 = __shfl_sync(0xffffffffu, key, 0);
+            const long long rel = (long long)key - k0 + (1ll << 26);
+            const bool narrow = __all_sync(0xffffffffu, (int)lane >= len || (rel >= 0 && rel < (1ll << 27)));
+            if (narrow) {
+                unsigned pk = ((int)lane < len) ? (((unsigned)rel << 5) | lane) : 0xffffffffu;
+                warp_sort_u32(pk);
+                const int src = (int)(pk & 31u);
+                const int r2 = __shfl_sync(0xffffffffu, row, src);
+                if ((int)lane < len) {
+                    key = (int)((long long)k0 + (long long)(pk >> 5) - (1ll << 26));
+                    row = r2;
+                }
+            } else {
+                warp_sort_pairs(key, row);
+            }
+        }
         if ((int)lane < len) {
             if (staged) {
                 s_pr[p0 - e0 + lane] = make_int2(key, row);

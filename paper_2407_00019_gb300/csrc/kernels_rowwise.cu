@@ -143,11 +143,11 @@ cudaError_t launch_tile_lines(const int32_t *ptr, int32_t n_lines, int64_t nnz, 
 
 // ------------------------------------------------------------------ expand
 // Tile of EXP_TILE consecutive entries; each thread writes EXP_ITEMS of them
-// with one 16-byte store. The pointers of the lines that cover the tile are
+// with 16-byte stores. The pointers of the lines that cover the tile are
 // staged in shared memory when they fit; each thread finds its first line by
 // binary search there and walks forward.
 constexpr int EXP_THREADS = 256;
-constexpr int EXP_ITEMS = 4;
+constexpr int EXP_ITEMS = 8;
 constexpr int EXP_TILE = EXP_THREADS * EXP_ITEMS;
 constexpr int EXP_WIN = 2048;
 
@@ -177,7 +177,9 @@ __global__ void __launch_bounds__(EXP_THREADS) k_expand(const int32_t *__restric
         v[j] = line;
     }
     if (k + EXP_ITEMS <= k1 && ((reinterpret_cast<uintptr_t>(out + k) & 15) == 0)) {
-        __stcs(reinterpret_cast<int4 *>(out + k), make_int4(v[0], v[1], v[2], v[3]));
+#pragma unroll
+        for (int h = 0; h < EXP_ITEMS / 4; ++h)
+            __stcs(reinterpret_cast<int4 *>(out + k) + h, make_int4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]));
     } else {
 #pragma unroll
         for (int j = 0; j < EXP_ITEMS; ++j)
@@ -208,7 +210,7 @@ constexpr int ELL_LINES = 128;
 constexpr int ELL_SPLIT = 2;
 constexpr int ELL_THREADS = ELL_LINES * ELL_SPLIT;
 constexpr int ELL_STAGE_CAP = 4096;  // entries per stage (48 KB)
-using EllPipe = StagePipe<ELL_STAGE_CAP, true>;
+using EllPipe = StagePipe<ELL_STAGE_CAP, 1>;
 
 template <bool FUSED>
 __global__ void __launch_bounds__(ELL_THREADS) k_lines_to_ell(

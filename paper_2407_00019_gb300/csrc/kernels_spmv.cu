@@ -8,8 +8,9 @@
 //             row lists built once per handle.
 //  ELL-Row  : one thread per two rows, 128-bit loads of the column-major
 //             slots (values and indices), FMA in slot order (Fig. 3 order).
-//  COO-Row  : tiles of 2048 entries, thread-local then block segmented
-//             reduction; partial sums of rows that cross tile edges are
+//  COO-Row  : 2048-entry tiles in shared memory; row segments found with
+//             integer work, FMA chains per segment with lanes on consecutive
+//             segments; partial sums of rows that cross tile edges are
 //             finished by a second, per-tile kernel in tile order
 //             (deterministic).
 //  COO-Col, ELL-Col, CCS : the column-major products of Fig. 1: each entry
@@ -82,72 +83,108 @@ cudaError_t launch_spmv_crs_vector(int v, const int32_t *irp, const int32_t *ico
     return cudaGetLastError();
 }
 
-// Rows staged by TMA: persistent CTAs take tiles of LINES consecutive rows;
-// the tile's VAL / ICOL range arrives in shared memory through the two-stage
-// bulk-copy pipeline while the previous tile is multiplied. S lanes per row
-// sum strided entries in order; a fixed shuffle tree combines them.
-constexpr int CRS_STAGE_CAP = 4096;
-using CrsPipe = StagePipe<CRS_STAGE_CAP, true>;
+// Rows staged by TMA: persistent CTAs take tiles of R consecutive rows; the
+// tile's VAL / ICOL range arrives in shared memory through the two-stage
+// bulk-copy pipeline (stage_pipe.cuh) while the previous tile is multiplied,
+// with no load instructions spent on it. Then all threads gather x for the
+// tile's entries into shared memory, eight independent gathers in flight per
+// thread, and S lanes per row run the FMA chains (storage order, strided by
+// lane) and a fixed shuffle tree combines them. R * (longest row) fits a
+// stage, so every row of a tile is resident.
+constexpr int CRS_STAGE_CAP = 2048;
+using CrsPipe = StagePipe<CRS_STAGE_CAP, 1>;
+constexpr size_t kCrsStreamSmem = CrsPipe::kSmem + (size_t)CRS_STAGE_CAP * 8;
 
 template <int S>
 __global__ void __launch_bounds__(256) k_spmv_crs_stream(const int32_t *__restrict__ irp,
                                                           const int32_t *__restrict__ icol,
-                                                          const double *__restrict__ val, int32_t n_rows,
+                                                          const double *__restrict__ val, int32_t n_rows, int R,
                                                           int n_tiles, int can_stage, const double *__restrict__ x,
                                                           double *__restrict__ y, int *status) {
-    constexpr int LINES = 256 / S;
     extern __shared__ __align__(128) unsigned char smem[];
     CrsPipe P;
     P.setup(smem);
+    double *s_x = reinterpret_cast<double *>(smem + CrsPipe::kSmem);
     const int lt = threadIdx.x / S, sub = threadIdx.x % S;
     auto range = [&](int tile, long long *e0, long long *e1) {
-        const long long r0 = (long long)tile * LINES;
-        const long long r1 = min(r0 + LINES, (long long)n_rows);
+        const long long r0 = (long long)tile * R;
+        const long long r1 = min(r0 + R, (long long)n_rows);
         *e0 = irp[r0];
         *e1 = irp[r1];
     };
     auto body = [&](int tile, int st, const StageMeta &m) {
-        const long long r = (long long)tile * LINES + lt;
+        const long long r = (long long)tile * R + lt;
+        const bool own = lt < R && r < n_rows;
+        // row bounds first: their latency overlaps the gathers below
+        const int rs = own ? __ldg(irp + r) : 0;
+        const int re = own ? __ldg(irp + r + 1) : 0;
+        const int e0 = (int)m.e0;
+        const int n = (int)(m.e1 - m.e0);
+        const bool fits = n <= CRS_STAGE_CAP;
+        if (fits) {
+            for (int q0 = threadIdx.x; q0 < n; q0 += 8 * 256) {
+                int c[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int q = q0 + u * 256;
+                    c[u] = (q < n) ? P.idx_at(m, st, icol, e0 + q) : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int q = q0 + u * 256;
+                    if (q < n) s_x[q] = __ldg(x + c[u]);
+                }
+            }
+        }
+        __syncthreads();
         double acc = 0.0;
-        if (r < n_rows) {
-            const int s = irp[r], e = irp[r + 1];
-            if (m.staged && s >= m.a0v && e <= m.b0v && s >= m.a0i && e <= m.b0i) {
-                const double *sv = P.sval(st);
-                const int32_t *si = P.sidx(st);
-                const int ov = (int)(s - m.a0v), oi = (int)(s - m.a0i);
-                const int len = e - s;
-                for (int k = sub; k < len; k += S) acc = fma(sv[ov + k], __ldg(x + si[oi + k]), acc);
+        if (own) {
+            if (fits && m.staged && rs >= m.a0v && re <= m.b0v) {
+                const double *sv = P.sval(st) + (rs - m.a0v);
+                const double *sx = s_x + (rs - e0);
+                const int len = re - rs;
+                for (int k = sub; k < len; k += S) acc = fma(sv[k], sx[k], acc);
+            } else if (fits) {
+                for (int k = rs + sub; k < re; k += S) acc = fma(P.val_at(m, st, val, k), s_x[k - e0], acc);
             } else {
-                for (int k = s + sub; k < e; k += S)
+                for (int k = rs + sub; k < re; k += S)
                     acc = fma(P.val_at(m, st, val, k), __ldg(x + P.idx_at(m, st, icol, k)), acc);
             }
         }
 #pragma unroll
         for (int o = S / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, S);
-        if (sub == 0 && r < n_rows) y[r] = acc;
+        if (sub == 0 && own) y[r] = acc;
     };
     pipe_tiles(P, n_tiles, val, icol, can_stage != 0, status, range, body);
 }
 
-size_t crs_stream_smem_bytes() { return CrsPipe::kSmem; }
+size_t crs_stream_smem_bytes() { return kCrsStreamSmem; }
 
-cudaError_t launch_spmv_crs_stream(int S, const int32_t *irp, const int32_t *icol, const double *val,
+// Rows per tile for S lanes per row: the largest power of two with
+// R * S <= 256 and R * max_row_len <= the stage capacity (0: no fit).
+int crs_stream_rows(int S, int max_row_len) {
+    for (int R = 256 / S; R >= 1; R >>= 1)
+        if ((long long)R * max_row_len <= CRS_STAGE_CAP) return R;
+    return 0;
+}
+
+cudaError_t launch_spmv_crs_stream(int S, int R, const int32_t *irp, const int32_t *icol, const double *val,
                                    int32_t n_rows, const double *x, double *y, int *status, cudaStream_t s) {
     if (n_rows <= 0) return cudaSuccess;
-    const int lines = 256 / S;
-    const int n_tiles = (int)ceil_div_u(n_rows, lines);
+    if (R <= 0 || R * S > 256) return cudaErrorInvalidValue;
+    const int n_tiles = (int)ceil_div_u(n_rows, R);
     const int can_stage = ((reinterpret_cast<uintptr_t>(val) & 15) == 0) &&
                           ((reinterpret_cast<uintptr_t>(icol) & 15) == 0);
-    int grid = sm_count() * 2;
+    int grid = sm_count() * 3;
     if (grid > n_tiles) grid = n_tiles;
     switch (S) {
 #define STREAM_CASE(SS)                                                                                  \
     case SS: {                                                                                           \
-        cudaError_t e = set_smem_attr(k_spmv_crs_stream<SS>, CrsPipe::kSmem);                            \
+        cudaError_t e = set_smem_attr(k_spmv_crs_stream<SS>, kCrsStreamSmem);                            \
         if (e != cudaSuccess) return e;                                                                  \
         KernelScope ks("spmv_crs_stream_s" #SS, s);                                                      \
-        k_spmv_crs_stream<SS><<<grid, 256, CrsPipe::kSmem, s>>>(irp, icol, val, n_rows, n_tiles, can_stage, x, \
-                                                                 y, status);                            \
+        k_spmv_crs_stream<SS><<<grid, 256, kCrsStreamSmem, s>>>(irp, icol, val, n_rows, R, n_tiles, can_stage, \
+                                                                 x, y, status);                         \
         break;                                                                                           \
     }
         STREAM_CASE(1)
@@ -244,6 +281,117 @@ cudaError_t launch_spmv_crs_tile(int S, const int32_t *irp, const int32_t *icol,
         TILE_CASE(4)
         TILE_CASE(8)
 #undef TILE_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// Rows of a tile in ELL order: a CTA stages 128 consecutive rows' VAL and
+// ICOL in shared memory with coalesced loads (eight per thread in flight),
+// then SPLIT threads per row walk the row's entries; for a fixed slot the
+// lanes of a warp handle consecutive rows, so their x gathers land on
+// neighbouring columns for banded matrices, as in ELL-Row. FMA chains in
+// storage order (strided by part), partials of the SPLIT threads added in a
+// fixed order.
+constexpr int CRS_ROWS_R = 128;
+
+template <int SPLIT>
+__global__ void __launch_bounds__(CRS_ROWS_R *SPLIT) k_spmv_crs_rows(const int32_t *__restrict__ irp,
+                                                                     const int32_t *__restrict__ icol,
+                                                                     const double *__restrict__ val, int32_t n_rows,
+                                                                     int cap, const double *__restrict__ x,
+                                                                     double *__restrict__ y) {
+    constexpr int R = CRS_ROWS_R;
+    constexpr int T = R * SPLIT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *s_v = reinterpret_cast<double *>(smem);
+    int32_t *s_c = reinterpret_cast<int32_t *>(s_v + cap);
+    __shared__ int32_t s_ptr[R + 1];
+    __shared__ double s_part[SPLIT > 1 ? (SPLIT - 1) * R : 1];
+    const long long r0 = (long long)blockIdx.x * R;
+    const int nr = (int)min((long long)R, (long long)n_rows - r0);
+    const int e0 = __ldg(irp + r0), e1 = __ldg(irp + r0 + nr);
+    const int n = e1 - e0;
+    const bool staged = n <= cap;
+    for (int i = threadIdx.x; i <= nr; i += T) s_ptr[i] = irp[r0 + i];
+    if (staged) {
+        for (int q0 = threadIdx.x; q0 < n; q0 += 8 * T) {
+            double v[8];
+            int c[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int q = q0 + u * T;
+                v[u] = (q < n) ? __ldcs(val + e0 + q) : 0.0;
+                c[u] = (q < n) ? __ldcs(icol + e0 + q) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int q = q0 + u * T;
+                if (q < n) {
+                    s_v[q] = v[u];
+                    s_c[q] = c[u];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int r = threadIdx.x % R, part = threadIdx.x / R;
+    double acc = 0.0;
+    if (r < nr) {
+        const int s = s_ptr[r] - e0, e = s_ptr[r + 1] - e0;
+        if (staged) {
+            int k = s + part;
+            for (; k + 3 * SPLIT < e; k += 4 * SPLIT) {
+                const int c0 = s_c[k], c1 = s_c[k + SPLIT], c2 = s_c[k + 2 * SPLIT], c3 = s_c[k + 3 * SPLIT];
+                const double x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+                acc = fma(s_v[k], x0, acc);
+                acc = fma(s_v[k + SPLIT], x1, acc);
+                acc = fma(s_v[k + 2 * SPLIT], x2, acc);
+                acc = fma(s_v[k + 3 * SPLIT], x3, acc);
+            }
+            for (; k < e; k += SPLIT) acc = fma(s_v[k], __ldg(x + s_c[k]), acc);
+        } else {
+            for (int k = e0 + s + part; k < e0 + e; k += SPLIT)
+                acc = fma(__ldcs(val + k), __ldg(x + __ldcs(icol + k)), acc);
+        }
+    }
+    if (SPLIT > 1) {
+        if (part > 0) s_part[(part - 1) * R + r] = acc;
+        __syncthreads();
+        if (part == 0)
+            for (int p = 1; p < SPLIT; ++p) acc += s_part[(p - 1) * R + r];
+    }
+    if (part == 0 && r < nr) y[r0 + r] = acc;
+}
+
+// Shared-memory capacity (entries) for 128-row tiles of rows up to
+// max_row_len long; 0 when that would leave fewer than two CTAs per SM.
+int crs_rows_cap(int max_row_len) {
+    const long long cap = (long long)CRS_ROWS_R * (max_row_len > 0 ? max_row_len : 1);
+    return cap * 12 <= 96 * 1024 ? (int)((cap + 3) & ~3ll) : 0;
+}
+
+cudaError_t launch_spmv_crs_rows(int split, int cap, const int32_t *irp, const int32_t *icol, const double *val,
+                                 int32_t n_rows, const double *x, double *y, cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    if (cap <= 0) return cudaErrorInvalidValue;
+    const unsigned grid = ceil_div_u(n_rows, CRS_ROWS_R);
+    const size_t smem = (size_t)cap * 12;
+    switch (split) {
+#define ROWS_CASE(SP)                                                                         \
+    case SP: {                                                                                \
+        cudaError_t e = set_smem_attr(k_spmv_crs_rows<SP>, smem);                             \
+        if (e != cudaSuccess) return e;                                                       \
+        KernelScope ks("spmv_crs_rows_p" #SP, s);                                             \
+        k_spmv_crs_rows<SP><<<grid, CRS_ROWS_R * SP, smem, s>>>(irp, icol, val, n_rows, cap, x, y); \
+        break;                                                                                \
+    }
+        ROWS_CASE(1)
+        ROWS_CASE(2)
+        ROWS_CASE(4)
+        ROWS_CASE(8)
+#undef ROWS_CASE
         default:
             return cudaErrorInvalidValue;
     }
@@ -496,26 +644,21 @@ constexpr int COO_TILE = COO_THREADS * COO_ITEMS;
 
 size_t coo_row_scratch_bytes(int64_t nnz) {
     const long long tiles = (nnz + COO_TILE - 1) / COO_TILE;
-    return (size_t)(tiles > 0 ? tiles : 1) * sizeof(double2);
+    return (size_t)(tiles > 0 ? tiles : 1) * sizeof(double2) + 16;  // carries + a status word
 }
 
-struct SegPair {
-    int f;     // a row starts inside the covered range
-    double v;  // partial sum of the row open at the end of the range
-};
-__device__ __forceinline__ SegPair seg_combine(SegPair a, SegPair b) {
-    SegPair r;
-    r.f = a.f | b.f;
-    r.v = b.f ? b.v : a.v + b.v;
-    return r;
-}
-
-// Phase A: striped, coalesced loads of IROW / ICOL / VAL and the x gathers,
-// eight in flight per thread, into shared memory padded by one slot per
-// COO_ITEMS (blocked reads below are then bank-conflict free). Phase B: each
-// thread reduces its COO_ITEMS consecutive entries with an FMA chain per row
-// segment; a block segmented scan carries partial rows between threads.
-__device__ __forceinline__ int coo_pad(int q) { return q + q / COO_ITEMS; }
+// One CTA per 2048-entry tile, several CTAs per SM. Phase A: coalesced loads
+// of IROW / ICOL / VAL (eight per thread in flight) into shared memory.
+// Segments (runs of one row) are then found with integer work only (a head
+// flag per entry, one block scan). Phase B: consecutive threads take
+// consecutive segments, so for a fixed position the x gathers of a warp hit
+// neighbouring columns on banded matrices; when a tile has few segments,
+// SPLIT threads share each one (entries strided by part, partials added in a
+// fixed order); segments longer than COO_LONG are summed by a warp. One FMA
+// per entry, storage order within each part. A segment that continues from
+// the previous tile or into the next one leaves its partial in `carry` for
+// k_coo_row_carry.
+constexpr int COO_LONG = 64;
 
 __global__ void __launch_bounds__(COO_THREADS) k_coo_row_tiles(const int32_t *__restrict__ irow,
                                                                 const int32_t *__restrict__ icol,
@@ -523,117 +666,129 @@ __global__ void __launch_bounds__(COO_THREADS) k_coo_row_tiles(const int32_t *__
                                                                 int32_t n_rows, int32_t n_cols,
                                                                 const double *__restrict__ x,
                                                                 double *__restrict__ y, double2 *__restrict__ carry) {
-    constexpr int PADDED = COO_TILE + COO_TILE / COO_ITEMS;
-    __shared__ double s_v[PADDED];
-    __shared__ double s_x[PADDED];
-    __shared__ int32_t s_r[PADDED];
-    __shared__ SegPair s_w[COO_THREADS / 32];
-    const long long t0 = (long long)blockIdx.x * COO_TILE;
-    const long long t1 = min(t0 + (long long)COO_TILE, (long long)nnz);
-    const int nt = (int)(t1 - t0);
-    // tile edges: the row of the entry before and after the tile
-    const int ra = __ldg(irow + t0);
-    const bool cin = (t0 > 0) && __ldg(irow + t0 - 1) == ra;
+    __shared__ double s_v[COO_TILE];
+    __shared__ int32_t s_c[COO_TILE];
+    __shared__ int32_t s_r[COO_TILE];
+    __shared__ int32_t s_seg[COO_TILE + 1];
+    __shared__ double s_part[COO_THREADS];
+    __shared__ int s_wc[COO_THREADS / 32];
+    __shared__ int s_nseg, s_prev, s_next;
+    const unsigned lane = lane_id();
+    const int w = threadIdx.x >> 5;
+    const long long e0 = (long long)blockIdx.x * COO_TILE;
+    const int n = (int)min((long long)COO_TILE, (long long)nnz - e0);
+    if (threadIdx.x == 0) {
+        s_prev = (e0 > 0) ? __ldg(irow + e0 - 1) : -1;
+        s_next = (e0 + n < nnz) ? __ldg(irow + e0 + n) : -1;
+    }
     {
         int r[COO_ITEMS], c[COO_ITEMS];
         double v[COO_ITEMS];
 #pragma unroll
         for (int u = 0; u < COO_ITEMS; ++u) {
             const int q = u * COO_THREADS + threadIdx.x;
-            const bool h = q < nt;
-            r[u] = h ? __ldcs(irow + t0 + q) : 0;
-            c[u] = h ? __ldcs(icol + t0 + q) : 0;
-            v[u] = h ? __ldcs(val + t0 + q) : 0.0;
+            const bool h = q < n;
+            r[u] = h ? __ldcs(irow + e0 + q) : 0;
+            c[u] = h ? __ldcs(icol + e0 + q) : 0;
+            v[u] = h ? __ldcs(val + e0 + q) : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < COO_ITEMS; ++u) {
             const int q = u * COO_THREADS + threadIdx.x;
-            if (q < nt) {
+            if (q < n) {
                 const bool okc = (unsigned)c[u] < (unsigned)n_cols;
-                s_r[coo_pad(q)] = r[u];
-                s_v[coo_pad(q)] = okc ? v[u] : 0.0;
-                s_x[coo_pad(q)] = okc ? __ldg(x + c[u]) : 0.0;
+                s_r[q] = r[u];
+                s_c[q] = okc ? c[u] : 0;
+                s_v[q] = okc ? v[u] : 0.0;
             }
         }
     }
     __syncthreads();
+    // segment starts: thread t looks at entries 8t .. 8t+7
     const int qb = (int)threadIdx.x * COO_ITEMS;
-    const int m = max(0, min(COO_ITEMS, nt - qb));
-    const long long k = t0 + qb;
-    const int prev_row = (m > 0) ? ((qb > 0) ? s_r[coo_pad(qb - 1)] : (k > 0 ? __ldg(irow + k - 1) : -1)) : -1;
-    const long long after = k + m;
-    const int next_row = (m > 0 && after < nnz) ? ((after < t1) ? s_r[coo_pad(qb + m)] : __ldg(irow + after)) : -1;
-    const int r0 = (m > 0) ? s_r[coo_pad(qb)] : -1;
-    const bool cont_prev = (m > 0) && (prev_row == r0);
-    if (m > 0)
-        for (int rr = prev_row + 1; rr < r0 && rr < n_rows; ++rr) y[rr] = 0.0;
-    double first_part = 0.0, part = 0.0;
-    int nseg = 1;
-    int cur = r0;
+    int rr[COO_ITEMS + 1];
 #pragma unroll
-    for (int j = 0; j < COO_ITEMS; ++j) {
-        if (j < m) {
-            const int rj = s_r[coo_pad(qb + j)];
-            if (rj != cur) {
-                if (nseg == 1) first_part = part;
-                else if ((unsigned)cur < (unsigned)n_rows) y[cur] = part;
-                for (int rr = cur + 1; rr < rj && rr < n_rows; ++rr) y[rr] = 0.0;
-                cur = rj;
-                part = 0.0;
-                ++nseg;
-            }
-            part = fma(s_v[coo_pad(qb + j)], s_x[coo_pad(qb + j)], part);
-        }
+    for (int j = 0; j <= COO_ITEMS; ++j) {
+        const int q = qb + j - 1;
+        rr[j] = (q >= 0 && q < n) ? s_r[q] : -2;
     }
-    // block segmented exclusive scan of (row-start flag, last-row partial)
-    SegPair me;
-    me.f = (m > 0) && (nseg > 1 || !cont_prev);
-    me.v = (m > 0) ? part : 0.0;
-    const unsigned lane = lane_id();
-    const int w = threadIdx.x >> 5;
-    SegPair inc = me;
+    int cnt = 0;
+#pragma unroll
+    for (int j = 1; j <= COO_ITEMS; ++j) cnt += (qb + j - 1 < n) && (qb + j - 1 == 0 || rr[j] != rr[j - 1]);
+    int inc = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        SegPair up;
-        up.f = __shfl_up_sync(0xffffffffu, inc.f, o);
-        up.v = __shfl_up_sync(0xffffffffu, inc.v, o);
-        if ((int)lane >= o) inc = seg_combine(up, inc);
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if ((int)lane >= o) inc += t;
     }
-    SegPair ex;
-    ex.f = __shfl_up_sync(0xffffffffu, inc.f, 1);
-    ex.v = __shfl_up_sync(0xffffffffu, inc.v, 1);
-    if (lane == 0) { ex.f = 0; ex.v = 0.0; }
-    if (lane == 31) s_w[w] = inc;
+    if (lane == 31) s_wc[w] = inc;
     __syncthreads();
-    SegPair wp;
-    wp.f = 0;
-    wp.v = 0.0;
-    for (int j = 0; j < w; ++j) wp = seg_combine(wp, s_w[j]);
-    const SegPair carry_in = seg_combine(wp, ex);
-    if (m == 0) return;
-    const double cin_v = cont_prev ? carry_in.v : 0.0;
-    // first segment, if it ends inside this thread
-    if (nseg > 1) {
-        const double tot = first_part + cin_v;
-        if (r0 == ra && cin) carry[blockIdx.x].x = tot;
-        else if ((unsigned)r0 < (unsigned)n_rows) y[r0] = tot;
+    int off = inc - cnt, tot = 0;
+    for (int j = 0; j < COO_THREADS / 32; ++j) {
+        if (j < w) off += s_wc[j];
+        tot += s_wc[j];
     }
-    // last segment
-    const int lrow = cur;
-    const bool cont_next = (after < nnz) && next_row == lrow;
-    const double ltot = part + (nseg == 1 ? cin_v : 0.0);
-    if (cont_next) {
-        if (after >= t1) {  // continues into the next tile
-            carry[blockIdx.x].y = ltot;
-            if (lrow == ra && cin) carry[blockIdx.x].x = ltot;
+#pragma unroll
+    for (int j = 1; j <= COO_ITEMS; ++j)
+        if ((qb + j - 1 < n) && (qb + j - 1 == 0 || rr[j] != rr[j - 1])) s_seg[off++] = qb + j - 1;
+    if (threadIdx.x == 0) {
+        s_seg[tot] = n;
+        s_nseg = tot;
+    }
+    __syncthreads();
+    const int nseg = s_nseg;
+    const int prev_row = s_prev, next_row = s_next;
+    const bool last_tile = e0 + n >= nnz;
+    auto emit = [&](int g, int row, double sum) {
+        const bool cin = (g == 0) && prev_row == row;
+        const bool cout = (g == nseg - 1) && next_row == row;
+        if (cin || cout) {
+            if (cin) carry[blockIdx.x].x = sum;
+            if (cout) carry[blockIdx.x].y = sum;
+        } else if ((unsigned)row < (unsigned)n_rows) {
+            y[row] = sum;
         }
-    } else {
-        if (lrow == ra && cin) carry[blockIdx.x].x = ltot;
-        else if ((unsigned)lrow < (unsigned)n_rows) y[lrow] = ltot;
+        if (g == 0)
+            for (int q = prev_row + 1; q < row && q < n_rows; ++q) y[q] = 0.0;
+        const int upto = (g + 1 < nseg) ? s_r[s_seg[g + 1]] : (last_tile ? n_rows : row + 1);
+        for (int q = row + 1; q < upto && q < n_rows; ++q) y[q] = 0.0;
+    };
+    // threads per segment
+    int ns = 1;
+    while (ns < nseg && ns < COO_THREADS) ns <<= 1;
+    const int split = (ns >= COO_THREADS) ? 1 : min(8, COO_THREADS / ns);
+    const int gs = (split == 1) ? COO_THREADS : ns;
+    const int part = (int)threadIdx.x / gs;
+    for (int g0 = 0; g0 < nseg; g0 += gs) {
+        const int g = g0 + (int)threadIdx.x % gs;
+        double acc = 0.0;
+        bool mine = part < split && g < nseg;
+        int q0 = 0, q1 = 0;
+        if (mine) {
+            q0 = s_seg[g];
+            q1 = s_seg[g + 1];
+            if (q1 - q0 > COO_LONG) mine = false;
+        }
+        if (mine)
+            for (int q = q0 + part; q < q1; q += split) acc = fma(s_v[q], __ldg(x + s_c[q]), acc);
+        if (split > 1) {
+            if (mine && part > 0) s_part[threadIdx.x] = acc;
+            __syncthreads();
+            if (mine && part == 0)
+                for (int p = 1; p < split; ++p) acc += s_part[p * gs + threadIdx.x];
+            __syncthreads();
+        }
+        if (mine && part == 0) emit(g, s_r[q0], acc);
     }
-    // empty rows after the last entry of the matrix
-    if (after == nnz)
-        for (int rr = lrow + 1; rr < n_rows; ++rr) y[rr] = 0.0;
+    // long segments: one warp each
+    for (int g = w; g < nseg; g += COO_THREADS / 32) {
+        const int q0 = s_seg[g], q1 = s_seg[g + 1];
+        if (q1 - q0 <= COO_LONG) continue;
+        double acc = 0.0;
+        for (int q = q0 + (int)lane; q < q1; q += 32) acc = fma(s_v[q], __ldg(x + s_c[q]), acc);
+        acc = warp_sum(acc);
+        if (lane == 0) emit(g, s_r[q0], acc);
+    }
 }
 
 // Rows that cross tile edges: the tile where the row starts walks forward
@@ -662,7 +817,8 @@ __global__ void __launch_bounds__(256) k_coo_row_carry(const int32_t *__restrict
 
 cudaError_t launch_spmv_coo_row(const int32_t *irow, const int32_t *icol, const double *val, int64_t nnz,
                                 int32_t n_rows, int32_t n_cols, const double *x, double *y, void *scratch,
-                                cudaStream_t s) {
+                                int *status, cudaStream_t s) {
+    (void)status;  // no device-side waits in this kernel
     if (nnz <= 0) return cudaMemsetAsync(y, 0, sizeof(double) * (size_t)n_rows, s);
     const long long tiles = (nnz + COO_TILE - 1) / COO_TILE;
     double2 *carry = reinterpret_cast<double2 *>(scratch);

@@ -61,7 +61,7 @@ extern "C" spmv_status spmv_apply_coo_row_noalloc(int32_t n_rows, int32_t n_cols
     void *scratch = nullptr;
     spmv_status st = scratch_for_current_device(&scratch);
     if (st != SPMV_OK) return st;
-    if (launch_spmv_coo_row(irow, icol, val, nnz, n_rows, n_cols, x, y, scratch,
+    if (launch_spmv_coo_row(irow, icol, val, nnz, n_rows, n_cols, x, y, scratch, nullptr,
                             reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) {
         cudaGetLastError();
         return SPMV_ERR_CUDA;

@@ -1,5 +1,5 @@
 // Two-stage TMA pipeline that copies a contiguous range of a float64 array
-// (and optionally the same range of an int32 array) into shared memory.
+// (and the same range of up to two int32 arrays) into shared memory.
 //
 // One thread issues, for stage `st`, two 1-D bulk copies (cp.async.bulk) of
 // the 16-byte-aligned interior of the entry range [e0, e1); the few entries
@@ -17,15 +17,17 @@ namespace spmvat {
 struct StageMeta {
     long long e0, e1;    // the entry range of the tile
     long long a0v, b0v;  // staged value range [a0v, b0v)
-    long long a0i, b0i;  // staged index range [a0i, b0i)
+    long long a0i, b0i;  // staged index range [a0i, b0i) (both index arrays)
     int staged;
     int pad;
 };
 
-template <int CAP, bool WITH_IDX>
+// NIDX = number of int32 arrays staged with the float64 one (0, 1 or 2).
+template <int CAP, int NIDX>
 struct StagePipe {
+    static constexpr bool WITH_IDX = NIDX > 0;
     static constexpr size_t kHeader = 128;
-    static constexpr size_t kStage = (size_t)CAP * 8 + (WITH_IDX ? (size_t)CAP * 4 : 0);
+    static constexpr size_t kStage = (size_t)CAP * 8 + (size_t)NIDX * CAP * 4;
     static constexpr size_t kSmem = kHeader + 2 * kStage;
     static_assert(CAP % 4 == 0, "stage capacity must keep 16-byte alignment");
 
@@ -48,10 +50,13 @@ struct StagePipe {
     __device__ int32_t *sidx(int st) const {
         return reinterpret_cast<int32_t *>(base + st * kStage + (size_t)CAP * 8);
     }
+    __device__ int32_t *sidx2(int st) const {
+        return reinterpret_cast<int32_t *>(base + st * kStage + (size_t)CAP * 12);
+    }
 
-    // Thread 0 only. `can_stage`: both base pointers are 16-byte aligned.
+    // Thread 0 only. `can_stage`: all base pointers are 16-byte aligned.
     __device__ void issue(int st, long long e0, long long e1, const double *val, const int32_t *idx,
-                          bool can_stage) {
+                          bool can_stage, const int32_t *idx2 = nullptr) {
         StageMeta m;
         if (e1 < e0) e1 = e0;
         m.e0 = e0;
@@ -66,9 +71,10 @@ struct StagePipe {
         m.pad = 0;
         meta[st] = m;
         if (m.staged) {
-            mbar_arrive_expect_tx(&bar[st], bv + bi);
+            mbar_arrive_expect_tx(&bar[st], bv + (unsigned)NIDX * bi);
             if (bv) bulk_g2s(sval(st), val + m.a0v, bv, &bar[st]);
-            if (WITH_IDX && bi) bulk_g2s(sidx(st), idx + m.a0i, bi, &bar[st]);
+            if (NIDX >= 1 && bi) bulk_g2s(sidx(st), idx + m.a0i, bi, &bar[st]);
+            if (NIDX >= 2 && bi) bulk_g2s(sidx2(st), idx2 + m.a0i, bi, &bar[st]);
         } else {
             mbar_arrive_expect_tx(&bar[st], 0);
         }
@@ -83,6 +89,9 @@ struct StagePipe {
     __device__ __forceinline__ int32_t idx_at(const StageMeta &m, int st, const int32_t *idx, long long k) const {
         return (m.staged && k >= m.a0i && k < m.b0i) ? sidx(st)[k - m.a0i] : idx[k];
     }
+    __device__ __forceinline__ int32_t idx2_at(const StageMeta &m, int st, const int32_t *idx2, long long k) const {
+        return (m.staged && k >= m.a0i && k < m.b0i) ? sidx2(st)[k - m.a0i] : idx2[k];
+    }
 };
 
 // Standard loop over tiles with the pipeline. `range(tile, &e0, &e1)` gives
@@ -91,12 +100,12 @@ struct StagePipe {
 // flight and returns false.
 template <class Pipe, class RangeF, class BodyF>
 __device__ bool pipe_tiles(Pipe &P, int n_tiles, const double *val, const int32_t *idx, bool can_stage,
-                           int *status, RangeF range, BodyF body) {
+                           int *status, RangeF range, BodyF body, const int32_t *idx2 = nullptr) {
     int it = 0;
     if (threadIdx.x == 0 && (int)blockIdx.x < n_tiles) {
         long long e0, e1;
         range((int)blockIdx.x, &e0, &e1);
-        P.issue(0, e0, e1, val, idx, can_stage);
+        P.issue(0, e0, e1, val, idx, can_stage, idx2);
     }
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
         const int st = it & 1;
@@ -104,7 +113,7 @@ __device__ bool pipe_tiles(Pipe &P, int n_tiles, const double *val, const int32_
         if (threadIdx.x == 0 && next < n_tiles) {
             long long e0, e1;
             range(next, &e0, &e1);
-            P.issue(st ^ 1, e0, e1, val, idx, can_stage);
+            P.issue(st ^ 1, e0, e1, val, idx, can_stage, idx2);
         }
         const bool ok = P.wait(st, it >> 1);
         if (__syncthreads_or(!ok)) {

@@ -226,7 +226,7 @@ def test_unaligned_caller_arrays_take_the_global_path():
         M.close()
 
 
-@pytest.mark.parametrize("kernel,S", [("tile", 1), ("tile", 2), ("tile", 4), ("tile", 8), ("stream", 1),
+@pytest.mark.parametrize("kernel,S", [("rows", 1), ("rows", 2), ("rows", 4), ("rows", 8), ("tile", 1), ("tile", 2), ("tile", 4), ("tile", 8), ("stream", 1),
                                       ("stream", 2), ("stream", 4), ("stream", 8), ("vector", 0)])
 def test_crs_kernel_variants(monkeypatch, kernel, S):
     """Every CRS schedule the plan can pick gives results inside the tolerance."""
