@@ -167,12 +167,15 @@ __global__ void __launch_bounds__(EXP_THREADS) k_expand(const int32_t *__restric
     const long long k = k0 + (long long)threadIdx.x * EXP_ITEMS;
     if (k >= k1) return;
     int line = sm ? lo + last_le(s_ptr, 0, wn - 1, k) : last_le(ptr, lo, hi + 1, k);
+    // the next line's first entry stays in a register: one compare per entry
+    long long nb = (line < hi) ? (long long)(sm ? s_ptr[line + 1 - lo] : ptr[line + 1]) : LLONG_MAX;
     int v[EXP_ITEMS];
 #pragma unroll
     for (int j = 0; j < EXP_ITEMS; ++j) {
         const long long kk = k + j;
-        if (kk < k1) {
-            while (line < hi && (long long)(sm ? s_ptr[line + 1 - lo] : ptr[line + 1]) <= kk) ++line;
+        while (kk >= nb) {
+            ++line;
+            nb = (line < hi) ? (long long)(sm ? s_ptr[line + 1 - lo] : ptr[line + 1]) : LLONG_MAX;
         }
         v[j] = line;
     }
