@@ -114,6 +114,10 @@ def kernel_bytes(name: str, bm: dict, n_rows: int, n_cols: int, nnz: int):
     }
     if name.startswith("spmv_crs_"):
         return bm["spmv_crs"]
+    if name.startswith("spmv_coo_row_rows"):
+        return bm["spmv_coo_row"]
+    if name == "coo_row_tile_bounds":
+        return 8 * (n_rows // 128 + 1)
     return table.get(name)
 
 
@@ -448,8 +452,9 @@ def main():
         g = per_kernel[kname]["GB/s"]
         return {"GB/s": g, "pct_hbm": 100.0 * g / peak if g else None,
                 "ms": per_kernel[kname]["ms_per_launch"]}
-    crs_k = [k for k in per_kernel if k.startswith("spmv_crs_v")]
-    per_format = {"crs": fmt_rate(crs_k[0]) if crs_k else None, "coo_row": fmt_rate("spmv_coo_row"),
+    crs_k = [k for k in per_kernel if k.startswith("spmv_crs_")]
+    coo_k = [k for k in per_kernel if k.startswith("spmv_coo_row") and not k.endswith("carry")]
+    per_format = {"crs": fmt_rate(crs_k[0]) if crs_k else None, "coo_row": fmt_rate(coo_k[0]) if coo_k else None,
                   "ell_row": fmt_rate("spmv_ell_row"), "coo_col": fmt_rate("spmv_coo_col"),
                   "ell_col": fmt_rate("spmv_ell_col")}
     # CRS -> ELL cost in CRS-SpMV units: standalone build, and the fused

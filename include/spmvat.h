@@ -159,7 +159,8 @@ uint64_t spmv_ell_bytes(int32_t n_lines, int32_t width);
  *  - (SPMV_CRS, ROWWISE): the CRS itself plus its SpMV schedule (row bins);
  *    borrows IRP/ICOL/VAL. SYNC (runs spmv_analyze).
  *  - (SPMV_COO, ROWWISE): COO-Row, IROW(k) = row of entry k; borrows
- *    VAL/ICOL, which COO-Row shares with the CRS (Sec. 2.1). Asynchronous.
+ *    VAL/ICOL, which COO-Row shares with the CRS (Sec. 2.1). SYNC (it reads
+ *    the size of its SpMV tiles).
  *  - (SPMV_ELL, ROWWISE): ELL-Row, width W = longest row, each row's entries
  *    in CRS order in slots 0..len-1, padding slots value +0.0 with the
  *    column of the row's last entry (0 for an empty row). SYNC.
@@ -180,8 +181,8 @@ spmv_status spmv_transform(const spmv_crs *A, spmv_format format, spmv_layout la
  * (SPMV_CRS, COLWISE) or (SPMV_COO, COLWISE) handle (an ELL-Column handle
  * does not keep its CCS): to SPMV_COO (COO-Column, Phase II of Sec. 2.1) or
  * SPMV_ELL (ELL-Column). The new handle shares the CCS arrays with `src`;
- * the two may be destroyed in any order. SPMV_ELL is SYNC (it reads the
- * longest column), SPMV_COO asynchronous. */
+ * the two may be destroyed in any order. Asynchronous; a bounded wait of the
+ * ELL build that runs out is reported by spmv_matrix_status. */
 spmv_status spmv_transform_from(const spmv_matrix *src, spmv_format format,
                                 uint64_t mem_cap_bytes, spmv_matrix **out,
                                 spmv_stream_t stream);
@@ -200,9 +201,9 @@ spmv_status spmv_transform_apply(const spmv_crs *A, const double *x, double *y,
                                  uint64_t mem_cap_bytes, spmv_matrix **out,
                                  spmv_stream_t stream);
 
-/* SYNC. Reports whether any bounded device wait inside spmv_apply on this
- * handle has run out since the handle was built (SPMV_ERR_TIMEOUT), else
- * SPMV_OK. spmv_apply itself does not wait for the stream. */
+/* SYNC. Reports whether any bounded device wait in the asynchronous build of
+ * this handle or inside spmv_apply on it has run out (SPMV_ERR_TIMEOUT), else
+ * SPMV_OK. Neither of those calls waits for the stream. */
 spmv_status spmv_matrix_status(const spmv_matrix *M, spmv_stream_t stream);
 
 /* Fill `out` with the handle's arrays and sizes. */

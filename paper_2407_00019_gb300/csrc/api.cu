@@ -168,6 +168,9 @@ struct spmv_matrix {
     // CRS schedule
     int crs_binned = 0;
     int crs_v = 1;
+    int coo_rows_split = 0;        // > 0: COO-Row over row-aligned tiles, threads per row
+    int coo_rows_cap = 0;          //      shared-memory entries per tile
+    const int32_t *coo_tb = nullptr; //    tile bounds
     int crs_rows_split = 0;        // > 0: ELL-order row-tile kernel, threads per row
     int crs_rows_cap = 0;          //      and its shared-memory capacity (entries)
     int crs_tile_s = 0;            // > 0: row-tile kernel with S lanes per row
@@ -357,6 +360,25 @@ spmv_status build_coo_row(const spmv_crs *A, uint64_t cap, spmv_matrix **out, cu
     CK(cudaMemsetAsync(sw->p, 0, 16, s));
     M->status = reinterpret_cast<int *>(sw->p);
     M->bufs.push_back(sw);
+    // SpMV schedule: row-aligned tiles when the largest tile fits shared memory
+    if (A->nnz > 0) {
+        const int64_t tiles = ((int64_t)A->n_rows + 127) / 128;
+        BufPtr tb;
+        CKS(alloc_buf((size_t)(tiles + 1) * 4, s, &tb));
+        int32_t *maxn = reinterpret_cast<int32_t *>(sw->p) + 1;  // second word of the status block
+        CK(launch_row_tile_bounds(reinterpret_cast<const int32_t *>(irow->p), A->nnz, A->n_rows,
+                                  reinterpret_cast<int32_t *>(tb->p), maxn, s));
+        int h[2] = {0, 0};
+        CK(cudaMemcpyAsync(h, sw->p, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const int cap = coo_rows_cap(h[1]);
+        if (cap > 0 && !getenv("SPMVAT_COO_ENTRY_TILES")) {
+            M->coo_rows_cap = cap;
+            M->coo_rows_split = ((double)A->nnz / A->n_rows <= 8.0) ? 2 : 4;
+            M->coo_tb = reinterpret_cast<const int32_t *>(tb->p);
+            M->bufs.push_back(tb);
+        }
+    }
     M->ptr = A->irp;
     M->idx = A->icol;
     M->idx2 = reinterpret_cast<const int32_t *>(irow->p);
@@ -402,7 +424,7 @@ spmv_status build_ell_row(const spmv_crs *A, const spmv_stats &st, uint64_t cap,
 // `ell_cap_check`: when >= 0, fail with MEMORY_CAP before building if an
 // ELL-Column of the longest column would exceed it (checked after the count).
 spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bool want_ell,
-                   std::unique_ptr<spmv_matrix> &M, cudaStream_t s) {
+                   std::unique_ptr<spmv_matrix> &M, cudaStream_t s, const int *irp_status) {
     const int64_t nnz = A->nnz;
     const int32_t nc = A->n_cols;
     const uint64_t own = (uint64_t)(nc + 1) * 4 + (uint64_t)nnz * 12;
@@ -424,10 +446,13 @@ spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bo
     CK(launch_col_count(A->icol, nnz, nc, d_cp, reinterpret_cast<int32_t *>(rank->p), d_status, s));
     CK(launch_scan(d_cp, nc, scan_scr->p, d_colmax, 32, d_long + 1, d_long, d_status, kSpinLimit, 0, s));
     int hw[2] = {0, 0};
+    int hirp = 0;
     if (want_ell) {
         // the ELL-Column width decides the cap check before anything else is built
         CK(cudaMemcpyAsync(hw, words->p, sizeof(hw), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&hirp, irp_status, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        CKS(status_from_dev(hirp));
         CKS(status_from_dev(hw[0]));
         if (cap_ell_col && ell_bytes(nc, hw[1]) > cap_ell_col) return SPMV_ERR_MEMORY_CAP;
     }
@@ -442,7 +467,9 @@ spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bo
                         reinterpret_cast<int32_t *>(rank->p), reinterpret_cast<int32_t *>(trow->p),
                         reinterpret_cast<double *>(tval->p), d_status, s));
     CK(cudaMemcpyAsync(hw, words->p, sizeof(hw), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&hirp, irp_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    CKS(status_from_dev(hirp));
     CKS(status_from_dev(hw[0]));
     const int32_t colmax = hw[1];
     M->ptr = d_cp;
@@ -473,15 +500,14 @@ spmv_status ell_col_from_ccs(const spmv_matrix *src, uint64_t cap, spmv_matrix *
     CK(launch_lines_to_ell(src->ptr, src->idx, src->val, src->n_cols, src->n_rows, W, ld,
                            reinterpret_cast<double *>(ev->p), reinterpret_cast<int32_t *>(ei->p), nullptr, nullptr,
                            reinterpret_cast<int *>(stw->p), s, "ccs_to_ell_col"));
-    int hst = 0;
-    CK(cudaMemcpyAsync(&hst, stw->p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    CKS(status_from_dev(hst));
+    // The CCS indices were produced and checked by Phase I, so only a bounded
+    // wait of the build can fail: it is reported by spmv_matrix_status.
     M->width = W;
     M->ld = ld;
     M->idx = reinterpret_cast<const int32_t *>(ei->p);
     M->val = reinterpret_cast<const double *>(ev->p);
-    M->bufs = {ev, ei};
+    M->status = reinterpret_cast<int *>(stw->p);
+    M->bufs = {ev, ei, stw};
     *out = M.release();
     return SPMV_OK;
 }
@@ -539,6 +565,11 @@ spmv_status apply_core(const spmv_matrix *M, const double *x, double *y, cudaStr
                 }
                 return SPMV_OK;
             case SPMV_COO: {
+                if (M->coo_rows_split > 0) {
+                    CK(launch_spmv_coo_row_rows(M->coo_rows_split, M->coo_rows_cap, M->idx2, M->idx, M->val, M->coo_tb,
+                                                M->n_rows, M->n_cols, x, y, s));
+                    return SPMV_OK;
+                }
                 BufPtr scr;
                 CKS(alloc_buf(coo_row_scratch_bytes(M->nnz), s, &scr));
                 CK(launch_spmv_coo_row(M->idx2, M->idx, M->val, M->nnz, M->n_rows, M->n_cols, x, y, scr->p,
@@ -666,11 +697,15 @@ spmv_status spmv_transform(const spmv_crs *A, spmv_format format, spmv_layout la
     // column-wise: Phase I first
     std::unique_ptr<spmv_matrix> M(new_handle(A, SPMV_CRS, SPMV_COLWISE, s));
     if (!M) return SPMV_ERR_OOM;
-    {
-        spmv_stats st;
-        CKS(analyze_core(A, false, &st, s));  // IRP checks before Phase I
-    }
-    CKS(phase1(A, format == SPMV_CRS ? mem_cap_bytes : 0, mem_cap_bytes, format == SPMV_ELL, M, s));
+    // IRP checks run ahead of Phase I; their result is read with Phase I's own
+    // status at its final synchronisation (Phase I kernels stay in bounds on
+    // any IRP).
+    BufPtr acc_buf;
+    CKS(alloc_buf(sizeof(AnalyzeAcc), s, &acc_buf));
+    CK(cudaMemsetAsync(acc_buf->p, 0, sizeof(AnalyzeAcc), s));
+    CK(launch_analyze(A->irp, A->n_rows, A->nnz, reinterpret_cast<AnalyzeAcc *>(acc_buf->p), s));
+    const int *irp_status = &reinterpret_cast<AnalyzeAcc *>(acc_buf->p)->status;
+    CKS(phase1(A, format == SPMV_CRS ? mem_cap_bytes : 0, mem_cap_bytes, format == SPMV_ELL, M, s, irp_status));
     M->bufs = M->ccs_bufs;
     if (format == SPMV_CRS) {
         *out = M.release();

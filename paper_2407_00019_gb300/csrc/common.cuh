@@ -203,6 +203,13 @@ size_t coo_row_scratch_bytes(int64_t nnz);
 cudaError_t launch_spmv_coo_row(const int32_t *irow, const int32_t *icol, const double *val, int64_t nnz,
                                 int32_t n_rows, int32_t n_cols, const double *x, double *y, void *scratch,
                                 int *status, cudaStream_t s);
+// row-aligned COO-Row: tile bounds (int32[ceil(n_rows/128) + 1]) and largest tile
+cudaError_t launch_row_tile_bounds(const int32_t *irow, int64_t nnz, int32_t n_rows, int32_t *tb, int32_t *maxn,
+                                   cudaStream_t s);
+int coo_rows_cap(int max_n);
+cudaError_t launch_spmv_coo_row_rows(int split, int cap, const int32_t *irow, const int32_t *icol,
+                                     const double *val, const int32_t *tb, int32_t n_rows, int32_t n_cols,
+                                     const double *x, double *y, cudaStream_t s);
 cudaError_t launch_spmv_coo_col(const int32_t *row, const int32_t *col, const double *val, int64_t nnz,
                                 int32_t n_rows, const double *x, double *y, cudaStream_t s);
 cudaError_t launch_spmv_ccs(const int32_t *cp, const int32_t *trow, const double *tval, int32_t n_rows,

@@ -638,6 +638,7 @@ cudaError_t launch_spmv_ell_col(const double *eval, const int32_t *eidx, int32_t
 }
 
 // ================================================================= COO-Row
+constexpr int COO_ROWS_R = 128;  // rows per tile of the row-aligned COO-Row kernel
 constexpr int COO_THREADS = 256;
 constexpr int COO_ITEMS = 8;
 constexpr int COO_TILE = COO_THREADS * COO_ITEMS;
@@ -789,6 +790,159 @@ __global__ void __launch_bounds__(COO_THREADS) k_coo_row_tiles(const int32_t *__
         acc = warp_sum(acc);
         if (lane == 0) emit(g, s_r[q0], acc);
     }
+}
+
+// ---- COO-Row over row-aligned tiles --------------------------------------
+// tb[t] = first entry of row t*R in the row-sorted IROW (one parallel
+// binary search per tile); *maxn = the largest tile's entry count.
+__global__ void __launch_bounds__(256) k_row_tile_bounds(const int32_t *__restrict__ irow, int64_t nnz, int R,
+                                                          long long n_tiles, int32_t *__restrict__ tb,
+                                                          int32_t *__restrict__ maxn) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > n_tiles) return;
+    long long lo = 0, hi = nnz;  // first index with irow >= t*R
+    const long long key = t * R;
+    if (t == n_tiles) {
+        lo = nnz;
+    } else {
+        while (lo < hi) {
+            const long long mid = (lo + hi) >> 1;
+            if ((long long)__ldg(irow + mid) < key) lo = mid + 1; else hi = mid;
+        }
+    }
+    tb[t] = (int32_t)lo;
+    // the tile size needs the next bound: search for it too
+    if (t < n_tiles) {
+        long long lo2 = lo, hi2 = nnz;
+        const long long key2 = (t + 1) * R;
+        while (lo2 < hi2) {
+            const long long mid = (lo2 + hi2) >> 1;
+            if ((long long)__ldg(irow + mid) < key2) lo2 = mid + 1; else hi2 = mid;
+        }
+        atomicMax(maxn, (int32_t)(lo2 - lo));
+    }
+}
+
+cudaError_t launch_row_tile_bounds(const int32_t *irow, int64_t nnz, int32_t n_rows, int32_t *tb, int32_t *maxn,
+                                   cudaStream_t s) {
+    const long long n_tiles = ((long long)n_rows + COO_ROWS_R - 1) / COO_ROWS_R;
+    KernelScope ks("coo_row_tile_bounds", s);
+    k_row_tile_bounds<<<ceil_div_u(n_tiles + 1, 256), 256, 0, s>>>(irow, nnz, COO_ROWS_R, n_tiles, tb, maxn);
+    return cudaGetLastError();
+}
+
+// A CTA takes 128 consecutive rows: their entries [tb[t], tb[t+1]) are
+// loaded into shared memory with coalesced loads, each row finds its first
+// entry by binary search over the staged IROW, then SPLIT threads per row run
+// the FMA chains with lanes on consecutive rows (as k_spmv_crs_rows). Rows
+// never cross tiles, so no partial sums are carried.
+template <int SPLIT>
+__global__ void __launch_bounds__(COO_ROWS_R *SPLIT) k_coo_row_rows(const int32_t *__restrict__ irow,
+                                                                     const int32_t *__restrict__ icol,
+                                                                     const double *__restrict__ val,
+                                                                     const int32_t *__restrict__ tb, int32_t n_rows,
+                                                                     int32_t n_cols, int cap,
+                                                                     const double *__restrict__ x,
+                                                                     double *__restrict__ y) {
+    constexpr int R = COO_ROWS_R;
+    constexpr int T = R * SPLIT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *s_v = reinterpret_cast<double *>(smem);
+    int32_t *s_c = reinterpret_cast<int32_t *>(s_v + cap);
+    int32_t *s_r = s_c + cap;
+    __shared__ int32_t s_ptr[R + 1];
+    __shared__ double s_part[SPLIT > 1 ? (SPLIT - 1) * R : 1];
+    const long long r0 = (long long)blockIdx.x * R;
+    const int nr = (int)min((long long)R, (long long)n_rows - r0);
+    const int e0 = __ldg(tb + blockIdx.x), e1 = __ldg(tb + blockIdx.x + 1);
+    const int n = e1 - e0;  // <= cap by construction of the schedule
+    for (int q0 = threadIdx.x; q0 < n; q0 += 8 * T) {
+        double v[8];
+        int c[8], r[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u * T;
+            v[u] = (q < n) ? __ldcs(val + e0 + q) : 0.0;
+            c[u] = (q < n) ? __ldcs(icol + e0 + q) : 0;
+            r[u] = (q < n) ? __ldcs(irow + e0 + q) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u * T;
+            if (q < n) {
+                const bool ok = (unsigned)c[u] < (unsigned)n_cols;
+                s_v[q] = ok ? v[u] : 0.0;
+                s_c[q] = ok ? c[u] : 0;
+                s_r[q] = r[u];
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x <= (unsigned)nr) {  // first entry of row r0 + i: lower bound in s_r
+        const long long key = r0 + threadIdx.x;
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((long long)s_r[mid] < key) lo = mid + 1; else hi = mid;
+        }
+        s_ptr[threadIdx.x] = lo;
+    }
+    __syncthreads();
+    const int r = threadIdx.x % R, part = threadIdx.x / R;
+    double acc = 0.0;
+    if (r < nr) {
+        const int s = s_ptr[r], e = s_ptr[r + 1];
+        int k = s + part;
+        for (; k + 3 * SPLIT < e; k += 4 * SPLIT) {
+            const int c0 = s_c[k], c1 = s_c[k + SPLIT], c2 = s_c[k + 2 * SPLIT], c3 = s_c[k + 3 * SPLIT];
+            const double x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+            acc = fma(s_v[k], x0, acc);
+            acc = fma(s_v[k + SPLIT], x1, acc);
+            acc = fma(s_v[k + 2 * SPLIT], x2, acc);
+            acc = fma(s_v[k + 3 * SPLIT], x3, acc);
+        }
+        for (; k < e; k += SPLIT) acc = fma(s_v[k], __ldg(x + s_c[k]), acc);
+    }
+    if (SPLIT > 1) {
+        if (part > 0) s_part[(part - 1) * R + r] = acc;
+        __syncthreads();
+        if (part == 0)
+            for (int p = 1; p < SPLIT; ++p) acc += s_part[(p - 1) * R + r];
+    }
+    if (part == 0 && r < nr) y[r0 + r] = acc;
+}
+
+// shared-memory entries for row tiles whose largest tile has max_n entries
+// (0: would leave fewer than two CTAs per SM)
+int coo_rows_cap(int max_n) {
+    const long long cap = ((long long)(max_n > 0 ? max_n : 1) + 3) & ~3ll;
+    return cap * 16 <= 96 * 1024 ? (int)cap : 0;
+}
+
+cudaError_t launch_spmv_coo_row_rows(int split, int cap, const int32_t *irow, const int32_t *icol,
+                                     const double *val, const int32_t *tb, int32_t n_rows, int32_t n_cols,
+                                     const double *x, double *y, cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    if (cap <= 0) return cudaErrorInvalidValue;
+    const unsigned grid = ceil_div_u(n_rows, COO_ROWS_R);
+    const size_t smem = (size_t)cap * 16;
+    switch (split) {
+#define COOR_CASE(SP)                                                                                  \
+    case SP: {                                                                                         \
+        cudaError_t e = set_smem_attr(k_coo_row_rows<SP>, smem);                                       \
+        if (e != cudaSuccess) return e;                                                                \
+        KernelScope ks("spmv_coo_row_rows_p" #SP, s);                                                  \
+        k_coo_row_rows<SP><<<grid, COO_ROWS_R * SP, smem, s>>>(irow, icol, val, tb, n_rows, n_cols, cap, x, y); \
+        break;                                                                                         \
+    }
+        COOR_CASE(1)
+        COOR_CASE(2)
+        COOR_CASE(4)
+#undef COOR_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 // Rows that cross tile edges: the tile where the row starts walks forward

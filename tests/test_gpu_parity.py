@@ -242,3 +242,19 @@ def test_crs_kernel_variants(monkeypatch, kernel, S):
         assert_spmv_close(run_apply(M, torch.from_numpy(xh).cuda(), H.n_rows), H, xh, what=f"{name}/{kernel}{S}")
         L.spmv_matrix_status(M)
         M.close()
+
+
+@pytest.mark.parametrize("entry_tiles", [False, True])
+def test_coo_row_schedules(monkeypatch, entry_tiles):
+    """Row-aligned tiles and entry tiles with carries agree with the oracle."""
+    import torch
+    L = lib()
+    if entry_tiles:
+        monkeypatch.setenv("SPMVAT_COO_ENTRY_TILES", "1")
+    for name in ("laplace37x23", "stencil27_24", "random_empty_rows", "long_row", "all_empty"):
+        H = case(name)
+        xh = xvec(H.n_cols, seed=8)
+        M = L.spmv_transform(dev(H), L.SPMV_COO, L.SPMV_ROWWISE)
+        assert_spmv_close(run_apply(M, torch.from_numpy(xh).cuda(), H.n_rows), H, xh,
+                          what=f"{name}/entry_tiles={entry_tiles}")
+        M.close()
