@@ -107,6 +107,11 @@ def kernel_bytes(name: str, bm: dict, n_rows: int, n_cols: int, nnz: int):
         "scan_lookback": 8 * n_cols,
         "col_scatter": 16 * nnz + 4 * (n_rows + 1) + 4 * n_cols,
         "col_fixup_tiles": 28 * nnz + 4 * n_cols,
+        # slot path: ICOL in, rank out, (k, row) into the slot array; slots in,
+        # VAL gathered, ICOL_T + VAL_T out
+        "col_claim": 16 * nnz + 4 * (n_rows + 1) + 4 * n_cols,
+        "col_fixup_slots": 28 * nnz + 4 * n_cols,
+        "col_overflow": 0,
         "tile_lines": 4 * (nnz // 2048 + 1),
         "spmv_coo_row_carry": 16 * (nnz // 2048 + 1),
         "col_fixup_block": 0,

@@ -443,7 +443,22 @@ spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bo
     CK(cudaMemsetAsync(d_cp, 0, (size_t)(nc + 1) * 4, s));
     CK(cudaMemsetAsync(words->p, 0, 64, s));
     CK(cudaMemsetAsync(d_long, 0, 4, s));
-    CK(launch_col_count(A->icol, nnz, nc, d_cp, reinterpret_cast<int32_t *>(rank->p), d_status, s));
+    // Slot path (count and placement in one pass, placement into a
+    // slot-major array) when that array is at most 4x the pairs array, i.e.
+    // columns hold 8 or more entries on average; else count, then scatter.
+    const bool slots = !getenv("SPMVAT_PHASE1_SCATTER") &&
+                       (int64_t)col_slot_cap() * nc <= 4 * nnz && nnz > 0;
+    BufPtr tslots, sct0;
+    int32_t *d_over = reinterpret_cast<int32_t *>(words->p) + 2;
+    if (slots) {
+        CKS(alloc_buf(col_slot_bytes(nc), s, &tslots));
+        CKS(alloc_buf(col_scatter_scratch_bytes(nnz), s, &sct0));
+        CK(launch_col_claim(A->irp, A->n_rows, A->icol, nnz, nc, d_cp, reinterpret_cast<int32_t *>(rank->p),
+                            reinterpret_cast<int2 *>(tslots->p), d_over, reinterpret_cast<int32_t *>(sct0->p),
+                            d_status, s));
+    } else {
+        CK(launch_col_count(A->icol, nnz, nc, d_cp, reinterpret_cast<int32_t *>(rank->p), d_status, s));
+    }
     CK(launch_scan(d_cp, nc, scan_scr->p, d_colmax, 32, d_long + 1, d_long, d_status, kSpinLimit, 0, s));
     int hw[2] = {0, 0};
     int hirp = 0;
@@ -456,16 +471,28 @@ spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bo
         CKS(status_from_dev(hw[0]));
         if (cap_ell_col && ell_bytes(nc, hw[1]) > cap_ell_col) return SPMV_ERR_MEMORY_CAP;
     }
-    BufPtr sct;
     CKS(alloc_buf((size_t)nnz * 4, s, &trow));
     CKS(alloc_buf((size_t)nnz * 8, s, &tval));
     CKS(alloc_buf((size_t)nnz * 8 + 16, s, &pairs));  // slack: staged copies round the end up
-    CKS(alloc_buf(col_scatter_scratch_bytes(nnz), s, &sct));
-    CK(launch_col_scatter(A->irp, A->n_rows, A->icol, nnz, nc, d_cp, reinterpret_cast<int32_t *>(rank->p),
-                          reinterpret_cast<int2 *>(pairs->p), reinterpret_cast<int32_t *>(sct->p), d_status, s));
-    CK(launch_col_fixup(d_cp, nc, A->irp, A->n_rows, A->val, reinterpret_cast<int2 *>(pairs->p), d_long + 1,
-                        reinterpret_cast<int32_t *>(rank->p), reinterpret_cast<int32_t *>(trow->p),
-                        reinterpret_cast<double *>(tval->p), d_status, s));
+    if (slots) {
+        // entries beyond the slot capacity (long columns) go to the pairs
+        // array at IRP_T[col] + rank; the grid exits at once when there are none
+        CK(launch_col_scatter(A->irp, A->n_rows, A->icol, nnz, nc, d_cp, reinterpret_cast<int32_t *>(rank->p),
+                              reinterpret_cast<int2 *>(pairs->p), reinterpret_cast<int32_t *>(sct0->p), d_status, s,
+                              col_slot_cap(), d_over, true));
+        CK(launch_col_fixup_slots(d_cp, nc, A->irp, A->n_rows, A->val, reinterpret_cast<const int2 *>(tslots->p),
+                                  reinterpret_cast<int2 *>(pairs->p), d_long + 1,
+                                  reinterpret_cast<int32_t *>(rank->p), reinterpret_cast<int32_t *>(trow->p),
+                                  reinterpret_cast<double *>(tval->p), s));
+    } else {
+        BufPtr sct;
+        CKS(alloc_buf(col_scatter_scratch_bytes(nnz), s, &sct));
+        CK(launch_col_scatter(A->irp, A->n_rows, A->icol, nnz, nc, d_cp, reinterpret_cast<int32_t *>(rank->p),
+                              reinterpret_cast<int2 *>(pairs->p), reinterpret_cast<int32_t *>(sct->p), d_status, s));
+        CK(launch_col_fixup(d_cp, nc, A->irp, A->n_rows, A->val, reinterpret_cast<int2 *>(pairs->p), d_long + 1,
+                            reinterpret_cast<int32_t *>(rank->p), reinterpret_cast<int32_t *>(trow->p),
+                            reinterpret_cast<double *>(tval->p), d_status, s));
+    }
     CK(cudaMemcpyAsync(hw, words->p, sizeof(hw), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&hirp, irp_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

@@ -167,9 +167,22 @@ cudaError_t launch_scan(int32_t *a, int64_t n, void *scratch, int32_t *maxv, int
                         int32_t *long_list, int32_t *long_count, int *status, long long spin_limit,
                         int debug_stall_first, cudaStream_t s);
 size_t col_scatter_scratch_bytes(int64_t nnz);
+// Places entries with rank >= min_rank at IRP_T[col] + rank as (k, row).
+// With only_if != NULL the grid returns at once when *only_if == 0.
+// have_tile_lines: `scratch` already holds the tile lines of this nnz.
 cudaError_t launch_col_scatter(const int32_t *irp, int32_t n_rows, const int32_t *icol, int64_t nnz,
                                int32_t n_cols, const int32_t *cp, const int32_t *rank, int2 *pairs,
-                               int32_t *scratch, int *status, cudaStream_t s);
+                               int32_t *scratch, int *status, cudaStream_t s, int min_rank = 0,
+                               const int32_t *only_if = nullptr, bool have_tile_lines = false);
+// Slot path of Phase I: count + place ranks < col_slot_cap() in T (slot-major).
+size_t col_slot_bytes(int32_t n_cols);
+int col_slot_cap();
+cudaError_t launch_col_claim(const int32_t *irp, int32_t n_rows, const int32_t *icol, int64_t nnz, int32_t n_cols,
+                             int32_t *nc, int32_t *rank, int2 *T, int32_t *n_over, int32_t *scratch, int *status,
+                             cudaStream_t s);
+cudaError_t launch_col_fixup_slots(const int32_t *cp, int32_t n_cols, const int32_t *irp, int32_t n_rows,
+                                   const double *val, const int2 *T, int2 *pairs, const int32_t *long_list,
+                                   int32_t *keys_tmp, int32_t *trow, double *tval, cudaStream_t s);
 // `pairs` must have 16 bytes of slack after its nnz elements.
 // `long_list` is preceded by its device-side count.
 cudaError_t launch_col_fixup(const int32_t *cp, int32_t n_cols, const int32_t *irp, int32_t n_rows,

@@ -211,14 +211,17 @@ constexpr int SCT_THREADS = 256;
 constexpr int SCT_ITEMS = 8;
 constexpr int SCT_TILE = SCT_THREADS * SCT_ITEMS;
 constexpr int SCT_WIN = 2048;
+constexpr int SLOT_CAP = 32;  // ranks kept in the slot-major array T
 
 __global__ void __launch_bounds__(SCT_THREADS) k_col_scatter(const int32_t *__restrict__ irp, int32_t n_rows,
                                                               const int32_t *__restrict__ icol, int64_t nnz,
                                                               int32_t n_cols, const int32_t *__restrict__ cp,
                                                               const int32_t *__restrict__ rank,
                                                               const int32_t *__restrict__ tl, long long n_tiles,
-                                                              int2 *__restrict__ pairs, int *status) {
+                                                              int2 *__restrict__ pairs, int *status, int min_rank,
+                                                              const int32_t *__restrict__ only_if) {
     __shared__ int32_t s_ptr[SCT_WIN];
+    if (only_if && *only_if == 0) return;  // nothing to place: the whole grid returns at once
     const long long k0 = (long long)blockIdx.x * SCT_TILE;
     const long long k1 = min(k0 + (long long)SCT_TILE, (long long)nnz);
     const long long k = k0 + (long long)threadIdx.x * SCT_ITEMS;
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(SCT_THREADS) k_col_scatter(const int32_t *__re
     for (int j = 0; j < SCT_ITEMS; ++j) {
         const bool ok = (k + j < k1) && (unsigned)c[j] < (unsigned)n_cols;
         bad |= (k + j < k1) && !ok;
-        pos[j] = ok ? (long long)__ldg(cp + c[j]) + r[j] : -1;
+        pos[j] = (ok && r[j] >= min_rank) ? (long long)__ldg(cp + c[j]) + r[j] : -1;
     }
     const int lo = tl[blockIdx.x];
     const int hi = (blockIdx.x + 1 < n_tiles) ? tl[blockIdx.x + 1] : n_rows - 1;
@@ -273,14 +276,100 @@ size_t col_scatter_scratch_bytes(int64_t nnz) { return tile_lines_bytes(nnz, SCT
 
 cudaError_t launch_col_scatter(const int32_t *irp, int32_t n_rows, const int32_t *icol, int64_t nnz,
                                int32_t n_cols, const int32_t *cp, const int32_t *rank, int2 *pairs,
-                               int32_t *scratch, int *status, cudaStream_t s) {
+                               int32_t *scratch, int *status, cudaStream_t s, int min_rank,
+                               const int32_t *only_if, bool have_tile_lines) {
+    if (nnz <= 0) return cudaSuccess;
+    if (!have_tile_lines) {
+        cudaError_t e = launch_tile_lines(irp, n_rows, nnz, SCT_TILE, scratch, s);
+        if (e != cudaSuccess) return e;
+    }
+    const long long n_tiles = (nnz + SCT_TILE - 1) / SCT_TILE;
+    KernelScope ks(min_rank > 0 ? "col_overflow" : "col_scatter", s);
+    k_col_scatter<<<(unsigned)n_tiles, SCT_THREADS, 0, s>>>(irp, n_rows, icol, nnz, n_cols, cp, rank, scratch,
+                                                             n_tiles, pairs, status, min_rank, only_if);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- claim
+// Count and place in one pass (the slot path of Phase I). For entry k of row
+// i in column j: r = atomicAdd(NC[j], 1) is its rank; when r < SLOT_CAP the
+// pair (k, i) goes straight to T[r * n_cols + j], a slot-major array like an
+// ELL over columns, so the fix-up can read a column tile with coalesced
+// loads. Ranks are stored for every entry; entries with r >= SLOT_CAP are
+// counted in *n_over and placed later by k_col_scatter (min_rank = SLOT_CAP).
+__global__ void __launch_bounds__(SCT_THREADS) k_col_claim(const int32_t *__restrict__ irp, int32_t n_rows,
+                                                            const int32_t *__restrict__ icol, int64_t nnz,
+                                                            int32_t n_cols, int32_t *__restrict__ nc,
+                                                            int32_t *__restrict__ rank,
+                                                            const int32_t *__restrict__ tl, long long n_tiles,
+                                                            int2 *__restrict__ T, int32_t *__restrict__ n_over,
+                                                            int *status) {
+    __shared__ int32_t s_ptr[SCT_WIN];
+    const long long k0 = (long long)blockIdx.x * SCT_TILE;
+    const long long k1 = min(k0 + (long long)SCT_TILE, (long long)nnz);
+    const long long k = k0 + (long long)threadIdx.x * SCT_ITEMS;
+    int c[SCT_ITEMS];
+    if (k + SCT_ITEMS <= k1 && ((reinterpret_cast<uintptr_t>(icol + k) & 15) == 0)) {
+#pragma unroll
+        for (int h = 0; h < SCT_ITEMS / 4; ++h) {
+            const int4 q = __ldcs(reinterpret_cast<const int4 *>(icol + k) + h);
+            c[4 * h] = q.x; c[4 * h + 1] = q.y; c[4 * h + 2] = q.z; c[4 * h + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < SCT_ITEMS; ++j) c[j] = (k + j < k1) ? icol[k + j] : -1;
+    }
+    int r[SCT_ITEMS];
+    int bad = 0, over = 0;
+#pragma unroll
+    for (int j = 0; j < SCT_ITEMS; ++j) {
+        const bool has = k + j < k1;
+        const bool ok = has && (unsigned)c[j] < (unsigned)n_cols;
+        bad |= has && !ok;
+        r[j] = ok ? atomicAdd(nc + c[j], 1) : -1;
+    }
+    const int lo = tl[blockIdx.x];
+    const int hi = (blockIdx.x + 1 < n_tiles) ? tl[blockIdx.x + 1] : n_rows - 1;
+    const int wn = hi - lo + 2;
+    const bool sm = wn <= SCT_WIN;
+    if (sm)
+        for (int i = threadIdx.x; i < wn; i += SCT_THREADS) s_ptr[i] = irp[lo + i];
+    __syncthreads();
+    if (k < k1) {
+        int row = sm ? lo + last_le(s_ptr, 0, wn - 1, k) : last_le(irp, lo, hi + 1, k);
+#pragma unroll
+        for (int j = 0; j < SCT_ITEMS; ++j) {
+            const long long kk = k + j;
+            if (kk >= k1) break;
+            while (row < hi && (long long)(sm ? s_ptr[row + 1 - lo] : irp[row + 1]) <= kk) ++row;
+            if (r[j] < 0) continue;
+            if (r[j] < SLOT_CAP) T[(long long)r[j] * n_cols + c[j]] = make_int2((int)kk, row);
+            else over = 1;
+        }
+        if (k + SCT_ITEMS <= k1 && ((reinterpret_cast<uintptr_t>(rank + k) & 15) == 0)) {
+#pragma unroll
+            for (int h = 0; h < SCT_ITEMS / 4; ++h)
+                __stcs(reinterpret_cast<int4 *>(rank + k) + h, make_int4(r[4 * h], r[4 * h + 1], r[4 * h + 2], r[4 * h + 3]));
+        } else {
+#pragma unroll
+            for (int j = 0; j < SCT_ITEMS; ++j)
+                if (k + j < k1) rank[k + j] = r[j];
+        }
+    }
+    if (__any_sync(0xffffffffu, over) && lane_id() == 0) atomicAdd(n_over, 1);
+    if (__any_sync(0xffffffffu, bad) && lane_id() == 0) atomicOr(status, ST_BAD_INDEX);
+}
+
+cudaError_t launch_col_claim(const int32_t *irp, int32_t n_rows, const int32_t *icol, int64_t nnz, int32_t n_cols,
+                             int32_t *nc, int32_t *rank, int2 *T, int32_t *n_over, int32_t *scratch, int *status,
+                             cudaStream_t s) {
     if (nnz <= 0) return cudaSuccess;
     cudaError_t e = launch_tile_lines(irp, n_rows, nnz, SCT_TILE, scratch, s);
     if (e != cudaSuccess) return e;
     const long long n_tiles = (nnz + SCT_TILE - 1) / SCT_TILE;
-    KernelScope ks("col_scatter", s);
-    k_col_scatter<<<(unsigned)n_tiles, SCT_THREADS, 0, s>>>(irp, n_rows, icol, nnz, n_cols, cp, rank, scratch,
-                                                             n_tiles, pairs, status);
+    KernelScope ks("col_claim", s);
+    k_col_claim<<<(unsigned)n_tiles, SCT_THREADS, 0, s>>>(irp, n_rows, icol, nnz, n_cols, nc, rank, scratch, n_tiles,
+                                                           T, n_over, status);
     return cudaGetLastError();
 }
 
@@ -412,6 +501,125 @@ __global__ void __launch_bounds__(FT_THREADS) k_fixup_tiles(const int32_t *__res
     }
 }
 
+// Short columns from the slot array T (the slot path). One CTA per 64
+// columns: thread (r, c) loads T[r * n_cols + j0 + c] for r < NC[j0 + c], so
+// each slot row of the tile is one coalesced 512-byte read, into a compact
+// per-column layout in shared memory, together with the entry's CCS position.
+// Then, as in k_fixup_tiles: a warp per column orders it (packed 32-bit
+// bitonic network when out of order), and a flat pass writes ICOL_T and
+// VAL_T = VAL[k] with four gathers in flight per thread. Columns longer than
+// SLOT_CAP copy their slots to `pairs` at IRP_T[j] + r for k_fixup_block.
+constexpr int FS_COLS = 64;
+
+__global__ void __launch_bounds__(FT_THREADS) k_fixup_slots(const int32_t *__restrict__ cp, int32_t n_cols,
+                                                             const double *__restrict__ val,
+                                                             const int2 *__restrict__ T, int2 *__restrict__ pairs,
+                                                             int32_t *__restrict__ trow, double *__restrict__ tval) {
+    __shared__ int2 s_pr[FS_COLS * SLOT_CAP];
+    __shared__ int32_t s_pos[FS_COLS * SLOT_CAP];
+    __shared__ int32_t s_cp[FS_COLS + 1];
+    __shared__ int32_t s_off[FS_COLS + 1];
+    __shared__ int s_maxl;
+    const unsigned lane = lane_id();
+    const int w = threadIdx.x >> 5;
+    const long long c0 = (long long)blockIdx.x * FS_COLS;
+    const int nc = (int)min((long long)FS_COLS, (long long)n_cols - c0);
+    for (int i = threadIdx.x; i <= nc; i += FT_THREADS) s_cp[i] = cp[c0 + i];
+    __syncthreads();
+    if (w == 0) {  // compact offsets of the short columns, and the longest short one
+        int a = 0, b = 0, l0 = 0, l1 = 0;
+        if ((int)lane < nc) { l0 = s_cp[lane + 1] - s_cp[lane]; a = (l0 <= SLOT_CAP) ? l0 : 0; }
+        if ((int)lane + 32 < nc) { l1 = s_cp[lane + 33] - s_cp[lane + 32]; b = (l1 <= SLOT_CAP) ? l1 : 0; }
+        int ia = a, ib = b;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ta = __shfl_up_sync(0xffffffffu, ia, o), tb = __shfl_up_sync(0xffffffffu, ib, o);
+            if ((int)lane >= o) { ia += ta; ib += tb; }
+        }
+        const int tot_a = __shfl_sync(0xffffffffu, ia, 31);
+        s_off[lane] = ia - a;
+        s_off[lane + 32] = tot_a + ib - b;
+        if (lane == 31) s_off[64] = tot_a + ib;
+        int m = max(min(l0, SLOT_CAP), min(l1, SLOT_CAP));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) s_maxl = m;
+    }
+    __syncthreads();
+    const int maxl = s_maxl;
+    // stage: thread t covers column t % 64 and slots t / 64, +4, +8, ...
+    {
+        const int cc = threadIdx.x % FS_COLS;
+        const int len = (cc < nc) ? s_cp[cc + 1] - s_cp[cc] : 0;
+        const bool longc = len > SLOT_CAP;
+        const long long j = c0 + cc;
+        for (int rr = threadIdx.x / FS_COLS; rr < maxl; rr += FT_THREADS / FS_COLS) {
+            if (rr < len && rr < SLOT_CAP) {
+                const int2 pr = __ldcs(T + (long long)rr * n_cols + j);
+                if (longc) {
+                    pairs[(long long)s_cp[cc] + rr] = pr;
+                } else {
+                    s_pr[s_off[cc] + rr] = pr;
+                    s_pos[s_off[cc] + rr] = s_cp[cc] + rr;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int jj = w; jj < nc; jj += FT_THREADS / 32) {
+        const int len = s_cp[jj + 1] - s_cp[jj];
+        if (len <= 0 || len > SLOT_CAP) continue;
+        const int o = s_off[jj];
+        int key = INT_MAX, row = 0;
+        if ((int)lane < len) {
+            const int2 q = s_pr[o + lane];
+            key = q.x;
+            row = q.y;
+        }
+        const int nxt = __shfl_down_sync(0xffffffffu, key, 1);
+        if (__any_sync(0xffffffffu, (int)lane + 1 < len && key > nxt)) {
+            const int k0 = __shfl_sync(0xffffffffu, key, 0);
+            const long long rel = (long long)key - k0 + (1ll << 26);
+            const bool narrow = __all_sync(0xffffffffu, (int)lane >= len || (rel >= 0 && rel < (1ll << 27)));
+            if (narrow) {
+                unsigned pk = ((int)lane < len) ? (((unsigned)rel << 5) | lane) : 0xffffffffu;
+                warp_sort_u32(pk);
+                const int src = (int)(pk & 31u);
+                const int r2 = __shfl_sync(0xffffffffu, row, src);
+                if ((int)lane < len) {
+                    key = (int)((long long)k0 + (long long)(pk >> 5) - (1ll << 26));
+                    row = r2;
+                }
+            } else {
+                warp_sort_pairs(key, row);
+            }
+            if ((int)lane < len) s_pr[o + lane] = make_int2(key, row);
+        }
+    }
+    __syncthreads();
+    const int ns = s_off[nc];
+    for (int q0 = threadIdx.x; q0 < ns; q0 += 4 * FT_THREADS) {
+        int2 pr[4];
+        int pos[4];
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * FT_THREADS;
+            pr[u] = (q < ns) ? s_pr[q] : make_int2(-1, 0);
+            pos[u] = (q < ns) ? s_pos[q] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = (pr[u].x >= 0) ? __ldg(val + pr[u].x) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (pr[u].x >= 0) {
+                __stcs(trow + pos[u], pr[u].y);
+                __stcs(tval + pos[u], v[u]);
+            }
+        }
+    }
+}
+
 // Long columns (> 32 entries): one CTA each.
 constexpr int FIX_THREADS = 256;
 constexpr int FIX_CHUNK = 4096;
@@ -516,6 +724,26 @@ __global__ void __launch_bounds__(FIX_THREADS) k_fixup_block(
         __syncthreads();
     }
 }
+
+cudaError_t launch_col_fixup_slots(const int32_t *cp, int32_t n_cols, const int32_t *irp, int32_t n_rows,
+                                   const double *val, const int2 *T, int2 *pairs, const int32_t *long_list,
+                                   int32_t *keys_tmp, int32_t *trow, double *tval, cudaStream_t s) {
+    if (n_cols <= 0) return cudaSuccess;
+    {
+        KernelScope ks("col_fixup_slots", s);
+        k_fixup_slots<<<ceil_div_u(n_cols, FS_COLS), FT_THREADS, 0, s>>>(cp, n_cols, val, T, pairs, trow, tval);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const int32_t *long_count = long_list - 1;
+    KernelScope ks("col_fixup_block", s);
+    k_fixup_block<<<(unsigned)sm_count() * 2u, FIX_THREADS, 0, s>>>(cp, irp, n_rows, val, pairs, long_list,
+                                                                     long_count, keys_tmp, trow, tval);
+    return cudaGetLastError();
+}
+
+size_t col_slot_bytes(int32_t n_cols) { return (size_t)SLOT_CAP * (size_t)n_cols * sizeof(int2); }
+int col_slot_cap() { return SLOT_CAP; }
 
 cudaError_t launch_col_fixup(const int32_t *cp, int32_t n_cols, const int32_t *irp, int32_t n_rows,
                              const double *val, int2 *pairs, const int32_t *long_list, int32_t *keys_tmp,

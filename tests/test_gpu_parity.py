@@ -258,3 +258,48 @@ def test_coo_row_schedules(monkeypatch, entry_tiles):
         assert_spmv_close(run_apply(M, torch.from_numpy(xh).cuda(), H.n_rows), H, xh,
                           what=f"{name}/entry_tiles={entry_tiles}")
         M.close()
+
+
+@pytest.mark.parametrize("name", ["stencil27_24", "powerlaw_60k", "random_duplicates", "dense_column", "wide",
+                                  "tall", "all_empty", "one_by_one"])
+def test_phase1_count_scatter_path_bit_exact(monkeypatch, name):
+    """The count-then-scatter path of Phase I (used when columns are short on
+    average) gives the same CCS as the slot path and the oracle."""
+    L = lib()
+    monkeypatch.setenv("SPMVAT_PHASE1_SCATTER", "1")
+    H = case(name)
+    irp_t, icol_t, val_t, _ = oracle.crs_to_ccs(H.n_rows, H.n_cols, H.irp, H.icol, H.val)
+    M = L.spmv_transform(dev(H), L.SPMV_CRS, L.SPMV_COLWISE)
+    arr = M.arrays()
+    assert np.array_equal(arr["ptr"].cpu().numpy(), irp_t)
+    assert np.array_equal(arr["idx"].cpu().numpy(), icol_t)
+    assert np.array_equal(bits(arr["val"].cpu().numpy()), bits(val_t))
+    M.close()
+
+
+def test_phase1_slot_path_with_long_columns():
+    """Columns longer than the slot capacity (32) next to short ones, on a
+    matrix dense enough per column for the slot path."""
+    L = lib()
+    n = 3000
+    base = synth.random_crs(n, n, 12, seed=71)
+    rows = []
+    for i in range(n):
+        c = set(base.icol[base.irp[i]:base.irp[i + 1]].tolist())
+        if i % 3 == 0:
+            c.add(5)        # column 5: 1000 entries
+        if i % 40 == 0:
+            c.add(9)        # column 9: 75 entries
+        rows.append(sorted(c))
+    irp = np.zeros(n + 1, np.int64)
+    irp[1:] = np.cumsum([len(r) for r in rows])
+    icol = np.concatenate([np.array(r, np.int32) for r in rows])
+    H = synth.CRS(n, n, irp.astype(np.int32), icol, synth.normal(71, 5, np.arange(icol.size)))
+    assert 32 * n <= 4 * H.nnz  # the slot path is taken
+    irp_t, icol_t, val_t, _ = oracle.crs_to_ccs(H.n_rows, H.n_cols, H.irp, H.icol, H.val)
+    M = L.spmv_transform(dev(H), L.SPMV_CRS, L.SPMV_COLWISE)
+    arr = M.arrays()
+    assert np.array_equal(arr["ptr"].cpu().numpy(), irp_t)
+    assert np.array_equal(arr["idx"].cpu().numpy(), icol_t)
+    assert np.array_equal(bits(arr["val"].cpu().numpy()), bits(val_t))
+    M.close()
