@@ -160,9 +160,9 @@ class Step:
 def calibrate_dstar(L, torch, quick: bool = True):
     """Off-line phase (Sec. 2.2) on a small synthetic set on this device."""
     import spmv_synth as synth
-    mats = [synth.laplacian_2d_5pt(256), synth.stencil_3d_27pt(40),
-            synth.random_crs(200000, 200000, 12, seed=41),
-            synth.power_law(200000, kmax=2000, seed=42), synth.power_law(200000, kmax=20000, seed=43)]
+    mats = [synth.laplacian_2d_5pt(1024), synth.stencil_3d_27pt(64),
+            synth.random_crs(1000000, 1000000, 12, seed=41),
+            synth.power_law(1000000, kmax=2000, seed=42), synth.power_law(1000000, kmax=20000, seed=43)]
     dev = [L.Crs.from_host(H) for H in mats]
     dstar, d, r = L.spmv_calibrate(dev, c=1.0, timing_reps=5 if quick else 20, warmup_reps=2)
     return dstar, d, r
@@ -177,12 +177,13 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.out = []
+        self.out = []  # (host time of arrival, line)
+        self.window = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -191,11 +192,16 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.out.append(line.strip())
+            self.out.append((time.perf_counter(), line.strip()))
+
+    def mark(self, t0: float, t1: float):
+        """Host-time window of the timed region."""
+        self.window = (t0, t1)
 
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.05)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -204,7 +210,15 @@ class ClockSampler:
         self.thread.join(timeout=2)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.out:
+        lines = self.out
+        if self.window:
+            t0, t1 = self.window
+            inside = [(t, l) for t, l in self.out if t0 <= t <= t1 + 0.03]
+            if not inside and self.out:  # the region was shorter than one period: nearest sample
+                mid = 0.5 * (t0 + t1)
+                inside = [min(self.out, key=lambda tl: abs(tl[0] - mid))]
+            lines = inside
+        for _, line in lines:
             f = [v.strip() for v in line.split(",")]
             if len(f) < 9:
                 continue
@@ -278,7 +292,7 @@ def oracle_bytes(H, W, Wc) -> float:
 
 def cpu_baseline(H, xh, budget_s: float = 12.0) -> dict:
     """Times the oracle on a bounded row sample of the workload."""
-    frac = 8
+    frac = 4
     rows = max(1, H.n_rows // frac)
     S = H.row_slice(0, rows)
     xs = xh  # the slice keeps all columns
@@ -407,22 +421,24 @@ def main():
         bm.pop("crs_to_ell_row"); bm.pop("spmv_ell_row")
     step_bytes = float(sum(bm.values()))
 
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(args.warmup):
         step.run()
     stream = torch.cuda.current_stream()
     barrier_sync(torch)
     L.spmv_profile_read(reset=True)
     L.spmv_profile_enable(True)
-    clocks = ClockSampler(local)
-    clocks.start()
     launches0 = L.spmv_launch_count()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     barrier_sync(torch)
+    h0 = time.perf_counter()
     ev[0].record(stream)
     for i in range(args.steps):
         step.run()
         ev[i + 1].record(stream)
     barrier_sync(torch)
+    clocks.mark(h0, time.perf_counter())
     launches = L.spmv_launch_count() - launches0
     clk = clocks.stop()
     L.spmv_profile_enable(False)
@@ -483,27 +499,54 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        pin = {k: torch.from_numpy(v).pin_memory() for k, v in (("irp", H.irp), ("icol", H.icol), ("val", H.val))}
+        # Each step copies its own CRS arrays and x from pinned host memory and
+        # reads its y back; step i+1's upload runs on a copy stream while step i
+        # computes (two device buffers, ordered by events).
+        pin = [torch.from_numpy(a).pin_memory() for a in (H.irp, H.icol, H.val)]
         xpin = torch.from_numpy(xh).pin_memory()
         yhost = torch.empty(H.n_rows, dtype=torch.float64).pin_memory()
-        h2d = sum(t.numel() * t.element_size() for t in pin.values()) + xpin.numel() * 8
+        h2d = sum(t.numel() * t.element_size() for t in pin) + xpin.numel() * 8
         d2h = yhost.numel() * 8
-        estep = Step(L, A, x, ys, dstar, w["cap"])
+        bufs = []
+        for _ in range(2):
+            irp_d, icol_d, val_d = (torch.empty_like(t, device=device) for t in pin)
+            x_d = torch.empty_like(xpin, device=device)
+            bufs.append((L.Crs(H.n_rows, H.n_cols, irp_d, icol_d, val_d), x_d))
+        copy_stream = torch.cuda.Stream(device=device)
+        loaded = [torch.cuda.Event() for _ in range(2)]
+        consumed = [torch.cuda.Event() for _ in range(2)]
+
+        def upload(b):
+            A_b, x_b = bufs[b]
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(consumed[b])
+                for dst, src in zip((A_b.irp, A_b.icol, A_b.val), pin):
+                    dst.copy_(src, non_blocking=True)
+                x_b.copy_(xpin, non_blocking=True)
+                loaded[b].record(copy_stream)
+
+        for b in range(2):
+            consumed[b].record(stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier_sync(torch)
         e0.record(stream)
-        for _ in range(args.steps):
-            A.irp.copy_(pin["irp"], non_blocking=True)
-            A.icol.copy_(pin["icol"], non_blocking=True)
-            A.val.copy_(pin["val"], non_blocking=True)
-            x.copy_(xpin, non_blocking=True)
+        upload(0)
+        for i in range(args.steps):
+            b = i % 2
+            if i + 1 < args.steps:
+                upload(1 - b)
+            stream.wait_event(loaded[b])
+            A_b, x_b = bufs[b]
+            estep = Step(L, A_b, x_b, ys, dstar, w["cap"])
             estep.run()
             yhost.copy_(ys["ell_row" if estep.chosen == "ELL-Row" else "crs"], non_blocking=True)
+            consumed[b].record(stream)
         e1.record(stream)
         barrier_sync(torch)
         et_max, eb_all = reduce_max_sum(torch, e0.elapsed_time(e1), step_bytes * args.steps, device)
         e2e = {"value": eb_all / (et_max * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": et_max / args.steps}
+               "d2h_bytes_per_step": d2h, "ms_per_step": et_max / args.steps,
+               "overlap": "upload of step i+1 on a copy stream during step i"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
