@@ -182,6 +182,27 @@ def test_measure_and_calibrate_follow_eqs_1_to_3():
             assert dm == L.spmv_analyze(A)["dmat"]
 
 
+def test_offline_calibration_on_table1_shaped_set(tmp_path):
+    # the off-line phase end to end at 2 % scale: D_mat of each point is the
+    # oracle's sigma/mu, D* follows the rule, the result reloads
+    import torch
+
+    from paper_2407_00019_gb300 import calibrate as C
+    mats = C.table1_shaped_set(scale=0.02)
+    for rule in (0, 1):
+        res = C.run_offline(mats, rule=rule, timing_reps=3, warmup_reps=1)
+        d = [p[0] for p in res["points"]]
+        r = [p[1] for p in res["points"]]
+        assert len(d) == len(C.TABLE1_SHAPES)
+        assert all(x > 0 and math.isfinite(x) for x in r)
+        for H, dm in zip(mats, d):
+            assert math.isclose(dm, oracle.analyze(H.n_rows, H.irp)["dmat"], rel_tol=1e-12)
+        assert res["dstar"] == oracle.dstar_from_points(d, r, 1.0, rule)
+        path = str(tmp_path / f"d{rule}.json")
+        C.save_dstar(path, res)
+        assert C.load_dstar(path, device=torch.cuda.get_device_name()) == res["dstar"]
+
+
 def test_profile_counts_launches():
     import torch
     L = lib()
