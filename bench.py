@@ -45,6 +45,9 @@ WORKLOADS = {
     "powerlaw_4m": dict(kind="powerlaw", n=4_000_000, seed_a=3, seed_x=4, cap=40 * 10 ** 9,
                         desc="n = 4e6, truncated power-law row lengths (exponent 2, mean 16, max 20000), "
                              "sorted unique random columns"),
+    "batch_10k": dict(kind="batch", count=10000, seed=5, n_lo=100, n_hi=20000, cap=60 * 10 ** 9,
+                      desc="10,000 matrices, n log-uniform in [100, 20000]; even: 2-D 5-point stencil on a "
+                           "ceil(sqrt(n)) grid cut to n, odd: Poisson(8) row lengths, unique random columns"),
 }
 DEFAULT_WORKLOAD = "stencil27_128"
 
@@ -338,6 +341,233 @@ def run_reference(args, w: dict) -> None:
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------- batches
+def _batch_part(args):
+    import spmv_synth as synth
+    lo, hi, seed, n_lo, n_hi = args
+    return [synth.batch_matrix(i, seed, n_lo, n_hi) for i in range(lo, hi)]
+
+
+def make_batch(w: dict, rank: int = 0):
+    """The batch's host matrices, generated by a spawned process pool."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    seed = w["seed"] + 100000 * rank
+    n, step = w["count"], 250
+    parts = [(lo, min(n, lo + step), seed, w["n_lo"], w["n_hi"]) for lo in range(0, n, step)]
+    workers = max(1, min(16, (os.cpu_count() or 2) - 1))
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        out = []
+        for part in ex.map(_batch_part, parts):
+            out.extend(part)
+    return out
+
+
+def batch_bytes(mats, plans) -> float:
+    """Algorithmic bytes of one product over the batch: CRS 12 nnz + 4 (n+1),
+    ELL 12 ld W, plus x and y once each."""
+    b = 0.0
+    for H, P in zip(mats, plans):
+        if P["format"] == 2:
+            b += 12.0 * P["ld"] * P["width"]
+        else:
+            b += 12.0 * H.nnz + 4.0 * (H.n_rows + 1)
+        b += 8.0 * H.n_cols + 8.0 * H.n_rows
+    return b
+
+
+def run_batch(args, w: dict) -> None:
+    """One step = one product y = A x over every matrix of the batch (one
+    launch). Also timed: the batch build (analysis, on-line rule, ELL
+    build fused with a first product) and the same products as a loop of
+    one spmv_apply per matrix, plain and captured in a CUDA graph."""
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        import spmv_synth as synth
+        mats = [synth.batch_matrix(i, w["seed"], w["n_lo"], w["n_hi"]) for i in range(400)]
+        xs = [synth.vector_pm1(H.n_cols, seed=7 + i) for i, H in enumerate(mats)]
+        for H, x in list(zip(mats, xs))[:args.warmup]:
+            oracle.spmv_crs(H.n_rows, H.irp, H.icol, H.val, x)
+        t0 = time.perf_counter()
+        nb = 0.0
+        for _ in range(args.steps):
+            for H, x in zip(mats, xs):
+                oracle.spmv_crs(H.n_rows, H.irp, H.icol, H.val, x)
+                nb += 12.0 * H.nnz + 4.0 * (H.n_rows + 1) + 8.0 * (H.n_cols + H.n_rows)
+        tot = time.perf_counter() - t0
+        v = nb / tot / 1e9
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": args.workload, "sample_matrices": 400},
+                          "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                           "sample": "matrices 0..399 of the batch per step, CRS SpMV, single "
+                                                     "thread"},
+                          "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                          "gpu_launches": 0}), flush=True)
+        return
+    mats = make_batch(w, rank)  # before the first GPU call (spawned pool)
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    import paper_2407_00019_gb300 as L
+    import spmv_synth as synth
+    L.load_library()
+    dev = L.Crs.batch_from_host(mats, device=device)
+    nc = sum(H.n_cols for H in mats)
+    nr = sum(H.n_rows for H in mats)
+    xh = synth.vector_pm1(nc, seed=7 + 1000 * rank)
+    x = torch.from_numpy(xh).to(device)
+    y = torch.empty(nr, dtype=torch.float64, device=device)
+    if args.dstar is None:
+        dstar, _, _ = calibrate_dstar(L, torch)
+    else:
+        dstar = args.dstar
+    stream = torch.cuda.current_stream()
+    # build: analysis + on-line rule + ELL build fused with the first product
+    create_ms = []
+    for _ in range(3):
+        barrier_sync(torch)
+        t0 = time.perf_counter()
+        B = L.spmv_batch_create(dev, x=x, y=y, dstar=dstar, mem_cap_bytes=w["cap"])
+        torch.cuda.synchronize()
+        create_ms.append(1e3 * (time.perf_counter() - t0))
+        B.close()
+    B = L.spmv_batch_create(dev, dstar=dstar, mem_cap_bytes=w["cap"])
+    info, plans = B.info(), B.plans()
+    step_bytes = batch_bytes(mats, plans)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    for _ in range(args.warmup):
+        B.apply(x, y)
+    barrier_sync(torch)
+    L.spmv_profile_read(reset=True)
+    L.spmv_profile_enable(True)
+    launches0 = L.spmv_launch_count()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier_sync(torch)
+    h0 = time.perf_counter()
+    ev[0].record(stream)
+    for i in range(args.steps):
+        B.apply(x, y)
+        ev[i + 1].record(stream)
+    barrier_sync(torch)
+    clocks.mark(h0, time.perf_counter())
+    launches = L.spmv_launch_count() - launches0
+    clk = clocks.stop()
+    L.spmv_profile_enable(False)
+    prof = L.spmv_profile_read(reset=True)
+    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    t_max, bytes_all = reduce_max_sum(torch, ev[0].elapsed_time(ev[-1]), step_bytes * args.steps, device)
+    value = bytes_all / (t_max * 1e-3) / 1e9
+    peak, peak_kind = measured_hbm_peak()
+    n_k, ms_k = prof["batch_apply"]
+    achieved = step_bytes / (ms_k / n_k * 1e-3) / 1e9
+
+    # the per-matrix loop: one CRS handle and one spmv_apply per matrix
+    handles = [L.spmv_transform(A, L.SPMV_CRS, L.SPMV_ROWWISE) for A in dev]
+    views = [(x[P["x_offset"]:P["x_offset"] + H.n_cols], y[P["y_offset"]:P["y_offset"] + H.n_rows])
+             for H, P in zip(mats, plans)]
+    loop_reps = 3
+
+    def loop():
+        for M, (xv, yv) in zip(handles, views):
+            L.spmv_apply(M, xv, yv)
+
+    loop()
+    barrier_sync(torch)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(loop_reps):
+        loop()
+    e1.record(stream)
+    barrier_sync(torch)
+    loop_ms = e0.elapsed_time(e1) / loop_reps
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        loop()
+    g.replay()
+    barrier_sync(torch)
+    e0.record(stream)
+    for _ in range(loop_reps):
+        g.replay()
+    e1.record(stream)
+    barrier_sync(torch)
+    graph_ms = e0.elapsed_time(e1) / loop_reps
+    del g
+    for M in handles:
+        M.close()
+
+    e2e = None
+    if not args.no_e2e:
+        xpin = torch.from_numpy(xh).pin_memory()
+        ypin = torch.empty(nr, dtype=torch.float64).pin_memory()
+        barrier_sync(torch)
+        e0.record(stream)
+        for _ in range(args.steps):
+            x.copy_(xpin, non_blocking=True)
+            B.apply(x, y)
+            ypin.copy_(y, non_blocking=True)
+        e1.record(stream)
+        barrier_sync(torch)
+        et, eb = reduce_max_sum(torch, e0.elapsed_time(e1), step_bytes * args.steps, device)
+        e2e = {"value": eb / (et * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": 8 * nc,
+               "d2h_bytes_per_step": 8 * nr, "ms_per_step": et / args.steps}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        nb, k = 0.0, 0
+        while time.perf_counter() - t0 < 10.0 and k < len(mats):
+            H, P = mats[k], plans[k]
+            oracle.spmv_crs(H.n_rows, H.irp, H.icol, H.val, xh[P["x_offset"]:P["x_offset"] + H.n_cols])
+            nb += 12.0 * H.nnz + 4.0 * (H.n_rows + 1) + 8.0 * (H.n_cols + H.n_rows)
+            k += 1
+        tc = time.perf_counter() - t0
+        cpu = {"value": nb / tc / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"CRS SpMV of matrices 0..{k - 1} of {len(mats)}, {tc:.1f} s, single thread"}
+
+    if rank == 0:
+        srt = sorted(per_step)
+        p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
+        fmt_count = {"ELL-Row": info["n_ell"], "CRS": info["n_matrices"] - info["n_ell"]}
+        tpr = {}
+        for P in plans:
+            if P["format"] == 0:
+                tpr[str(P["threads_per_row"])] = tpr.get(str(P["threads_per_row"]), 0) + 1
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": w["desc"], "matrices": len(mats), "rows": nr,
+                       "nnz": info["total_nnz"], "step_bytes": step_bytes, "tiles": info["n_tiles"],
+                       "grid": info["grid"], "l2": "inputs larger than L2 (%.0f MB); no flush" % (step_bytes / 1e6),
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"kernel": "batch_apply", "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                         "traffic": stored_traffic("batch_apply", args.workload),
+                         "algorithmic_bytes_per_launch": step_bytes},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "p50_ms": statistics.median(per_step), "p99_ms": p99,
+            "batch": {"create_ms": statistics.median(create_ms), "per_matrix_loop_ms": loop_ms,
+                      "per_matrix_graph_ms": graph_ms, "speedup_vs_loop": loop_ms / (t_max / args.steps),
+                      "speedup_vs_graph": graph_ms / (t_max / args.steps), "dstar": dstar if math.isfinite(dstar)
+                      else "inf", "formats": fmt_count, "crs_threads_per_row": tpr},
+        }
+        print(json.dumps(line), flush=True)
+    B.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 # ------------------------------------------------------------------- main
 def measured_hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -386,6 +616,9 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = WORKLOADS[args.workload]
+    if w["kind"] == "batch":
+        run_batch(args, w)
+        return
     if args.impl == "reference":
         run_reference(args, w)
         return

@@ -280,6 +280,74 @@ spmv_status spmv_apply_coo_row_noalloc(int32_t n_rows, int32_t n_cols, int64_t n
                                        const int32_t *icol, const double *val, const double *x, double *y,
                                        spmv_stream_t stream);
 
+/* ---- Batches of independent matrices ------------------------------------
+ * The paper's method handles one matrix per library call. A batch applies it
+ * to m matrices at once: one analysis launch computes Eq. (4) for every
+ * matrix and checks its CRS, the on-line rule of Sec. 2.2 is taken per
+ * matrix (ELL-Row iff D_mat < p->dstar and the batch's ELL arrays, counted
+ * matrix by matrix in order, stay within p->mem_cap_bytes; else CRS), one
+ * launch builds all ELL-Row arrays (Sec. 2.1), and each product is one
+ * launch over all matrices instead of one per matrix.
+ *
+ * Vectors are concatenated: matrix i reads x[x_offset_i, x_offset_i +
+ * n_cols_i) and writes y[y_offset_i, y_offset_i + n_rows_i), where x_offset_i
+ * is the sum of n_cols and y_offset_i the sum of n_rows of matrices 0..i-1.
+ * The batch borrows every CRS array: keep them alive and unchanged until
+ * spmv_batch_destroy. */
+typedef struct spmv_batch spmv_batch;
+
+typedef struct spmv_batch_info {
+    int32_t n_matrices;
+    int32_t n_ell;         /* matrices stored as ELL-Row */
+    int64_t total_rows;    /* length of the concatenated y */
+    int64_t total_cols;    /* length of the concatenated x */
+    int64_t total_nnz;
+    int64_t n_tiles;       /* row tiles of one product launch */
+    int32_t grid;          /* CTAs of the persistent product launch */
+    int32_t pad;
+    uint64_t ell_bytes;    /* device bytes of all ELL-Row arrays */
+    uint64_t owned_bytes;  /* all device bytes the batch keeps alive */
+} spmv_batch_info;
+
+/* Plan of one matrix of a batch. */
+typedef struct spmv_batch_plan {
+    double mu, sigma, dmat;   /* Eq. (4) */
+    int32_t max_row_len;
+    int32_t format;           /* SPMV_ELL or SPMV_CRS (row-wise) */
+    int32_t threads_per_row;  /* CRS: lanes sharing a row (1, 8 or 32); ELL: 1 */
+    int32_t rows_per_tile;    /* rows per warp tile (at most 32) */
+    int32_t width, ld;        /* ELL: slots per row and leading dimension; CRS: 0 */
+    int64_t x_offset, y_offset;
+    const double *ell_val;    /* ELL: device float64[width * ld], slot k of row r at k*ld + r;
+                                 rows n_rows..ld-1 are not written. CRS: NULL */
+    const int32_t *ell_idx;   /* ELL: column of each slot (padding: +0.0 value, the row's
+                                 last column or 0 for an empty row). CRS: NULL */
+} spmv_batch_plan;
+
+/* SYNC (once, after the analysis launch; the ELL build is then enqueued
+ * asynchronously). mats: host array of m CRS descriptors whose arrays are
+ * device memory. p may be NULL (dstar 0: all CRS, no cap). If x and y
+ * (device, concatenated as above) are both given, the build launch also
+ * computes y = A x for every matrix; give both or neither. Errors:
+ * SPMV_ERR_INVALID_ARG (bad sizes or pointers), SPMV_ERR_INVALID_MATRIX (any
+ * matrix with a malformed IRP or a column index out of range), SPMV_ERR_OOM. */
+spmv_status spmv_batch_create(const spmv_crs *mats, int32_t m, const spmv_at_params *p, const double *x,
+                              double *y, spmv_batch **out, spmv_stream_t stream);
+
+/* y = A x for every matrix of the batch: one kernel launch, no allocation,
+ * no synchronisation, no host work beyond the launch, so that the call can
+ * be captured in a CUDA graph. Deterministic. x, y: device, concatenated. */
+spmv_status spmv_batch_apply(const spmv_batch *B, const double *x, double *y, spmv_stream_t stream);
+
+/* Sizes of a batch (host). */
+spmv_status spmv_batch_info_get(const spmv_batch *B, spmv_batch_info *out);
+
+/* Plans of matrices first .. first+count-1 into out[0..count-1] (host). */
+spmv_status spmv_batch_plan_get(const spmv_batch *B, int32_t first, int32_t count, spmv_batch_plan *out);
+
+/* Frees the batch's device memory (stream-ordered on the creating stream). */
+void spmv_batch_destroy(spmv_batch *B);
+
 /* Instrumentation: number of kernels this library has launched so far. */
 uint64_t spmv_launch_count(void);
 

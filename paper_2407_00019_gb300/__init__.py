@@ -23,7 +23,8 @@ __all__ = [
     "spmv_ell_bytes", "spmv_transform", "spmv_transform_from", "spmv_apply", "spmv_transform_apply",
     "spmv_describe", "spmv_matrix_status", "spmv_destroy", "spmv_r_ell", "spmv_dstar_from_points", "spmv_measure",
     "spmv_calibrate", "spmv_autotune", "spmv_autotune_choose", "spmv_apply_coo_row_noalloc", "spmv_launch_count", "spmv_profile_enable", "spmv_profile_read",
-    "spmv_debug_scan_timeout",
+    "spmv_debug_scan_timeout", "spmv_batch_create", "spmv_batch_apply", "spmv_batch_info_get",
+    "spmv_batch_plan_get", "spmv_batch_destroy", "Batch",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -71,6 +72,21 @@ class _DescT(ctypes.Structure):
                 ("n_cols", ctypes.c_int32), ("nnz", ctypes.c_int64), ("width", ctypes.c_int32),
                 ("ld", ctypes.c_int32), ("ptr", ctypes.c_void_p), ("idx", ctypes.c_void_p),
                 ("idx2", ctypes.c_void_p), ("val", ctypes.c_void_p), ("owned_bytes", ctypes.c_uint64)]
+
+
+class _BatchInfoT(ctypes.Structure):
+    _fields_ = [("n_matrices", ctypes.c_int32), ("n_ell", ctypes.c_int32), ("total_rows", ctypes.c_int64),
+                ("total_cols", ctypes.c_int64), ("total_nnz", ctypes.c_int64), ("n_tiles", ctypes.c_int64),
+                ("grid", ctypes.c_int32), ("pad", ctypes.c_int32), ("ell_bytes", ctypes.c_uint64),
+                ("owned_bytes", ctypes.c_uint64)]
+
+
+class _BatchPlanT(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_double), ("sigma", ctypes.c_double), ("dmat", ctypes.c_double),
+                ("max_row_len", ctypes.c_int32), ("format", ctypes.c_int32), ("threads_per_row", ctypes.c_int32),
+                ("rows_per_tile", ctypes.c_int32), ("width", ctypes.c_int32), ("ld", ctypes.c_int32),
+                ("x_offset", ctypes.c_int64), ("y_offset", ctypes.c_int64), ("ell_val", ctypes.c_void_p),
+                ("ell_idx", ctypes.c_void_p)]
 
 
 class _KernelTimeT(ctypes.Structure):
@@ -124,6 +140,11 @@ def load_library():
         "spmv_profile_enable": (ctypes.c_int, [i32]),
         "spmv_profile_read": (i32, [P(_KernelTimeT), i32, i32]),
         "spmv_debug_scan_timeout": (ctypes.c_int, [i32, i32, P(i32), vp]),
+        "spmv_batch_create": (ctypes.c_int, [P(_CrsT), i32, P(_AtParamsT), vp, vp, P(vp), vp]),
+        "spmv_batch_apply": (ctypes.c_int, [vp, vp, vp, vp]),
+        "spmv_batch_info_get": (ctypes.c_int, [vp, P(_BatchInfoT)]),
+        "spmv_batch_plan_get": (ctypes.c_int, [vp, i32, i32, P(_BatchPlanT)]),
+        "spmv_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -175,6 +196,21 @@ class Crs:
     def c(self):
         return self._c
 
+    @classmethod
+    def batch_from_host(cls, mats, device="cuda"):
+        """Copy host CRS matrices into three device tensors (one per array)
+        and return one Crs per matrix viewing its part of them."""
+        import numpy as np
+        import torch
+        nnz = [int(A.irp[-1]) for A in mats]
+        e_off = np.concatenate(([0], np.cumsum(nnz)))
+        p_off = np.concatenate(([0], np.cumsum([A.n_rows + 1 for A in mats])))
+        irp = torch.from_numpy(np.concatenate([A.irp for A in mats]).astype(np.int32)).to(device)
+        icol = torch.from_numpy(np.concatenate([A.icol for A in mats]).astype(np.int32)).to(device)
+        val = torch.from_numpy(np.concatenate([A.val for A in mats]).astype(np.float64)).to(device)
+        return [cls(A.n_rows, A.n_cols, irp[p_off[i]:p_off[i + 1]], icol[e_off[i]:e_off[i + 1]],
+                    val[e_off[i]:e_off[i + 1]]) for i, A in enumerate(mats)]
+
 
 class Matrix:
     """Owning wrapper of an spmv_matrix handle; keeps borrowed tensors alive."""
@@ -217,6 +253,35 @@ class Matrix:
             out["idx2"] = device_view(d["idx2"], d["nnz"], torch.int32)
         out["val"] = device_view(d["val"], d["nnz"], torch.float64)
         return out
+
+
+class Batch:
+    """Owning wrapper of an spmv_batch handle; keeps the borrowed CRS alive."""
+
+    def __init__(self, handle, keep=()):
+        self.handle = ctypes.c_void_p(handle)
+        self._keep = tuple(keep)
+
+    def close(self):
+        if self.handle and self.handle.value:
+            load_library().spmv_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+            self._keep = ()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, x, y, stream=None):
+        spmv_batch_apply(self, x, y, stream)
+
+    def info(self) -> dict:
+        return spmv_batch_info_get(self)
+
+    def plans(self, first=0, count=None) -> list:
+        return spmv_batch_plan_get(self, first, count)
 
 
 class _CudaArray:
@@ -411,3 +476,37 @@ def spmv_debug_scan_timeout(n: int, spin_limit: int, stream=None) -> int:
     _check(load_library().spmv_debug_scan_timeout(int(n), int(spin_limit), ctypes.byref(obs), _stream(stream)),
            "spmv_debug_scan_timeout")
     return int(obs.value)
+
+
+def spmv_batch_create(mats, x=None, y=None, stream=None, **params) -> Batch:
+    """One batch over the Crs list `mats` (on-line rule per matrix with the
+    AT parameters given); with x and y also the first product."""
+    m = len(mats)
+    arr = (_CrsT * max(m, 1))(*[A.c for A in mats])
+    h = ctypes.c_void_p()
+    p = _params(**params)
+    _check(load_library().spmv_batch_create(arr, m, ctypes.byref(p), _ptr(x), _ptr(y), ctypes.byref(h),
+                                            _stream(stream)), "spmv_batch_create")
+    return Batch(h.value, keep=tuple(mats))
+
+
+def spmv_batch_apply(B: Batch, x, y, stream=None) -> None:
+    _check(load_library().spmv_batch_apply(B.handle, _ptr(x), _ptr(y), _stream(stream)), "spmv_batch_apply")
+
+
+def spmv_batch_info_get(B: Batch) -> dict:
+    i = _BatchInfoT()
+    _check(load_library().spmv_batch_info_get(B.handle, ctypes.byref(i)), "spmv_batch_info_get")
+    return {f: getattr(i, f) for f, _ in _BatchInfoT._fields_ if f != "pad"}
+
+
+def spmv_batch_plan_get(B: Batch, first: int = 0, count=None) -> list:
+    if count is None:
+        count = spmv_batch_info_get(B)["n_matrices"] - first
+    out = (_BatchPlanT * max(count, 1))()
+    _check(load_library().spmv_batch_plan_get(B.handle, int(first), int(count), out), "spmv_batch_plan_get")
+    return [{f: getattr(out[i], f) for f, _ in _BatchPlanT._fields_} for i in range(count)]
+
+
+def spmv_batch_destroy(B: Batch) -> None:
+    B.close()

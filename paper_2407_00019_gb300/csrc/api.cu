@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "host_mem.h"
 #include "spmvat.h"
 
 using namespace spmvat;
@@ -21,11 +22,6 @@ using namespace spmvat;
 namespace {
 
 // ------------------------------------------------------------------ memory
-struct Hooks {
-    spmv_alloc_fn alloc = nullptr;
-    spmv_free_fn free = nullptr;
-    void *ctx = nullptr;
-};
 std::mutex g_mu;
 Hooks g_hooks;
 cudaMemPool_t g_pools[64] = {};
@@ -47,18 +43,9 @@ cudaMemPool_t pool_for(int dev) {
     return g_pools[dev];
 }
 
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-    cudaStream_t stream = nullptr;
-    Hooks hooks;
-    ~DevBuf() {
-        if (!p) return;
-        if (hooks.free) hooks.free(p, bytes, hooks.ctx, stream);
-        else if (cudaFreeAsync(p, stream) != cudaSuccess) cudaGetLastError();
-    }
-};
-using BufPtr = std::shared_ptr<DevBuf>;
+}  // namespace
+
+namespace spmvat {
 
 spmv_status alloc_buf(size_t bytes, cudaStream_t s, BufPtr *out) {
     Hooks h;
@@ -92,6 +79,16 @@ spmv_status alloc_buf(size_t bytes, cudaStream_t s, BufPtr *out) {
     return SPMV_OK;
 }
 
+spmv_status status_from_dev(int st) {
+    if (st & ST_TIMEOUT) return SPMV_ERR_TIMEOUT;
+    if (st & (ST_BAD_INDEX | ST_BAD_PTR)) return SPMV_ERR_INVALID_MATRIX;
+    return SPMV_OK;
+}
+
+}  // namespace spmvat
+
+namespace {
+
 // ------------------------------------------------------- launch accounting
 std::atomic<unsigned long long> g_launches{0};
 std::atomic<int> g_profile_on{0};
@@ -117,28 +114,10 @@ cudaEvent_t get_event() {
 
 int g_sm_count[64] = {};
 
-// status helpers
-#define CK(call)                                            \
-    do {                                                    \
-        cudaError_t e_ = (call);                            \
-        if (e_ != cudaSuccess) { cudaGetLastError(); return SPMV_ERR_CUDA; } \
-    } while (0)
-#define CKS(call)                                           \
-    do {                                                    \
-        spmv_status s_ = (call);                            \
-        if (s_ != SPMV_OK) return s_;                       \
-    } while (0)
-
 inline cudaStream_t S(spmv_stream_t s) { return reinterpret_cast<cudaStream_t>(s); }
 inline int32_t round_up32(int64_t n) { return (int32_t)((n + 31) / 32 * 32); }
 inline uint64_t ell_bytes(int64_t lines, int64_t width) {
     return (uint64_t)round_up32(lines) * (uint64_t)width * 12ull;
-}
-
-spmv_status status_from_dev(int st) {
-    if (st & ST_TIMEOUT) return SPMV_ERR_TIMEOUT;
-    if (st & (ST_BAD_INDEX | ST_BAD_PTR)) return SPMV_ERR_INVALID_MATRIX;
-    return SPMV_OK;
 }
 
 spmv_status check_crs(const spmv_crs *A) {

@@ -1,0 +1,583 @@
+// Batches of independent matrices: the row statistics of Eq. (4), the
+// CRS -> ELL-Row transformation of Sec. 2.1 and the SpMV of Sec. 3, run for
+// every matrix of a batch in one persistent launch each.
+//
+// Work items are row tiles of at most 32 rows that never cross a matrix,
+// recorded as {matrix, first row, first entry, entries} and ordered by
+// matrix; every warp of the persistent grid takes items w, w + (number of
+// warps), ... and loads the record of its next item while it works on the
+// current one. A matrix's descriptor says how its tiles run:
+//  - CRS with short rows: the tile's n entries are contiguous, so the 32
+//    lanes split them into equal runs of m = ceil(n / 32) (merge-path
+//    split): lane j loads entries [j m, j m + m), their columns, then the x
+//    values, and sums them with one FMA per entry. Rows that cross a run
+//    boundary are closed by the lane that holds their start, adding the
+//    other lanes' partial sums in lane order. Every FMA then runs on full
+//    lanes: FP64 issue (2 FMA / clock / SM) is as scarce as HBM bandwidth
+//    for SpMV on this GPU, and one lane per row would idle most lanes on
+//    rows shorter than the longest in the warp;
+//  - CRS with long rows: 8 or 32 lanes per row, partial sums combined by a
+//    fixed butterfly;
+//  - ELL-Row, one lane per row: slot k of consecutive rows is contiguous
+//    (Fig. 3 layout), so each slot is one coalesced load.
+#include <climits>
+
+#include "common.cuh"
+
+namespace spmvat {
+namespace {
+
+constexpr int T = kBatchThreads;
+
+// ---- warp-level tiles of the product and build launches -------------------
+// Every warp owns one tile; a CTA is 8 independent warps (no block barrier).
+constexpr int WCAP = 256;  // entries a warp stages at once (8 per lane)
+constexpr int WU = WCAP / 32;
+constexpr int MMAX = 8;    // merge-path: entries per lane, so tiles of up to 256 entries
+struct WarpSmem {          // staging of the ELL build and the long-tile product
+    double v[WCAP];
+    double xv[WCAP];       // x at the staged entries' columns, or their column indices
+};
+struct RowSmem {           // merge-path bookkeeping of one warp
+    double run[32 * MMAX]; // running sum of each lane's run at each entry (reset after a row's last entry)
+    uint32_t last[8];      // bit k: entry k is the last entry of its row
+};
+union BuildSmem {
+    WarpSmem ws;
+    RowSmem rs;
+};
+
+// Entries [c0, c0 + cn) of val / icol (cn <= WCAP) into the warp's shared
+// memory; with GATHER also x at their columns. Every load of a phase is
+// issued before its first use.
+template <bool GATHER>
+__device__ __forceinline__ void warp_stage(WarpSmem &ws, const double *__restrict__ val,
+                                           const int32_t *__restrict__ icol, int c0, int cn,
+                                           const double *__restrict__ x) {
+    const int lane = (int)lane_id();
+    double v[WU];
+    int32_t c[WU];
+#pragma unroll
+    for (int u = 0; u < WU; ++u) {
+        const int q = lane + 32 * u;
+        v[u] = (q < cn) ? __ldcs(val + c0 + q) : 0.0;
+        c[u] = (q < cn) ? __ldcs(icol + c0 + q) : 0;
+    }
+    if (GATHER) {
+        double xv[WU];
+#pragma unroll
+        for (int u = 0; u < WU; ++u) xv[u] = (lane + 32 * u < cn) ? __ldg(x + c[u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < WU; ++u) {
+            const int q = lane + 32 * u;
+            if (q < cn) {
+                ws.v[q] = v[u];
+                ws.xv[q] = xv[u];
+            }
+        }
+    } else {
+        int32_t *sc = reinterpret_cast<int32_t *>(ws.xv);
+#pragma unroll
+        for (int u = 0; u < WU; ++u) {
+            const int q = lane + 32 * u;
+            if (q < cn) {
+                ws.v[q] = v[u];
+                sc[q] = c[u];
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// CRS rows [row0, row0 + nr), nr <= 32 / V, V lanes per row: lane j of a
+// row sums entries j, j + V, ... in storage order; the V partial sums are
+// combined by a fixed butterfly.
+template <int V>
+__device__ __forceinline__ void vector_tile(const int32_t *__restrict__ irp, const int32_t *__restrict__ icol,
+                                            const double *__restrict__ val, int row0, int nr,
+                                            const double *__restrict__ x, double *__restrict__ y) {
+    const int lane = (int)lane_id(), sub = lane / V, j = lane % V;
+    double acc = 0.0;
+    if (sub < nr) {
+        const int a = __ldg(irp + row0 + sub), b = __ldg(irp + row0 + sub + 1);
+        int k = a + j;
+        for (; k + 3 * V < b; k += 4 * V) {
+            const int32_t c0 = __ldcs(icol + k), c1 = __ldcs(icol + k + V), c2 = __ldcs(icol + k + 2 * V),
+                          c3 = __ldcs(icol + k + 3 * V);
+            const double v0 = __ldcs(val + k), v1 = __ldcs(val + k + V), v2 = __ldcs(val + k + 2 * V),
+                         v3 = __ldcs(val + k + 3 * V);
+            const double x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+            acc = fma(v0, x0, acc);
+            acc = fma(v1, x1, acc);
+            acc = fma(v2, x2, acc);
+            acc = fma(v3, x3, acc);
+        }
+        for (; k < b; k += V) acc = fma(__ldcs(val + k), __ldg(x + __ldcs(icol + k)), acc);
+    }
+#pragma unroll
+    for (int o = V / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (j == 0 && sub < nr) y[row0 + sub] = acc;
+}
+
+// A lane's run of M entries: running sum in storage order, one FMA per
+// entry, restarted after each row's last entry (bit u of `ends`).
+template <int M>
+__device__ __forceinline__ void run_fma(const double (&v)[MMAX], const double (&xv)[MMAX], int beg, int end,
+                                        uint32_t ends, double *run) {
+    double s = 0.0;
+#pragma unroll
+    for (int u = 0; u < M; ++u) {
+        if (beg + u < end) {
+            s = fma(v[u], xv[u], s);
+            run[beg + u] = s;
+            if ((ends >> u) & 1u) s = 0.0;
+        }
+    }
+}
+
+// The arithmetic of a merge-path tile (see the top of this file): lane j
+// holds the values v and x values xv of its run [beg, end) of the tile's n
+// entries (m = ceil(n / 32) per lane); lane r < nr holds the start rb and end
+// re of row r relative to the tile's first entry. Lane j sums its run with
+// one FMA per entry, restarting after each row's last entry, and leaves the
+// running sums in run[]; lane r then adds row r's pieces in lane order and
+// writes yr[r]. Each row is thus summed in storage order with one extra
+// addition per run boundary it crosses.
+__device__ __forceinline__ void merge_sum(uint32_t *last, double *run, int m, int beg, int end, int nr, int rb,
+                                          int re, const double (&v)[MMAX], const double (&xv)[MMAX],
+                                          double *__restrict__ yr) {
+    const int lane = (int)lane_id();
+    if (lane < 8) last[lane] = 0u;
+    __syncwarp();
+    if (lane < nr && re > rb) atomicOr(&last[(re - 1) >> 5], 1u << ((re - 1) & 31));
+    __syncwarp();
+    // bits beg .. beg + m - 1 of the last-entry map (m <= 8: at most two words)
+    const int w0 = beg >> 5, sh = beg & 31;
+    uint64_t two = last[min(w0, 7)];
+    if (w0 + 1 < 8) two |= (uint64_t)last[w0 + 1] << 32;
+    const uint32_t ends = (uint32_t)(two >> sh);
+    // exactly m steps: an FP64 instruction whose lanes are all switched off
+    // still takes its issue slot on the (narrow) FP64 pipe
+    switch (m) {
+        case 1: run_fma<1>(v, xv, beg, end, ends, run); break;
+        case 2: run_fma<2>(v, xv, beg, end, ends, run); break;
+        case 3: run_fma<3>(v, xv, beg, end, ends, run); break;
+        case 4: run_fma<4>(v, xv, beg, end, ends, run); break;
+        case 5: run_fma<5>(v, xv, beg, end, ends, run); break;
+        case 6: run_fma<6>(v, xv, beg, end, ends, run); break;
+        case 7: run_fma<7>(v, xv, beg, end, ends, run); break;
+        case 8: run_fma<8>(v, xv, beg, end, ends, run); break;
+        default: break;
+    }
+    __syncwarp();
+    if (lane < nr) {
+        double t = 0.0;
+        if (re > rb) {
+            const int j0 = rb / m, j1 = (re - 1) / m;
+            t = run[min(re, (j0 + 1) * m) - 1];
+            for (int j = j0 + 1; j <= j1; ++j) t += run[min(re, (j + 1) * m) - 1];
+        }
+        yr[lane] = t;
+    }
+    __syncwarp();
+}
+
+// Row bounds of a tile relative to its first entry e0: lane r < nr gets the
+// start and end of row r.
+__device__ __forceinline__ void tile_bounds(const int32_t *__restrict__ irp, int row0, int nr, int e0, int n,
+                                            int *rb, int *re) {
+    const int lane = (int)lane_id();
+    *rb = 0;
+    *re = 0;
+    if (lane < nr) {
+        *rb = __ldg(irp + row0 + lane) - e0;
+        *re = lane + 1 < nr ? __ldg(irp + row0 + lane + 1) - e0 : n;
+    }
+}
+
+// CRS rows [row0, row0 + nr) whose n <= 32 * MMAX entries start at entry e0,
+// loaded straight into registers.
+__device__ __forceinline__ void merge_tile(RowSmem &rs, const int32_t *__restrict__ irp,
+                                           const int32_t *__restrict__ icol, const double *__restrict__ val,
+                                           int row0, int nr, int e0, int n, const double *__restrict__ x,
+                                           double *__restrict__ y) {
+    const int lane = (int)lane_id();
+    const int m = (n + 31) >> 5;  // warp-uniform
+    const int beg = min(n, lane * m), end = min(n, beg + m);
+    const double *vp = val + e0 + beg;
+    const int32_t *cp = icol + e0 + beg;
+    double v[MMAX], xv[MMAX];
+    int32_t c[MMAX];
+#pragma unroll
+    for (int u = 0; u < MMAX; ++u) {
+        v[u] = 0.0;
+        c[u] = 0;
+        if (u < m && beg + u < end) {
+            v[u] = __ldcs(vp + u);
+            c[u] = __ldcs(cp + u);
+        }
+    }
+    int rb, re;
+    tile_bounds(irp, row0, nr, e0, n, &rb, &re);
+#pragma unroll
+    for (int u = 0; u < MMAX; ++u) xv[u] = (u < m && beg + u < end) ? __ldg(x + c[u]) : 0.0;
+    merge_sum(rs.last, rs.run, m, beg, end, nr, rb, re, v, xv, y + row0);
+}
+
+// Tiles too large for merge_tile: 8 lanes per row, 4 rows at a time.
+__device__ __forceinline__ void vector_rows8(const int32_t *__restrict__ irp, const int32_t *__restrict__ icol,
+                                             const double *__restrict__ val, int row0, int nr,
+                                             const double *__restrict__ x, double *__restrict__ y) {
+    for (int r0 = 0; r0 < nr; r0 += 4) vector_tile<8>(irp, icol, val, row0 + r0, min(4, nr - r0), x, y);
+}
+
+// ELL-Row rows [row0, row0 + nr), nr <= 32, one lane per row, slots summed in
+// slot order (padding slots included, as in the single-matrix ELL-Row SpMV).
+__device__ __forceinline__ void ell_tile(const double *__restrict__ ev, const int32_t *__restrict__ ec, int ld,
+                                         int width, int row0, int nr, const double *__restrict__ x,
+                                         double *__restrict__ y) {
+    const int r = (int)lane_id();
+    if (r >= nr) return;
+    const double *pv = ev + row0 + r;
+    const int32_t *pc = ec + row0 + r;
+    const size_t L = (size_t)ld;
+    double acc = 0.0;
+    int k = 0;
+    for (; k + 4 <= width; k += 4) {
+        const int32_t c0 = __ldcs(pc + k * L), c1 = __ldcs(pc + (k + 1) * L), c2 = __ldcs(pc + (k + 2) * L),
+                      c3 = __ldcs(pc + (k + 3) * L);
+        const double v0 = __ldcs(pv + k * L), v1 = __ldcs(pv + (k + 1) * L), v2 = __ldcs(pv + (k + 2) * L),
+                     v3 = __ldcs(pv + (k + 3) * L);
+        const double x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+        acc = fma(v0, x0, acc);
+        acc = fma(v1, x1, acc);
+        acc = fma(v2, x2, acc);
+        acc = fma(v3, x3, acc);
+    }
+    for (; k < width; ++k) acc = fma(__ldcs(pv + k * L), __ldg(x + __ldcs(pc + k * L)), acc);
+    y[row0 + r] = acc;
+}
+
+// CRS rows [row0, row0 + nr) -> ELL-Row slots (Sec. 2.1, Fig. 3): slot k of
+// row i at k * ld + i; padding slots get value +0.0 and the row's last column
+// (0 for an empty row). With MUL, also y for these rows in ELL slot order
+// (the order of ell_tile, so the results agree bit for bit).
+template <bool MUL>
+__device__ __forceinline__ void ell_build_tile(WarpSmem &ws, const BatchMat *__restrict__ M, int row0, int nr,
+                                               const double *__restrict__ x, double *__restrict__ y) {
+    const int32_t *irp = M->irp, *icol = M->icol;
+    const double *val = M->val;
+    const int lane = (int)lane_id();
+    int a = 0, b = 0;
+    if (lane < nr) {
+        a = __ldg(irp + row0 + lane);
+        b = __ldg(irp + row0 + lane + 1);
+    }
+    const int e0 = __shfl_sync(0xffffffffu, a, 0), e1 = __shfl_sync(0xffffffffu, b, nr - 1);
+    const bool staged = e1 - e0 <= WCAP;
+    if (staged) warp_stage<false>(ws, val, icol, e0, e1 - e0, nullptr);
+    if (lane < nr) {
+        const int len = b - a;
+        const double *sv = staged ? ws.v + (a - e0) : val + a;
+        const int32_t *sc = staged ? reinterpret_cast<const int32_t *>(ws.xv) + (a - e0) : icol + a;
+        const int32_t last = len > 0 ? sc[len - 1] : 0;
+        const int width = M->width;
+        const size_t L = (size_t)M->ld;
+        double *pv = M->eval + row0 + lane;
+        int32_t *pc = M->ecol + row0 + lane;
+        double acc = 0.0;
+        for (int k = 0; k < width; ++k) {
+            const bool real = k < len;
+            const double v = real ? sv[k] : 0.0;
+            const int32_t c = real ? sc[k] : last;
+            __stcs(pv + k * L, v);
+            __stcs(pc + k * L, c);
+            if (MUL) acc = fma(v, __ldg(x + c), acc);
+        }
+        if (MUL) y[row0 + lane] = acc;
+    }
+    __syncwarp();
+}
+
+// One CRS tile of matrix M by its schedule: rows [row0, row0 + nr), entries
+// [e0, e0 + n).
+__device__ __forceinline__ void crs_tile(RowSmem &rs, const BatchMat *__restrict__ M, int row0, int nr, int e0,
+                                         int n, const double *x, double *y) {
+    const int32_t *irp = M->irp, *icol = M->icol;
+    const double *val = M->val;
+    switch (M->tpr) {
+        case 8: vector_tile<8>(irp, icol, val, row0, nr, x, y); break;
+        case 32: vector_tile<32>(irp, icol, val, row0, nr, x, y); break;
+        default:
+            if (n <= 32 * MMAX) merge_tile(rs, irp, icol, val, row0, nr, e0, n, x, y);
+            else vector_rows8(irp, icol, val, row0, nr, x, y);
+            break;
+    }
+}
+
+__global__ void __launch_bounds__(T) k_batch_analyze(const BatchMat *__restrict__ mats,
+                                                     const int2 *__restrict__ chunks, long long n_chunks,
+                                                     BatchAcc *__restrict__ acc) {
+    __shared__ unsigned long long s_a[T / 32], s_b[T / 32];
+    __shared__ int s_mx[T / 32], s_mn[T / 32], s_em[T / 32];
+    for (long long ci = blockIdx.x; ci < n_chunks; ci += gridDim.x) {
+        const int2 ch = __ldg(chunks + ci);
+        const BatchMat *M = mats + ch.x;
+        const int n = M->n_rows;
+        const long long nnz = M->nnz;
+        const int32_t *irp = M->irp;
+        const int r0 = ch.y, nr = min(kBatchChunk, n - r0);
+        unsigned long long s1 = 0, s2 = 0;
+        int mx = 0, mn = 0, em = 0, bad = 0;
+        for (int i = threadIdx.x; i < nr; i += T) {
+            const int a = __ldg(irp + r0 + i), b = __ldg(irp + r0 + i + 1);
+            if (a < 0 || b < a || (long long)b > nnz) {
+                bad = 1;
+            } else {
+                const int len = b - a;
+                s1 += (unsigned long long)len;
+                s2 += (unsigned long long)len * (unsigned long long)len;
+                mx = max(mx, len);
+                mn = max(mn, INT_MAX - len);
+                em += (len == 0);
+            }
+        }
+        if (threadIdx.x == 0) {
+            if (r0 == 0 && __ldg(irp) != 0) bad = 1;
+            if (r0 + nr == n && (long long)__ldg(irp + n) != nnz) bad = 1;
+        }
+        bad = __syncthreads_or(bad);
+        unsigned badidx = 0;
+        if (!bad && nnz > 0) {
+            // the chunk's entries: [irp[r0], irp[r0 + nr]) lies in [0, nnz] here
+            const int ea = __ldg(irp + r0), eb = __ldg(irp + r0 + nr);
+            const int32_t *icol = M->icol;
+            const unsigned nc = (unsigned)M->n_cols;
+            for (int k = ea + (int)threadIdx.x; k < eb; k += T) badidx |= (unsigned)__ldcs(icol + k) >= nc;
+        }
+        s1 = warp_sum(s1);
+        s2 = warp_sum(s2);
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        mn = __reduce_max_sync(0xffffffffu, mn);
+        em = __reduce_add_sync(0xffffffffu, em);
+        const int w = threadIdx.x >> 5;
+        if (lane_id() == 0) {
+            s_a[w] = s1;
+            s_b[w] = s2;
+            s_mx[w] = mx;
+            s_mn[w] = mn;
+            s_em[w] = em;
+        }
+        const int anybad = __syncthreads_or((int)badidx);
+        if (threadIdx.x == 0) {
+            unsigned long long a = 0, b = 0;
+            int x1 = 0, x2 = 0, e = 0;
+            for (int j = 0; j < T / 32; ++j) {
+                a += s_a[j];
+                b += s_b[j];
+                x1 = max(x1, s_mx[j]);
+                x2 = max(x2, s_mn[j]);
+                e += s_em[j];
+            }
+            BatchAcc *A = acc + ch.x;
+            atomicAdd(&A->sum_len, a);
+            atomicAdd(&A->sum_len2, b);
+            atomicMax(&A->max_len, x1);
+            atomicMax(&A->min_len, x2);
+            atomicAdd(&A->n_empty, e);
+            if (bad) atomicOr(&A->status, ST_BAD_PTR);
+            if (anybad) atomicOr(&A->status, ST_BAD_INDEX);
+        }
+        __syncthreads();
+    }
+}
+
+// Fills entries .z (first entry) and .w (entry count) of every tile record.
+__global__ void __launch_bounds__(T) k_batch_tile_info(const BatchMat *__restrict__ mats, int4 *__restrict__ tiles,
+                                                       long long n_tiles) {
+    for (long long t = (long long)blockIdx.x * T + threadIdx.x; t < n_tiles; t += (long long)gridDim.x * T) {
+        int4 tl = tiles[t];
+        const BatchMat *M = mats + tl.x;
+        const int nr = min(M->rpt, M->n_rows - tl.y);
+        const int a = __ldg(M->irp + tl.y), b = __ldg(M->irp + tl.y + nr);
+        tl.z = a;
+        tl.w = b - a;
+        tiles[t] = tl;
+    }
+}
+
+template <bool MUL>
+__global__ void __launch_bounds__(T) k_batch_build(const BatchMat *__restrict__ mats, const int4 *__restrict__ tiles,
+                                                   long long n_tiles, const double *__restrict__ x,
+                                                   double *__restrict__ y) {
+    __shared__ BuildSmem sm_all[T / 32];  // a warp uses one member per tile
+    WarpSmem &ws = sm_all[threadIdx.x >> 5].ws;
+    RowSmem &rs = sm_all[threadIdx.x >> 5].rs;
+    const long long nw = (long long)gridDim.x * (T / 32);
+    for (long long t = (long long)blockIdx.x * (T / 32) + (threadIdx.x >> 5); t < n_tiles; t += nw) {
+        const int4 tl = __ldg(tiles + t);
+        const BatchMat *M = mats + tl.x;
+        const int nr = min(M->rpt, M->n_rows - tl.y);
+        const double *xm = MUL ? x + M->xoff : nullptr;
+        double *ym = MUL ? y + M->yoff : nullptr;
+        if (M->fmt == BATCH_ELL) ell_build_tile<MUL>(ws, M, tl.y, nr, xm, ym);
+        else if (MUL) crs_tile(rs, M, tl.y, nr, tl.z, tl.w, xm, ym);
+    }
+}
+
+// ---- the product launch: merge-path tiles double-buffered with cp.async ----
+constexpr int AT = 128;  // threads per CTA of the product launch
+struct PipeSmem {        // one warp: two stages of tile entries
+    double v[2][WCAP];   // values; a lane's run sums later overwrite its own entries
+    int32_t c[2][WCAP];  // column indices
+    uint32_t last[8];
+};
+
+__device__ __forceinline__ void cp_async_8(void *s, const void *g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_4(void *s, const void *g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ bool is_merge(const BatchMat *__restrict__ M, int n) {
+    return M->fmt == BATCH_CRS && M->tpr == 1 && n <= 32 * MMAX;
+}
+
+// Copies of a merge tile's n entries from e0 into stage st, coalesced (lane
+// q copies entries q, q + 32, ...).
+__device__ __forceinline__ void stage_issue(PipeSmem &ps, int st, const BatchMat *__restrict__ M, int e0, int n) {
+    const double *val = M->val + e0;
+    const int32_t *icol = M->icol + e0;
+    for (int q = (int)lane_id(); q < n; q += 32) {
+        cp_async_8(&ps.v[st][q], val + q);
+        cp_async_4(&ps.c[st][q], icol + q);
+    }
+}
+
+// Every warp walks its tiles; the entries of its next merge tile are copied
+// into the other stage while it works on the current one, so only the x
+// gathers (and the row bounds, loaded alongside) wait on memory.
+__global__ void __launch_bounds__(AT) k_batch_apply(const BatchMat *__restrict__ mats, const int4 *__restrict__ tiles,
+                                                    long long n_tiles, const double *__restrict__ x,
+                                                    double *__restrict__ y) {
+    __shared__ PipeSmem ps_all[AT / 32];
+    PipeSmem &ps = ps_all[threadIdx.x >> 5];
+    const int lane = (int)lane_id();
+    const long long nw = (long long)gridDim.x * (AT / 32);
+    long long t = (long long)blockIdx.x * (AT / 32) + (threadIdx.x >> 5);
+    if (t >= n_tiles) return;
+    int4 cur = __ldg(tiles + t);
+    if (is_merge(mats + cur.x, cur.w)) stage_issue(ps, 0, mats + cur.x, cur.z, cur.w);
+    cp_async_commit();
+    int4 nxt = t + nw < n_tiles ? __ldg(tiles + t + nw) : cur;
+    for (int it = 0; t < n_tiles; t += nw, ++it) {
+        const int st = it & 1;
+        if (t + nw < n_tiles && is_merge(mats + nxt.x, nxt.w)) stage_issue(ps, st ^ 1, mats + nxt.x, nxt.z, nxt.w);
+        cp_async_commit();
+        const int4 after = t + 2 * nw < n_tiles ? __ldg(tiles + t + 2 * nw) : nxt;
+        const BatchMat *M = mats + cur.x;
+        const int nr = min(M->rpt, M->n_rows - cur.y);
+        const double *xm = x + M->xoff;
+        double *ym = y + M->yoff;
+        if (M->fmt == BATCH_ELL) {
+            ell_tile(M->eval, M->ecol, M->ld, M->width, cur.y, nr, xm, ym);
+        } else if (is_merge(M, cur.w)) {
+            const int n = cur.w, m = (n + 31) >> 5;
+            const int beg = min(n, lane * m), end = min(n, beg + m);
+            int rb, re;
+            tile_bounds(M->irp, cur.y, nr, cur.z, n, &rb, &re);
+            cp_async_wait_prev();  // this tile's copies (all groups but the newest)
+            __syncwarp();
+            double v[MMAX], xv[MMAX];
+#pragma unroll
+            for (int u = 0; u < MMAX; ++u) {
+                const bool ok = u < m && beg + u < end;
+                const int32_t c = ok ? ps.c[st][beg + u] : 0;
+                xv[u] = ok ? __ldg(xm + c) : 0.0;
+                v[u] = ok ? ps.v[st][beg + u] : 0.0;
+            }
+            merge_sum(ps.last, ps.v[st], m, beg, end, nr, rb, re, v, xv, ym + cur.y);
+        } else {
+            const int32_t *irp = M->irp, *icol = M->icol;
+            const double *val = M->val;
+            if (M->tpr == 32) vector_tile<32>(irp, icol, val, cur.y, nr, xm, ym);
+            else vector_rows8(irp, icol, val, cur.y, nr, xm, ym);
+        }
+        cur = nxt;
+        nxt = after;
+    }
+    cp_async_wait_all();
+}
+
+int g_grid[64][4] = {};
+
+}  // namespace
+
+int batch_grid(int kernel) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int &g = g_grid[dev & 63][kernel & 3];
+    if (!g) {
+        int occ = 0;
+        cudaError_t e = cudaErrorInvalidValue;
+        switch (kernel) {
+            case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_analyze, T, 0); break;
+            case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_build<false>, T, 0); break;
+            case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_build<true>, T, 0); break;
+            default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_apply, AT, 0); break;
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            occ = 1;
+        }
+        g = (occ > 0 ? occ : 1) * sm_count();
+    }
+    return g;
+}
+
+cudaError_t launch_batch_analyze(const BatchMat *mats, const int2 *chunks, long long n_chunks, BatchAcc *acc,
+                                 cudaStream_t s) {
+    if (n_chunks <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<long long>(n_chunks, batch_grid(0));
+    KernelScope ks("batch_analyze", s);
+    k_batch_analyze<<<grid, T, 0, s>>>(mats, chunks, n_chunks, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_tile_info(const BatchMat *mats, int4 *tiles, long long n_tiles, cudaStream_t s) {
+    if (n_tiles <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<long long>((n_tiles + T - 1) / T, (long long)sm_count() * 8);
+    KernelScope ks("batch_tile_info", s);
+    k_batch_tile_info<<<grid, T, 0, s>>>(mats, tiles, n_tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_build(const BatchMat *mats, const int4 *tiles, long long n_tiles, const double *x,
+                               double *y, cudaStream_t s) {
+    if (n_tiles <= 0) return cudaSuccess;
+    if (x) {
+        const unsigned grid = (unsigned)std::min<long long>(n_tiles, batch_grid(2));
+        KernelScope ks("batch_build_apply", s);
+        k_batch_build<true><<<grid, T, 0, s>>>(mats, tiles, n_tiles, x, y);
+    } else {
+        const unsigned grid = (unsigned)std::min<long long>(n_tiles, batch_grid(1));
+        KernelScope ks("batch_build", s);
+        k_batch_build<false><<<grid, T, 0, s>>>(mats, tiles, n_tiles, nullptr, nullptr);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_apply(const BatchMat *mats, const int4 *tiles, long long n_tiles, const double *x,
+                               double *y, cudaStream_t s) {
+    if (n_tiles <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<long long>((n_tiles + AT / 32 - 1) / (AT / 32), batch_grid(3));
+    KernelScope ks("batch_apply", s);
+    k_batch_apply<<<grid, AT, 0, s>>>(mats, tiles, n_tiles, x, y);
+    return cudaGetLastError();
+}
+
+}  // namespace spmvat

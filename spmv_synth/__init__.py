@@ -34,6 +34,8 @@ __all__ = [
     "power_law_xmin",
     "random_crs",
     "banded_random_crs",
+    "batch_matrix",
+    "batch_set",
     "vector_pm1",
 ]
 
@@ -413,3 +415,46 @@ def _sorted_distinct_shift(lens: np.ndarray, width: int, seed: int, stream: int)
         out[ptr[r0]:ptr[r1]] = c.astype(np.int32)
         r0 = r1
     return out
+
+
+def _poisson_inv(lam: float, u: np.ndarray) -> np.ndarray:
+    """Poisson(lam) by inversion of its CDF at uniforms u."""
+    kmax = int(lam + 12.0 * math.sqrt(lam) + 12.0)
+    k = np.arange(kmax + 1, dtype=np.float64)
+    logp = k * math.log(lam) - lam - np.array([math.lgamma(v + 1.0) for v in k])
+    cdf = np.cumsum(np.exp(logp))
+    return np.minimum(np.searchsorted(cdf, u, side="right"), kmax).astype(np.int64)
+
+
+def batch_matrix(idx: int, seed: int = 5, n_lo: int = 100, n_hi: int = 20000) -> CRS:
+    """Matrix `idx` of a batch of small uneven matrices, drawn with seed
+    seed + idx: n = round(exp(U[ln n_lo, ln n_hi])) (stream 30). Even idx: a
+    2-D 5-point stencil (diagonal 4, neighbours -1) on a ceil(sqrt(n)) square
+    grid, natural order, cut to its first n rows and columns. Odd idx: row
+    lengths Poisson(8) (stream 31, at most n), distinct ascending uniform
+    columns (stream 32), values N(0, 1) (stream 33)."""
+    sd = seed + int(idx)
+    u = float(uniform01(sd, 30, np.zeros(1, dtype=np.uint64))[0])
+    n = int(round(math.exp(math.log(n_lo) + u * (math.log(n_hi) - math.log(n_lo)))))
+    n = max(1, n)
+    if idx % 2 == 0:
+        g = int(math.ceil(math.sqrt(n)))
+        i = np.arange(n, dtype=np.int64)
+        gx, gy = i % g, i // g
+        offs = [(-g, gy > 0), (-1, gx > 0), (0, np.ones(n, bool)), (1, (gx < g - 1) & (i + 1 < n)), (g, i + g < n)]
+        cols = np.stack([i + o for o, _ in offs], axis=1)
+        mask = np.stack([m for _, m in offs], axis=1)
+        irp, icol = _compress(cols, mask, n, n)
+        vals = np.where(np.stack([np.full(n, o == 0) for o, _ in offs], axis=1), 4.0, -1.0)
+        return CRS(n, n, irp, icol, vals[mask].astype(np.float64))
+    lens = np.minimum(_poisson_inv(8.0, uniform01(sd, 31, np.arange(n, dtype=np.uint64))), n)
+    irp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=irp[1:])
+    icol = _sorted_unique_cols(lens, n, sd, 32)
+    val = normal(sd, 33, np.arange(int(irp[-1]), dtype=np.uint64))
+    return CRS(n, n, irp.astype(np.int32), icol, val)
+
+
+def batch_set(count: int, seed: int = 5, n_lo: int = 100, n_hi: int = 20000) -> list:
+    """Matrices 0..count-1 of batch_matrix."""
+    return [batch_matrix(i, seed, n_lo, n_hi) for i in range(count)]

@@ -57,3 +57,26 @@ def test_random_crs_options():
     r = np.repeat(np.arange(B.n_rows), np.diff(B.irp))
     key = r * B.n_cols + B.icol
     assert np.all(np.diff(key) >= 0) and np.any(np.diff(key) == 0)
+
+
+def test_batch_matrix_recipe():
+    # even members: the 5-point stencil of a square grid cut to n rows / cols
+    ms = synth.batch_set(40, seed=5)
+    ns = np.array([A.n_rows for A in ms])
+    assert ns.min() >= 100 and ns.max() <= 20000
+    for i, A in enumerate(ms):
+        assert A.n_rows == A.n_cols and A.irp[-1] == A.nnz
+        seg_ok = all(np.all(np.diff(A.icol[A.irp[r]:A.irp[r + 1]]) > 0) for r in range(0, A.n_rows, 17))
+        assert seg_ok and A.icol.min() >= 0 and A.icol.max() < A.n_cols
+        if i % 2 == 0:
+            g = math.ceil(math.sqrt(A.n_rows))
+            full = synth.laplacian_2d_5pt(g)
+            # the cut keeps exactly the entries of the full stencil inside [0, n)^2
+            n = A.n_rows
+            rows = np.repeat(np.arange(full.n_rows), np.diff(full.irp))
+            keep = (rows < n) & (full.icol < n)
+            assert np.array_equal(A.icol, full.icol[keep]) and np.array_equal(A.val, full.val[keep])
+        else:
+            assert abs(np.diff(A.irp).mean() - 8.0) < 8.0 * 5 / math.sqrt(A.n_rows * 8.0) + 0.05
+    B = synth.batch_matrix(7, seed=5)
+    assert np.array_equal(B.icol, ms[7].icol) and np.array_equal(B.val, ms[7].val)
