@@ -315,7 +315,8 @@ typedef struct spmv_batch_plan {
     int32_t max_row_len;
     int32_t format;           /* SPMV_ELL or SPMV_CRS (row-wise) */
     int32_t threads_per_row;  /* CRS: lanes sharing a row (1, 8 or 32); ELL: 1 */
-    int32_t rows_per_tile;    /* rows per warp tile (at most 32) */
+    int32_t rows_per_tile;    /* rows per warp tile; CRS with one lane per entry: at most this
+                                 many rows and 256 entries (a longer row: a tile of its own) */
     int32_t width, ld;        /* ELL: slots per row and leading dimension; CRS: 0 */
     int64_t x_offset, y_offset;
     const double *ell_val;    /* ELL: device float64[width * ld], slot k of row r at k*ld + r;
@@ -330,7 +331,8 @@ typedef struct spmv_batch_plan {
  * (device, concatenated as above) are both given, the build launch also
  * computes y = A x for every matrix; give both or neither. Errors:
  * SPMV_ERR_INVALID_ARG (bad sizes or pointers), SPMV_ERR_INVALID_MATRIX (any
- * matrix with a malformed IRP or a column index out of range), SPMV_ERR_OOM. */
+ * matrix with a malformed IRP or a column index out of range), SPMV_ERR_OOM,
+ * SPMV_ERR_UNSUPPORTED (m above 2^26). */
 spmv_status spmv_batch_create(const spmv_crs *mats, int32_t m, const spmv_at_params *p, const double *x,
                               double *y, spmv_batch **out, spmv_stream_t stream);
 

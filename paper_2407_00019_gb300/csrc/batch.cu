@@ -18,18 +18,17 @@ using namespace spmvat;
 struct spmv_batch {
     int32_t m = 0;
     int64_t total_rows = 0, total_cols = 0, total_nnz = 0;
-    int64_t n_tiles = 0, n_ell_tiles = 0;
+    int64_t n_tiles = 0;
     int32_t n_ell = 0;
     uint64_t ell_bytes = 0;
     std::vector<BatchMat> host_mats;
     std::vector<spmv_batch_plan> plans;
-    BufPtr mats, tiles, ell_tiles, ell_pool;
+    BufPtr mats, tiles, ell_pool;
     const BatchMat *d_mats = nullptr;
     const int4 *d_tiles = nullptr;
-    const int4 *d_ell_tiles = nullptr;
     uint64_t owned() const {
         uint64_t t = 0;
-        for (const BufPtr *b : {&mats, &tiles, &ell_tiles, &ell_pool})
+        for (const BufPtr *b : {&mats, &tiles, &ell_pool})
             if (*b) t += (*b)->bytes;
         return t;
     }
@@ -50,19 +49,6 @@ int threads_per_row(double mu, int max_len) {
     }
     if (max_len <= 256 || mu <= 16.0) return 1;
     return mu <= 128.0 ? 8 : 32;
-}
-
-// Rows of a one-lane-per-entry (merge-path) tile: about kTileEntries entries
-// on average, so that each lane has ~6 entries in flight and a tile rarely
-// exceeds the 256 entries one warp sums at once.
-constexpr double kTileEntries = 192.0;
-int rows_per_stream_tile(double mu) {
-    if (const char *e = std::getenv("SPMVAT_BATCH_RPT")) {
-        const int v = std::atoi(e);
-        if (v >= 1 && v <= 32) return v;
-    }
-    if (mu <= kTileEntries / 32.0) return 32;
-    return std::max(1, std::min(32, (int)(kTileEntries / mu)));
 }
 
 spmv_status check_one(const spmv_crs &A) {
@@ -150,7 +136,7 @@ spmv_status create_core(const spmv_crs *mats, int32_t m, const spmv_at_params *p
         } else {
             D.fmt = BATCH_CRS;
             D.tpr = threads_per_row(P.mu, a.max_len);
-            D.rpt = D.tpr == 1 ? rows_per_stream_tile(P.mu) : 32 / D.tpr;
+            D.rpt = 32 / D.tpr;  // one lane per entry: at most 32 rows (and 256 entries) per tile
         }
         P.format = D.fmt == BATCH_ELL ? SPMV_ELL : SPMV_CRS;
         P.threads_per_row = D.tpr;
@@ -172,30 +158,31 @@ spmv_status create_core(const spmv_crs *mats, int32_t m, const spmv_at_params *p
             B->plans[i].ell_idx = D.ecol;
         }
     }
-    std::vector<int4> tiles, ell_tiles;
-    for (int32_t i = 0; i < m; ++i) {
-        const BatchMat &D = B->host_mats[i];
-        for (int32_t r = 0; r < D.n_rows; r += D.rpt) {
-            tiles.push_back(make_int4(i, r, 0, 0));
-            if (D.fmt == BATCH_ELL && D.width > 0) ell_tiles.push_back(make_int4(i, r, 0, 0));
-        }
-    }
-    B->n_tiles = (int64_t)tiles.size();
-    B->n_ell_tiles = (int64_t)ell_tiles.size();
     // the descriptors again, now with the plan; the analysis launch is done
     // with the first copy (the stream was synchronised above)
     CK(cudaMemcpyAsync(B->mats->p, B->host_mats.data(), sizeof(BatchMat) * (size_t)m, cudaMemcpyHostToDevice, s));
-    CKS(upload(tiles, s, &B->tiles));
-    if (B->n_ell_tiles > 0) CKS(upload(ell_tiles, s, &B->ell_tiles));
     B->d_mats = reinterpret_cast<const BatchMat *>(B->mats->p);
-    CK(launch_batch_tile_info(B->d_mats, reinterpret_cast<int4 *>(B->tiles->p), B->n_tiles, s));
-    if (B->n_ell_tiles > 0)
-        CK(launch_batch_tile_info(B->d_mats, reinterpret_cast<int4 *>(B->ell_tiles->p), B->n_ell_tiles, s));
+    // tiles: count per matrix, offsets on the host, then the records
+    BufPtr cnt_buf;
+    CKS(alloc_buf(sizeof(long long) * (size_t)m, s, &cnt_buf));
+    long long *d_cnt = reinterpret_cast<long long *>(cnt_buf->p);
+    CK(launch_batch_tiles(B->d_mats, m, d_cnt, nullptr, s));
+    std::vector<long long> cnt(m);
+    CK(cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(long long) * (size_t)m, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    long long total = 0;
+    for (int32_t i = 0; i < m; ++i) {
+        const long long c = cnt[i];
+        cnt[i] = total;
+        total += c;
+    }
+    B->n_tiles = total;
+    CK(cudaMemcpyAsync(d_cnt, cnt.data(), sizeof(long long) * (size_t)m, cudaMemcpyHostToDevice, s));
+    CKS(alloc_buf(sizeof(int4) * (size_t)std::max<long long>(total, 1), s, &B->tiles));
+    CK(launch_batch_tiles(B->d_mats, m, d_cnt, reinterpret_cast<int4 *>(B->tiles->p), s));
     B->d_tiles = reinterpret_cast<const int4 *>(B->tiles->p);
-    B->d_ell_tiles = B->ell_tiles ? reinterpret_cast<const int4 *>(B->ell_tiles->p) : nullptr;
     // One launch builds every ELL matrix (and, given x, computes y for all).
-    if (x) CK(launch_batch_build(B->d_mats, B->d_tiles, B->n_tiles, x, y, s));
-    else if (B->n_ell_tiles > 0) CK(launch_batch_build(B->d_mats, B->d_ell_tiles, B->n_ell_tiles, nullptr, nullptr, s));
+    if (x || B->n_ell > 0) CK(launch_batch_build(B->d_mats, B->d_tiles, B->n_tiles, x, y, s));
     return SPMV_OK;
 }
 
@@ -208,6 +195,7 @@ spmv_status spmv_batch_create(const spmv_crs *mats, int32_t m, const spmv_at_par
     if (!out) return SPMV_ERR_INVALID_ARG;
     *out = nullptr;
     if (!mats || m <= 0) return SPMV_ERR_INVALID_ARG;
+    if (m > (1 << kBatchMatBits)) return SPMV_ERR_UNSUPPORTED;
     if ((x == nullptr) != (y == nullptr)) return SPMV_ERR_INVALID_ARG;
     for (int32_t i = 0; i < m; ++i) CKS(check_one(mats[i]));
     spmv_batch *B = new (std::nothrow) spmv_batch();

@@ -236,9 +236,9 @@ cudaError_t launch_bin_rows(const int32_t *irp, int32_t n_rows, void *scratch, i
                             int *status, cudaStream_t s);
 
 // Batches of independent matrices (kernels_batch.cu). One descriptor per
-// matrix; work items ("tiles") are records {matrix, first row, first entry,
-// entry count} of at most 32 rows that never cross a matrix, ordered by
-// matrix.
+// matrix; work items ("tiles") are records {matrix and row count, first
+// row, first entry, entry count} of at most 32 rows that never cross a
+// matrix, ordered by matrix.
 enum : int { BATCH_CRS = 0, BATCH_ELL = 2 };
 struct BatchMat {
     const int32_t *irp, *icol;  // the caller's CRS
@@ -251,7 +251,7 @@ struct BatchMat {
     int width, ld;              // ELL width and leading dimension
     int fmt;                    // BATCH_CRS or BATCH_ELL
     int tpr;                    // CRS tiles: lanes per row (1, 8, 32)
-    int rpt;                    // rows per tile (1..32)
+    int rpt;                    // rows per tile (1..32; CRS with one lane per entry: at most)
     int pad;
 };
 struct BatchAcc {               // per-matrix statistics of the analysis pass
@@ -262,14 +262,16 @@ struct BatchAcc {               // per-matrix statistics of the analysis pass
     int status;
 };
 constexpr int kBatchThreads = 256;
+constexpr int kBatchMatBits = 26;  // tile records pack the matrix index (< 2^26) and the row count
 constexpr int kBatchChunk = 2048; // rows per work item of the analysis pass
 int batch_grid(int kernel);       // persistent grid: 0 analyze, 1 build, 2 build+multiply, 3 apply
 cudaError_t launch_batch_analyze(const BatchMat *mats, const int2 *chunks, long long n_chunks, BatchAcc *acc,
                                  cudaStream_t s);
 // ELL transform of the ELL matrices' tiles; with x (and y) also y = A x for
 // every tile given.
-// Entry range (.z, .w) of every tile record from the descriptors' IRP.
-cudaError_t launch_batch_tile_info(const BatchMat *mats, int4 *tiles, long long n_tiles, cudaStream_t s);
+// Tile records of every matrix: with tiles == NULL the count per matrix
+// into cnt[m]; otherwise the records, matrix i's from tiles[cnt[i]] on.
+cudaError_t launch_batch_tiles(const BatchMat *mats, int m, long long *cnt, int4 *tiles, cudaStream_t s);
 cudaError_t launch_batch_build(const BatchMat *mats, const int4 *tiles, long long n_tiles, const double *x,
                                double *y, cudaStream_t s);
 cudaError_t launch_batch_apply(const BatchMat *mats, const int4 *tiles, long long n_tiles, const double *x,

@@ -34,6 +34,10 @@ constexpr int T = kBatchThreads;
 constexpr int WCAP = 256;  // entries a warp stages at once (8 per lane)
 constexpr int WU = WCAP / 32;
 constexpr int MMAX = 8;    // merge-path: entries per lane, so tiles of up to 256 entries
+// Greedy tiles of several rows stop at 224 entries (m <= 7): lane j reads
+// slot j * m + u of the shared arrays, and m = 8 would put 8 lanes on each
+// bank; m = 5 and 7, the usual sizes, give at most 2.
+constexpr int kTileCap = 224;
 struct WarpSmem {          // staging of the ELL build and the long-tile product
     double v[WCAP];
     double xv[WCAP];       // x at the staged entries' columns, or their column indices
@@ -224,11 +228,12 @@ __device__ __forceinline__ void merge_tile(RowSmem &rs, const int32_t *__restric
     merge_sum(rs.last, rs.run, m, beg, end, nr, rb, re, v, xv, y + row0);
 }
 
-// Tiles too large for merge_tile: 8 lanes per row, 4 rows at a time.
-__device__ __forceinline__ void vector_rows8(const int32_t *__restrict__ irp, const int32_t *__restrict__ icol,
-                                             const double *__restrict__ val, int row0, int nr,
-                                             const double *__restrict__ x, double *__restrict__ y) {
-    for (int r0 = 0; r0 < nr; r0 += 4) vector_tile<8>(irp, icol, val, row0 + r0, min(4, nr - r0), x, y);
+// A CRS tile of one lane per entry with more than 32 * MMAX entries: by
+// construction a single row, summed by the whole warp.
+__device__ __forceinline__ void long_rows(const int32_t *__restrict__ irp, const int32_t *__restrict__ icol,
+                                          const double *__restrict__ val, int row0, int nr,
+                                          const double *__restrict__ x, double *__restrict__ y) {
+    for (int r = 0; r < nr; ++r) vector_tile<32>(irp, icol, val, row0 + r, 1, x, y);
 }
 
 // ELL-Row rows [row0, row0 + nr), nr <= 32, one lane per row, slots summed in
@@ -310,7 +315,7 @@ __device__ __forceinline__ void crs_tile(RowSmem &rs, const BatchMat *__restrict
         case 32: vector_tile<32>(irp, icol, val, row0, nr, x, y); break;
         default:
             if (n <= 32 * MMAX) merge_tile(rs, irp, icol, val, row0, nr, e0, n, x, y);
-            else vector_rows8(irp, icol, val, row0, nr, x, y);
+            else long_rows(irp, icol, val, row0, nr, x, y);
             break;
     }
 }
@@ -392,17 +397,54 @@ __global__ void __launch_bounds__(T) k_batch_analyze(const BatchMat *__restrict_
     }
 }
 
-// Fills entries .z (first entry) and .w (entry count) of every tile record.
-__global__ void __launch_bounds__(T) k_batch_tile_info(const BatchMat *__restrict__ mats, int4 *__restrict__ tiles,
-                                                       long long n_tiles) {
-    for (long long t = (long long)blockIdx.x * T + threadIdx.x; t < n_tiles; t += (long long)gridDim.x * T) {
-        int4 tl = tiles[t];
-        const BatchMat *M = mats + tl.x;
-        const int nr = min(M->rpt, M->n_rows - tl.y);
-        const int a = __ldg(M->irp + tl.y), b = __ldg(M->irp + tl.y + nr);
-        tl.z = a;
-        tl.w = b - a;
-        tiles[t] = tl;
+// .x of a tile record: the matrix index (below 2^26) and the row count
+// (1..32, stored minus one in the top bits).
+__device__ __forceinline__ int tile_key(int mat, int nr) { return mat | ((nr - 1) << kBatchMatBits); }
+__device__ __forceinline__ int tile_mat(int key) { return key & ((1 << kBatchMatBits) - 1); }
+__device__ __forceinline__ int tile_rows(int key) { return (int)((unsigned)key >> kBatchMatBits) + 1; }
+
+// Tiles of every matrix, one warp per matrix, in row order. CRS matrices
+// with one lane per entry: greedy runs of whole rows, at most 32 rows and
+// kTileCap entries each (a longer row is a tile of its own: a merge tile up
+// to 32 * MMAX entries, else summed by the whole warp). Other matrices: rpt rows per tile. Without FILL, writes the
+// tile count of each matrix to cnt[i]; with FILL, writes the records
+// {matrix, first row, first entry, entries} from tiles[cnt[i]] on.
+template <bool FILL>
+__global__ void __launch_bounds__(T) k_batch_tiles(const BatchMat *__restrict__ mats, int m,
+                                                   long long *__restrict__ cnt, int4 *__restrict__ tiles) {
+    const int lane = (int)lane_id();
+    const int nwarps = (int)(gridDim.x * (T / 32));
+    for (int i = (int)(blockIdx.x * (T / 32) + (threadIdx.x >> 5)); i < m; i += nwarps) {
+        const BatchMat *M = mats + i;
+        const int n = M->n_rows;
+        const int32_t *irp = M->irp;
+        const long long out = FILL ? cnt[i] : 0;
+        long long count = 0;
+        if (M->fmt == BATCH_CRS && M->tpr == 1) {
+            int r = 0;
+            while (r < n) {
+                const int rows = min(32, n - r);
+                const int e0 = __ldg(irp + r);
+                const int end_l = lane < rows ? __ldg(irp + r + lane + 1) : INT_MAX;
+                const unsigned fit = __ballot_sync(0xffffffffu, lane < rows && end_l - e0 <= kTileCap);
+                const int k = max(1, __popc(fit));  // row ends grow with the lane: rows r .. r + k - 1 fit
+                const int e1 = __shfl_sync(0xffffffffu, end_l, k - 1);
+                if (FILL && lane == 0) tiles[out + count] = make_int4(tile_key(i, k), r, e0, e1 - e0);
+                ++count;
+                r += k;
+            }
+        } else {
+            const int rpt = M->rpt;
+            count = (n + rpt - 1) / rpt;
+            if (FILL) {
+                for (long long k = lane; k < count; k += 32) {
+                    const int r = (int)k * rpt, nr = min(rpt, n - r);
+                    const int a = __ldg(irp + r), b = __ldg(irp + r + nr);
+                    tiles[out + k] = make_int4(tile_key(i, nr), r, a, b - a);
+                }
+            }
+        }
+        if (!FILL && lane == 0) cnt[i] = count;
     }
 }
 
@@ -416,8 +458,8 @@ __global__ void __launch_bounds__(T) k_batch_build(const BatchMat *__restrict__ 
     const long long nw = (long long)gridDim.x * (T / 32);
     for (long long t = (long long)blockIdx.x * (T / 32) + (threadIdx.x >> 5); t < n_tiles; t += nw) {
         const int4 tl = __ldg(tiles + t);
-        const BatchMat *M = mats + tl.x;
-        const int nr = min(M->rpt, M->n_rows - tl.y);
+        const BatchMat *M = mats + tile_mat(tl.x);
+        const int nr = tile_rows(tl.x);
         const double *xm = MUL ? x + M->xoff : nullptr;
         double *ym = MUL ? y + M->yoff : nullptr;
         if (M->fmt == BATCH_ELL) ell_build_tile<MUL>(ws, M, tl.y, nr, xm, ym);
@@ -471,16 +513,17 @@ __global__ void __launch_bounds__(AT) k_batch_apply(const BatchMat *__restrict__
     long long t = (long long)blockIdx.x * (AT / 32) + (threadIdx.x >> 5);
     if (t >= n_tiles) return;
     int4 cur = __ldg(tiles + t);
-    if (is_merge(mats + cur.x, cur.w)) stage_issue(ps, 0, mats + cur.x, cur.z, cur.w);
+    if (is_merge(mats + tile_mat(cur.x), cur.w)) stage_issue(ps, 0, mats + tile_mat(cur.x), cur.z, cur.w);
     cp_async_commit();
     int4 nxt = t + nw < n_tiles ? __ldg(tiles + t + nw) : cur;
     for (int it = 0; t < n_tiles; t += nw, ++it) {
         const int st = it & 1;
-        if (t + nw < n_tiles && is_merge(mats + nxt.x, nxt.w)) stage_issue(ps, st ^ 1, mats + nxt.x, nxt.z, nxt.w);
+        if (t + nw < n_tiles && is_merge(mats + tile_mat(nxt.x), nxt.w))
+            stage_issue(ps, st ^ 1, mats + tile_mat(nxt.x), nxt.z, nxt.w);
         cp_async_commit();
         const int4 after = t + 2 * nw < n_tiles ? __ldg(tiles + t + 2 * nw) : nxt;
-        const BatchMat *M = mats + cur.x;
-        const int nr = min(M->rpt, M->n_rows - cur.y);
+        const BatchMat *M = mats + tile_mat(cur.x);
+        const int nr = tile_rows(cur.x);
         const double *xm = x + M->xoff;
         double *ym = y + M->yoff;
         if (M->fmt == BATCH_ELL) {
@@ -504,8 +547,9 @@ __global__ void __launch_bounds__(AT) k_batch_apply(const BatchMat *__restrict__
         } else {
             const int32_t *irp = M->irp, *icol = M->icol;
             const double *val = M->val;
-            if (M->tpr == 32) vector_tile<32>(irp, icol, val, cur.y, nr, xm, ym);
-            else vector_rows8(irp, icol, val, cur.y, nr, xm, ym);
+            if (M->tpr == 8) vector_tile<8>(irp, icol, val, cur.y, nr, xm, ym);
+            else if (M->tpr == 32) vector_tile<32>(irp, icol, val, cur.y, nr, xm, ym);
+            else long_rows(irp, icol, val, cur.y, nr, xm, ym);
         }
         cur = nxt;
         nxt = after;
@@ -548,11 +592,16 @@ cudaError_t launch_batch_analyze(const BatchMat *mats, const int2 *chunks, long 
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_tile_info(const BatchMat *mats, int4 *tiles, long long n_tiles, cudaStream_t s) {
-    if (n_tiles <= 0) return cudaSuccess;
-    const unsigned grid = (unsigned)std::min<long long>((n_tiles + T - 1) / T, (long long)sm_count() * 8);
-    KernelScope ks("batch_tile_info", s);
-    k_batch_tile_info<<<grid, T, 0, s>>>(mats, tiles, n_tiles);
+cudaError_t launch_batch_tiles(const BatchMat *mats, int m, long long *cnt, int4 *tiles, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<long long>((m + T / 32 - 1) / (T / 32), (long long)sm_count() * 8);
+    if (tiles) {
+        KernelScope ks("batch_tiles", s);
+        k_batch_tiles<true><<<grid, T, 0, s>>>(mats, m, cnt, tiles);
+    } else {
+        KernelScope ks("batch_tile_count", s);
+        k_batch_tiles<false><<<grid, T, 0, s>>>(mats, m, cnt, nullptr);
+    }
     return cudaGetLastError();
 }
 
