@@ -350,6 +350,76 @@ spmv_status spmv_batch_plan_get(const spmv_batch *B, int32_t first, int32_t coun
 /* Frees the batch's device memory (stream-ordered on the creating stream). */
 void spmv_batch_destroy(spmv_batch *B);
 
+/* ---- Serving: continuous batching over a pool of matrices ----------------
+ * A server owns N CUDA streams ("slots") and a worker thread. Clients
+ * register matrices (the pool) and submit requests; a request asks for k
+ * products y_j = A x_j with one matrix of the pool. The worker admits queued
+ * requests in arrival order whenever a slot is free, so requests start and
+ * finish independently (no batch barrier). Per matrix it keeps a resident
+ * format cache: the on-line rule of Sec. 2.2 picks the target format at
+ * registration (ELL-Row iff D_mat < dstar and its ELL fits the budget), and
+ * the transformation is built, once, when the matrix has been asked for at
+ * least amortize_products products in total (the transformation costs a few
+ * CRS products, Sec. 2.2; it pays off only over several). Until then, and
+ * whenever the cache is full, requests run on CRS. Cached formats are evicted
+ * least-recently-used, never while a request uses them; the cache never holds
+ * more than mem_budget_bytes. The paper has no serving layer: this is the
+ * library's use of its method under a stream of requests. */
+typedef struct spmv_server spmv_server;
+
+typedef struct spmv_server_params {
+    uint64_t mem_budget_bytes;   /* device bytes the format cache may hold; 0 = no limit */
+    double dstar;                /* D*: target format ELL-Row iff D_mat < dstar */
+    int32_t n_streams;           /* slots (requests in flight); <= 0 means 4 */
+    int32_t amortize_products;   /* products seen before a transformation is built; <= 0 means 2 */
+    int32_t flags;               /* reserved, 0 */
+    int32_t pad;
+} spmv_server_params;
+
+typedef struct spmv_server_stats {
+    uint64_t submitted, completed, failed, products;
+    double bytes;                /* algorithmic bytes of the completed products (byte model of the format used) */
+    double p50_ms, p99_ms, mean_ms, max_ms; /* submit -> completion, completed requests */
+    double busy_s;               /* first submission to last completion */
+    uint64_t cache_hits;         /* requests served from a cached transformation */
+    uint64_t cache_misses;       /* requests served in CRS while their target was ELL-Row */
+    uint64_t transforms, evictions;
+    uint64_t cache_bytes, peak_cache_bytes;
+} spmv_server_stats;
+
+/* Creates the server and its worker thread on the current CUDA device. */
+spmv_status spmv_server_create(const spmv_server_params *p, spmv_server **out);
+
+/* SYNC. Adds a matrix (device arrays owned by the caller, kept alive and
+ * unchanged until spmv_server_destroy) to the pool: analysis, target format,
+ * CRS schedule. *id receives its index. */
+spmv_status spmv_server_add_matrix(spmv_server *S, const spmv_crs *A, int32_t *id);
+
+/* Queues a request of k >= 0 products with matrix `id`: x (device,
+ * k * n_cols float64, product j reads x + j * n_cols) and y (device,
+ * k * n_rows float64, overwritten). If `after` is not NULL, the request
+ * starts only after the work enqueued on that stream so far (the producer of
+ * x). The caller keeps x and y alive until the request completes. *req
+ * receives the request's id. Thread-safe. */
+spmv_status spmv_server_submit(spmv_server *S, int32_t id, int32_t k, const double *x, double *y,
+                               spmv_stream_t after, uint64_t *req);
+
+/* Waits up to timeout_ms (< 0: no limit) for request `req`; then returns its
+ * status (SPMV_ERR_TIMEOUT if it has not completed) and, if the pointers are
+ * not NULL, its latency (ms) and the format it ran in. A request can be
+ * waited for once. Thread-safe. */
+spmv_status spmv_server_wait(spmv_server *S, uint64_t req, int32_t timeout_ms, double *latency_ms,
+                             int32_t *format);
+
+/* Waits up to timeout_ms for every submitted request. */
+spmv_status spmv_server_drain(spmv_server *S, int32_t timeout_ms);
+
+/* Counters and latency percentiles; reset != 0 clears them afterwards. */
+spmv_status spmv_server_stats_get(spmv_server *S, spmv_server_stats *out, int32_t reset);
+
+/* Drains, stops the worker and frees the cache and the streams. */
+void spmv_server_destroy(spmv_server *S);
+
 /* Instrumentation: number of kernels this library has launched so far. */
 uint64_t spmv_launch_count(void);
 

@@ -24,7 +24,7 @@ __all__ = [
     "spmv_describe", "spmv_matrix_status", "spmv_destroy", "spmv_r_ell", "spmv_dstar_from_points", "spmv_measure",
     "spmv_calibrate", "spmv_autotune", "spmv_autotune_choose", "spmv_apply_coo_row_noalloc", "spmv_launch_count", "spmv_profile_enable", "spmv_profile_read",
     "spmv_debug_scan_timeout", "spmv_batch_create", "spmv_batch_apply", "spmv_batch_info_get",
-    "spmv_batch_plan_get", "spmv_batch_destroy", "Batch",
+    "spmv_batch_plan_get", "spmv_batch_destroy", "Batch", "Server", "spmv_server_create",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -89,6 +89,18 @@ class _BatchPlanT(ctypes.Structure):
                 ("ell_idx", ctypes.c_void_p)]
 
 
+class _ServerParamsT(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("dstar", ctypes.c_double), ("n_streams", ctypes.c_int32),
+                ("amortize_products", ctypes.c_int32), ("flags", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class _ServerStatsT(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "products")] + \
+               [(n, ctypes.c_double) for n in ("bytes", "p50_ms", "p99_ms", "mean_ms", "max_ms", "busy_s")] + \
+               [(n, ctypes.c_uint64) for n in ("cache_hits", "cache_misses", "transforms", "evictions",
+                                                "cache_bytes", "peak_cache_bytes")]
+
+
 class _KernelTimeT(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
 
@@ -145,6 +157,13 @@ def load_library():
         "spmv_batch_info_get": (ctypes.c_int, [vp, P(_BatchInfoT)]),
         "spmv_batch_plan_get": (ctypes.c_int, [vp, i32, i32, P(_BatchPlanT)]),
         "spmv_batch_destroy": (None, [vp]),
+        "spmv_server_create": (ctypes.c_int, [P(_ServerParamsT), P(vp)]),
+        "spmv_server_add_matrix": (ctypes.c_int, [vp, P(_CrsT), P(i32)]),
+        "spmv_server_submit": (ctypes.c_int, [vp, i32, i32, vp, vp, vp, P(u64)]),
+        "spmv_server_wait": (ctypes.c_int, [vp, u64, i32, P(dbl), P(i32)]),
+        "spmv_server_drain": (ctypes.c_int, [vp, i32]),
+        "spmv_server_stats_get": (ctypes.c_int, [vp, P(_ServerStatsT), i32]),
+        "spmv_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -510,3 +529,63 @@ def spmv_batch_plan_get(B: Batch, first: int = 0, count=None) -> list:
 
 def spmv_batch_destroy(B: Batch) -> None:
     B.close()
+
+
+class Server:
+    """Owning wrapper of an spmv_server (continuous batching over a matrix
+    pool); keeps the registered matrices alive."""
+
+    def __init__(self, mem_budget_bytes=0, dstar=0.0, n_streams=4, amortize_products=2):
+        p = _ServerParamsT(int(mem_budget_bytes), float(dstar), int(n_streams), int(amortize_products), 0, 0)
+        h = ctypes.c_void_p()
+        _check(load_library().spmv_server_create(ctypes.byref(p), ctypes.byref(h)), "spmv_server_create")
+        self.handle = h
+        self._mats = []
+
+    def add_matrix(self, A: Crs) -> int:
+        i = ctypes.c_int32()
+        _check(load_library().spmv_server_add_matrix(self.handle, ctypes.byref(A.c), ctypes.byref(i)),
+               "spmv_server_add_matrix")
+        self._mats.append(A)
+        return i.value
+
+    def submit(self, mat_id: int, k: int, x, y, after=None) -> int:
+        """Queue k products with matrix mat_id: x (k * n_cols), y (k * n_rows)
+        device tensors; `after`: a stream whose current work must finish first
+        (default: the current torch stream)."""
+        r = ctypes.c_uint64()
+        _check(load_library().spmv_server_submit(self.handle, int(mat_id), int(k), _ptr(x), _ptr(y),
+                                                 _stream(after), ctypes.byref(r)), "spmv_server_submit")
+        return r.value
+
+    def wait(self, req: int, timeout_ms: int = -1):
+        """Returns (latency_ms, format) of a completed request."""
+        lat, fmt = ctypes.c_double(), ctypes.c_int32()
+        _check(load_library().spmv_server_wait(self.handle, ctypes.c_uint64(req), int(timeout_ms),
+                                               ctypes.byref(lat), ctypes.byref(fmt)), "spmv_server_wait")
+        return lat.value, fmt.value
+
+    def drain(self, timeout_ms: int = -1) -> None:
+        _check(load_library().spmv_server_drain(self.handle, int(timeout_ms)), "spmv_server_drain")
+
+    def stats(self, reset: bool = False) -> dict:
+        st = _ServerStatsT()
+        _check(load_library().spmv_server_stats_get(self.handle, ctypes.byref(st), int(bool(reset))),
+               "spmv_server_stats_get")
+        return {f: getattr(st, f) for f, _ in _ServerStatsT._fields_}
+
+    def close(self):
+        if self.handle and self.handle.value:
+            load_library().spmv_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+            self._mats = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spmv_server_create(**kw) -> Server:
+    return Server(**kw)

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libspmvat.so")
 SOURCES = ["api.cu", "kernels_rowwise.cu", "kernels_colwise.cu", "kernels_spmv.cu", "noalloc.cu", "batch.cu",
-           "kernels_batch.cu"]
+           "kernels_batch.cu", "server.cu"]
 HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "stage_pipe.cuh"), os.path.join(CSRC, "host_mem.h"), os.path.join(INCLUDE, "spmvat.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

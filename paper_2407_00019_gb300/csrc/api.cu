@@ -584,7 +584,6 @@ spmv_status apply_core(const spmv_matrix *M, const double *x, double *y, cudaStr
             }
             case SPMV_ELL:
                 if (M->width == 0) { CK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)M->n_rows, s)); return SPMV_OK; }
-                if ((reinterpret_cast<uintptr_t>(y) & 15) != 0) return SPMV_ERR_INVALID_ARG;
                 CK(launch_spmv_ell_row(M->val, M->idx, M->n_rows, M->width, M->ld, x, y, s));
                 return SPMV_OK;
         }

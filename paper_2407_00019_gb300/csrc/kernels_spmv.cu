@@ -554,7 +554,7 @@ template <int UNROLL>
 __global__ void __launch_bounds__(256) k_spmv_ell_row(const double *__restrict__ eval,
                                                        const int32_t *__restrict__ eidx, int32_t n_rows,
                                                        int32_t width, int32_t ld, const double *__restrict__ x,
-                                                       double *__restrict__ y) {
+                                                       double *__restrict__ y, bool y16) {
     const long long pairs = ((long long)n_rows + 1) >> 1;
     const long long step = (long long)ld >> 1;  // one slot column, in double2 / int2
     const double2 *pv = reinterpret_cast<const double2 *>(eval);
@@ -584,10 +584,11 @@ __global__ void __launch_bounds__(256) k_spmv_ell_row(const double *__restrict__
             a1 = fma(v.y, __ldg(x + c.y), a1);
         }
         const long long i = 2 * p;
-        if (i + 1 < n_rows) {
+        if (y16 && i + 1 < n_rows) {
             __stcs(reinterpret_cast<double2 *>(y + i), make_double2(a0, a1));
         } else {
             y[i] = a0;
+            if (i + 1 < n_rows) y[i + 1] = a1;
         }
     }
 }
@@ -595,11 +596,11 @@ __global__ void __launch_bounds__(256) k_spmv_ell_row(const double *__restrict__
 cudaError_t launch_spmv_ell_row(const double *eval, const int32_t *eidx, int32_t n_rows, int32_t width,
                                 int32_t ld, const double *x, double *y, cudaStream_t s) {
     if (n_rows <= 0) return cudaSuccess;
-    if ((reinterpret_cast<uintptr_t>(y) & 15) != 0) return cudaErrorMisalignedAddress;
+    const bool y16 = (reinterpret_cast<uintptr_t>(y) & 15) == 0;  // else two 8-byte stores per pair
     const long long pairs = ((long long)n_rows + 1) >> 1;
     const unsigned grid = ceil_div_u(pairs, 256);
     KernelScope ks("spmv_ell_row", s);
-    k_spmv_ell_row<4><<<grid, 256, 0, s>>>(eval, eidx, n_rows, width, ld, x, y);
+    k_spmv_ell_row<4><<<grid, 256, 0, s>>>(eval, eidx, n_rows, width, ld, x, y, y16);
     return cudaGetLastError();
 }
 

@@ -226,6 +226,28 @@ def test_unaligned_caller_arrays_take_the_global_path():
         M.close()
 
 
+def test_outputs_at_any_8_byte_offset():
+    """y (and x) need only 8-byte alignment: every row-wise format writes the
+    same bits into y + 1 as into an aligned y."""
+    import torch
+    L = lib()
+    H = synth.laplacian_2d_5pt(37, 23)  # odd row count
+    A = dev(H)
+    xh = xvec(H.n_cols, seed=8)
+    xb = torch.empty(H.n_cols + 1, dtype=torch.float64, device="cuda")
+    xb[1:].copy_(torch.from_numpy(xh))
+    for fmt in (L.SPMV_CRS, L.SPMV_COO, L.SPMV_ELL):
+        M = L.spmv_transform(A, fmt, L.SPMV_ROWWISE)
+        ya = torch.empty(H.n_rows, dtype=torch.float64, device="cuda")
+        yb = torch.full((H.n_rows + 1,), float("nan"), dtype=torch.float64, device="cuda")
+        L.spmv_apply(M, xb[1:], ya)
+        L.spmv_apply(M, xb[1:], yb[1:])
+        torch.cuda.synchronize()
+        assert np.array_equal(bits(ya.cpu().numpy()), bits(yb[1:].cpu().numpy()))
+        assert_spmv_close(ya.cpu().numpy(), H, xh, what=f"offset y, format {fmt}")
+        M.close()
+
+
 @pytest.mark.parametrize("kernel,S", [("rows", 1), ("rows", 2), ("rows", 4), ("rows", 8), ("tile", 1), ("tile", 2), ("tile", 4), ("tile", 8), ("stream", 1),
                                       ("stream", 2), ("stream", 4), ("stream", 8), ("vector", 0)])
 def test_crs_kernel_variants(monkeypatch, kernel, S):
