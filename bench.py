@@ -48,6 +48,11 @@ WORKLOADS = {
     "batch_10k": dict(kind="batch", count=10000, seed=5, n_lo=100, n_hi=20000, cap=60 * 10 ** 9,
                       desc="10,000 matrices, n log-uniform in [100, 20000]; even: 2-D 5-point stencil on a "
                            "ceil(sqrt(n)) grid cut to n, odd: Poisson(8) row lengths, unique random columns"),
+    "serve_300": dict(kind="serve", count=300, seed=6, n_lo=1000, n_hi=200000, rate=2000.0, kmax=64,
+                      requests=4000, warm_requests=300, budget=60 * 10 ** 9, streams=8, amortize=2,
+                      desc="serving: pool of 300 matrices, n log-uniform in [1e3, 2e5], half cut 2-D 5-point "
+                           "stencils, half power law (mean 16); Poisson arrivals at 2000/s, 1-64 products per "
+                           "request with fresh seeded x; 60 GB format-cache budget"),
 }
 DEFAULT_WORKLOAD = "stencil27_128"
 
@@ -568,6 +573,125 @@ def run_batch(args, w: dict) -> None:
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------- serving
+def _serve_part(args):
+    import spmv_synth as synth
+    lo, hi, seed, n_lo, n_hi = args
+    return [synth.serve_matrix(i, seed, n_lo, n_hi) for i in range(lo, hi)]
+
+
+def run_serve(args, w: dict) -> None:
+    """Requests arrive as a Poisson process; each asks for k products with one
+    matrix of the pool. The client (this process) makes each request's x on
+    the device from a per-request seed, submits it and moves on; a waiter
+    thread collects completions. Reported: aggregate algorithmic GB/s over
+    the served interval and submit-to-completion latency percentiles."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import threading
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "serving has no CPU counterpart: the oracle "
+                              "computes products, it does not schedule requests"}), flush=True)
+        return
+    seed = w["seed"] + 100000 * rank
+    parts = [(lo, min(w["count"], lo + 20), seed, w["n_lo"], w["n_hi"]) for lo in range(0, w["count"], 20)]
+    workers = max(1, min(16, (os.cpu_count() or 2) - 1))
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        pool = [H for part in ex.map(_serve_part, parts) for H in part]
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    import paper_2407_00019_gb300 as L
+    L.load_library()
+    dev = L.Crs.batch_from_host(pool, device=device)
+    dstar = args.dstar if args.dstar is not None else calibrate_dstar(L, torch)[0]
+    S = L.Server(mem_budget_bytes=w["budget"], dstar=dstar, n_streams=w["streams"],
+                 amortize_products=w["amortize"])
+    ids = [S.add_matrix(A) for A in dev]
+    rng = __import__("numpy").random.default_rng(seed)
+    n_req = w["warm_requests"] + w["requests"]
+    gaps = rng.exponential(1.0 / w["rate"], size=n_req)
+    mats = rng.integers(0, len(pool), size=n_req)
+    ks = rng.integers(1, w["kmax"] + 1, size=n_req)
+    done_q, lock = [], threading.Lock()
+
+    def waiter():
+        while True:
+            with lock:
+                item = done_q.pop(0) if done_q else None
+            if item is None:
+                time.sleep(0.0002)
+                continue
+            if item == "stop":
+                return
+            S.wait(item[0], 600000)
+
+    th = threading.Thread(target=waiter, daemon=True)
+    th.start()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = None
+    t0 = time.perf_counter()
+    t_next = t0
+    for r in range(n_req):
+        if r == w["warm_requests"]:
+            S.drain(600000)
+            S.stats(reset=True)
+            launches0 = L.spmv_launch_count()
+            h0 = time.perf_counter()
+            t_next = h0
+        t_next += gaps[r]
+        while time.perf_counter() < t_next:
+            pass
+        i, k = int(mats[r]), int(ks[r])
+        A = dev[i]
+        g = torch.Generator(device=device)
+        g.manual_seed(seed * 1000003 + r)
+        x = torch.rand(k * A.n_cols, generator=g, dtype=torch.float64, device=device)
+        y = torch.empty(k * A.n_rows, dtype=torch.float64, device=device)
+        h = S.submit(ids[i], k, x, y)
+        with lock:
+            done_q.append((h, x, y))
+    S.drain(600000)
+    h1 = time.perf_counter()
+    with lock:
+        done_q.append("stop")
+    th.join()
+    clocks.mark(h0, h1)
+    clk = clocks.stop()
+    launches = L.spmv_launch_count() - launches0
+    st = S.stats()
+    S.close()
+    value = st["bytes"] / st["busy_s"] / 1e9 if st["busy_s"] > 0 else 0.0
+    peak, peak_kind = measured_hbm_peak()
+    t_max, b_all = reduce_max_sum(torch, st["busy_s"] * 1e3, st["bytes"], device)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": b_all / (t_max * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": world,
+            "steps": w["requests"], "warmup": w["warm_requests"], "ms_per_step": st["busy_s"] * 1e3 / w["requests"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": w["desc"], "pool_nnz": int(sum(H.nnz for H in pool)),
+                       "pool_rows": int(sum(H.n_rows for H in pool)), "streams": w["streams"],
+                       "amortize_products": w["amortize"], "dstar": dstar if math.isfinite(dstar) else "inf",
+                       "offered_req_per_s": w["rate"], "parallelism": f"replicas x{world}"},
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
+            "served_req_per_s": st["completed"] / st["busy_s"] if st["busy_s"] > 0 else None,
+            "products": st["products"], "frac_of_hbm_peak": value / peak, "peak": peak, "peak_source": peak_kind,
+            "cache": {k: st[k] for k in ("cache_hits", "cache_misses", "transforms", "evictions", "cache_bytes",
+                                         "peak_cache_bytes")},
+            "gpu_launches": int(launches), "clocks": clk,
+            "e2e": None, "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 # ------------------------------------------------------------------- main
 def measured_hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -611,13 +735,19 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--rate", type=float, default=None, help="serving: offered requests per second")
     ap.add_argument("--dstar", type=float, default=None,
                     help="use this D* instead of the off-line calibration (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.rate is not None:
+        w["rate"] = args.rate
     if w["kind"] == "batch":
         run_batch(args, w)
+        return
+    if w["kind"] == "serve":
+        run_serve(args, w)
         return
     if args.impl == "reference":
         run_reference(args, w)

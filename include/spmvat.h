@@ -358,21 +358,25 @@ void spmv_batch_destroy(spmv_batch *B);
  * finish independently (no batch barrier). Per matrix it keeps a resident
  * format cache: the on-line rule of Sec. 2.2 picks the target format at
  * registration (ELL-Row iff D_mat < dstar and its ELL fits the budget), and
- * the transformation is built, once, when the matrix has been asked for at
- * least amortize_products products in total (the transformation costs a few
- * CRS products, Sec. 2.2; it pays off only over several). Until then, and
- * whenever the cache is full, requests run on CRS. Cached formats are evicted
+ * the transformation is built, once, when the matrix has been asked for as
+ * many products in total as it takes to pay for it: k >= TT / (1 - 1/SP)
+ * (Sec. 2.2, Eqs. (1)-(3), with the bytes each step moves standing in for its
+ * time), and at least amortize_products. A transformation that can never pay
+ * (SP <= 1) or would fill more than a quarter of the budget is not built.
+ * Until then, and whenever the cache is full, requests run on CRS. Cached formats are evicted
  * least-recently-used, never while a request uses them; the cache never holds
  * more than mem_budget_bytes. The paper has no serving layer: this is the
  * library's use of its method under a stream of requests. */
 typedef struct spmv_server spmv_server;
 
+#define SPMV_SERVER_FIXED_THRESHOLD 1 /* flag: build after amortize_products products, without the
+                                          break-even model (only the budget limits the cache) */
 typedef struct spmv_server_params {
     uint64_t mem_budget_bytes;   /* device bytes the format cache may hold; 0 = no limit */
     double dstar;                /* D*: target format ELL-Row iff D_mat < dstar */
     int32_t n_streams;           /* slots (requests in flight); <= 0 means 4 */
-    int32_t amortize_products;   /* products seen before a transformation is built; <= 0 means 2 */
-    int32_t flags;               /* reserved, 0 */
+    int32_t amortize_products;   /* least products seen before a transformation is built; <= 0 means 2 */
+    int32_t flags;               /* SPMV_SERVER_FIXED_THRESHOLD or 0 */
     int32_t pad;
 } spmv_server_params;
 
@@ -399,7 +403,8 @@ spmv_status spmv_server_add_matrix(spmv_server *S, const spmv_crs *A, int32_t *i
  * k * n_cols float64, product j reads x + j * n_cols) and y (device,
  * k * n_rows float64, overwritten). If `after` is not NULL, the request
  * starts only after the work enqueued on that stream so far (the producer of
- * x). The caller keeps x and y alive until the request completes. *req
+ * x); pass cudaStreamLegacy for the legacy default stream, since NULL here
+ * means no such dependency. The caller keeps x and y alive until the request completes. *req
  * receives the request's id. Thread-safe. */
 spmv_status spmv_server_submit(spmv_server *S, int32_t id, int32_t k, const double *x, double *y,
                                spmv_stream_t after, uint64_t *req);

@@ -535,8 +535,10 @@ class Server:
     """Owning wrapper of an spmv_server (continuous batching over a matrix
     pool); keeps the registered matrices alive."""
 
-    def __init__(self, mem_budget_bytes=0, dstar=0.0, n_streams=4, amortize_products=2):
-        p = _ServerParamsT(int(mem_budget_bytes), float(dstar), int(n_streams), int(amortize_products), 0, 0)
+    FIXED_THRESHOLD = 1
+
+    def __init__(self, mem_budget_bytes=0, dstar=0.0, n_streams=4, amortize_products=2, flags=0):
+        p = _ServerParamsT(int(mem_budget_bytes), float(dstar), int(n_streams), int(amortize_products), int(flags), 0)
         h = ctypes.c_void_p()
         _check(load_library().spmv_server_create(ctypes.byref(p), ctypes.byref(h)), "spmv_server_create")
         self.handle = h
@@ -554,8 +556,11 @@ class Server:
         device tensors; `after`: a stream whose current work must finish first
         (default: the current torch stream)."""
         r = ctypes.c_uint64()
-        _check(load_library().spmv_server_submit(self.handle, int(mat_id), int(k), _ptr(x), _ptr(y),
-                                                 _stream(after), ctypes.byref(r)), "spmv_server_submit")
+        s = _stream(after)
+        if not s.value:
+            s = ctypes.c_void_p(1)  # cudaStreamLegacy: torch's default stream has handle 0, which means "none"
+        _check(load_library().spmv_server_submit(self.handle, int(mat_id), int(k), _ptr(x), _ptr(y), s,
+                                                 ctypes.byref(r)), "spmv_server_submit")
         return r.value
 
     def wait(self, req: int, timeout_ms: int = -1):

@@ -61,6 +61,7 @@ struct MatEntry {
     cudaEvent_t built = nullptr;     // recorded after the transformation's kernels
     uint64_t fast_bytes = 0;
     int64_t products = 0;            // products asked for so far
+    int64_t breakeven = 0;           // products before the transformation pays off; < 0: never
     int inflight_fast = 0;           // running requests that use `fast`
     uint64_t last_use = 0;
     double bytes_crs = 0.0, bytes_fast = 0.0;  // algorithmic bytes per product
@@ -157,7 +158,7 @@ void admit(spmv_server *S, Request *r, int slot) {
     if (E->target != SPMV_CRS) {
         if (E->fast) {
             H = E->fast;
-        } else if (E->products >= S->p.amortize_products && make_room(S, E->target_bytes)) {
+        } else if (E->breakeven >= 0 && E->products >= E->breakeven && make_room(S, E->target_bytes)) {
             spmv_matrix *M = nullptr;
             if (!E->built && cudaEventCreateWithFlags(&E->built, cudaEventDisableTiming) != cudaSuccess) {
                 cudaGetLastError();
@@ -343,8 +344,28 @@ spmv_status spmv_server_add_matrix(spmv_server *S, const spmv_crs *A, int32_t *i
     E->target = fmt;
     E->target_bytes = st.ell_bytes + kHandleSlack;
     const double n = (double)A->n_rows, nc = (double)A->n_cols;
+    const double ell = 12.0 * (double)((A->n_rows + 31) / 32 * 32) * (double)st.max_row_len;
     E->bytes_crs = 12.0 * (double)A->nnz + 4.0 * (n + 1.0) + 8.0 * nc + 8.0 * n;
-    E->bytes_fast = 12.0 * (double)((A->n_rows + 31) / 32 * 32) * (double)st.max_row_len + 8.0 * nc + 8.0 * n;
+    E->bytes_fast = ell + 8.0 * nc + 8.0 * n;
+    // Break-even of the transformation (Sec. 2.2, Eqs. (1)-(3)) with moved
+    // bytes standing in for times: SP = CRS bytes / ELL bytes per product,
+    // TT = transformation bytes / CRS bytes; k products pay for it once
+    // k t_crs >= t_trans + k t_ell, i.e. k >= TT / (1 - 1 / SP). Never when
+    // SP <= 1, nor when one transformation would take over a quarter of the
+    // cache budget (it would evict everything else).
+    const double trans = 12.0 * (double)A->nnz + 4.0 * (n + 1.0) + ell;
+    const double sp = E->bytes_crs / E->bytes_fast, tt = trans / E->bytes_crs;
+    const bool fits = S->p.mem_budget_bytes == 0 || E->target_bytes <= S->p.mem_budget_bytes / 4;
+    if (fmt == SPMV_CRS) {
+        E->breakeven = -1;
+    } else if (S->p.flags & SPMV_SERVER_FIXED_THRESHOLD) {
+        E->breakeven = S->p.amortize_products;
+    } else if (sp <= 1.0 || !fits) {
+        E->breakeven = -1;
+    } else {
+        const double k = std::ceil(tt / (1.0 - 1.0 / sp));
+        E->breakeven = std::max<int64_t>(S->p.amortize_products, k < 1e15 ? (int64_t)k : (int64_t)1e15);
+    }
     std::lock_guard<std::mutex> lk(S->pool_mu);
     *id = (int32_t)S->mats.size();
     S->mats.push_back(std::move(E));

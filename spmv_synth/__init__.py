@@ -36,6 +36,7 @@ __all__ = [
     "banded_random_crs",
     "batch_matrix",
     "batch_set",
+    "serve_matrix",
     "vector_pm1",
 ]
 
@@ -458,3 +459,24 @@ def batch_matrix(idx: int, seed: int = 5, n_lo: int = 100, n_hi: int = 20000) ->
 def batch_set(count: int, seed: int = 5, n_lo: int = 100, n_hi: int = 20000) -> list:
     """Matrices 0..count-1 of batch_matrix."""
     return [batch_matrix(i, seed, n_lo, n_hi) for i in range(count)]
+
+
+def serve_matrix(idx: int, seed: int = 6, n_lo: int = 1000, n_hi: int = 2000000) -> CRS:
+    """Matrix `idx` of a serving pool, drawn with seed seed + idx: n =
+    round(exp(U[ln n_lo, ln n_hi])) (stream 40). Even idx: the cut 2-D
+    5-point stencil of batch_matrix. Odd idx: power_law(n) with mean 16 and
+    longest row min(20000, n)."""
+    sd = seed + int(idx)
+    u = float(uniform01(sd, 40, np.zeros(1, dtype=np.uint64))[0])
+    n = max(1, int(round(math.exp(math.log(n_lo) + u * (math.log(n_hi) - math.log(n_lo))))))
+    if idx % 2 == 0:
+        g = int(math.ceil(math.sqrt(n)))
+        i = np.arange(n, dtype=np.int64)
+        gx, gy = i % g, i // g
+        offs = [(-g, gy > 0), (-1, gx > 0), (0, np.ones(n, bool)), (1, (gx < g - 1) & (i + 1 < n)), (g, i + g < n)]
+        cols = np.stack([i + o for o, _ in offs], axis=1)
+        mask = np.stack([m for _, m in offs], axis=1)
+        irp, icol = _compress(cols, mask, n, n)
+        vals = np.where(np.stack([np.full(n, o == 0) for o, _ in offs], axis=1), 4.0, -1.0)
+        return CRS(n, n, irp, icol, vals[mask].astype(np.float64))
+    return power_law(n, mean=16.0, kmax=min(20000, n), seed=sd)

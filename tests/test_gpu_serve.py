@@ -72,11 +72,12 @@ def test_alone_equals_mix():
     pool = _pool()
     dev = [L.Crs.from_host(H) for H in pool]
     reqs = _requests(pool, 40)
-    alone = L.Server(dstar=math.inf, n_streams=1, amortize_products=1)
+    fixed = L.Server.FIXED_THRESHOLD
+    alone = L.Server(dstar=math.inf, n_streams=1, amortize_products=1, flags=fixed)
     ids = [alone.add_matrix(A) for A in dev]
     y_alone, _ = _run(alone, dev, ids, reqs, concurrent=False)
     alone.close()
-    mix = L.Server(dstar=math.inf, n_streams=6, amortize_products=1)
+    mix = L.Server(dstar=math.inf, n_streams=6, amortize_products=1, flags=fixed)
     ids = [mix.add_matrix(A) for A in dev]
     y_mix, fmts = _run(mix, dev, ids, reqs, concurrent=True)
     st = mix.stats()
@@ -96,7 +97,7 @@ def test_amortisation_threshold_then_cache_hits():
     L = lib()
     H = synth.laplacian_2d_5pt(64)
     A = L.Crs.from_host(H)
-    S = L.Server(dstar=math.inf, n_streams=2, amortize_products=5)
+    S = L.Server(dstar=math.inf, n_streams=2, amortize_products=5, flags=L.Server.FIXED_THRESHOLD)
     mid = S.add_matrix(A)
     fmts = []
     for r in range(5):
@@ -111,13 +112,50 @@ def test_amortisation_threshold_then_cache_hits():
     S.close()
 
 
+def _breakeven(H):
+    # Eqs. (1)-(3) with bytes for times: k >= TT / (1 - 1 / SP)
+    n, nnz = H.n_rows, H.nnz
+    W = int(np.diff(H.irp).max())
+    ell = 12.0 * ((n + 31) // 32 * 32) * W
+    crs = 12.0 * nnz + 4.0 * (n + 1) + 16.0 * n
+    sp = crs / (ell + 16.0 * n)
+    tt = (12.0 * nnz + 4.0 * (n + 1) + ell) / crs
+    return math.ceil(tt / (1.0 - 1.0 / sp)) if sp > 1 else None
+
+
+def test_breakeven_model_decides_when_to_transform():
+    import torch
+    L = lib()
+    H = synth.laplacian_2d_5pt(64)
+    P = synth.power_law(5000, kmax=400, seed=5)
+    k_star = _breakeven(H)
+    assert k_star is not None and k_star > 2 and _breakeven(P) is None
+    S = L.Server(dstar=math.inf, n_streams=2, amortize_products=2)
+    ids = [S.add_matrix(L.Crs.from_host(M)) for M in (H, P)]
+    seen, fmts = 0, []
+    for r in range(6):
+        k = (k_star + 2) // 3
+        x = torch.from_numpy(np.tile(synth.vector_pm1(H.n_cols, seed=r), k)).cuda()
+        y = torch.empty(k * H.n_rows, dtype=torch.float64, device="cuda")
+        fmts.append(S.wait(S.submit(ids[0], k, x, y), 60000)[1])
+        seen += k
+        assert fmts[-1] == (L.SPMV_ELL if seen >= k_star else L.SPMV_CRS)
+        xp = torch.from_numpy(synth.vector_pm1(P.n_cols, seed=r)).cuda()
+        yp = torch.empty(P.n_rows, dtype=torch.float64, device="cuda")
+        assert S.wait(S.submit(ids[1], 1, xp, yp), 60000)[1] == L.SPMV_CRS  # SP < 1: never
+        assert_spmv_close(yp.cpu().numpy(), P, xp.cpu().numpy(), what="power law")
+    assert L.SPMV_ELL in fmts and S.stats()["transforms"] == 1
+    S.close()
+
+
 def test_budget_evicts_idle_entries():
     import torch
     L = lib()
     pool = [synth.laplacian_2d_5pt(80), synth.laplacian_2d_5pt(81)]
     dev = [L.Crs.from_host(H) for H in pool]
     one = max(L.spmv_analyze(A)["ell_bytes"] for A in dev)
-    S = L.Server(mem_budget_bytes=one + one // 2, dstar=math.inf, n_streams=1, amortize_products=1)
+    S = L.Server(mem_budget_bytes=one + one // 2, dstar=math.inf, n_streams=1, amortize_products=1,
+                 flags=L.Server.FIXED_THRESHOLD)
     ids = [S.add_matrix(A) for A in dev]
     reqs = [(r % 2, 1, synth.vector_pm1(pool[r % 2].n_cols, seed=r)) for r in range(6)]
     ys, fmts = _run(S, dev, ids, reqs, concurrent=False)
@@ -155,7 +193,7 @@ def test_two_client_threads():
     L = lib()
     pool = _pool()[:3]
     dev = [L.Crs.from_host(H) for H in pool]
-    S = L.Server(dstar=math.inf, n_streams=4, amortize_products=3)
+    S = L.Server(dstar=math.inf, n_streams=4, amortize_products=3, flags=L.Server.FIXED_THRESHOLD)
     ids = [S.add_matrix(A) for A in dev]
     reqs = _requests(pool, 30, seed=4)
     out = [None] * len(reqs)
