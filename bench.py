@@ -48,6 +48,8 @@ WORKLOADS = {
     "batch_10k": dict(kind="batch", count=10000, seed=5, n_lo=100, n_hi=20000, cap=60 * 10 ** 9,
                       desc="10,000 matrices, n log-uniform in [100, 20000]; even: 2-D 5-point stencil on a "
                            "ceil(sqrt(n)) grid cut to n, odd: Poisson(8) row lengths, unique random columns"),
+    "batch_1k": dict(kind="batch", count=1000, seed=5, n_lo=100, n_hi=20000, cap=60 * 10 ** 9,
+                     desc="first 1,000 matrices of batch_10k (374 MB per product, > L2; profiling size)"),
     "serve_300": dict(kind="serve", count=300, seed=6, n_lo=1000, n_hi=200000, rate=2000.0, kmax=64,
                       requests=4000, warm_requests=300, budget=60 * 10 ** 9, streams=8, amortize=2,
                       desc="serving: pool of 300 matrices, n log-uniform in [1e3, 2e5], half cut 2-D 5-point "
@@ -381,6 +383,44 @@ def batch_bytes(mats, plans) -> float:
     return b
 
 
+def per_matrix_loop(L, torch, dev, mats, plans, x, y, stream):
+    """The same products as a loop of one spmv_apply per matrix (one CRS
+    handle each), plain and captured in one CUDA graph; ms per loop."""
+    handles = [L.spmv_transform(A, L.SPMV_CRS, L.SPMV_ROWWISE) for A in dev]
+    views = [(x[P["x_offset"]:P["x_offset"] + H.n_cols], y[P["y_offset"]:P["y_offset"] + H.n_rows])
+             for H, P in zip(mats, plans)]
+    reps = 3
+
+    def loop():
+        for M, (xv, yv) in zip(handles, views):
+            L.spmv_apply(M, xv, yv)
+
+    loop()
+    barrier_sync(torch)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        loop()
+    e1.record(stream)
+    barrier_sync(torch)
+    loop_ms = e0.elapsed_time(e1) / reps
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        loop()
+    g.replay()
+    barrier_sync(torch)
+    e0.record(stream)
+    for _ in range(reps):
+        g.replay()
+    e1.record(stream)
+    barrier_sync(torch)
+    graph_ms = e0.elapsed_time(e1) / reps
+    del g
+    for M in handles:
+        M.close()
+    return loop_ms, graph_ms
+
+
 def run_batch(args, w: dict) -> None:
     """One step = one product y = A x over every matrix of the batch (one
     launch). Also timed: the batch build (analysis, on-line rule, ELL
@@ -476,39 +516,10 @@ def run_batch(args, w: dict) -> None:
     n_k, ms_k = prof["batch_apply"]
     achieved = step_bytes / (ms_k / n_k * 1e-3) / 1e9
 
-    # the per-matrix loop: one CRS handle and one spmv_apply per matrix
-    handles = [L.spmv_transform(A, L.SPMV_CRS, L.SPMV_ROWWISE) for A in dev]
-    views = [(x[P["x_offset"]:P["x_offset"] + H.n_cols], y[P["y_offset"]:P["y_offset"] + H.n_rows])
-             for H, P in zip(mats, plans)]
-    loop_reps = 3
-
-    def loop():
-        for M, (xv, yv) in zip(handles, views):
-            L.spmv_apply(M, xv, yv)
-
-    loop()
-    barrier_sync(torch)
+    loop_ms = graph_ms = None
+    if not args.no_loop:
+        loop_ms, graph_ms = per_matrix_loop(L, torch, dev, mats, plans, x, y, stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(loop_reps):
-        loop()
-    e1.record(stream)
-    barrier_sync(torch)
-    loop_ms = e0.elapsed_time(e1) / loop_reps
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, capture_error_mode="relaxed"):
-        loop()
-    g.replay()
-    barrier_sync(torch)
-    e0.record(stream)
-    for _ in range(loop_reps):
-        g.replay()
-    e1.record(stream)
-    barrier_sync(torch)
-    graph_ms = e0.elapsed_time(e1) / loop_reps
-    del g
-    for M in handles:
-        M.close()
 
     e2e = None
     if not args.no_e2e:
@@ -563,9 +574,11 @@ def run_batch(args, w: dict) -> None:
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "p50_ms": statistics.median(per_step), "p99_ms": p99,
             "batch": {"create_ms": statistics.median(create_ms), "per_matrix_loop_ms": loop_ms,
-                      "per_matrix_graph_ms": graph_ms, "speedup_vs_loop": loop_ms / (t_max / args.steps),
-                      "speedup_vs_graph": graph_ms / (t_max / args.steps), "dstar": dstar if math.isfinite(dstar)
-                      else "inf", "formats": fmt_count, "crs_threads_per_row": tpr},
+                      "per_matrix_graph_ms": graph_ms,
+                      "speedup_vs_loop": loop_ms / (t_max / args.steps) if loop_ms else None,
+                      "speedup_vs_graph": graph_ms / (t_max / args.steps) if graph_ms else None,
+                      "dstar": dstar if math.isfinite(dstar) else "inf", "formats": fmt_count,
+                      "crs_threads_per_row": tpr},
         }
         print(json.dumps(line), flush=True)
     B.close()
@@ -736,6 +749,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--rate", type=float, default=None, help="serving: offered requests per second")
+    ap.add_argument("--no-loop", action="store_true", help="batches: skip the per-matrix loop comparison")
     ap.add_argument("--dstar", type=float, default=None,
                     help="use this D* instead of the off-line calibration (profiling runs)")
     args = ap.parse_args()
@@ -926,7 +940,7 @@ def main():
                        "W_col": Wc, "D_mat": stats["dmat"], "step_bytes": step_bytes,
                        "l2": "inputs larger than L2 (CRS %.0f MB vs 129 MB L2); no flush" % (
                            (12 * H.nnz + 4 * H.n_rows) / 1e6),
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "launches_before_timed": int(launches0)},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
