@@ -547,19 +547,29 @@ __global__ void __launch_bounds__(FT_THREADS) k_fixup_slots(const int32_t *__res
     }
     __syncthreads();
     const int maxl = s_maxl;
-    // stage: thread t covers column t % 64 and slots t / 64, +4, +8, ...
+    // stage: thread t covers column t % 64 and slots t / 64 + 4 u (u < 8),
+    // every load issued before the first store
     {
+        constexpr int RSTEP = FT_THREADS / FS_COLS;   // 4
+        constexpr int NU = SLOT_CAP / RSTEP;          // 8
         const int cc = threadIdx.x % FS_COLS;
         const int len = (cc < nc) ? s_cp[cc + 1] - s_cp[cc] : 0;
         const bool longc = len > SLOT_CAP;
-        const long long j = c0 + cc;
-        for (int rr = threadIdx.x / FS_COLS; rr < maxl; rr += FT_THREADS / FS_COLS) {
-            if (rr < len && rr < SLOT_CAP) {
-                const int2 pr = __ldcs(T + (long long)rr * n_cols + j);
+        const int lim = min(min(len, SLOT_CAP), maxl);
+        const int r0 = threadIdx.x / FS_COLS;
+        const int2 *tp = T + (long long)r0 * n_cols + (c0 + cc);
+        int2 pr[NU];
+#pragma unroll
+        for (int u = 0; u < NU; ++u)
+            if (r0 + u * RSTEP < lim) pr[u] = __ldcs(tp + (long long)(u * RSTEP) * n_cols);
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            const int rr = r0 + u * RSTEP;
+            if (rr < lim) {
                 if (longc) {
-                    pairs[(long long)s_cp[cc] + rr] = pr;
+                    pairs[(long long)s_cp[cc] + rr] = pr[u];
                 } else {
-                    s_pr[s_off[cc] + rr] = pr;
+                    s_pr[s_off[cc] + rr] = pr[u];
                     s_pos[s_off[cc] + rr] = s_cp[cc] + rr;
                 }
             }
@@ -597,25 +607,22 @@ __global__ void __launch_bounds__(FT_THREADS) k_fixup_slots(const int32_t *__res
         }
     }
     __syncthreads();
+    // write-out: ns <= FS_COLS * SLOT_CAP = 8 per thread, all VAL gathers in flight at once
+    constexpr int NW = FS_COLS * SLOT_CAP / FT_THREADS;
     const int ns = s_off[nc];
-    for (int q0 = threadIdx.x; q0 < ns; q0 += 4 * FT_THREADS) {
-        int2 pr[4];
-        int pos[4];
-        double v[4];
+    double v[NW];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int q = q0 + u * FT_THREADS;
-            pr[u] = (q < ns) ? s_pr[q] : make_int2(-1, 0);
-            pos[u] = (q < ns) ? s_pos[q] : 0;
-        }
+    for (int u = 0; u < NW; ++u) {
+        const int q = threadIdx.x + u * FT_THREADS;
+        v[u] = (q < ns) ? __ldg(val + s_pr[q].x) : 0.0;
+    }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = (pr[u].x >= 0) ? __ldg(val + pr[u].x) : 0.0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (pr[u].x >= 0) {
-                __stcs(trow + pos[u], pr[u].y);
-                __stcs(tval + pos[u], v[u]);
-            }
+    for (int u = 0; u < NW; ++u) {
+        const int q = threadIdx.x + u * FT_THREADS;
+        if (q < ns) {
+            const int pos = s_pos[q];
+            __stcs(trow + pos, s_pr[q].y);
+            __stcs(tval + pos, v[u]);
         }
     }
 }
