@@ -341,6 +341,14 @@ spmv_status spmv_batch_create(const spmv_crs *mats, int32_t m, const spmv_at_par
  * be captured in a CUDA graph. Deterministic. x, y: device, concatenated. */
 spmv_status spmv_batch_apply(const spmv_batch *B, const double *x, double *y, spmv_stream_t stream);
 
+/* nvec products per matrix in one launch: y_j = A x_j for j < nvec, vector j
+ * of the concatenated x at x + j * ldx (ldx >= total_cols), of y at
+ * y + j * ldy (ldy >= total_rows). Each matrix's entries are read once for all
+ * vectors. Every product has the bits spmv_batch_apply would give it. Like
+ * spmv_batch_apply: no allocation, no synchronisation. */
+spmv_status spmv_batch_apply_multi(const spmv_batch *B, const double *x, int64_t ldx, double *y, int64_t ldy,
+                                   int32_t nvec, spmv_stream_t stream);
+
 /* Sizes of a batch (host). */
 spmv_status spmv_batch_info_get(const spmv_batch *B, spmv_batch_info *out);
 

@@ -24,7 +24,7 @@ __all__ = [
     "spmv_describe", "spmv_matrix_status", "spmv_destroy", "spmv_r_ell", "spmv_dstar_from_points", "spmv_measure",
     "spmv_calibrate", "spmv_autotune", "spmv_autotune_choose", "spmv_apply_coo_row_noalloc", "spmv_launch_count", "spmv_profile_enable", "spmv_profile_read",
     "spmv_debug_scan_timeout", "spmv_batch_create", "spmv_batch_apply", "spmv_batch_info_get",
-    "spmv_batch_plan_get", "spmv_batch_destroy", "Batch", "Server", "spmv_server_create",
+    "spmv_batch_plan_get", "spmv_batch_destroy", "Batch", "spmv_batch_apply_multi", "Server", "spmv_server_create",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -154,6 +154,7 @@ def load_library():
         "spmv_debug_scan_timeout": (ctypes.c_int, [i32, i32, P(i32), vp]),
         "spmv_batch_create": (ctypes.c_int, [P(_CrsT), i32, P(_AtParamsT), vp, vp, P(vp), vp]),
         "spmv_batch_apply": (ctypes.c_int, [vp, vp, vp, vp]),
+        "spmv_batch_apply_multi": (ctypes.c_int, [vp, vp, i64, vp, i64, i32, vp]),
         "spmv_batch_info_get": (ctypes.c_int, [vp, P(_BatchInfoT)]),
         "spmv_batch_plan_get": (ctypes.c_int, [vp, i32, i32, P(_BatchPlanT)]),
         "spmv_batch_destroy": (None, [vp]),
@@ -295,6 +296,14 @@ class Batch:
 
     def apply(self, x, y, stream=None):
         spmv_batch_apply(self, x, y, stream)
+
+    def apply_multi(self, x, y, nvec, ldx=None, ldy=None, stream=None):
+        """nvec products: vector j of x at j * ldx, of y at j * ldy."""
+        i = self.info()
+        ldx = i["total_cols"] if ldx is None else ldx
+        ldy = i["total_rows"] if ldy is None else ldy
+        _check(load_library().spmv_batch_apply_multi(self.handle, _ptr(x), int(ldx), _ptr(y), int(ldy), int(nvec),
+                                                     _stream(stream)), "spmv_batch_apply_multi")
 
     def info(self) -> dict:
         return spmv_batch_info_get(self)
@@ -594,3 +603,7 @@ class Server:
 
 def spmv_server_create(**kw) -> Server:
     return Server(**kw)
+
+
+def spmv_batch_apply_multi(B: Batch, x, y, nvec: int, ldx=None, ldy=None, stream=None) -> None:
+    B.apply_multi(x, y, nvec, ldx, ldy, stream)

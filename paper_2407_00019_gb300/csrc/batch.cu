@@ -215,6 +215,16 @@ spmv_status spmv_batch_apply(const spmv_batch *B, const double *x, double *y, sp
     return SPMV_OK;
 }
 
+spmv_status spmv_batch_apply_multi(const spmv_batch *B, const double *x, int64_t ldx, double *y, int64_t ldy,
+                                   int32_t nvec, spmv_stream_t stream) {
+    if (!B || nvec < 0) return SPMV_ERR_INVALID_ARG;
+    if (nvec == 0) return SPMV_OK;
+    if (!x || !y || ldx < B->total_cols || ldy < B->total_rows) return SPMV_ERR_INVALID_ARG;
+    CK(launch_batch_apply_multi(B->d_mats, B->d_tiles, B->n_tiles, x, (long long)ldx, y, (long long)ldy, nvec,
+                                S(stream)));
+    return SPMV_OK;
+}
+
 spmv_status spmv_batch_info_get(const spmv_batch *B, spmv_batch_info *out) {
     if (!B || !out) return SPMV_ERR_INVALID_ARG;
     memset(out, 0, sizeof(*out));

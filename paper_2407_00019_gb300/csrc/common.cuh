@@ -264,7 +264,7 @@ struct BatchAcc {               // per-matrix statistics of the analysis pass
 constexpr int kBatchThreads = 256;
 constexpr int kBatchMatBits = 26;  // tile records pack the matrix index (< 2^26) and the row count
 constexpr int kBatchChunk = 2048; // rows per work item of the analysis pass
-int batch_grid(int kernel);       // persistent grid: 0 analyze, 1 build, 2 build+multiply, 3 apply
+int batch_grid(int kernel);       // persistent grid: 0 analyze, 1 build, 2 build+multiply, 3 apply, 4 multi
 cudaError_t launch_batch_analyze(const BatchMat *mats, const int2 *chunks, long long n_chunks, BatchAcc *acc,
                                  cudaStream_t s);
 // ELL transform of the ELL matrices' tiles; with x (and y) also y = A x for
@@ -276,5 +276,8 @@ cudaError_t launch_batch_build(const BatchMat *mats, const int4 *tiles, long lon
                                double *y, cudaStream_t s);
 cudaError_t launch_batch_apply(const BatchMat *mats, const int4 *tiles, long long n_tiles, const double *x,
                                double *y, cudaStream_t s);
+// nvec products y_j = A x_j (vector j at x + j * ldx, y + j * ldy), one launch.
+cudaError_t launch_batch_apply_multi(const BatchMat *mats, const int4 *tiles, long long n_tiles, const double *x,
+                                     long long ldx, double *y, long long ldy, int nvec, cudaStream_t s);
 
 }  // namespace spmvat

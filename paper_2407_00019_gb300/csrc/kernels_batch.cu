@@ -147,9 +147,10 @@ __device__ __forceinline__ void run_fma(const double (&v)[MMAX], const double (&
 // running sums in run[]; lane r then adds row r's pieces in lane order and
 // writes yr[r]. Each row is thus summed in storage order with one extra
 // addition per run boundary it crosses.
-__device__ __forceinline__ void merge_sum(uint32_t *last, double *run, int m, int beg, int end, int nr, int rb,
-                                          int re, const double (&v)[MMAX], const double (&xv)[MMAX],
-                                          double *__restrict__ yr) {
+//
+// merge_ends marks each row's last entry (a bitmap in `last`) and returns the
+// bits of the lane's own run; merge_run sums and assembles one product.
+__device__ __forceinline__ uint32_t merge_ends(uint32_t *last, int beg, int nr, int rb, int re) {
     const int lane = (int)lane_id();
     if (lane < 8) last[lane] = 0u;
     __syncwarp();
@@ -159,7 +160,13 @@ __device__ __forceinline__ void merge_sum(uint32_t *last, double *run, int m, in
     const int w0 = beg >> 5, sh = beg & 31;
     uint64_t two = last[min(w0, 7)];
     if (w0 + 1 < 8) two |= (uint64_t)last[w0 + 1] << 32;
-    const uint32_t ends = (uint32_t)(two >> sh);
+    return (uint32_t)(two >> sh);
+}
+
+__device__ __forceinline__ void merge_run(double *run, int m, int beg, int end, int nr, int rb, int re, uint32_t ends,
+                                          const double (&v)[MMAX], const double (&xv)[MMAX],
+                                          double *__restrict__ yr) {
+    const int lane = (int)lane_id();
     // exactly m steps: an FP64 instruction whose lanes are all switched off
     // still takes its issue slot on the (narrow) FP64 pipe
     switch (m) {
@@ -184,6 +191,13 @@ __device__ __forceinline__ void merge_sum(uint32_t *last, double *run, int m, in
         yr[lane] = t;
     }
     __syncwarp();
+}
+
+__device__ __forceinline__ void merge_sum(uint32_t *last, double *run, int m, int beg, int end, int nr, int rb,
+                                          int re, const double (&v)[MMAX], const double (&xv)[MMAX],
+                                          double *__restrict__ yr) {
+    const uint32_t ends = merge_ends(last, beg, nr, rb, re);
+    merge_run(run, m, beg, end, nr, rb, re, ends, v, xv, yr);
 }
 
 // Row bounds of a tile relative to its first entry e0: lane r < nr gets the
@@ -557,14 +571,43 @@ __global__ void __launch_bounds__(AT) k_batch_apply(const BatchMat *__restrict__
     cp_async_wait_all();
 }
 
-int g_grid[64][4] = {};
+// ---- several products per launch: y_j = A x_j, j < nvec ------------------
+// Work items are (tile, vector) pairs, tile-major, dealt round robin to the
+// warps: the nvec products of one tile run on neighbouring warps at the same
+// time, so the tile's entries come from DRAM once and from L1/L2 for the
+// other vectors, and a request with few tiles still fills the GPU. Each item
+// runs exactly the arithmetic of k_batch_apply, so every product has the same
+// bits as a single-product launch. Vector j of the concatenated x starts at
+// x + j * ldx, of y at y + j * ldy.
+__global__ void __launch_bounds__(AT) k_batch_apply_multi(const BatchMat *__restrict__ mats,
+                                                          const int4 *__restrict__ tiles, long long n_tiles,
+                                                          const double *__restrict__ x, long long ldx,
+                                                          double *__restrict__ y, long long ldy, int nvec) {
+    __shared__ RowSmem rs_all[AT / 32];
+    RowSmem &rs = rs_all[threadIdx.x >> 5];
+    const long long nw = (long long)gridDim.x * (AT / 32);
+    const long long n_items = n_tiles * nvec;
+    for (long long it = (long long)blockIdx.x * (AT / 32) + (threadIdx.x >> 5); it < n_items; it += nw) {
+        const long long t = it / nvec;
+        const int j = (int)(it - t * nvec);
+        const int4 tl = __ldg(tiles + t);
+        const BatchMat *M = mats + tile_mat(tl.x);
+        const int nr = tile_rows(tl.x);
+        const double *xm = x + j * ldx + M->xoff;
+        double *ym = y + j * ldy + M->yoff;
+        if (M->fmt == BATCH_ELL) ell_tile(M->eval, M->ecol, M->ld, M->width, tl.y, nr, xm, ym);
+        else crs_tile(rs, M, tl.y, nr, tl.z, tl.w, xm, ym);
+    }
+}
+
+int g_grid[64][5] = {};
 
 }  // namespace
 
 int batch_grid(int kernel) {
     int dev = 0;
     cudaGetDevice(&dev);
-    int &g = g_grid[dev & 63][kernel & 3];
+    int &g = g_grid[dev & 63][kernel % 5];
     if (!g) {
         int occ = 0;
         cudaError_t e = cudaErrorInvalidValue;
@@ -572,7 +615,8 @@ int batch_grid(int kernel) {
             case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_analyze, T, 0); break;
             case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_build<false>, T, 0); break;
             case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_build<true>, T, 0); break;
-            default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_apply, AT, 0); break;
+            case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_apply, AT, 0); break;
+            default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_apply_multi, AT, 0); break;
         }
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -626,6 +670,20 @@ cudaError_t launch_batch_apply(const BatchMat *mats, const int4 *tiles, long lon
     const unsigned grid = (unsigned)std::min<long long>((n_tiles + AT / 32 - 1) / (AT / 32), batch_grid(3));
     KernelScope ks("batch_apply", s);
     k_batch_apply<<<grid, AT, 0, s>>>(mats, tiles, n_tiles, x, y);
+    return cudaGetLastError();
+}
+
+}  // namespace spmvat
+
+namespace spmvat {
+
+cudaError_t launch_batch_apply_multi(const BatchMat *mats, const int4 *tiles, long long n_tiles, const double *x,
+                                     long long ldx, double *y, long long ldy, int nvec, cudaStream_t s) {
+    if (n_tiles <= 0 || nvec <= 0) return cudaSuccess;
+    if (nvec == 1) return launch_batch_apply(mats, tiles, n_tiles, x, y, s);
+    const unsigned grid = (unsigned)std::min<long long>((n_tiles + AT / 32 - 1) / (AT / 32), batch_grid(4));
+    KernelScope ks("batch_apply_multi", s);
+    k_batch_apply_multi<<<grid, AT, 0, s>>>(mats, tiles, n_tiles, x, ldx, y, ldy, nvec);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,8 @@
 // Serving runtime (declared in include/spmvat.h): continuous batching of
 // SpMV requests over a pool of matrices, with a resident per-matrix format
-// cache under a device-memory budget.
+// cache under a device-memory budget. Each matrix is held as a batch of one
+// (its CRS schedule, and its ELL-Row when cached), so a request's k products
+// are one multi-vector launch that reads the matrix once.
 //
 // Threads: clients call add/submit/wait; one worker thread owns the slots,
 // the pending queue and the cache, and is the only caller of the transform
@@ -33,8 +35,8 @@ double now_s() { return std::chrono::duration<double>(Clock::now().time_since_ep
 
 enum : int { R_PENDING = 0, R_RUNNING = 1, R_DONE = 2, R_REAPED = 3 };
 
-// Admission counts a transformation as its arrays plus this much for the
-// handle's small buffers (each allocation is rounded up to 256 bytes).
+// Admission counts a transformation as its arrays and tile records plus this
+// much for its small buffers (each allocation is rounded up to 256 bytes).
 constexpr uint64_t kHandleSlack = 4096;
 
 struct Request {
@@ -56,8 +58,8 @@ struct MatEntry {
     spmv_crs A{};
     int32_t target = SPMV_CRS;
     uint64_t target_bytes = 0;       // device bytes of the target transformation
-    spmv_matrix *crs = nullptr;      // CRS schedule (always present)
-    spmv_matrix *fast = nullptr;     // cached transformation, or NULL
+    spmv_batch *crs = nullptr;       // the matrix alone as a batch, in CRS (always present)
+    spmv_batch *fast = nullptr;      // the same in its target format (cached), or NULL
     cudaEvent_t built = nullptr;     // recorded after the transformation's kernels
     uint64_t fast_bytes = 0;
     int64_t products = 0;            // products asked for so far
@@ -138,7 +140,7 @@ bool make_room(spmv_server *S, uint64_t bytes) {
         for (MatEntry *e : all)
             if (e->fast && e->inflight_fast == 0 && (!victim || e->last_use < victim->last_use)) victim = e;
         if (!victim) return false;
-        spmv_destroy(victim->fast);
+        spmv_batch_destroy(victim->fast);
         victim->fast = nullptr;
         std::lock_guard<std::mutex> lk(S->stats_mu);
         S->stats.cache_bytes -= victim->fast_bytes;
@@ -153,21 +155,24 @@ void admit(spmv_server *S, Request *r, int slot) {
     MatEntry *E = entry(S, r->mat);
     if (r->ready) cudaStreamWaitEvent(s, r->ready, 0);
     E->products += r->k;
-    spmv_matrix *H = E->crs;
+    spmv_batch *H = E->crs;
     bool miss = false;
     if (E->target != SPMV_CRS) {
         if (E->fast) {
             H = E->fast;
         } else if (E->breakeven >= 0 && E->products >= E->breakeven && make_room(S, E->target_bytes)) {
-            spmv_matrix *M = nullptr;
+            spmv_batch *M = nullptr;
             if (!E->built && cudaEventCreateWithFlags(&E->built, cudaEventDisableTiming) != cudaSuccess) {
                 cudaGetLastError();
                 E->built = nullptr;
             }
-            if (E->built && spmv_transform(&E->A, (spmv_format)E->target, SPMV_ROWWISE, 0, &M, s) == SPMV_OK) {
+            spmv_at_params ell;
+            memset(&ell, 0, sizeof(ell));
+            ell.dstar = INFINITY;  // the target is ELL-Row
+            if (E->built && spmv_batch_create(&E->A, 1, &ell, nullptr, nullptr, &M, s) == SPMV_OK) {
                 cudaEventRecord(E->built, s);  // requests on other slots wait for the build
-                spmv_matrix_desc d;
-                spmv_describe(M, &d);
+                spmv_batch_info d;
+                spmv_batch_info_get(M, &d);
                 E->fast = M;
                 E->fast_bytes = d.owned_bytes;
                 H = M;
@@ -195,9 +200,8 @@ void admit(spmv_server *S, Request *r, int slot) {
             else S->stats.cache_misses += 1;
         }
     }
-    const size_t nc = (size_t)E->A.n_cols, nr = (size_t)E->A.n_rows;
-    for (int32_t j = 0; j < r->k && r->status == SPMV_OK; ++j)
-        r->status = spmv_apply(H, r->x + j * nc, r->y + j * nr, s);
+    // the request's k products in one launch: the matrix is read once for all k
+    r->status = spmv_batch_apply_multi(H, r->x, E->A.n_cols, r->y, E->A.n_rows, r->k, s);
     r->state.store(R_RUNNING);
     S->slot_req[slot] = r;
     if (cudaLaunchHostFunc(s, on_done, r) != cudaSuccess) {
@@ -334,15 +338,18 @@ spmv_status spmv_server_add_matrix(spmv_server *S, const spmv_crs *A, int32_t *i
     spmv_stats st;
     spmv_status rc = spmv_autotune_choose(A, &ap, &fmt, &layout, &st, S->ctrl);
     if (rc != SPMV_OK) return rc;
-    rc = spmv_transform(A, SPMV_CRS, SPMV_ROWWISE, 0, &E->crs, S->ctrl);
+    spmv_at_params crs;
+    memset(&crs, 0, sizeof(crs));  // D* = 0: CRS
+    rc = spmv_batch_create(A, 1, &crs, nullptr, nullptr, &E->crs, S->ctrl);
     if (rc != SPMV_OK) return rc;
     if (cudaStreamSynchronize(S->ctrl) != cudaSuccess) {
         cudaGetLastError();
-        spmv_destroy(E->crs);
+        spmv_batch_destroy(E->crs);
         return SPMV_ERR_CUDA;
     }
     E->target = fmt;
-    E->target_bytes = st.ell_bytes + kHandleSlack;
+    // ELL arrays, one 16-byte tile record per 32 rows, descriptors
+    E->target_bytes = st.ell_bytes + 16ull * (uint64_t)((A->n_rows + 31) / 32) + kHandleSlack;
     const double n = (double)A->n_rows, nc = (double)A->n_cols;
     const double ell = 12.0 * (double)((A->n_rows + 31) / 32 * 32) * (double)st.max_row_len;
     E->bytes_crs = 12.0 * (double)A->nnz + 4.0 * (n + 1.0) + 8.0 * nc + 8.0 * n;
@@ -474,8 +481,8 @@ void spmv_server_destroy(spmv_server *S) {
     poke(S);
     if (S->worker.joinable()) S->worker.join();
     for (auto &e : S->mats) {
-        if (e->fast) spmv_destroy(e->fast);
-        if (e->crs) spmv_destroy(e->crs);
+        if (e->fast) spmv_batch_destroy(e->fast);
+        if (e->crs) spmv_batch_destroy(e->crs);
         if (e->built) cudaEventDestroy(e->built);
     }
     for (auto &s : S->streams) {

@@ -129,6 +129,33 @@ def test_every_threads_per_row_schedule(host_set, tpr, monkeypatch):
     _check_products(host_set, B.plans(), xh, y.cpu().numpy(), f"tpr={tpr}")
 
 
+@pytest.mark.parametrize("dstar", [0.0, 0.2])
+def test_multi_vector_products_equal_single_products(host_set, dstar, monkeypatch):
+    import torch
+    L = lib()
+    dev = L.Crs.batch_from_host(host_set)
+    B = L.spmv_batch_create(dev, dstar=dstar)
+    info = B.info()
+    nvec, nc, nr = 5, info["total_cols"], info["total_rows"]
+    ldx, ldy = nc + 3, nr + 1  # padded strides, y at odd offsets
+    xs = [synth.vector_pm1(nc, seed=40 + j) for j in range(nvec)]
+    X = torch.zeros(nvec * ldx, dtype=torch.float64, device="cuda")
+    for j in range(nvec):
+        X[j * ldx:j * ldx + nc] = torch.from_numpy(xs[j])
+    Y = torch.full((nvec * ldy,), float("nan"), dtype=torch.float64, device="cuda")
+    B.apply_multi(X, Y, nvec, ldx, ldy)
+    for j in range(nvec):
+        y1 = torch.empty(nr, dtype=torch.float64, device="cuda")
+        B.apply(X[j * ldx:j * ldx + nc], y1)
+        torch.cuda.synchronize()
+        assert np.array_equal(bits(Y[j * ldy:j * ldy + nr].cpu().numpy()), bits(y1.cpu().numpy()))
+        if j in (0, nvec - 1):
+            _check_products(host_set, B.plans(), xs[j], y1.cpu().numpy(), f"multi {j}")
+    assert torch.isnan(Y[nr:ldy]).all()  # padding between vectors untouched
+    with pytest.raises(L.SpmvError):
+        B.apply_multi(X, Y, 2, nc - 1, ldy)
+
+
 def test_memory_cap_takes_matrices_in_order(host_set):
     L = lib()
     dev = L.Crs.batch_from_host(host_set)
