@@ -257,9 +257,29 @@ void bin_counts_from_hist(const spmv_stats &st, int64_t cnt[kNumBins]) {
 
 const int kBinV[kNumBins] = {1, 2, 4, 8, 16, 32, 0};
 
+// The column-index check of a CRS whose IRP analyze_core has already checked.
+spmv_status validate_icol(const spmv_crs *A, cudaStream_t s) {
+    if (A->nnz <= 0) return SPMV_OK;
+    BufPtr w;
+    CKS(alloc_buf(16, s, &w));
+    CK(cudaMemsetAsync(w->p, 0, 16, s));
+    CK(launch_validate_idx(A->icol, A->nnz, A->n_cols, reinterpret_cast<int *>(w->p), s));
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, w->p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return status_from_dev(h);
+}
+
+spmv_status crs_plan_from(const spmv_crs *A, const spmv_stats &st, uint64_t cap, spmv_matrix **out, cudaStream_t s);
+
 spmv_status build_crs_plan(const spmv_crs *A, uint64_t cap, spmv_matrix **out, cudaStream_t s) {
     spmv_stats st;
     CKS(analyze_core(A, true, &st, s));
+    return crs_plan_from(A, st, cap, out, s);
+}
+
+// CRS schedule from statistics of an analysed, index-checked CRS.
+spmv_status crs_plan_from(const spmv_crs *A, const spmv_stats &st, uint64_t cap, spmv_matrix **out, cudaStream_t s) {
     std::unique_ptr<spmv_matrix> M(new_handle(A, SPMV_CRS, SPMV_ROWWISE, s));
     if (!M) return SPMV_ERR_OOM;
     M->ptr = A->irp;
@@ -898,9 +918,11 @@ spmv_status spmv_autotune(const spmv_crs *A, const spmv_at_params *p, spmv_matri
     if (stats) *stats = st;
     const bool fits = !p->mem_cap_bytes || st.ell_bytes <= p->mem_cap_bytes;
     if (st.dmat < p->dstar && fits) return build_ell_row(A, st, p->mem_cap_bytes, nullptr, nullptr, chosen, s);
+    // CRS (or COO-Row): the statistics are known, only the indices need checking
+    CKS(validate_icol(A, s));
     if (p->flags & SPMV_AT_TRY_COO) {
         spmv_matrix *crs = nullptr, *coo = nullptr;
-        CKS(build_crs_plan(A, p->mem_cap_bytes, &crs, s));
+        CKS(crs_plan_from(A, st, p->mem_cap_bytes, &crs, s));
         std::unique_ptr<spmv_matrix> crs_h(crs);
         spmv_status e = build_coo_row(A, p->mem_cap_bytes, &coo, s);
         if (e == SPMV_ERR_MEMORY_CAP) { *chosen = crs_h.release(); return SPMV_OK; }
@@ -920,7 +942,7 @@ spmv_status spmv_autotune(const spmv_crs *A, const spmv_at_params *p, spmv_matri
         *chosen = (to < tc) ? coo_h.release() : crs_h.release();
         return SPMV_OK;
     }
-    return build_crs_plan(A, p->mem_cap_bytes, chosen, s);
+    return crs_plan_from(A, st, p->mem_cap_bytes, chosen, s);
 }
 
 spmv_status spmv_autotune_choose(const spmv_crs *A, const spmv_at_params *p, int32_t *format, int32_t *layout,
