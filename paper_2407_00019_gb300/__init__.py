@@ -344,11 +344,12 @@ def spmv_set_allocator(alloc=None, free=None, ctx=None):
     free(ptr, bytes, ctx, stream), or restore the default pool (both None)."""
     L = load_library()
     if alloc is None and free is None:
-        _alloc_keepalive.clear()
         _check(L.spmv_set_allocator(None, None, None), "spmv_set_allocator")
         return
     a, f = _ALLOC_FN(alloc), _FREE_FN(free)
-    _alloc_keepalive[:] = [a, f]
+    # kept for the life of the process: a buffer allocated through a hook is
+    # freed through the same hook, possibly after the hook was replaced
+    _alloc_keepalive.extend([a, f])
     _check(L.spmv_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), ctx),
            "spmv_set_allocator")
 

@@ -409,9 +409,11 @@ __device__ __forceinline__ void warp_sort_u32(unsigned &key) {
 #pragma unroll
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
             const unsigned ok = __shfl_xor_sync(0xffffffffu, key, stride);
-            const bool asc = (lane & size) == 0;
-            const bool lower = (lane & stride) == 0;
-            key = ((lower == asc) == (ok < key)) ? ok : key;
+            // keep the smaller key where the lane's stride bit equals its
+            // size bit (lower half of an ascending pair, or upper half of a
+            // descending one), else the larger: one min or max per stage
+            const bool kmin = (((lane & size) != 0) == ((lane & stride) != 0));
+            key = kmin ? min(key, ok) : max(key, ok);
         }
     }
 }

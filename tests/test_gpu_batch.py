@@ -233,3 +233,32 @@ def test_malformed_members_are_rejected():
         L.spmv_batch_create(dev, x=x, dstar=0.0)
     assert e.value.status == 1  # SPMV_ERR_INVALID_ARG
     torch.cuda.synchronize()
+
+
+def test_allocation_failure_is_reported_and_nothing_leaks(host_set):
+    import torch
+    L = lib()
+    dev = L.Crs.batch_from_host(host_set[:8])
+    live = {}
+
+    def alloc(n, ctx, s):
+        if n >= 4096:
+            return 0  # the tile list and the ELL pool cannot be had
+        p = torch.cuda.caching_allocator_alloc(n, stream=s)
+        live[p] = n
+        return p
+
+    def free(p, n, ctx, s):
+        live.pop(p)
+        torch.cuda.caching_allocator_delete(p)
+
+    L.spmv_set_allocator(alloc, free)
+    try:
+        with pytest.raises(L.SpmvError) as e:
+            L.spmv_batch_create(dev, dstar=math.inf)
+        assert e.value.status == 3  # SPMV_ERR_OOM
+    finally:
+        L.spmv_set_allocator(None, None)
+    torch.cuda.synchronize()
+    assert live == {}
+    L.spmv_batch_create(dev, dstar=math.inf).close()

@@ -235,3 +235,43 @@ def test_bad_arguments():
     h = S.submit(mid, 0, None, None)
     S.wait(h, 60000)
     S.close()
+
+
+def test_malformed_matrix_is_refused_at_registration():
+    L = lib()
+    H = synth.laplacian_2d_5pt(16)
+    H.icol[7] = H.n_cols  # column out of range
+    S = L.Server()
+    with pytest.raises(L.SpmvError) as e:
+        S.add_matrix(L.Crs.from_host(H))
+    assert e.value.status == 2  # SPMV_ERR_INVALID_MATRIX
+    S.close()
+
+
+def test_failed_transformation_falls_back_to_crs():
+    import torch
+    L = lib()
+    H = synth.laplacian_2d_5pt(64)
+    S = L.Server(dstar=math.inf, n_streams=1, amortize_products=1, flags=L.Server.FIXED_THRESHOLD)
+    mid = S.add_matrix(L.Crs.from_host(H))
+
+    def alloc(n, ctx, s):
+        return 0 if n >= 65536 else torch.cuda.caching_allocator_alloc(n, stream=s)
+
+    def free(p, n, ctx, s):
+        torch.cuda.caching_allocator_delete(p)
+
+    xs = synth.vector_pm1(H.n_cols, seed=1)
+    x = torch.from_numpy(xs).cuda()
+    y = torch.full((H.n_rows,), float("nan"), dtype=torch.float64, device="cuda")
+    L.spmv_set_allocator(alloc, free)
+    try:
+        _, fmt = S.wait(S.submit(mid, 1, x, y), 60000)  # the ELL-Row build cannot allocate
+    finally:
+        L.spmv_set_allocator(None, None)
+    assert fmt == L.SPMV_CRS and S.stats()["transforms"] == 0
+    assert_spmv_close(y.cpu().numpy(), H, xs, what="fallback")
+    _, fmt = S.wait(S.submit(mid, 1, x, y), 60000)  # memory is back: built now
+    assert fmt == L.SPMV_ELL
+    assert_spmv_close(y.cpu().numpy(), H, xs, what="after fallback")
+    S.close()
