@@ -33,6 +33,7 @@ if ROOT not in sys.path:
 METRIC = "SpMV GB/s (% HBM peak) per format; CRS->ELL cost in CRS-SpMV units; p99 ms"
 L2_BYTES = 129 * 1024 * 1024
 FALLBACK_HBM_GBS = 6800.0
+PROFILE_STEPS = 3  # sequential steps timed per kernel after the timed region
 
 WORKLOADS = {
     "stencil27_128": dict(kind="stencil27", N=128, seed_a=1, seed_x=2, cap=0,
@@ -138,33 +139,86 @@ def kernel_bytes(name: str, bm: dict, n_rows: int, n_cols: int, nnz: int):
 
 # --------------------------------------------------------------- the step
 class Step:
-    """All hot-path rows through the C ABI on one device-resident matrix."""
+    """All hot-path rows through the C ABI on one device-resident matrix.
 
-    def __init__(self, L, A, x, ys, dstar: float, cap: int):
+    Three pipelines share nothing but the input: the on-line AT with the CRS
+    schedule and ELL-Row (and their products), COO-Row (and its product), and
+    the column-wise path (Phase I, Phase II, CCS->ELL-Column and their
+    products). With `concurrent` they run at the same time on three CUDA
+    streams, each driven by its own host thread (the library's calls
+    synchronise per call, so one host thread would serialise them). Without
+    it, they run one after the other on the current stream."""
+
+    def __init__(self, L, A, x, ys, dstar: float, cap: int, concurrent: bool = False):
         self.L, self.A, self.x, self.ys = L, A, x, ys
         self.dstar, self.cap = dstar, cap
         self.chosen = None
+        self.concurrent = concurrent
+        if concurrent:
+            import concurrent.futures as cf
+            import torch
+            self.torch = torch
+            self.device = torch.cuda.current_device()
+            self.streams = [torch.cuda.Stream() for _ in range(3)]
+            self.pool = cf.ThreadPoolExecutor(2)
 
-    def run(self):
+    def _at(self, s):
         L, A = self.L, self.A
-        chosen, stats = L.spmv_autotune(A, dstar=self.dstar, mem_cap_bytes=self.cap)
+        chosen, stats = L.spmv_autotune(A, stream=s, dstar=self.dstar, mem_cap_bytes=self.cap)
         fmt = chosen.describe()["format"]
         self.chosen = {0: "CRS", 1: "COO-Row", 2: "ELL-Row"}[fmt]
         mats = {}
-        mats["crs"] = chosen if fmt == L.SPMV_CRS else L.spmv_transform(A, L.SPMV_CRS, L.SPMV_ROWWISE)
-        mats["coo_row"] = L.spmv_transform(A, L.SPMV_COO, L.SPMV_ROWWISE)
+        mats["crs"] = chosen if fmt == L.SPMV_CRS else L.spmv_transform(A, L.SPMV_CRS, L.SPMV_ROWWISE, stream=s)
         if fmt == L.SPMV_ELL:
             mats["ell_row"] = chosen
         elif not self.cap or stats["ell_bytes"] <= self.cap:
-            mats["ell_row"] = L.spmv_transform(A, L.SPMV_ELL, L.SPMV_ROWWISE, self.cap)
-        ccs = L.spmv_transform(A, L.SPMV_CRS, L.SPMV_COLWISE, self.cap)
-        mats["coo_col"] = L.spmv_transform_from(ccs, L.SPMV_COO, self.cap)
-        mats["ell_col"] = L.spmv_transform_from(ccs, L.SPMV_ELL, self.cap)
+            mats["ell_row"] = L.spmv_transform(A, L.SPMV_ELL, L.SPMV_ROWWISE, self.cap, stream=s)
         for name, M in mats.items():
-            L.spmv_apply(M, self.x, self.ys[name])
-        for M in list(mats.values()) + [ccs]:
+            L.spmv_apply(M, self.x, self.ys[name], stream=s)
+        self.stats = stats
+        return list(mats.values())
+
+    def _coo(self, s):
+        L = self.L
+        if self.concurrent:
+            self.torch.cuda.set_device(self.device)
+        M = L.spmv_transform(self.A, L.SPMV_COO, L.SPMV_ROWWISE, stream=s)
+        L.spmv_apply(M, self.x, self.ys["coo_row"], stream=s)
+        return [M]
+
+    def _col(self, s):
+        L, A = self.L, self.A
+        if self.concurrent:
+            self.torch.cuda.set_device(self.device)
+        ccs = L.spmv_transform(A, L.SPMV_CRS, L.SPMV_COLWISE, self.cap, stream=s)
+        mats = {"coo_col": L.spmv_transform_from(ccs, L.SPMV_COO, self.cap, stream=s),
+                "ell_col": L.spmv_transform_from(ccs, L.SPMV_ELL, self.cap, stream=s)}
+        for name, M in mats.items():
+            L.spmv_apply(M, self.x, self.ys[name], stream=s)
+        return list(mats.values()) + [ccs]
+
+    def run(self):
+        if not self.concurrent:
+            hs = self._at(None) + self._coo(None) + self._col(None)
+            for M in hs:
+                M.close()
+            return self.stats
+        torch = self.torch
+        main = torch.cuda.current_stream()
+        start = torch.cuda.Event()
+        start.record(main)
+        for st in self.streams:
+            st.wait_event(start)
+        f_col = self.pool.submit(self._col, self.streams[2])
+        f_coo = self.pool.submit(self._coo, self.streams[1])
+        hs = self._at(self.streams[0]) + f_coo.result() + f_col.result()
+        for st in self.streams:
+            e = torch.cuda.Event()
+            e.record(st)
+            main.wait_event(e)
+        for M in hs:  # freed in stream order on the streams that made them
             M.close()
-        return stats
+        return self.stats
 
 
 def calibrate_dstar(L, torch, quick: bool = True):
@@ -750,6 +804,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--rate", type=float, default=None, help="serving: offered requests per second")
     ap.add_argument("--no-loop", action="store_true", help="batches: skip the per-matrix loop comparison")
+    ap.add_argument("--sequential", action="store_true",
+                    help="run the row-wise and column-wise pipelines of a step one after the other on one stream")
     ap.add_argument("--dstar", type=float, default=None,
                     help="use this D* instead of the off-line calibration (profiling runs)")
     args = ap.parse_args()
@@ -786,7 +842,8 @@ def main():
         dstar, d_pts, r_pts = calibrate_dstar(L, torch)
     else:
         dstar, d_pts, r_pts = args.dstar, [], []
-    step = Step(L, A, x, ys, dstar, w["cap"])
+    step = Step(L, A, x, ys, dstar, w["cap"], concurrent=not args.sequential)
+    seq_step = Step(L, A, x, ys, dstar, w["cap"])
     stats = L.spmv_analyze(A)
     W = stats["W"]
     ccs = L.spmv_transform(A, L.SPMV_CRS, L.SPMV_COLWISE)
@@ -804,8 +861,6 @@ def main():
         step.run()
     stream = torch.cuda.current_stream()
     barrier_sync(torch)
-    L.spmv_profile_read(reset=True)
-    L.spmv_profile_enable(True)
     launches0 = L.spmv_launch_count()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     barrier_sync(torch)
@@ -818,6 +873,13 @@ def main():
     clocks.mark(h0, time.perf_counter())
     launches = L.spmv_launch_count() - launches0
     clk = clocks.stop()
+    # per-kernel device times from steps run one kernel at a time (in the
+    # timed steps the two pipelines overlap, which stretches each launch)
+    L.spmv_profile_read(reset=True)
+    L.spmv_profile_enable(True)
+    for _ in range(PROFILE_STEPS):
+        seq_step.run()
+    torch.cuda.synchronize()
     L.spmv_profile_enable(False)
     prof = L.spmv_profile_read(reset=True)
     per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
@@ -890,6 +952,7 @@ def main():
             x_d = torch.empty_like(xpin, device=device)
             bufs.append((L.Crs(H.n_rows, H.n_cols, irp_d, icol_d, val_d), x_d))
         copy_stream = torch.cuda.Stream(device=device)
+        estep = Step(L, A, x, ys, dstar, w["cap"], concurrent=not args.sequential)
         loaded = [torch.cuda.Event() for _ in range(2)]
         consumed = [torch.cuda.Event() for _ in range(2)]
 
@@ -914,7 +977,7 @@ def main():
                 upload(1 - b)
             stream.wait_event(loaded[b])
             A_b, x_b = bufs[b]
-            estep = Step(L, A_b, x_b, ys, dstar, w["cap"])
+            estep.A, estep.x = A_b, x_b
             estep.run()
             yhost.copy_(ys["ell_row" if estep.chosen == "ELL-Row" else "crs"], non_blocking=True)
             consumed[b].record(stream)
@@ -940,7 +1003,10 @@ def main():
                        "W_col": Wc, "D_mat": stats["dmat"], "step_bytes": step_bytes,
                        "l2": "inputs larger than L2 (CRS %.0f MB vs 129 MB L2); no flush" % (
                            (12 * H.nnz + 4 * H.n_rows) / 1e6),
-                       "parallelism": f"replicas x{world}", "launches_before_timed": int(launches0)},
+                       "parallelism": f"replicas x{world}", "launches_before_timed": int(launches0),
+                       "step_schedule": "sequential" if args.sequential else
+                       "three independent pipelines (AT+CRS+ELL-Row, COO-Row, column-wise) on three streams",
+                       "per_kernel": f"{PROFILE_STEPS} sequential steps after the timed region"},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
