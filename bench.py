@@ -143,9 +143,10 @@ class Step:
 
     Three pipelines share nothing but the input: the on-line AT with the CRS
     schedule and ELL-Row (and their products), COO-Row (and its product), and
-    the column-wise path (Phase I, Phase II, CCS->ELL-Column and their
-    products). With `concurrent` they run at the same time on three CUDA
-    streams, each driven by its own host thread (the library's calls
+    the column-wise path (Phase I, then Phase II and CCS->ELL-Column, which
+    both only read the CCS, and their products). With `concurrent` they run
+    at the same time on CUDA streams (four: the column-wise path forks after
+    Phase I), each driven by its own host thread (the library's calls
     synchronise per call, so one host thread would serialise them). Without
     it, they run one after the other on the current stream."""
 
@@ -159,8 +160,11 @@ class Step:
             import torch
             self.torch = torch
             self.device = torch.cuda.current_device()
-            self.streams = [torch.cuda.Stream() for _ in range(3)]
-            self.pool = cf.ThreadPoolExecutor(2)
+            self.streams = [torch.cuda.Stream() for _ in range(4)]
+            # three workers: the column-wise task, the COO-Row task and the
+            # column-wise task's second branch (which it waits for, so fewer
+            # workers could deadlock)
+            self.pool = cf.ThreadPoolExecutor(3)
 
     def _at(self, s):
         L, A = self.L, self.A
@@ -186,16 +190,29 @@ class Step:
         L.spmv_apply(M, self.x, self.ys["coo_row"], stream=s)
         return [M]
 
-    def _col(self, s):
+    def _col_branch(self, ccs, fmt, name, s):
+        L = self.L
+        if self.concurrent:
+            self.torch.cuda.set_device(self.device)
+        M = L.spmv_transform_from(ccs, fmt, self.cap, stream=s)
+        L.spmv_apply(M, self.x, self.ys[name], stream=s)
+        return [M]
+
+    def _col(self, s, s2=None):
         L, A = self.L, self.A
         if self.concurrent:
             self.torch.cuda.set_device(self.device)
         ccs = L.spmv_transform(A, L.SPMV_CRS, L.SPMV_COLWISE, self.cap, stream=s)
-        mats = {"coo_col": L.spmv_transform_from(ccs, L.SPMV_COO, self.cap, stream=s),
-                "ell_col": L.spmv_transform_from(ccs, L.SPMV_ELL, self.cap, stream=s)}
-        for name, M in mats.items():
-            L.spmv_apply(M, self.x, self.ys[name], stream=s)
-        return list(mats.values()) + [ccs]
+        if s2 is None:
+            hs = self._col_branch(ccs, L.SPMV_COO, "coo_col", s) + self._col_branch(ccs, L.SPMV_ELL, "ell_col", s)
+            return hs + [ccs]
+        # Phase II and CCS -> ELL-Column both only read the CCS: one branch per stream
+        built = self.torch.cuda.Event()
+        built.record(s)
+        s2.wait_event(built)
+        f = self.pool.submit(self._col_branch, ccs, L.SPMV_ELL, "ell_col", s2)
+        hs = self._col_branch(ccs, L.SPMV_COO, "coo_col", s)
+        return hs + f.result() + [ccs]
 
     def run(self):
         if not self.concurrent:
@@ -209,7 +226,7 @@ class Step:
         start.record(main)
         for st in self.streams:
             st.wait_event(start)
-        f_col = self.pool.submit(self._col, self.streams[2])
+        f_col = self.pool.submit(self._col, self.streams[2], self.streams[3])
         f_coo = self.pool.submit(self._coo, self.streams[1])
         hs = self._at(self.streams[0]) + f_coo.result() + f_col.result()
         for st in self.streams:
@@ -1005,7 +1022,7 @@ def main():
                            (12 * H.nnz + 4 * H.n_rows) / 1e6),
                        "parallelism": f"replicas x{world}", "launches_before_timed": int(launches0),
                        "step_schedule": "sequential" if args.sequential else
-                       "three independent pipelines (AT+CRS+ELL-Row, COO-Row, column-wise) on three streams",
+                       "independent pipelines (AT+CRS+ELL-Row, COO-Row, Phase I then Phase II | CCS->ELL-Col) on four streams",
                        "per_kernel": f"{PROFILE_STEPS} sequential steps after the timed region"},
             "roofline": roofline,
             "cpu_baseline": cpu,
