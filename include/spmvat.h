@@ -141,6 +141,13 @@ const char *spmv_status_string(spmv_status s);
  * (both NULL). Affects allocations made after the call. */
 spmv_status spmv_set_allocator(spmv_alloc_fn alloc, spmv_free_fn free_fn, void *ctx);
 
+/* SYNC. Grows the library's private device-memory pool (on the current
+ * device) by allocating `bytes` and freeing them: the pool keeps freed memory,
+ * so later transformations on any stream sub-allocate from it instead of
+ * mapping new memory in the middle of a computation. No effect when
+ * allocator hooks are installed. SPMV_ERR_OOM if the memory is not there. */
+spmv_status spmv_reserve(uint64_t bytes, spmv_stream_t stream);
+
 /* SYNC. Row-length statistics of a CRS matrix: mu, sigma, D_mat (Eq. (4),
  * Sec. 2.2), the ELL width W and a length histogram. Reads IRP only, which
  * is why Sec. 4.4 calls D_mat cheap to obtain. Also checks IRP: irp[0] = 0,

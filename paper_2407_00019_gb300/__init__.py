@@ -19,7 +19,7 @@ __all__ = [
     "SpmvError", "Crs", "Matrix", "load_library", "library_path", "device_view",
     "SPMV_CRS", "SPMV_COO", "SPMV_ELL", "SPMV_ROWWISE", "SPMV_COLWISE",
     "SPMV_DSTAR_PREFIX", "SPMV_DSTAR_MAXPASS", "SPMV_AT_TRY_COO",
-    "spmv_version", "spmv_status_string", "spmv_set_allocator", "spmv_analyze", "spmv_validate",
+    "spmv_version", "spmv_status_string", "spmv_set_allocator", "spmv_reserve", "spmv_analyze", "spmv_validate",
     "spmv_ell_bytes", "spmv_transform", "spmv_transform_from", "spmv_apply", "spmv_transform_apply",
     "spmv_describe", "spmv_matrix_status", "spmv_destroy", "spmv_r_ell", "spmv_dstar_from_points", "spmv_measure",
     "spmv_calibrate", "spmv_autotune", "spmv_autotune_choose", "spmv_apply_coo_row_noalloc", "spmv_launch_count", "spmv_profile_enable", "spmv_profile_read",
@@ -131,6 +131,7 @@ def load_library():
         "spmv_version": (i32, []),
         "spmv_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "spmv_set_allocator": (ctypes.c_int, [vp, vp, vp]),
+        "spmv_reserve": (ctypes.c_int, [u64, vp]),
         "spmv_analyze": (ctypes.c_int, [P(_CrsT), P(_StatsT), vp]),
         "spmv_validate": (ctypes.c_int, [P(_CrsT), vp]),
         "spmv_ell_bytes": (u64, [i32, i32]),
@@ -337,6 +338,11 @@ def spmv_status_string(status: int) -> str:
 
 
 _alloc_keepalive = []
+
+
+def spmv_reserve(nbytes: int, stream=None) -> None:
+    """Grow the library's private memory pool by nbytes (kept for reuse)."""
+    _check(load_library().spmv_reserve(int(nbytes), _stream(stream)), "spmv_reserve")
 
 
 def spmv_set_allocator(alloc=None, free=None, ctx=None):

@@ -687,6 +687,28 @@ spmv_status spmv_set_allocator(spmv_alloc_fn alloc, spmv_free_fn free_fn, void *
     return SPMV_OK;
 }
 
+spmv_status spmv_reserve(uint64_t bytes, spmv_stream_t stream) {
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (g_hooks.alloc) return SPMV_OK;  // the caller's allocator owns the memory
+    }
+    if (bytes == 0) return SPMV_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return SPMV_ERR_CUDA; }
+    cudaMemPool_t pool = pool_for(dev);
+    if (!pool) return SPMV_ERR_CUDA;
+    cudaStream_t s = S(stream);
+    void *p = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&p, (size_t)bytes, pool, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? SPMV_ERR_OOM : SPMV_ERR_CUDA;
+    }
+    CK(cudaFreeAsync(p, s));
+    CK(cudaStreamSynchronize(s));  // freed and complete: any stream may reuse it at once
+    return SPMV_OK;
+}
+
 uint64_t spmv_ell_bytes(int32_t n_lines, int32_t width) {
     if (n_lines < 0 || width < 0) return 0;
     return ell_bytes(n_lines, width);

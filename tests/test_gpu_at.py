@@ -221,3 +221,21 @@ def test_profile_counts_launches():
     assert L.spmv_launch_count() - n0 == 7
     assert prof["spmv_ell_row"][0] == 7 and prof["spmv_ell_row"][1] > 0
     M.close()
+
+
+def test_reserve_grows_the_pool_and_respects_hooks():
+    import torch
+    L = lib()
+    L.spmv_reserve(64 << 20)
+    L.spmv_reserve(0)
+    calls = []
+    L.spmv_set_allocator(lambda n, ctx, s: calls.append(n) or 0, lambda p, n, ctx, s: None)
+    try:
+        L.spmv_reserve(64 << 20)  # the caller's allocator owns the memory: nothing to do
+    finally:
+        L.spmv_set_allocator(None, None)
+    assert calls == []
+    with pytest.raises(L.SpmvError) as e:
+        L.spmv_reserve(1 << 60)
+    assert e.value.status == 3  # SPMV_ERR_OOM
+    torch.cuda.synchronize()
