@@ -213,6 +213,7 @@ constexpr int ELL_LINES = 128;
 constexpr int ELL_SPLIT = 2;
 constexpr int ELL_THREADS = ELL_LINES * ELL_SPLIT;
 constexpr int ELL_STAGE_CAP = 4096;  // entries per stage (48 KB)
+constexpr int ELL_KB = 8;            // slots a thread handles at once
 using EllPipe = StagePipe<ELL_STAGE_CAP, 1>;
 
 template <bool FUSED>
@@ -245,20 +246,40 @@ __global__ void __launch_bounds__(ELL_THREADS) k_lines_to_ell(
                 if (len < 0 || len > width) { bad = 1; len = len < 0 ? 0 : width; }
                 int last = len > 0 ? P.idx_at(m, st, idx, s + len - 1) : 0;
                 if ((unsigned)last >= (unsigned)idx_bound) { bad = 1; last = 0; }
-                for (int k = part; k < width; k += ELL_SPLIT) {
-                    double v;
-                    int32_t c;
-                    if (k < len) {
-                        v = P.val_at(m, st, val, s + k);
-                        c = P.idx_at(m, st, idx, s + k);
-                        if ((unsigned)c >= (unsigned)idx_bound) { bad = 1; c = 0; }
-                        if (FUSED) acc = fma(v, __ldg(x + c), acc);
-                    } else {
-                        v = 0.0;
-                        c = last;
+                // slots in batches of ELL_KB per thread: every value, index
+                // and x gather of a batch is issued before its first use
+                for (int k0 = part; k0 < width; k0 += ELL_SPLIT * ELL_KB) {
+                    double v[ELL_KB];
+                    int32_t c[ELL_KB];
+#pragma unroll
+                    for (int u = 0; u < ELL_KB; ++u) {
+                        const int k = k0 + u * ELL_SPLIT;
+                        v[u] = 0.0;
+                        c[u] = last;
+                        if (k < len) {
+                            v[u] = P.val_at(m, st, val, s + k);
+                            c[u] = P.idx_at(m, st, idx, s + k);
+                            if ((unsigned)c[u] >= (unsigned)idx_bound) { bad = 1; c[u] = 0; }
+                        }
                     }
-                    __stcs(eval + (long long)k * ld + l, v);
-                    __stcs(eidx + (long long)k * ld + l, c);
+                    double xv[ELL_KB];
+                    if (FUSED) {
+#pragma unroll
+                        for (int u = 0; u < ELL_KB; ++u) xv[u] = (k0 + u * ELL_SPLIT < len) ? __ldg(x + c[u]) : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < ELL_KB; ++u) {
+                        const int k = k0 + u * ELL_SPLIT;
+                        if (k < width) {
+                            __stcs(eval + (long long)k * ld + l, v[u]);
+                            __stcs(eidx + (long long)k * ld + l, c[u]);
+                        }
+                    }
+                    if (FUSED) {
+#pragma unroll
+                        for (int u = 0; u < ELL_KB; ++u)
+                            if (k0 + u * ELL_SPLIT < len) acc = fma(v[u], xv[u], acc);
+                    }
                 }
             } else {
                 for (int k = part; k < width; k += ELL_SPLIT) {
