@@ -126,6 +126,12 @@ def kernel_bytes(name: str, bm: dict, n_rows: int, n_cols: int, nnz: int):
         "tile_lines": 4 * (nnz // 2048 + 1),
         "spmv_coo_row_carry": 16 * (nnz // 2048 + 1),
         "col_fixup_block": 0,
+        # row-value slot path (the default for >= 8 entries per column): ICOL +
+        # VAL in, one 16-byte {row, value} slot out; slots in, ICOL_T + VAL_T out
+        "col_claim_rv": 28 * nnz + 4 * (n_rows + 1) + 4 * n_cols,
+        "col_fixup_rv": 28 * nnz + 4 * (n_cols + 1),
+        "col_overflow_rv": 0,
+        "col_fixup_long_rv": 0,
         "crs_to_ell_row_fused_spmv": bm["crs_to_ell_row"] + 8 * n_cols + 8 * n_rows,
     }
     if name.startswith("spmv_crs_"):

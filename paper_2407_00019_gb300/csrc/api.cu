@@ -420,36 +420,45 @@ spmv_status build_ell_row(const spmv_crs *A, const spmv_stats &st, uint64_t cap,
 }
 
 // Phase I (CRS -> CCS). On success M holds the CCS in ccs_bufs/bufs.
-// `ell_cap_check`: when >= 0, fail with MEMORY_CAP before building if an
-// ELL-Column of the longest column would exceed it (checked after the count).
-spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bool want_ell,
-                   std::unique_ptr<spmv_matrix> &M, cudaStream_t s, const int *irp_status) {
+// Three ways to the same CCS, bit for bit:
+//   RV    : slots carry (row, value); no gathers, no per-entry ranks. Needs
+//           >= 8 entries per column on average, no repeated (i, j), columns of
+//           at most col_rv_long_cap() entries and few entries beyond the slots;
+//           the kernels report ST_REDO when one of these fails.
+//   KSLOT : slots carry (k, row); any matrix with >= 8 entries per column.
+//   COUNT : count, scan, scatter of (k, row); any matrix.
+enum class P1 { RV, KSLOT, COUNT };
+constexpr spmv_status kRedo = (spmv_status)-1;  // internal: rerun on KSLOT
+
+spmv_status phase1_try(const spmv_crs *A, uint64_t cap_ell_col, bool want_ell, P1 mode,
+                       std::unique_ptr<spmv_matrix> &M, cudaStream_t s, const int *irp_status) {
     const int64_t nnz = A->nnz;
     const int32_t nc = A->n_cols;
-    const uint64_t own = (uint64_t)(nc + 1) * 4 + (uint64_t)nnz * 12;
-    if (!want_ell && cap_ccs && own > cap_ccs) return SPMV_ERR_MEMORY_CAP;
-    BufPtr cp, trow, tval, rank, pairs, scan_scr, words, longl;
+    const bool rv = mode == P1::RV, slots = mode != P1::COUNT;
+    BufPtr cp, trow, tval, rank, pairs, scan_scr, words, longl, tslots, sct0, ovl;
     CKS(alloc_buf((size_t)(nc + 1) * 4, s, &cp));
-    CKS(alloc_buf((size_t)nnz * 4, s, &rank));
+    if (!rv) CKS(alloc_buf((size_t)nnz * 4, s, &rank));
     CKS(alloc_buf(scan_scratch_bytes(nc), s, &scan_scr));
-    CKS(alloc_buf(64, s, &words));  // [0] status [1] colmax
+    CKS(alloc_buf(64, s, &words));  // [0] status [1] colmax [2] entries beyond the slots
     const int64_t max_long = std::min<int64_t>(nc, nnz / 33 + 1);
     CKS(alloc_buf((size_t)(max_long + 1) * 4, s, &longl));  // [0] count, then the list
     int32_t *d_cp = reinterpret_cast<int32_t *>(cp->p);
     int *d_status = reinterpret_cast<int *>(words->p);
     int32_t *d_colmax = reinterpret_cast<int32_t *>(words->p) + 1;
+    int32_t *d_over = reinterpret_cast<int32_t *>(words->p) + 2;
     int32_t *d_long = reinterpret_cast<int32_t *>(longl->p);
     CK(cudaMemsetAsync(d_cp, 0, (size_t)(nc + 1) * 4, s));
     CK(cudaMemsetAsync(words->p, 0, 64, s));
     CK(cudaMemsetAsync(d_long, 0, 4, s));
-    // Slot path (count and placement in one pass, placement into a
-    // slot-major array) when that array is at most 4x the pairs array, i.e.
-    // columns hold 8 or more entries on average; else count, then scatter.
-    const bool slots = !getenv("SPMVAT_PHASE1_SCATTER") &&
-                       (int64_t)col_slot_cap() * nc <= 4 * nnz && nnz > 0;
-    BufPtr tslots, sct0;
-    int32_t *d_over = reinterpret_cast<int32_t *>(words->p) + 2;
-    if (slots) {
+    const int64_t ov_cap = nnz / 8 + 1024;
+    if (rv) {
+        CKS(alloc_buf(col_rv_slot_bytes(nc), s, &tslots));
+        CKS(alloc_buf(col_scatter_scratch_bytes(nnz), s, &sct0));
+        CKS(alloc_buf((size_t)ov_cap * sizeof(int4), s, &ovl));
+        CK(launch_col_claim_rv(A->irp, A->n_rows, A->icol, A->val, nnz, nc, d_cp, tslots->p,
+                               reinterpret_cast<int4 *>(ovl->p), ov_cap, d_over,
+                               reinterpret_cast<int32_t *>(sct0->p), d_status, s));
+    } else if (slots) {
         CKS(alloc_buf(col_slot_bytes(nc), s, &tslots));
         CKS(alloc_buf(col_scatter_scratch_bytes(nnz), s, &sct0));
         CK(launch_col_claim(A->irp, A->n_rows, A->icol, nnz, nc, d_cp, reinterpret_cast<int32_t *>(rank->p),
@@ -469,34 +478,44 @@ spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bo
         CKS(status_from_dev(hirp));
         CKS(status_from_dev(hw[0]));
         if (cap_ell_col && ell_bytes(nc, hw[1]) > cap_ell_col) return SPMV_ERR_MEMORY_CAP;
+        if (hw[0] & ST_REDO) return kRedo;
     }
     CKS(alloc_buf((size_t)nnz * 4, s, &trow));
     CKS(alloc_buf((size_t)nnz * 8, s, &tval));
-    CKS(alloc_buf((size_t)nnz * 8 + 16, s, &pairs));  // slack: staged copies round the end up
-    if (slots) {
-        // entries beyond the slot capacity (long columns) go to the pairs
-        // array at IRP_T[col] + rank; the grid exits at once when there are none
-        CK(launch_col_scatter(A->irp, A->n_rows, A->icol, nnz, nc, d_cp, reinterpret_cast<int32_t *>(rank->p),
-                              reinterpret_cast<int2 *>(pairs->p), reinterpret_cast<int32_t *>(sct0->p), d_status, s,
-                              col_slot_cap(), d_over, true));
-        CK(launch_col_fixup_slots(d_cp, nc, A->irp, A->n_rows, A->val, reinterpret_cast<const int2 *>(tslots->p),
-                                  reinterpret_cast<int2 *>(pairs->p), d_long + 1,
-                                  reinterpret_cast<int32_t *>(rank->p), reinterpret_cast<int32_t *>(trow->p),
-                                  reinterpret_cast<double *>(tval->p), s));
+    if (rv) {
+        CK(launch_col_fixup_rv(d_cp, nc, A->n_rows, A->val, tslots->p, reinterpret_cast<const int4 *>(ovl->p),
+                               ov_cap,
+                               d_over, d_long + 1, reinterpret_cast<int32_t *>(trow->p),
+                               reinterpret_cast<double *>(tval->p), d_status, s));
     } else {
-        BufPtr sct;
-        CKS(alloc_buf(col_scatter_scratch_bytes(nnz), s, &sct));
-        CK(launch_col_scatter(A->irp, A->n_rows, A->icol, nnz, nc, d_cp, reinterpret_cast<int32_t *>(rank->p),
-                              reinterpret_cast<int2 *>(pairs->p), reinterpret_cast<int32_t *>(sct->p), d_status, s));
-        CK(launch_col_fixup(d_cp, nc, A->irp, A->n_rows, A->val, reinterpret_cast<int2 *>(pairs->p), d_long + 1,
-                            reinterpret_cast<int32_t *>(rank->p), reinterpret_cast<int32_t *>(trow->p),
-                            reinterpret_cast<double *>(tval->p), d_status, s));
+        CKS(alloc_buf((size_t)nnz * 8 + 16, s, &pairs));  // slack: staged copies round the end up
+        if (slots) {
+            // entries beyond the slot capacity (long columns) go to the pairs
+            // array at IRP_T[col] + rank; the grid exits at once when there are none
+            CK(launch_col_scatter(A->irp, A->n_rows, A->icol, nnz, nc, d_cp, reinterpret_cast<int32_t *>(rank->p),
+                                  reinterpret_cast<int2 *>(pairs->p), reinterpret_cast<int32_t *>(sct0->p), d_status,
+                                  s, col_slot_cap(), d_over, true));
+            CK(launch_col_fixup_slots(d_cp, nc, A->irp, A->n_rows, A->val,
+                                      reinterpret_cast<const int2 *>(tslots->p), reinterpret_cast<int2 *>(pairs->p),
+                                      d_long + 1, reinterpret_cast<int32_t *>(rank->p),
+                                      reinterpret_cast<int32_t *>(trow->p), reinterpret_cast<double *>(tval->p), s));
+        } else {
+            BufPtr sct;
+            CKS(alloc_buf(col_scatter_scratch_bytes(nnz), s, &sct));
+            CK(launch_col_scatter(A->irp, A->n_rows, A->icol, nnz, nc, d_cp, reinterpret_cast<int32_t *>(rank->p),
+                                  reinterpret_cast<int2 *>(pairs->p), reinterpret_cast<int32_t *>(sct->p), d_status,
+                                  s));
+            CK(launch_col_fixup(d_cp, nc, A->irp, A->n_rows, A->val, reinterpret_cast<int2 *>(pairs->p), d_long + 1,
+                                reinterpret_cast<int32_t *>(rank->p), reinterpret_cast<int32_t *>(trow->p),
+                                reinterpret_cast<double *>(tval->p), d_status, s));
+        }
     }
     CK(cudaMemcpyAsync(hw, words->p, sizeof(hw), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&hirp, irp_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     CKS(status_from_dev(hirp));
     CKS(status_from_dev(hw[0]));
+    if (hw[0] & ST_REDO) return kRedo;
     const int32_t colmax = hw[1];
     M->ptr = d_cp;
     M->idx = reinterpret_cast<const int32_t *>(trow->p);
@@ -504,6 +523,30 @@ spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bo
     M->ccs_bufs = {cp, trow, tval};
     M->colmax = colmax;
     return SPMV_OK;
+}
+
+// `cap_ell_col`: when want_ell, fail with MEMORY_CAP before building the CCS
+// if an ELL-Column of the longest column would exceed it (checked after the count).
+spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bool want_ell,
+                   std::unique_ptr<spmv_matrix> &M, cudaStream_t s, const int *irp_status) {
+    const int64_t nnz = A->nnz;
+    const int32_t nc = A->n_cols;
+    const uint64_t own = (uint64_t)(nc + 1) * 4 + (uint64_t)nnz * 12;
+    if (!want_ell && cap_ccs && own > cap_ccs) return SPMV_ERR_MEMORY_CAP;
+    // The slot paths need >= 8 entries per column on average (slot array at
+    // most 4x the pairs array); SPMVAT_PHASE1 = "scatter" | "kslot" | "rv"
+    // forces a path (tests and measurements).
+    const char *force = getenv("SPMVAT_PHASE1");
+    const bool dense_cols = (int64_t)col_slot_cap() * nc <= 4 * nnz && nnz > 0;
+    // the row-value fix-up packs (row << 5 | slot) into 32 bits
+    const bool rv_ok = A->n_rows < (1 << 27) - 1;
+    P1 mode = dense_cols ? (rv_ok ? P1::RV : P1::KSLOT) : P1::COUNT;
+    if (force && !strcmp(force, "scatter")) mode = P1::COUNT;
+    if (force && !strcmp(force, "kslot") && nnz > 0) mode = P1::KSLOT;
+    if (force && !strcmp(force, "rv") && nnz > 0 && rv_ok) mode = P1::RV;
+    spmv_status st = phase1_try(A, cap_ell_col, want_ell, mode, M, s, irp_status);
+    if (st == kRedo) st = phase1_try(A, cap_ell_col, want_ell, P1::KSLOT, M, s, irp_status);
+    return st;
 }
 
 spmv_status ell_col_from_ccs(const spmv_matrix *src, uint64_t cap, spmv_matrix **out, cudaStream_t s) {

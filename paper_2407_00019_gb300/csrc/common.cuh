@@ -13,6 +13,8 @@ enum : int {
     ST_BAD_INDEX = 1,  // an index (column / row / position) out of range
     ST_TIMEOUT = 2,    // a bounded wait ran out
     ST_BAD_PTR = 4,    // IRP not 0 .. nnz or not non-decreasing
+    ST_REDO = 8,       // a fast path met a case it does not cover (internal:
+                       // the host reruns the step on the general path)
 };
 
 // Per-call accumulator of spmv_analyze (one device struct).
@@ -183,6 +185,17 @@ cudaError_t launch_col_claim(const int32_t *irp, int32_t n_rows, const int32_t *
 cudaError_t launch_col_fixup_slots(const int32_t *cp, int32_t n_cols, const int32_t *irp, int32_t n_rows,
                                    const double *val, const int2 *T, int2 *pairs, const int32_t *long_list,
                                    int32_t *keys_tmp, int32_t *trow, double *tval, cudaStream_t s);
+// Row-value slot path of Phase I (no repeated (i, j) entries, columns of at
+// most col_rv_long_cap() entries, at most `ov_cap` entries beyond the slots;
+// otherwise ST_REDO; rows below 2^27 - 1). `slots`: col_rv_slot_bytes(n_cols) bytes.
+size_t col_rv_slot_bytes(int32_t n_cols);
+int col_rv_long_cap();
+cudaError_t launch_col_claim_rv(const int32_t *irp, int32_t n_rows, const int32_t *icol, const double *val,
+                                int64_t nnz, int32_t n_cols, int32_t *nc, void *slots, int4 *ov,
+                                int64_t ov_cap, int32_t *n_ov, int32_t *scratch, int *status, cudaStream_t s);
+cudaError_t launch_col_fixup_rv(const int32_t *cp, int32_t n_cols, int32_t n_rows, const double *val,
+                                const void *slots, const int4 *ov, int64_t ov_cap, const int32_t *n_ov,
+                                const int32_t *long_list, int32_t *trow, double *tval, int *status, cudaStream_t s);
 // `pairs` must have 16 bytes of slack after its nnz elements.
 // `long_list` is preceded by its device-side count.
 cudaError_t launch_col_fixup(const int32_t *cp, int32_t n_cols, const int32_t *irp, int32_t n_rows,

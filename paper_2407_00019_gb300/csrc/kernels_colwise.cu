@@ -23,6 +23,9 @@
 //                   Columns of <= 32 entries: one warp, bitonic network in
 //                   registers. Longer: one CTA, bitonic sort in shared memory
 //                   (<= 4096) or sorted chunks + merge-path merges.
+// The default path for columns with >= 8 entries on average carries (row,
+// value) instead of (k, row) and sorts each column by row in registers; see
+// "row-value slot path" below.
 #include <climits>
 
 #include "common.cuh"
@@ -774,4 +777,370 @@ cudaError_t launch_col_fixup(const int32_t *cp, int32_t n_cols, const int32_t *i
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------- row-value slot path
+// The slot path above carries (k, row) through the slot array, so its fix-up
+// gathers VAL[k] at scattered addresses. When no (i, j) pair repeats, the row
+// alone orders a column (the serial scatter lists a column's rows in
+// ascending order), so the slots can carry the row and the value instead:
+//   k_col_claim_rv  : r = atomicAdd(NC[j], 1); slot (r, j) = (i, VAL[k]) for
+//                     r < SLOT_CAP (VAL read once, coalesced); entries with
+//                     r >= SLOT_CAP become records {k, i, j, r} in a compact list.
+//   k_fixup_net     : one thread per column sorts the column's slots by row
+//                     with a register sorting network; rows and values are
+//                     written contiguously per CTA. Slots of longer columns go
+//                     straight to IRP_T[j] + r.
+//   k_ov_place_rv   : list records to IRP_T[j] + r (value gathered from VAL[k]).
+//   k_fixup_long_rv : columns of 33..RV_LONG_CAP entries sorted in place by row
+//                     (CTA bitonic network on (row, position) keys).
+// A repeated row within a column, a longer column or a full record list sets
+// ST_REDO; the host then rebuilds the CCS on the (k, row) slot path.
+// Slot (r, j) is one 16-byte record {row, value} at r * n_cols + j, so an
+// entry costs one store in the claim and one load in the fix-up.
+constexpr int RV_LONG_CAP = 4096;
+
+struct __align__(16) RowVal {
+    int32_t row;
+    int32_t pad;
+    double v;
+};
+
+size_t col_rv_slot_bytes(int32_t n_cols) { return (size_t)SLOT_CAP * (size_t)n_cols * sizeof(RowVal); }
+int col_rv_long_cap() { return RV_LONG_CAP; }
+
+__device__ __forceinline__ void slot_put(RowVal *slots, long long at, int row, double v) {
+    RowVal q;
+    q.row = row;
+    q.pad = 0;
+    q.v = v;
+    slots[at] = q;
+}
+__device__ __forceinline__ void slot_get(const RowVal *slots, long long at, int &row, double &v) {
+    const int4 q = __ldcs(reinterpret_cast<const int4 *>(slots) + at);
+    row = q.x;
+    v = __hiloint2double(q.w, q.z);
+}
+
+// Thread-striped items (item u of thread t is entry k0 + 256 u + t): one
+// warp instruction covers 32 consecutive entries, so a row's neighbouring
+// columns, which share a rank in banded matrices, land in the same sectors of
+// the slots and of NC. Rows are found per 8-entry block (one search and a
+// walk) and handed over through shared memory (one padding word per 32
+// entries: both orders conflict-free). The order in which the atomics of one
+// column arrive is arbitrary: every CTA whose rows touch a column may run at
+// the same time, so the fix-up sorts every column.
+__device__ __forceinline__ int pad32(int e) { return e + (e >> 5); }
+
+__global__ void __launch_bounds__(SCT_THREADS) k_col_claim_rv(const int32_t *__restrict__ irp, int32_t n_rows,
+                                                               const int32_t *__restrict__ icol,
+                                                               const double *__restrict__ val, int64_t nnz,
+                                                               int32_t n_cols, int32_t *__restrict__ nc,
+                                                               const int32_t *__restrict__ tl, long long n_tiles,
+                                                               RowVal *__restrict__ slots, int4 *__restrict__ ov,
+                                                               long long ov_cap, int32_t *__restrict__ n_ov,
+                                                               int *status) {
+    __shared__ int32_t s_ptr[SCT_WIN];
+    __shared__ int32_t s_row[SCT_TILE + SCT_TILE / 32];
+    const long long k0 = (long long)blockIdx.x * SCT_TILE;
+    const long long k1 = min(k0 + (long long)SCT_TILE, (long long)nnz);
+    const int wbase = (int)threadIdx.x;
+    constexpr int USTEP = SCT_THREADS;
+    int c[SCT_ITEMS];
+    double v[SCT_ITEMS];
+#pragma unroll
+    for (int u = 0; u < SCT_ITEMS; ++u) {
+        const long long k = k0 + wbase + USTEP * u;
+        c[u] = (k < k1) ? __ldcs(icol + k) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < SCT_ITEMS; ++u) {
+        const long long k = k0 + wbase + USTEP * u;
+        v[u] = (k < k1) ? __ldcs(val + k) : 0.0;
+    }
+    int r[SCT_ITEMS];
+    int bad = 0;
+#pragma unroll
+    for (int u = 0; u < SCT_ITEMS; ++u) {
+        const long long k = k0 + wbase + USTEP * u;
+        const bool has = k < k1;
+        const bool ok = has && (unsigned)c[u] < (unsigned)n_cols;
+        bad |= has && !ok;
+        r[u] = ok ? atomicAdd(nc + c[u], 1) : -1;
+    }
+    const int lo = tl[blockIdx.x];
+    const int hi = (blockIdx.x + 1 < n_tiles) ? tl[blockIdx.x + 1] : n_rows - 1;
+    const int wn = hi - lo + 2;
+    const bool sm = wn <= SCT_WIN;
+    if (sm)
+        for (int i = threadIdx.x; i < wn; i += SCT_THREADS) s_ptr[i] = irp[lo + i];
+    __syncthreads();
+    {
+        const long long kb = k0 + (long long)threadIdx.x * SCT_ITEMS;  // this thread's block of 8
+        if (kb < k1) {
+            int row = sm ? lo + last_le(s_ptr, 0, wn - 1, kb) : last_le(irp, lo, hi + 1, kb);
+#pragma unroll
+            for (int j = 0; j < SCT_ITEMS; ++j) {
+                const long long kk = kb + j;
+                while (row < hi && (long long)(sm ? s_ptr[row + 1 - lo] : irp[row + 1]) <= kk) ++row;
+                s_row[pad32((int)threadIdx.x * SCT_ITEMS + j)] = row;
+            }
+        }
+    }
+    __syncthreads();
+    int redo = 0;
+#pragma unroll
+    for (int u = 0; u < SCT_ITEMS; ++u) {
+        const int e = wbase + USTEP * u;
+        if (r[u] < 0) continue;
+        const int row = s_row[pad32(e)];
+        if (r[u] < SLOT_CAP) {
+            slot_put(slots, (long long)r[u] * n_cols + c[u], row, v[u]);
+        } else {
+            const int q = atomicAdd(n_ov, 1);
+            if (q < ov_cap) ov[q] = make_int4((int)(k0 + e), row, c[u], r[u]);
+            else redo = 1;
+        }
+    }
+    if (__any_sync(0xffffffffu, redo) && lane_id() == 0) atomicOr(status, ST_REDO);
+    if (__any_sync(0xffffffffu, bad) && lane_id() == 0) atomicOr(status, ST_BAD_INDEX);
+}
+
+cudaError_t launch_col_claim_rv(const int32_t *irp, int32_t n_rows, const int32_t *icol, const double *val,
+                                int64_t nnz, int32_t n_cols, int32_t *nc, void *slots, int4 *ov,
+                                int64_t ov_cap, int32_t *n_ov, int32_t *scratch, int *status, cudaStream_t s) {
+    if (nnz <= 0) return cudaSuccess;
+    cudaError_t e = launch_tile_lines(irp, n_rows, nnz, SCT_TILE, scratch, s);
+    if (e != cudaSuccess) return e;
+    const long long n_tiles = (nnz + SCT_TILE - 1) / SCT_TILE;
+    KernelScope ks("col_claim_rv", s);
+    k_col_claim_rv<<<(unsigned)n_tiles, SCT_THREADS, 0, s>>>(irp, n_rows, icol, val, nnz, n_cols, nc, scratch, n_tiles,
+                                                              reinterpret_cast<RowVal *>(slots), ov, ov_cap, n_ov,
+                                                              status);
+    return cudaGetLastError();
+}
+
+// Sorting networks (Batcher's odd-even merge sort) with compile-time
+// comparator lists, applied by one thread to keys held in registers.
+template <int N>
+struct SortNet {
+    int n;
+    unsigned char a[192], b[192];
+};
+template <int N>
+__host__ __device__ constexpr SortNet<N> make_sort_net() {
+    SortNet<N> t{};
+    t.n = 0;
+    for (int p = 1; p < N; p <<= 1)
+        for (int k = p; k >= 1; k >>= 1)
+            for (int j = k % p; j + k < N; j += 2 * k)
+                for (int i = 0; i < k && i < N - j - k; ++i)
+                    if ((i + j) / (2 * p) == (i + j + k) / (2 * p)) {
+                        t.a[t.n] = (unsigned char)(i + j);
+                        t.b[t.n] = (unsigned char)(i + j + k);
+                        ++t.n;
+                    }
+    return t;
+}
+template <int N>
+__device__ __forceinline__ void net_sort(uint32_t (&key)[SLOT_CAP]) {
+    constexpr SortNet<N> net = make_sort_net<N>();  // 19 / 63 / 191 comparators
+#pragma unroll
+    for (int i = 0; i < net.n; ++i) {
+        const uint32_t x = key[net.a[i]], y = key[net.b[i]];
+        key[net.a[i]] = min(x, y);
+        key[net.b[i]] = max(x, y);
+    }
+}
+
+// One thread per column, FN_COLS columns per CTA. Thread t reads the slots of
+// its column (one coalesced slot row per warp instruction), keeps the keys
+// (row << 5 | slot) in registers and the values in shared memory, sorts the
+// keys with the smallest network that covers the CTA's longest short column
+// (8, 16 or 32 inputs; padding keys 0xffffffff), and records each sorted key
+// at its compact position; then all threads write ICOL_T and VAL_T for the
+// CTA's columns contiguously. A thread sorts 32 keys in 382 min/max
+// instructions where a warp-wide network would spend 15 shuffle stages on one
+// column. Needs n_rows < 2^27 - 1 (the host checks); repeated rows set ST_REDO.
+constexpr int FN_COLS = 128;
+
+__global__ void __launch_bounds__(FN_COLS) k_fixup_net(const int32_t *__restrict__ cp, int32_t n_cols,
+                                                        const RowVal *__restrict__ slots, int32_t *__restrict__ trow,
+                                                        double *__restrict__ tval, int *status) {
+    __shared__ double s_val[SLOT_CAP][FN_COLS + 1];
+    __shared__ uint32_t s_key[FN_COLS * SLOT_CAP];
+    __shared__ uint8_t s_col[FN_COLS * SLOT_CAP];
+    __shared__ int32_t s_cp[FN_COLS + 1];
+    __shared__ int32_t s_off[FN_COLS + 1];
+    __shared__ int s_wsum[FN_COLS / 32], s_wmax[FN_COLS / 32];
+    __shared__ int s_redo;
+    const int t = threadIdx.x;
+    const unsigned lane = lane_id();
+    const int w = t >> 5;
+    const long long c0 = (long long)blockIdx.x * FN_COLS;
+    const int nc = (int)min((long long)FN_COLS, (long long)n_cols - c0);
+    for (int i = t; i <= nc; i += FN_COLS) s_cp[i] = cp[c0 + i];
+    if (t == 0) s_redo = 0;
+    __syncthreads();
+    const int len = (t < nc) ? s_cp[t + 1] - s_cp[t] : 0;
+    const bool shortc = len <= SLOT_CAP;
+    // compact offsets of the short columns and the longest short column
+    int a = shortc ? len : 0;
+    int inc = a;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if ((int)lane >= o) inc += v;
+    }
+    int m = a;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 31) s_wsum[w] = inc;
+    if (lane == 0) s_wmax[w] = m;
+    __syncthreads();
+    int woff = 0, maxl = 0;
+#pragma unroll
+    for (int j = 0; j < FN_COLS / 32; ++j) {
+        if (j < w) woff += s_wsum[j];
+        maxl = max(maxl, s_wmax[j]);
+    }
+    const int off = woff + inc - a;
+    s_off[t] = off;
+    if (t == FN_COLS - 1) s_off[FN_COLS] = off + a;
+    const long long at0 = c0 + t;
+    if (!shortc) {
+        // slots of a long column go to its place in the CCS; k_fixup_long_rv sorts it
+        for (int r = 0; r < SLOT_CAP; ++r) {
+            int row;
+            double v;
+            slot_get(slots, (long long)r * n_cols + at0, row, v);
+            trow[(long long)s_cp[t] + r] = row;
+            tval[(long long)s_cp[t] + r] = v;
+        }
+    }
+    uint32_t key[SLOT_CAP];
+    const int lim = shortc ? len : 0;
+#pragma unroll
+    for (int r = 0; r < SLOT_CAP; ++r) {
+        key[r] = 0xffffffffu;
+        if (r < lim) {
+            int row;
+            double v;
+            slot_get(slots, (long long)r * n_cols + at0, row, v);
+            key[r] = ((uint32_t)row << 5) | (uint32_t)r;
+            s_val[r][t] = v;
+        }
+    }
+    if (maxl <= 8) net_sort<8>(key);
+    else if (maxl <= 16) net_sort<16>(key);
+    else net_sort<32>(key);
+    bool dup = false;
+#pragma unroll
+    for (int r = 0; r < SLOT_CAP; ++r) {
+        if (r < lim) {
+            s_key[off + r] = key[r];
+            s_col[off + r] = (uint8_t)t;
+            if (r > 0 && (key[r] >> 5) == (key[r - 1] >> 5)) dup = true;
+        }
+    }
+    if (dup) s_redo = 1;
+    __syncthreads();
+    if (t == 0 && s_redo) atomicOr(status, ST_REDO);
+    const int ns = s_off[FN_COLS];
+    for (int q = t; q < ns; q += FN_COLS) {
+        const uint32_t k = s_key[q];
+        const int cc = s_col[q];
+        const long long pos = (long long)s_cp[cc] + (q - s_off[cc]);
+        __stcs(trow + pos, (int32_t)(k >> 5));
+        __stcs(tval + pos, s_val[k & 31u][cc]);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ov_place_rv(const int32_t *__restrict__ cp, int32_t n_cols,
+                                                      const double *__restrict__ val, const int4 *__restrict__ ov,
+                                                      long long ov_cap, const int32_t *__restrict__ n_ov,
+                                                      int32_t *__restrict__ trow, double *__restrict__ tval) {
+    const long long cnt = min((long long)*n_ov, ov_cap);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x) {
+        const int4 q = ov[i];  // {k, row, col, rank}
+        if ((unsigned)q.z >= (unsigned)n_cols) continue;
+        const long long pos = (long long)cp[q.z] + q.w;
+        if (pos >= cp[q.z + 1]) continue;
+        trow[pos] = q.y;
+        tval[pos] = __ldg(val + q.x);
+    }
+}
+
+// One CTA per long column (33 .. RV_LONG_CAP entries, in place): keys
+// (row << 32 | position) sorted in shared memory, then every value is read
+// before any is written back.
+constexpr int RVL_PER = RV_LONG_CAP / FIX_THREADS;  // 16
+
+__global__ void __launch_bounds__(FIX_THREADS) k_fixup_long_rv(const int32_t *__restrict__ cp,
+                                                                const int32_t *__restrict__ long_list,
+                                                                const int32_t *__restrict__ long_count,
+                                                                int32_t *__restrict__ trow,
+                                                                double *__restrict__ tval, int *status) {
+    __shared__ unsigned long long s[RV_LONG_CAP];
+    __shared__ int s_redo;
+    const int nl = *long_count;
+    for (int li = blockIdx.x; li < nl; li += gridDim.x) {
+        const int j = long_list[li];
+        const int p0 = cp[j], p1 = cp[j + 1];
+        const int L = p1 - p0;
+        if (L <= SLOT_CAP) continue;
+        if (L > RV_LONG_CAP) {
+            if (threadIdx.x == 0) atomicOr(status, ST_REDO);
+            continue;
+        }
+        if (threadIdx.x == 0) s_redo = 0;
+        int P = 64;
+        while (P < L) P <<= 1;
+        for (int i = threadIdx.x; i < P; i += FIX_THREADS)
+            s[i] = (i < L) ? (((unsigned long long)(unsigned)trow[p0 + i] << 32) | (unsigned)i) : ~0ull;
+        __syncthreads();
+        block_bitonic_u64(s, P);
+        double v[RVL_PER];
+#pragma unroll
+        for (int u = 0; u < RVL_PER; ++u) {
+            const int i = threadIdx.x + u * FIX_THREADS;
+            v[u] = (i < L) ? tval[p0 + (int)(s[i] & 0xffffffffu)] : 0.0;
+            if (i > 0 && i < L && (s[i] >> 32) == (s[i - 1] >> 32)) s_redo = 1;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < RVL_PER; ++u) {
+            const int i = threadIdx.x + u * FIX_THREADS;
+            if (i < L) {
+                trow[p0 + i] = (int32_t)(s[i] >> 32);
+                tval[p0 + i] = v[u];
+            }
+        }
+        if (threadIdx.x == 0 && s_redo) atomicOr(status, ST_REDO);
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_col_fixup_rv(const int32_t *cp, int32_t n_cols, int32_t n_rows, const double *val,
+                                const void *slots, const int4 *ov, int64_t ov_cap, const int32_t *n_ov,
+                                const int32_t *long_list, int32_t *trow, double *tval, int *status, cudaStream_t s) {
+    if (n_cols <= 0) return cudaSuccess;
+    {
+        KernelScope ks("col_fixup_rv", s);
+        k_fixup_net<<<ceil_div_u(n_cols, FN_COLS), FN_COLS, 0, s>>>(cp, n_cols, reinterpret_cast<const RowVal *>(slots),
+                                                                    trow, tval, status);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    {
+        KernelScope ks("col_overflow_rv", s);
+        k_ov_place_rv<<<(unsigned)sm_count() * 2u, 256, 0, s>>>(cp, n_cols, val, ov, ov_cap, n_ov, trow, tval);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const int32_t *long_count = long_list - 1;
+    KernelScope ks("col_fixup_long_rv", s);
+    k_fixup_long_rv<<<(unsigned)sm_count() * 2u, FIX_THREADS, 0, s>>>(cp, long_list, long_count, trow, tval, status);
+    return cudaGetLastError();
+}
+
 }  // namespace spmvat
+

@@ -282,20 +282,99 @@ def test_coo_row_schedules(monkeypatch, entry_tiles):
         M.close()
 
 
-@pytest.mark.parametrize("name", ["stencil27_24", "powerlaw_60k", "random_duplicates", "dense_column", "wide",
-                                  "tall", "all_empty", "one_by_one"])
-def test_phase1_count_scatter_path_bit_exact(monkeypatch, name):
-    """The count-then-scatter path of Phase I (used when columns are short on
-    average) gives the same CCS as the slot path and the oracle."""
-    L = lib()
-    monkeypatch.setenv("SPMVAT_PHASE1_SCATTER", "1")
-    H = case(name)
+def _ccs_matches_oracle(M, H):
     irp_t, icol_t, val_t, _ = oracle.crs_to_ccs(H.n_rows, H.n_cols, H.irp, H.icol, H.val)
-    M = L.spmv_transform(dev(H), L.SPMV_CRS, L.SPMV_COLWISE)
     arr = M.arrays()
     assert np.array_equal(arr["ptr"].cpu().numpy(), irp_t)
     assert np.array_equal(arr["idx"].cpu().numpy(), icol_t)
     assert np.array_equal(bits(arr["val"].cpu().numpy()), bits(val_t))
+
+
+def _claims(L, H):
+    """Builds the CCS of H with the kernel profile on; returns the handle and
+    how many claim passes ran (2 = the row-value path handed over to the
+    (k, row) slot path)."""
+    L.spmv_profile_enable(True)
+    L.spmv_profile_read(reset=True)
+    try:
+        M = L.spmv_transform(dev(H), L.SPMV_CRS, L.SPMV_COLWISE)
+        prof = L.spmv_profile_read(reset=True)
+    finally:
+        L.spmv_profile_enable(False)
+    return M, prof.get("col_claim_rv", (0, 0.0))[0] + prof.get("col_claim", (0, 0.0))[0]
+
+
+def shuffled_rows(H, seed=3):
+    """The same matrix with each row's entries in a seeded random order (no
+    repeated (i, j)): the serial scatter still lists every column's rows in
+    ascending order."""
+    icol, val = H.icol.copy(), H.val.copy()
+    rng = np.random.default_rng(seed)
+    for i in range(H.n_rows):
+        a, b = int(H.irp[i]), int(H.irp[i + 1])
+        p = rng.permutation(b - a) + a
+        icol[a:b], val[a:b] = H.icol[p], H.val[p]
+    return synth.CRS(H.n_rows, H.n_cols, H.irp.copy(), icol, val)
+
+
+def with_extra_columns(n, mean_len, seed, every):
+    """Random rows plus, for each (column, period) in `every`, that column in
+    every period-th row."""
+    base = synth.random_crs(n, n, mean_len, seed=seed)
+    rows = []
+    for i in range(n):
+        c = set(base.icol[base.irp[i]:base.irp[i + 1]].tolist())
+        for col, period in every:
+            if i % period == 0:
+                c.add(col)
+        rows.append(sorted(c))
+    irp = np.zeros(n + 1, np.int64)
+    irp[1:] = np.cumsum([len(r) for r in rows])
+    icol = np.concatenate([np.array(r, np.int32) for r in rows])
+    return synth.CRS(n, n, irp.astype(np.int32), icol, synth.normal(seed, 5, np.arange(icol.size)))
+
+
+@pytest.mark.parametrize("mode", ["scatter", "kslot", "rv"])
+@pytest.mark.parametrize("name", ["stencil27_24", "powerlaw_60k", "random_duplicates", "dense_column", "wide",
+                                  "tall", "all_empty", "one_by_one", "laplace37x23"])
+def test_phase1_paths_bit_exact(monkeypatch, mode, name):
+    """Every Phase I path (count + scatter; (k, row) slots; (row, value)
+    slots, which hands over to the (k, row) slots on repeated entries or
+    columns over 4096) gives the oracle's CCS bit for bit."""
+    L = lib()
+    monkeypatch.setenv("SPMVAT_PHASE1", mode)
+    H = case(name)
+    M = L.spmv_transform(dev(H), L.SPMV_CRS, L.SPMV_COLWISE)
+    _ccs_matches_oracle(M, H)
+    M.close()
+
+
+def test_phase1_row_value_path_on_shuffled_rows():
+    """Columns in arbitrary order within rows: the row-value path orders every
+    column by row (warp networks and the long-column sort both run)."""
+    L = lib()
+    H = shuffled_rows(with_extra_columns(3000, 12, 81, [(5, 3), (9, 40)]))
+    M, claims = _claims(L, H)
+    assert claims == 1
+    _ccs_matches_oracle(M, H)
+    M.close()
+
+
+@pytest.mark.parametrize("kind", ["duplicates", "column_over_4096", "many_beyond_slots"])
+def test_phase1_row_value_path_hands_over(kind):
+    """Matrices the row-value slot path does not cover are rebuilt on the
+    (k, row) slot path, and the result is still the serial CCS."""
+    L = lib()
+    if kind == "duplicates":
+        H = synth.random_crs(3001, 2999, 12, seed=82, dup=True)
+    elif kind == "column_over_4096":
+        H = with_extra_columns(6000, 10, 83, [(7, 1)])
+    else:
+        H = with_extra_columns(4000, 10, 84, [(c, 4) for c in range(200)])
+    assert 32 * H.n_cols <= 4 * H.nnz  # a slot path is taken
+    M, claims = _claims(L, H)
+    assert claims == 2
+    _ccs_matches_oracle(M, H)
     M.close()
 
 
@@ -304,24 +383,9 @@ def test_phase1_slot_path_with_long_columns():
     matrix dense enough per column for the slot path."""
     L = lib()
     n = 3000
-    base = synth.random_crs(n, n, 12, seed=71)
-    rows = []
-    for i in range(n):
-        c = set(base.icol[base.irp[i]:base.irp[i + 1]].tolist())
-        if i % 3 == 0:
-            c.add(5)        # column 5: 1000 entries
-        if i % 40 == 0:
-            c.add(9)        # column 9: 75 entries
-        rows.append(sorted(c))
-    irp = np.zeros(n + 1, np.int64)
-    irp[1:] = np.cumsum([len(r) for r in rows])
-    icol = np.concatenate([np.array(r, np.int32) for r in rows])
-    H = synth.CRS(n, n, irp.astype(np.int32), icol, synth.normal(71, 5, np.arange(icol.size)))
+    H = with_extra_columns(n, 12, 71, [(5, 3), (9, 40)])  # column 5: 1000 entries, column 9: 75
     assert 32 * n <= 4 * H.nnz  # the slot path is taken
-    irp_t, icol_t, val_t, _ = oracle.crs_to_ccs(H.n_rows, H.n_cols, H.irp, H.icol, H.val)
-    M = L.spmv_transform(dev(H), L.SPMV_CRS, L.SPMV_COLWISE)
-    arr = M.arrays()
-    assert np.array_equal(arr["ptr"].cpu().numpy(), irp_t)
-    assert np.array_equal(arr["idx"].cpu().numpy(), icol_t)
-    assert np.array_equal(bits(arr["val"].cpu().numpy()), bits(val_t))
+    M, claims = _claims(L, H)
+    assert claims == 1  # the row-value path covers columns of up to 4096 entries
+    _ccs_matches_oracle(M, H)
     M.close()
