@@ -129,6 +129,7 @@ def kernel_bytes(name: str, bm: dict, n_rows: int, n_cols: int, nnz: int):
         # row-value slot path (the default for >= 8 entries per column): ICOL +
         # VAL in, one 16-byte {row, value} slot out; slots in, ICOL_T + VAL_T out
         "col_claim_rv": 28 * nnz + 4 * (n_rows + 1) + 4 * n_cols,
+        "coo_col_tile_bounds": 8 * (n_cols // 128 + 1),
         "col_fixup_rv": 28 * nnz + 4 * (n_cols + 1),
         "col_overflow_rv": 0,
         "col_fixup_long_rv": 0,
@@ -138,6 +139,8 @@ def kernel_bytes(name: str, bm: dict, n_rows: int, n_cols: int, nnz: int):
         return bm["spmv_crs"]
     if name.startswith("spmv_coo_row_rows"):
         return bm["spmv_coo_row"]
+    if name.startswith("spmv_coo_col_cols"):
+        return bm["spmv_coo_col"]
     if name == "coo_row_tile_bounds":
         return 8 * (n_rows // 128 + 1)
     return table.get(name)

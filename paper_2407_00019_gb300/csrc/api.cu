@@ -38,6 +38,10 @@ cudaMemPool_t pool_for(int dev) {
         if (cudaMemPoolCreate(&p, &props) != cudaSuccess) { cudaGetLastError(); return nullptr; }
         unsigned long long keep = ULLONG_MAX;  // keep freed blocks for reuse
         cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        // never make one stream wait for another to reuse a block: callers
+        // run independent transformations on several streams at once
+        int no = 0;
+        cudaMemPoolSetAttribute(p, cudaMemPoolReuseAllowInternalDependencies, &no);
         g_pools[dev] = p;
     }
     return g_pools[dev];
@@ -147,7 +151,7 @@ struct spmv_matrix {
     // CRS schedule
     int crs_binned = 0;
     int crs_v = 1;
-    int coo_rows_split = 0;        // > 0: COO-Row over row-aligned tiles, threads per row
+    int coo_rows_split = 0;        // > 0: COO over row- (column-) aligned tiles, threads per line
     int coo_rows_cap = 0;          //      shared-memory entries per tile
     const int32_t *coo_tb = nullptr; //    tile bounds
     int crs_rows_split = 0;        // > 0: ELL-order row-tile kernel, threads per row
@@ -605,6 +609,19 @@ spmv_status coo_col_from_ccs(const spmv_matrix *src, uint64_t cap, spmv_matrix *
     M->colmax = src->colmax;
     M->bufs = src->ccs_bufs;
     M->bufs.push_back(tcol);
+    // SpMV schedule: 128-column tiles when a tile of the longest columns fits
+    // shared memory (bounded by the longest column, known here: no sync)
+    const int tcap = coo_rows_cap((int)std::min<int64_t>((int64_t)128 * src->colmax, (int64_t)(INT_MAX / 32)));
+    if (src->nnz > 0 && tcap > 0 && !getenv("SPMVAT_COO_ENTRY_TILES")) {
+        const int64_t tiles = ((int64_t)src->n_cols + 127) / 128;
+        BufPtr tb;
+        CKS(alloc_buf((size_t)(tiles + 1) * 4, s, &tb));
+        CK(launch_col_tile_bounds(src->ptr, src->n_cols, reinterpret_cast<int32_t *>(tb->p), nullptr, s));
+        M->coo_rows_cap = tcap;
+        M->coo_rows_split = ((double)src->nnz / src->n_cols <= 8.0) ? 2 : 4;
+        M->coo_tb = reinterpret_cast<const int32_t *>(tb->p);
+        M->bufs.push_back(tb);
+    }
     *out = M.release();
     return SPMV_OK;
 }
@@ -656,6 +673,11 @@ spmv_status apply_core(const spmv_matrix *M, const double *x, double *y, cudaStr
                 CK(launch_spmv_ccs(M->ptr, M->idx, M->val, M->n_rows, M->n_cols, x, y, s));
                 return SPMV_OK;
             case SPMV_COO:
+                if (M->coo_rows_split > 0) {
+                    CK(launch_spmv_coo_col_cols(M->coo_rows_split, M->coo_rows_cap, M->idx, M->idx2, M->val,
+                                                M->coo_tb, M->n_rows, M->n_cols, x, y, s));
+                    return SPMV_OK;
+                }
                 CK(launch_spmv_coo_col(M->idx, M->idx2, M->val, M->nnz, M->n_rows, x, y, s));
                 return SPMV_OK;
             case SPMV_ELL:

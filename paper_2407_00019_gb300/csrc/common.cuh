@@ -236,6 +236,12 @@ int coo_rows_cap(int max_n);
 cudaError_t launch_spmv_coo_row_rows(int split, int cap, const int32_t *irow, const int32_t *icol,
                                      const double *val, const int32_t *tb, int32_t n_rows, int32_t n_cols,
                                      const double *x, double *y, cudaStream_t s);
+// COO-Column over 128-column tiles (tb from launch_col_tile_bounds; cap from
+// coo_rows_cap of the largest tile); zeroes y first.
+cudaError_t launch_col_tile_bounds(const int32_t *ptr, int32_t n_cols, int32_t *tb, int32_t *maxn, cudaStream_t s);
+cudaError_t launch_spmv_coo_col_cols(int split, int cap, const int32_t *trow, const int32_t *tcol, const double *tval,
+                                     const int32_t *tb, int32_t n_rows, int32_t n_cols, const double *x, double *y,
+                                     cudaStream_t s);
 cudaError_t launch_spmv_coo_col(const int32_t *row, const int32_t *col, const double *val, int64_t nnz,
                                 int32_t n_rows, const double *x, double *y, cudaStream_t s);
 cudaError_t launch_spmv_ccs(const int32_t *cp, const int32_t *trow, const double *tval, int32_t n_rows,

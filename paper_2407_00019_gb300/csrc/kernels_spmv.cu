@@ -1012,6 +1012,128 @@ __global__ void __launch_bounds__(256) k_spmv_coo_col(const int32_t *__restrict_
     }
 }
 
+// COO-Column over column-aligned tiles: a CTA takes 128 consecutive columns,
+// stages their entries (TROW, TCOL, TVAL) in shared memory with coalesced
+// loads, finds each column's first entry by binary search over the staged
+// TCOL, and SPLIT threads per column add VAL * x[col] into y[row] with lanes
+// on consecutive columns. Lanes then hold the m-th entries of neighbouring
+// columns, which in banded matrices lie in neighbouring rows, so the 32
+// atomic adds of a warp instruction fall into a few sectors of y instead of
+// 32. `tb` are the tiles' first entries (tile t starts at column 128 t).
+template <int SPLIT>
+__global__ void __launch_bounds__(COO_ROWS_R *SPLIT) k_coo_col_cols(const int32_t *__restrict__ trow,
+                                                                     const int32_t *__restrict__ tcol,
+                                                                     const double *__restrict__ tval,
+                                                                     const int32_t *__restrict__ tb,
+                                                                     int32_t n_rows, int32_t n_cols, int cap,
+                                                                     const double *__restrict__ x,
+                                                                     double *__restrict__ y) {
+    constexpr int R = COO_ROWS_R;
+    constexpr int T = R * SPLIT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *s_v = reinterpret_cast<double *>(smem);
+    int32_t *s_c = reinterpret_cast<int32_t *>(s_v + cap);
+    int32_t *s_r = s_c + cap;
+    __shared__ int32_t s_ptr[R + 1];
+    const long long c0 = (long long)blockIdx.x * R;
+    const int nc = (int)min((long long)R, (long long)n_cols - c0);
+    const int e0 = __ldg(tb + blockIdx.x), e1 = __ldg(tb + blockIdx.x + 1);
+    const int n = e1 - e0;  // <= cap by construction of the schedule
+    for (int q0 = threadIdx.x; q0 < n; q0 += 8 * T) {
+        double v[8];
+        int c[8], r[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u * T;
+            v[u] = (q < n) ? __ldcs(tval + e0 + q) : 0.0;
+            c[u] = (q < n) ? __ldcs(tcol + e0 + q) : 0;
+            r[u] = (q < n) ? __ldcs(trow + e0 + q) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u * T;
+            if (q < n) {
+                const bool ok = (unsigned)r[u] < (unsigned)n_rows;
+                s_v[q] = ok ? v[u] : 0.0;
+                s_c[q] = c[u];
+                s_r[q] = ok ? r[u] : 0;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_ptr[nc] = n;  // every staged entry belongs to a column below c0 + nc
+    if (threadIdx.x < (unsigned)nc) {  // first entry of column c0 + i: lower bound in the staged TCOL
+        const long long key = c0 + threadIdx.x;
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((long long)s_c[mid] < key) lo = mid + 1; else hi = mid;
+        }
+        s_ptr[threadIdx.x] = lo;
+    }
+    __syncthreads();
+    const int j = threadIdx.x % R, part = threadIdx.x / R;
+    if (j >= nc) return;
+    const int st = s_ptr[j], en = s_ptr[j + 1];
+    if (st >= en) return;
+    const double xj = __ldg(x + c0 + j);
+    int k = st + part;
+    for (; k + 3 * SPLIT < en; k += 4 * SPLIT) {
+        const int r0 = s_r[k], r1 = s_r[k + SPLIT], r2 = s_r[k + 2 * SPLIT], r3 = s_r[k + 3 * SPLIT];
+        atomicAdd(y + r0, s_v[k] * xj);
+        atomicAdd(y + r1, s_v[k + SPLIT] * xj);
+        atomicAdd(y + r2, s_v[k + 2 * SPLIT] * xj);
+        atomicAdd(y + r3, s_v[k + 3 * SPLIT] * xj);
+    }
+    for (; k < en; k += SPLIT) atomicAdd(y + s_r[k], s_v[k] * xj);
+}
+
+// Tile bounds of the column-aligned schedule: tb[t] = ptr[min(128 t, n_cols)],
+// and the largest tile's entry count into *maxn.
+__global__ void __launch_bounds__(256) k_col_tile_bounds(const int32_t *__restrict__ ptr, int32_t n_cols,
+                                                          long long n_tiles, int32_t *__restrict__ tb,
+                                                          int32_t *__restrict__ maxn) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > n_tiles) return;
+    const int a = __ldg(ptr + min(t * COO_ROWS_R, (long long)n_cols));
+    tb[t] = a;
+    if (maxn && t < n_tiles) atomicMax(maxn, __ldg(ptr + min((t + 1) * COO_ROWS_R, (long long)n_cols)) - a);
+}
+
+cudaError_t launch_col_tile_bounds(const int32_t *ptr, int32_t n_cols, int32_t *tb, int32_t *maxn, cudaStream_t s) {
+    const long long n_tiles = ((long long)n_cols + COO_ROWS_R - 1) / COO_ROWS_R;
+    KernelScope ks("coo_col_tile_bounds", s);
+    k_col_tile_bounds<<<ceil_div_u(n_tiles + 1, 256), 256, 0, s>>>(ptr, n_cols, n_tiles, tb, maxn);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmv_coo_col_cols(int split, int cap, const int32_t *trow, const int32_t *tcol, const double *tval,
+                                     const int32_t *tb, int32_t n_rows, int32_t n_cols, const double *x, double *y,
+                                     cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(y, 0, sizeof(double) * (size_t)n_rows, s);
+    if (e != cudaSuccess || n_cols <= 0) return e;
+    if (cap <= 0) return cudaErrorInvalidValue;
+    const unsigned grid = ceil_div_u(n_cols, COO_ROWS_R);
+    const size_t smem = (size_t)cap * 16;
+    switch (split) {
+#define COOC_CASE(SP)                                                                                           \
+    case SP: {                                                                                                  \
+        e = set_smem_attr(k_coo_col_cols<SP>, smem);                                                            \
+        if (e != cudaSuccess) return e;                                                                         \
+        KernelScope ks("spmv_coo_col_cols_p" #SP, s);                                                           \
+        k_coo_col_cols<SP><<<grid, COO_ROWS_R * SP, smem, s>>>(trow, tcol, tval, tb, n_rows, n_cols, cap, x, y); \
+        break;                                                                                                  \
+    }
+        COOC_CASE(1)
+        COOC_CASE(2)
+        COOC_CASE(4)
+#undef COOC_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_spmv_coo_col(const int32_t *row, const int32_t *col, const double *val, int64_t nnz,
                                 int32_t n_rows, const double *x, double *y, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(y, 0, sizeof(double) * (size_t)n_rows, s);

@@ -282,6 +282,28 @@ def test_coo_row_schedules(monkeypatch, entry_tiles):
         M.close()
 
 
+@pytest.mark.parametrize("entry_tiles", [False, True])
+def test_coo_col_schedules(monkeypatch, entry_tiles):
+    """Column-aligned tiles (lanes on consecutive columns) and the flat entry
+    kernel agree with the oracle; a 9000-entry column exceeds the tile
+    capacity and takes the flat kernel either way."""
+    import torch
+    L = lib()
+    if entry_tiles:
+        monkeypatch.setenv("SPMVAT_COO_ENTRY_TILES", "1")
+    for name in ("laplace37x23", "stencil27_24", "random_empty_rows", "wide", "tall", "dense_column", "all_empty",
+                 "powerlaw_60k"):
+        H = case(name)
+        xh = xvec(H.n_cols, seed=9)
+        C = L.spmv_transform(dev(H), L.SPMV_CRS, L.SPMV_COLWISE)
+        M = L.spmv_transform_from(C, L.SPMV_COO)
+        C.close()
+        for rep in range(2):
+            assert_spmv_close(run_apply(M, torch.from_numpy(xh).cuda(), H.n_rows), H, xh,
+                              what=f"{name}/entry_tiles={entry_tiles}/{rep}")
+        M.close()
+
+
 def _ccs_matches_oracle(M, H):
     irp_t, icol_t, val_t, _ = oracle.crs_to_ccs(H.n_rows, H.n_cols, H.irp, H.icol, H.val)
     arr = M.arrays()
