@@ -353,9 +353,13 @@ spmv_status build_coo_row(const spmv_crs *A, uint64_t cap, spmv_matrix **out, cu
     if (cap && need > cap) return SPMV_ERR_MEMORY_CAP;
     std::unique_ptr<spmv_matrix> M(new_handle(A, SPMV_COO, SPMV_ROWWISE, s));
     if (!M) return SPMV_ERR_OOM;
-    BufPtr irow, scr;
+    BufPtr irow, scr, acc_buf;
     CKS(alloc_buf(need, s, &irow));
     CKS(alloc_buf(expand_scratch_bytes(A->nnz), s, &scr));
+    // IRP checks (the transformation reads no column index), read at the sync below
+    CKS(alloc_buf(sizeof(AnalyzeAcc), s, &acc_buf));
+    CK(cudaMemsetAsync(acc_buf->p, 0, sizeof(AnalyzeAcc), s));
+    CK(launch_analyze(A->irp, A->n_rows, A->nnz, reinterpret_cast<AnalyzeAcc *>(acc_buf->p), s));
     CK(launch_expand(A->irp, A->n_rows, A->nnz, reinterpret_cast<int32_t *>(irow->p),
                      reinterpret_cast<int32_t *>(scr->p), s, "crs_to_coo_row"));
     BufPtr sw;
@@ -363,17 +367,25 @@ spmv_status build_coo_row(const spmv_crs *A, uint64_t cap, spmv_matrix **out, cu
     CK(cudaMemsetAsync(sw->p, 0, 16, s));
     M->status = reinterpret_cast<int *>(sw->p);
     M->bufs.push_back(sw);
+    int hirp = 0;
+    CK(cudaMemcpyAsync(&hirp, &reinterpret_cast<AnalyzeAcc *>(acc_buf->p)->status, sizeof(int),
+                       cudaMemcpyDeviceToHost, s));
+    if (A->nnz <= 0) {
+        CK(cudaStreamSynchronize(s));
+        CKS(status_from_dev(hirp));
+    }
     // SpMV schedule: row-aligned tiles when the largest tile fits shared memory
     if (A->nnz > 0) {
         const int64_t tiles = ((int64_t)A->n_rows + 127) / 128;
         BufPtr tb;
         CKS(alloc_buf((size_t)(tiles + 1) * 4, s, &tb));
         int32_t *maxn = reinterpret_cast<int32_t *>(sw->p) + 1;  // second word of the status block
-        CK(launch_row_tile_bounds(reinterpret_cast<const int32_t *>(irow->p), A->nnz, A->n_rows,
-                                  reinterpret_cast<int32_t *>(tb->p), maxn, s));
+        CK(launch_line_tile_bounds(A->irp, A->n_rows, A->nnz, reinterpret_cast<int32_t *>(tb->p), maxn,
+                                   "coo_row_tile_bounds", s));
         int h[2] = {0, 0};
         CK(cudaMemcpyAsync(h, sw->p, sizeof(h), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        CKS(status_from_dev(hirp));
         const int cap = coo_rows_cap(h[1]);
         if (cap > 0 && !getenv("SPMVAT_COO_ENTRY_TILES")) {
             M->coo_rows_cap = cap;
@@ -616,7 +628,8 @@ spmv_status coo_col_from_ccs(const spmv_matrix *src, uint64_t cap, spmv_matrix *
         const int64_t tiles = ((int64_t)src->n_cols + 127) / 128;
         BufPtr tb;
         CKS(alloc_buf((size_t)(tiles + 1) * 4, s, &tb));
-        CK(launch_col_tile_bounds(src->ptr, src->n_cols, reinterpret_cast<int32_t *>(tb->p), nullptr, s));
+        CK(launch_line_tile_bounds(src->ptr, src->n_cols, src->nnz, reinterpret_cast<int32_t *>(tb->p), nullptr,
+                                   "coo_col_tile_bounds", s));
         M->coo_rows_cap = tcap;
         M->coo_rows_split = ((double)src->nnz / src->n_cols <= 8.0) ? 2 : 4;
         M->coo_tb = reinterpret_cast<const int32_t *>(tb->p);

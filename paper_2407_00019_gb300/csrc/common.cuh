@@ -229,16 +229,15 @@ size_t coo_row_scratch_bytes(int64_t nnz);
 cudaError_t launch_spmv_coo_row(const int32_t *irow, const int32_t *icol, const double *val, int64_t nnz,
                                 int32_t n_rows, int32_t n_cols, const double *x, double *y, void *scratch,
                                 int *status, cudaStream_t s);
-// row-aligned COO-Row: tile bounds (int32[ceil(n_rows/128) + 1]) and largest tile
-cudaError_t launch_row_tile_bounds(const int32_t *irow, int64_t nnz, int32_t n_rows, int32_t *tb, int32_t *maxn,
-                                   cudaStream_t s);
+// line-aligned COO: tile bounds (int32[ceil(n_lines/128) + 1]) from the line pointers, largest tile
+cudaError_t launch_line_tile_bounds(const int32_t *ptr, int32_t n_lines, int64_t nnz, int32_t *tb, int32_t *maxn,
+                                    const char *name, cudaStream_t s);
 int coo_rows_cap(int max_n);
 cudaError_t launch_spmv_coo_row_rows(int split, int cap, const int32_t *irow, const int32_t *icol,
                                      const double *val, const int32_t *tb, int32_t n_rows, int32_t n_cols,
                                      const double *x, double *y, cudaStream_t s);
-// COO-Column over 128-column tiles (tb from launch_col_tile_bounds; cap from
+// COO-Column over 128-column tiles (tb from launch_line_tile_bounds; cap from
 // coo_rows_cap of the largest tile); zeroes y first.
-cudaError_t launch_col_tile_bounds(const int32_t *ptr, int32_t n_cols, int32_t *tb, int32_t *maxn, cudaStream_t s);
 cudaError_t launch_spmv_coo_col_cols(int split, int cap, const int32_t *trow, const int32_t *tcol, const double *tval,
                                      const int32_t *tb, int32_t n_rows, int32_t n_cols, const double *x, double *y,
                                      cudaStream_t s);

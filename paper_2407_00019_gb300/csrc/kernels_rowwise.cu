@@ -29,40 +29,47 @@ __global__ void __launch_bounds__(AN_THREADS) k_analyze(const int32_t *__restric
     __shared__ int s_mm[AN_THREADS / 32][3];
     if (threadIdx.x < 32) s_hist[threadIdx.x] = 0ull;
     __syncthreads();
-    const long long i0 = ((long long)blockIdx.x * AN_THREADS + threadIdx.x) * AN_ITEMS;
-    int p[AN_ITEMS + 1];
-    if (i0 + AN_ITEMS <= n && ((reinterpret_cast<uintptr_t>(irp + i0) & 15) == 0)) {
-        const int4 q = *reinterpret_cast<const int4 *>(irp + i0);
-        p[0] = q.x; p[1] = q.y; p[2] = q.z; p[3] = q.w;
-        p[4] = irp[i0 + 4];
-    } else {
-#pragma unroll
-        for (int j = 0; j <= AN_ITEMS; ++j) p[j] = (i0 + j <= n) ? irp[i0 + j] : 0;
-    }
     unsigned long long sl = 0, sl2 = 0, ne = 0;
     int mx = 0, inv_mn = 0, bad = 0;
-    const unsigned lane = lane_id();
+    {
+        const long long i0 = ((long long)blockIdx.x * AN_THREADS + threadIdx.x) * AN_ITEMS;
+        int p[AN_ITEMS + 1];
+        if (i0 + AN_ITEMS <= n && ((reinterpret_cast<uintptr_t>(irp + i0) & 15) == 0)) {
+            const int4 q = *reinterpret_cast<const int4 *>(irp + i0);
+            p[0] = q.x; p[1] = q.y; p[2] = q.z; p[3] = q.w;
+            p[4] = irp[i0 + 4];
+        } else {
 #pragma unroll
-    for (int j = 0; j < AN_ITEMS; ++j) {
-        const long long i = i0 + j;
-        const bool has = i < n;
-        int len = 0;
-        if (has) {
-            len = p[j + 1] - p[j];
-            if (len < 0 || p[j] < 0 || (long long)p[j + 1] > nnz) { bad = 1; len = len < 0 ? 0 : len; }
-            if (i == 0 && p[0] != 0) bad = 1;
-            if (i == n - 1 && (long long)p[j + 1] != nnz) bad = 1;
-            sl += (unsigned)len;
-            sl2 += (unsigned long long)len * (unsigned long long)len;
-            ne += (len == 0);
-            mx = max(mx, len);
-            inv_mn = max(inv_mn, INT_MAX - len);
+            for (int j = 0; j <= AN_ITEMS; ++j) p[j] = (i0 + j <= n) ? irp[i0 + j] : 0;
         }
-        const int cls = has ? ((len == 0) ? 0 : 32 - __clz(len)) : 32;
-        const unsigned peers = __match_any_sync(0xffffffffu, cls);
-        if (has && (lanemask_lt() & peers) == 0) atomicAdd(&s_hist[cls], (unsigned long long)__popc(peers));
+#pragma unroll
+        for (int j = 0; j < AN_ITEMS; ++j) {
+            const long long i = i0 + j;
+            const bool has = i < n;
+            int len = 0;
+            if (has) {
+                len = p[j + 1] - p[j];
+                if (len < 0 || p[j] < 0 || (long long)p[j + 1] > nnz) { bad = 1; len = len < 0 ? 0 : len; }
+                if (i == 0 && p[0] != 0) bad = 1;
+                if (i == n - 1 && (long long)p[j + 1] != nnz) bad = 1;
+                sl += (unsigned)len;
+                sl2 += (unsigned long long)len * (unsigned long long)len;
+                ne += (len == 0);
+                mx = max(mx, len);
+                inv_mn = max(inv_mn, INT_MAX - len);
+            }
+            // length class histogram: one round per distinct class in the
+            // warp (regular matrices have one or two)
+            const int cls = has ? ((len == 0) ? 0 : 32 - __clz(len)) : 32;
+            unsigned todo = __ballot_sync(0xffffffffu, has);
+            while (todo) {
+                const int c = __shfl_sync(0xffffffffu, cls, __ffs(todo) - 1);
+                const unsigned m = __ballot_sync(0xffffffffu, has && cls == c);
+                if ((int)lane_id() == __ffs(todo) - 1) atomicAdd(&s_hist[c], (unsigned long long)__popc(m));
+                todo &= ~m;
+            }
+        }
     }
-    (void)lane;
     sl = warp_sum(sl);
     sl2 = warp_sum(sl2);
     ne = warp_sum(ne);
@@ -121,13 +128,18 @@ cudaError_t launch_validate_idx(const int32_t *idx, int64_t n, int32_t bound, in
 }
 
 // ------------------------------------------------------------- tile lines
-// out[t] = the line holding entry t*tile (largest i with ptr[i] <= t*tile),
-// one thread per tile: the searches run in parallel instead of serially at
-// the start of every CTA of the consumer.
-__global__ void __launch_bounds__(256) k_tile_lines(const int32_t *__restrict__ ptr, int32_t n_lines, int tile,
+// out[t] = the line holding entry t*tile (the largest i with ptr[i] <= t*tile,
+// which is the non-empty line containing that entry). One thread per line
+// writes the tiles whose first entry falls inside it: one coalesced pass over
+// ptr instead of a binary search per tile.
+__global__ void __launch_bounds__(256) k_tile_lines(const int32_t *__restrict__ ptr, int32_t n_lines, int shift,
                                                      long long n_tiles, int32_t *__restrict__ out) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n_tiles) out[t] = last_le(ptr, 0, n_lines, t * (long long)tile);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_lines) return;
+    const int a = max(__ldg(ptr + i), 0), b = __ldg(ptr + i + 1);
+    const unsigned tile = 1u << shift;
+    for (unsigned t = ((unsigned)a + tile - 1u) >> shift; (long long)t << shift < (long long)b && t < n_tiles; ++t)
+        out[t] = i;
 }
 
 size_t tile_lines_bytes(int64_t nnz, int tile) { return (size_t)((nnz + tile - 1) / tile + 1) * 4; }
@@ -136,8 +148,15 @@ cudaError_t launch_tile_lines(const int32_t *ptr, int32_t n_lines, int64_t nnz, 
                               cudaStream_t s) {
     const long long n_tiles = (nnz + tile - 1) / tile;
     if (n_tiles <= 0) return cudaSuccess;
+    // zero first: with a malformed ptr some tiles would get no writer, and
+    // every consumer indexes ptr with these values
+    cudaError_t e = cudaMemsetAsync(out, 0, (size_t)n_tiles * sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    int shift = 0;
+    while ((1 << shift) < tile) ++shift;
+    if ((1 << shift) != tile) return cudaErrorInvalidValue;  // tiles are powers of two
     KernelScope ks("tile_lines", s);
-    k_tile_lines<<<ceil_div_u(n_tiles, 256), 256, 0, s>>>(ptr, n_lines, tile, n_tiles, out);
+    k_tile_lines<<<ceil_div_u(n_lines, 256), 256, 0, s>>>(ptr, n_lines, shift, n_tiles, out);
     return cudaGetLastError();
 }
 

@@ -793,42 +793,30 @@ __global__ void __launch_bounds__(COO_THREADS) k_coo_row_tiles(const int32_t *__
     }
 }
 
-// ---- COO-Row over row-aligned tiles --------------------------------------
-// tb[t] = first entry of row t*R in the row-sorted IROW (one parallel
-// binary search per tile); *maxn = the largest tile's entry count.
-__global__ void __launch_bounds__(256) k_row_tile_bounds(const int32_t *__restrict__ irow, int64_t nnz, int R,
-                                                          long long n_tiles, int32_t *__restrict__ tb,
-                                                          int32_t *__restrict__ maxn) {
+// ---- COO over line-aligned tiles -----------------------------------------
+// Tile bounds of the 128-line schedules of COO-Row and COO-Column: tb[t] =
+// ptr[min(128 t, n_lines)], the first entry of line 128 t in the line-sorted
+// COO (ptr: the pointers of the compressed format the COO is made from), and
+// the largest tile's entry count into *maxn when given. Bounds are clamped to
+// [0, nnz], so the products stay in bounds even on malformed pointers.
+__global__ void __launch_bounds__(256) k_line_tile_bounds(const int32_t *__restrict__ ptr, int32_t n_lines,
+                                                           int64_t nnz, long long n_tiles, int32_t *__restrict__ tb,
+                                                           int32_t *__restrict__ maxn) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t > n_tiles) return;
-    long long lo = 0, hi = nnz;  // first index with irow >= t*R
-    const long long key = t * R;
-    if (t == n_tiles) {
-        lo = nnz;
-    } else {
-        while (lo < hi) {
-            const long long mid = (lo + hi) >> 1;
-            if ((long long)__ldg(irow + mid) < key) lo = mid + 1; else hi = mid;
-        }
-    }
-    tb[t] = (int32_t)lo;
-    // the tile size needs the next bound: search for it too
-    if (t < n_tiles) {
-        long long lo2 = lo, hi2 = nnz;
-        const long long key2 = (t + 1) * R;
-        while (lo2 < hi2) {
-            const long long mid = (lo2 + hi2) >> 1;
-            if ((long long)__ldg(irow + mid) < key2) lo2 = mid + 1; else hi2 = mid;
-        }
-        atomicMax(maxn, (int32_t)(lo2 - lo));
-    }
+    const auto bound = [&](long long u) {
+        return (int32_t)min(max((long long)__ldg(ptr + min(u * COO_ROWS_R, (long long)n_lines)), 0ll), (long long)nnz);
+    };
+    const int32_t a = bound(t);
+    tb[t] = a;
+    if (maxn && t < n_tiles) atomicMax(maxn, bound(t + 1) - a);
 }
 
-cudaError_t launch_row_tile_bounds(const int32_t *irow, int64_t nnz, int32_t n_rows, int32_t *tb, int32_t *maxn,
-                                   cudaStream_t s) {
-    const long long n_tiles = ((long long)n_rows + COO_ROWS_R - 1) / COO_ROWS_R;
-    KernelScope ks("coo_row_tile_bounds", s);
-    k_row_tile_bounds<<<ceil_div_u(n_tiles + 1, 256), 256, 0, s>>>(irow, nnz, COO_ROWS_R, n_tiles, tb, maxn);
+cudaError_t launch_line_tile_bounds(const int32_t *ptr, int32_t n_lines, int64_t nnz, int32_t *tb, int32_t *maxn,
+                                    const char *name, cudaStream_t s) {
+    const long long n_tiles = ((long long)n_lines + COO_ROWS_R - 1) / COO_ROWS_R;
+    KernelScope ks(name, s);
+    k_line_tile_bounds<<<ceil_div_u(n_tiles + 1, 256), 256, 0, s>>>(ptr, n_lines, nnz, n_tiles, tb, maxn);
     return cudaGetLastError();
 }
 
@@ -1086,25 +1074,6 @@ __global__ void __launch_bounds__(COO_ROWS_R *SPLIT) k_coo_col_cols(const int32_
         atomicAdd(y + r3, s_v[k + 3 * SPLIT] * xj);
     }
     for (; k < en; k += SPLIT) atomicAdd(y + s_r[k], s_v[k] * xj);
-}
-
-// Tile bounds of the column-aligned schedule: tb[t] = ptr[min(128 t, n_cols)],
-// and the largest tile's entry count into *maxn.
-__global__ void __launch_bounds__(256) k_col_tile_bounds(const int32_t *__restrict__ ptr, int32_t n_cols,
-                                                          long long n_tiles, int32_t *__restrict__ tb,
-                                                          int32_t *__restrict__ maxn) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t > n_tiles) return;
-    const int a = __ldg(ptr + min(t * COO_ROWS_R, (long long)n_cols));
-    tb[t] = a;
-    if (maxn && t < n_tiles) atomicMax(maxn, __ldg(ptr + min((t + 1) * COO_ROWS_R, (long long)n_cols)) - a);
-}
-
-cudaError_t launch_col_tile_bounds(const int32_t *ptr, int32_t n_cols, int32_t *tb, int32_t *maxn, cudaStream_t s) {
-    const long long n_tiles = ((long long)n_cols + COO_ROWS_R - 1) / COO_ROWS_R;
-    KernelScope ks("coo_col_tile_bounds", s);
-    k_col_tile_bounds<<<ceil_div_u(n_tiles + 1, 256), 256, 0, s>>>(ptr, n_cols, n_tiles, tb, maxn);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_spmv_coo_col_cols(int split, int cap, const int32_t *trow, const int32_t *tcol, const double *tval,

@@ -121,6 +121,10 @@ def test_malformed_input_is_reported_not_faulted():
     with pytest.raises(L.SpmvError) as e:
         L.spmv_analyze(B)
     assert e.value.status == 2
+    for fmt, lay in ((L.SPMV_COO, L.SPMV_ROWWISE), (L.SPMV_ELL, L.SPMV_ROWWISE), (L.SPMV_CRS, L.SPMV_COLWISE)):
+        with pytest.raises(L.SpmvError) as e:
+            L.spmv_transform(B, fmt, lay)
+        assert e.value.status == 2
     # the device still works
     L.spmv_validate(dev(H))
 
