@@ -489,15 +489,6 @@ struct PipeSmem {        // one warp: two stages of tile entries
     uint32_t last[8];
 };
 
-__device__ __forceinline__ void cp_async_8(void *s, const void *g) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(s)), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_4(void *s, const void *g) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(s)), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ bool is_merge(const BatchMat *__restrict__ M, int n) {
     return M->fmt == BATCH_CRS && M->tpr == 1 && n <= 32 * MMAX;

@@ -36,6 +36,8 @@ CASES = {
     "laplace64": lambda: synth.laplacian_2d_5pt(64),
     "laplace37x23": lambda: synth.laplacian_2d_5pt(37, 23),
     "stencil27_24": lambda: synth.stencil_3d_27pt(24),
+    "stencil27_37": lambda: synth.stencil_3d_27pt(37),
+    "laplace300x221": lambda: synth.laplacian_2d_5pt(300, 221),
     "powerlaw_60k": lambda: synth.power_law(60000, kmax=20000),
     "random_empty_rows": lambda: synth.random_crs(5003, 4001, 6, seed=21, empty_frac=0.3),
     "random_duplicates": lambda: synth.random_crs(3001, 2999, 8, seed=22, dup=True),
@@ -251,13 +253,14 @@ def test_outputs_at_any_8_byte_offset():
 @pytest.mark.parametrize("kernel,S", [("rows", 1), ("rows", 2), ("rows", 4), ("rows", 8), ("tile", 1), ("tile", 2), ("tile", 4), ("tile", 8), ("stream", 1),
                                       ("stream", 2), ("stream", 4), ("stream", 8), ("vector", 0)])
 def test_crs_kernel_variants(monkeypatch, kernel, S):
-    """Every CRS schedule the plan can pick gives results inside the tolerance."""
+    """Every CRS schedule the plan can pick gives results inside the tolerance,
+    on cases of one to several hundred row tiles with ragged last tiles."""
     import torch
     L = lib()
     monkeypatch.setenv("SPMVAT_CRS_KERNEL", kernel)
     if S:
         monkeypatch.setenv("SPMVAT_CRS_S", str(S))
-    for name in ("laplace37x23", "stencil27_24"):
+    for name in ("laplace37x23", "stencil27_24", "laplace300x221", "stencil27_37"):
         H = case(name)
         xh = xvec(H.n_cols, seed=7)
         M = L.spmv_transform(dev(H), L.SPMV_CRS, L.SPMV_ROWWISE)
