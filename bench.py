@@ -102,15 +102,15 @@ def byte_model(n_rows: int, n_cols: int, nnz: int, W: int, Wc: int) -> dict:
 def kernel_bytes(name: str, bm: dict, n_rows: int, n_cols: int, nnz: int):
     """Bytes one launch of a library kernel moves by design (None: not modelled)."""
     table = {
-        "spmv_ell_row": bm["spmv_ell_row"],
-        "spmv_coo_row": bm["spmv_coo_row"],
-        "spmv_coo_col": bm["spmv_coo_col"],
-        "spmv_ell_col": bm["spmv_ell_col"],
-        "crs_to_ell_row": bm["crs_to_ell_row"],
-        "ccs_to_ell_col": bm["ccs_to_ell_col"],
-        "crs_to_coo_row": bm["crs_to_coo_row"],
-        "ccs_to_coo_col": bm["ccs_to_coo_col"],
-        "analyze": bm["analyze"],
+        "spmv_ell_row": bm.get("spmv_ell_row"),
+        "spmv_coo_row": bm.get("spmv_coo_row"),
+        "spmv_coo_col": bm.get("spmv_coo_col"),
+        "spmv_ell_col": bm.get("spmv_ell_col"),
+        "crs_to_ell_row": bm.get("crs_to_ell_row"),
+        "ccs_to_ell_col": bm.get("ccs_to_ell_col"),
+        "crs_to_coo_row": bm.get("crs_to_coo_row"),
+        "ccs_to_coo_col": bm.get("ccs_to_coo_col"),
+        "analyze": bm.get("analyze"),
         "validate_idx": 4 * nnz,
         # Phase I as built here: ICOL in, rank out; rank + ICOL in, (k, row)
         # pairs out; pairs + VAL gather in, ICOL_T + VAL_T out
@@ -132,8 +132,13 @@ def kernel_bytes(name: str, bm: dict, n_rows: int, n_cols: int, nnz: int):
         "coo_col_tile_bounds": 8 * (n_cols // 128 + 1),
         "col_fixup_rv": 28 * nnz + 4 * (n_cols + 1),
         "col_overflow_rv": 0,
+        # grouped row-value path (the default): the same bytes, records in
+        # 64-column group regions; the fix-up also writes IRP_T
+        "col_claim_grp": 28 * nnz + 4 * (n_rows + 1),
+        "col_locality": 8 * 4096,
+        "col_fixup_grp": 28 * nnz + 4 * (n_cols + 1),
         "col_fixup_long_rv": 0,
-        "crs_to_ell_row_fused_spmv": bm["crs_to_ell_row"] + 8 * n_cols + 8 * n_rows,
+        "crs_to_ell_row_fused_spmv": (bm["crs_to_ell_row"] + 8 * n_cols + 8 * n_rows) if "crs_to_ell_row" in bm else None,
     }
     if name.startswith("spmv_crs_"):
         return bm["spmv_crs"]
@@ -350,37 +355,44 @@ def barrier_sync(torch):
 
 
 # ------------------------------------------------------------ CPU oracle
-def oracle_step(H, xh) -> dict:
-    """The same rows on the CPU oracle; returns {row: seconds}."""
+def oracle_step(H, xh, cap: int = 0) -> dict:
+    """The same rows on the CPU oracle; returns {row: seconds}. ELL-Row is
+    left out, as in the GPU step, when its bytes exceed the workload's cap."""
     import oracle
     t = {}
     c = time.perf_counter
     t0 = c(); st = oracle.analyze(H.n_rows, H.irp); t["analyze"] = c() - t0
+    ell = not cap or 12 * H.n_rows * int(st["W"]) + 4 * (H.n_rows + 1) <= cap
     t0 = c(); irow = oracle.crs_to_coo_row(H.n_rows, H.irp); t["crs_to_coo_row"] = c() - t0
-    t0 = c(); ev, ec, W = oracle.crs_to_ell_row(H.n_rows, H.irp, H.icol, H.val); t["crs_to_ell_row"] = c() - t0
+    W = int(st["W"])
+    if ell:
+        t0 = c(); ev, ec, W = oracle.crs_to_ell_row(H.n_rows, H.irp, H.icol, H.val); t["crs_to_ell_row"] = c() - t0
     t0 = c(); irp_t, icol_t, val_t, nc = oracle.crs_to_ccs(H.n_rows, H.n_cols, H.irp, H.icol, H.val)
     t["phase1_ccs"] = c() - t0
     t0 = c(); jcol = oracle.ccs_to_coo_col(H.n_cols, irp_t); t["ccs_to_coo_col"] = c() - t0
     t0 = c(); ev2, er2, W2 = oracle.ccs_to_ell_col(H.n_cols, irp_t, icol_t, val_t); t["ccs_to_ell_col"] = c() - t0
     t0 = c(); oracle.spmv_crs(H.n_rows, H.irp, H.icol, H.val, xh); t["spmv_crs"] = c() - t0
     t0 = c(); oracle.spmv_coo(H.n_rows, irow, H.icol, H.val, xh); t["spmv_coo_row"] = c() - t0
-    t0 = c(); oracle.spmv_ell_row(H.n_rows, W, ev, ec, xh); t["spmv_ell_row"] = c() - t0
+    if ell:
+        t0 = c(); oracle.spmv_ell_row(H.n_rows, W, ev, ec, xh); t["spmv_ell_row"] = c() - t0
     t0 = c(); oracle.spmv_coo(H.n_rows, icol_t, jcol, val_t, xh); t["spmv_coo_col"] = c() - t0
     t0 = c(); oracle.spmv_ell_col(H.n_rows, H.n_cols, W2, ev2, er2, xh); t["spmv_ell_col"] = c() - t0
-    t["_W"], t["_Wc"] = W, W2
+    t["_W"], t["_Wc"], t["_ell"] = W, W2, ell
     return t
 
 
-def oracle_bytes(H, W, Wc) -> float:
+def oracle_bytes(H, W, Wc, ell: bool = True) -> float:
     bm = byte_model(H.n_rows, H.n_cols, H.nnz, W, Wc)
     # the oracle's ELL has ld = n; the row set matches the GPU step minus the
     # CRS schedule (the oracle needs none)
     keys = ["analyze", "crs_to_coo_row", "crs_to_ell_row", "phase1_ccs", "ccs_to_coo_col", "ccs_to_ell_col",
             "spmv_crs", "spmv_coo_row", "spmv_ell_row", "spmv_coo_col", "spmv_ell_col"]
+    if not ell:
+        keys = [k for k in keys if k not in ("crs_to_ell_row", "spmv_ell_row")]
     return float(sum(bm[k] for k in keys))
 
 
-def cpu_baseline(H, xh, budget_s: float = 12.0) -> dict:
+def cpu_baseline(H, xh, budget_s: float = 12.0, cap: int = 0) -> dict:
     """Times the oracle on a bounded row sample of the workload."""
     frac = 4
     rows = max(1, H.n_rows // frac)
@@ -388,9 +400,9 @@ def cpu_baseline(H, xh, budget_s: float = 12.0) -> dict:
     xs = xh  # the slice keeps all columns
     tot_t, tot_b, runs = 0.0, 0.0, 0
     while tot_t < budget_s and runs < 20:
-        t = oracle_step(S, xs)
+        t = oracle_step(S, xs, cap)
         tot_t += sum(v for k, v in t.items() if not k.startswith("_"))
-        tot_b += oracle_bytes(S, t["_W"], t["_Wc"])
+        tot_b += oracle_bytes(S, t["_W"], t["_Wc"], t["_ell"])
         runs += 1
     return {"value": tot_b / tot_t / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
             "sample": f"rows 0..{rows} of {H.n_rows} ({S.nnz} nnz), {runs} oracle step(s), {tot_t:.1f} s, "
@@ -406,12 +418,12 @@ def run_reference(args, w: dict) -> None:
     rows = max(1, H.n_rows // 16)
     S = H.row_slice(0, rows)
     for _ in range(args.warmup):
-        oracle_step(S, xh)
+        oracle_step(S, xh, w.get("cap", 0))
     ts, bs = [], []
     for _ in range(args.steps):
-        t = oracle_step(S, xh)
+        t = oracle_step(S, xh, w.get("cap", 0))
         ts.append(sum(v for k, v in t.items() if not k.startswith("_")))
-        bs.append(oracle_bytes(S, t["_W"], t["_Wc"]))
+        bs.append(oracle_bytes(S, t["_W"], t["_Wc"], t["_ell"]))
     total = sum(ts)
     value = sum(bs) / total / 1e9
     line = {
@@ -939,20 +951,25 @@ def main():
                 "traffic": stored_traffic(top, args.workload),
                 "algorithmic_bytes_per_launch": top_b}
 
-    def fmt_rate(kname):
-        if kname not in per_kernel:
+    def fmt_rate(knames, model):
+        """One product's rate: the device time of all its kernels (a binned CRS
+        product is several launches, one per row bin) over the profiled steps,
+        each of which runs the product once."""
+        if not knames or model not in bm:
             return None
-        g = per_kernel[kname]["GB/s"]
-        return {"GB/s": g, "pct_hbm": 100.0 * g / peak if g else None,
-                "ms": per_kernel[kname]["ms_per_launch"]}
+        ms = sum(per_kernel[k]["ms_per_launch"] * per_kernel[k]["launches"] for k in knames) / PROFILE_STEPS
+        g = bm[model] / (ms * 1e-3) / 1e9
+        return {"GB/s": g, "pct_hbm": 100.0 * g / peak, "ms": ms, "kernels": sorted(knames)}
     crs_k = [k for k in per_kernel if k.startswith("spmv_crs_")]
-    coo_k = [k for k in per_kernel if k.startswith("spmv_coo_row") and not k.endswith("carry")]
-    per_format = {"crs": fmt_rate(crs_k[0]) if crs_k else None, "coo_row": fmt_rate(coo_k[0]) if coo_k else None,
-                  "ell_row": fmt_rate("spmv_ell_row"), "coo_col": fmt_rate("spmv_coo_col"),
-                  "ell_col": fmt_rate("spmv_ell_col")}
+    coo_k = [k for k in per_kernel if k.startswith("spmv_coo_row")]
+    cooc_k = [k for k in per_kernel if k.startswith("spmv_coo_col")]
+    per_format = {"crs": fmt_rate(crs_k, "spmv_crs"), "coo_row": fmt_rate(coo_k, "spmv_coo_row"),
+                  "ell_row": fmt_rate([k for k in per_kernel if k == "spmv_ell_row"], "spmv_ell_row"),
+                  "coo_col": fmt_rate(cooc_k, "spmv_coo_col"),
+                  "ell_col": fmt_rate([k for k in per_kernel if k == "spmv_ell_col"], "spmv_ell_col")}
     # CRS -> ELL cost in CRS-SpMV units: standalone build, and the fused
     # build + first SpMV counted beyond the SpMV it replaces
-    t_crs = per_kernel[crs_k[0]]["ms_per_launch"] if crs_k else None
+    t_crs = per_format["crs"]["ms"] if per_format["crs"] else None
     cost = None
     if t_crs and "crs_to_ell_row" in per_kernel:
         t_an = per_kernel["analyze"]["ms_per_launch"]
@@ -1023,7 +1040,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(H, xh)
+        cpu = cpu_baseline(H, xh, cap=w["cap"])
 
     if rank == 0:
         srt = sorted(per_step)

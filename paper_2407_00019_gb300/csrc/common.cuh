@@ -207,6 +207,23 @@ cudaError_t launch_col_claim_rv(const int32_t *irp, int32_t n_rows, const int32_
 cudaError_t launch_col_fixup_rv(const int32_t *cp, int32_t n_cols, int32_t n_rows, const double *val,
                                 const void *slots, const int4 *ov, int64_t ov_cap, const int32_t *n_ov,
                                 const int32_t *long_list, int32_t *trow, double *tval, int *status, cudaStream_t s);
+// Grouped row-value path of Phase I: records in regions of 64-column groups
+// (col_grp_region_bytes), group counts gcnt (col_grp_count + 1 entries, zeroed)
+// turned into the groups' first positions by launch_scan before the fix-up.
+long long col_grp_count(int32_t n_cols);
+size_t col_grp_region_bytes(int32_t n_cols);
+size_t col_grp_scratch_bytes(int64_t nnz);  // tile lines of the claim's tiles
+// number of `samples` evenly spread entries k with 1 <= ICOL[k+1] - ICOL[k] <= 8,
+// added into *out
+cudaError_t launch_col_locality(const int32_t *icol, int64_t nnz, int samples, int32_t *out, cudaStream_t s);
+cudaError_t launch_col_claim_grp(const int32_t *irp, int32_t n_rows, const int32_t *icol, const double *val,
+                                 int64_t nnz, int32_t n_cols, int32_t *gcnt, void *regions, int32_t *scratch,
+                                 int *status, cudaStream_t s);
+// writes IRP_T (cp), ICOL_T, VAL_T, the longest column and the long-column list
+// (preceded by its count)
+cudaError_t launch_col_fixup_grp(const int32_t *gpos, int32_t n_cols, const void *regions, int32_t *cp,
+                                 int32_t *trow, double *tval, int32_t *colmax, int32_t *long_list, int *status,
+                                 cudaStream_t s);
 // `pairs` must have 16 bytes of slack after its nnz elements.
 // `long_list` is preceded by its device-side count.
 cudaError_t launch_col_fixup(const int32_t *cp, int32_t n_cols, const int32_t *irp, int32_t n_rows,

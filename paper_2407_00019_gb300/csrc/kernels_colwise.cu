@@ -1142,5 +1142,344 @@ cudaError_t launch_col_fixup_rv(const int32_t *cp, int32_t n_cols, int32_t n_row
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------- grouped row-value path
+// The claim above stores each entry's 16-byte record at its own slot, so a
+// warp's stores scatter over many sectors. Here a record goes to the region
+// of its column group (GRP_COLS consecutive columns, GRP_CAP records):
+//   k_col_claim_grp : a CTA groups its tile's entries by column group in
+//                     shared memory (warp match, then a small hash table),
+//                     reserves one run per (CTA, group) with a single global
+//                     atomicAdd on the group's count, stages the records of
+//                     each run contiguously and writes them with coalesced
+//                     stores. On banded matrices a tile touches a few groups
+//                     with runs of ~100 records; entries whose group finds no
+//                     table slot take their own atomic and store.
+//   k_scan          : group counts -> the groups' first CCS positions.
+//   k_fixup_grp     : one CTA per group: records in (coalesced), a counting
+//                     sort by column in shared memory, IRP_T of the group's
+//                     columns, each column of <= 32 entries sorted by row with
+//                     the register network, the group's CCS range written
+//                     contiguously; longer columns are written unsorted and
+//                     listed for k_fixup_long_rv.
+// A group of more than GRP_CAP entries, a repeated row within a column or a
+// column over RV_LONG_CAP sets ST_REDO (the host then takes the (k, row) path).
+constexpr int GRP_COLS = 64;
+constexpr int GRP_CAP = GRP_COLS * SLOT_CAP;  // 2048 records (32 KB) per group
+constexpr int GCL_THREADS = 256;
+constexpr int GCL_ITEMS = 4;
+constexpr int GCL_TILE = GCL_THREADS * GCL_ITEMS;
+constexpr int GCL_WIN = 1024;
+constexpr int GCL_HASH = 512;
+constexpr int GCL_PROBES = 8;
+
+long long col_grp_count(int32_t n_cols) { return ((long long)n_cols + GRP_COLS - 1) / GRP_COLS; }
+size_t col_grp_scratch_bytes(int64_t nnz) { return tile_lines_bytes(nnz, GCL_TILE); }
+size_t col_grp_region_bytes(int32_t n_cols) {
+    return (size_t)col_grp_count(n_cols) * GRP_CAP * sizeof(RowVal);
+}
+
+__global__ void __launch_bounds__(GCL_THREADS) k_col_claim_grp(const int32_t *__restrict__ irp, int32_t n_rows,
+                                                                const int32_t *__restrict__ icol,
+                                                                const double *__restrict__ val, int64_t nnz,
+                                                                int32_t n_cols, int32_t *__restrict__ gcnt,
+                                                                const int32_t *__restrict__ tl, long long n_tiles,
+                                                                RowVal *__restrict__ regions, int *status) {
+    __shared__ int32_t s_ptr[GCL_WIN];
+    __shared__ int32_t s_row[GCL_TILE + GCL_TILE / 32];
+    __shared__ int32_t s_hkey[GCL_HASH];
+    __shared__ int32_t s_hcnt[GCL_HASH];   // run length, then the run's staging offset
+    __shared__ int32_t s_hbase[GCL_HASH];  // the run's first position in its group region
+    __shared__ RowVal s_rec[GCL_TILE];
+    __shared__ long long s_dst[GCL_TILE];
+    __shared__ int s_wsum[GCL_THREADS / 32];
+    __shared__ int s_total;
+    const int t = threadIdx.x;
+    const unsigned lane = lane_id();
+    const int w = t >> 5;
+    const long long k0 = (long long)blockIdx.x * GCL_TILE;
+    const long long k1 = min(k0 + (long long)GCL_TILE, (long long)nnz);
+    for (int i = t; i < GCL_HASH; i += GCL_THREADS) { s_hkey[i] = -1; s_hcnt[i] = 0; }
+    int c[GCL_ITEMS];
+    double v[GCL_ITEMS];
+#pragma unroll
+    for (int u = 0; u < GCL_ITEMS; ++u) {
+        const long long k = k0 + u * GCL_THREADS + t;
+        c[u] = (k < k1) ? __ldcs(icol + k) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < GCL_ITEMS; ++u) {
+        const long long k = k0 + u * GCL_THREADS + t;
+        v[u] = (k < k1) ? __ldcs(val + k) : 0.0;
+    }
+    const int lo = tl[blockIdx.x];
+    const int hi = (blockIdx.x + 1 < n_tiles) ? tl[blockIdx.x + 1] : n_rows - 1;
+    const int wn = hi - lo + 2;
+    const bool sm = wn <= GCL_WIN;
+    if (sm)
+        for (int i = t; i < wn; i += GCL_THREADS) s_ptr[i] = irp[lo + i];
+    __syncthreads();
+    {
+        const long long kb = k0 + (long long)t * GCL_ITEMS;  // this thread's block of entries
+        if (kb < k1) {
+            int row = sm ? lo + last_le(s_ptr, 0, wn - 1, kb) : last_le(irp, lo, hi + 1, kb);
+#pragma unroll
+            for (int j = 0; j < GCL_ITEMS; ++j) {
+                const long long kk = kb + j;
+                while (row < hi && (long long)(sm ? s_ptr[row + 1 - lo] : irp[row + 1]) <= kk) ++row;
+                s_row[pad32(t * GCL_ITEMS + j)] = row;
+            }
+        }
+    }
+    // runs: lanes of one instruction with the same group share one table
+    // update by their leader
+    int slot[GCL_ITEMS], local[GCL_ITEMS];
+    int bad = 0;
+#pragma unroll
+    for (int u = 0; u < GCL_ITEMS; ++u) {
+        const long long k = k0 + u * GCL_THREADS + t;
+        const bool has = k < k1;
+        const bool ok = has && (unsigned)c[u] < (unsigned)n_cols;
+        bad |= has && !ok;
+        const int g = ok ? (c[u] / GRP_COLS) : -1 - (int)lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, g);
+        const int leader = __ffs(peers) - 1;
+        int h = -1, base = 0;
+        if (ok && (int)lane == leader) {
+            h = (int)(((unsigned)g * 2654435761u) >> 23);  // 9 bits
+            for (int p = 0;; ++p) {
+                const int old = atomicCAS(&s_hkey[h], -1, g);
+                if (old == -1 || old == g) break;
+                if (p + 1 >= GCL_PROBES) { h = -1; break; }
+                h = (h + 1) & (GCL_HASH - 1);
+            }
+            if (h >= 0) base = atomicAdd(&s_hcnt[h], __popc(peers));
+        }
+        h = __shfl_sync(0xffffffffu, h, leader);
+        base = __shfl_sync(0xffffffffu, base, leader);
+        slot[u] = ok ? h : -2;  // -1: no table slot, the entry goes alone
+        local[u] = base + __popc(peers & lanemask_lt());
+    }
+    __syncthreads();
+    {
+        // staging offsets (exclusive scan over the table, two slots per
+        // thread) and one global reservation per occupied slot
+        const int a0 = s_hcnt[2 * t], a1 = s_hcnt[2 * t + 1];
+        int inc = a0 + a1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, inc, o);
+            if ((int)lane >= o) inc += x;
+        }
+        if (lane == 31) s_wsum[w] = inc;
+        const int b0 = a0 > 0 ? atomicAdd(gcnt + s_hkey[2 * t], a0) : 0;
+        const int b1 = a1 > 0 ? atomicAdd(gcnt + s_hkey[2 * t + 1], a1) : 0;
+        __syncthreads();
+        int woff = 0, tot = 0;
+#pragma unroll
+        for (int j = 0; j < GCL_THREADS / 32; ++j) {
+            if (j < w) woff += s_wsum[j];
+            tot += s_wsum[j];
+        }
+        const int excl = woff + inc - a0 - a1;
+        s_hcnt[2 * t] = excl;
+        s_hcnt[2 * t + 1] = excl + a0;
+        s_hbase[2 * t] = b0;
+        s_hbase[2 * t + 1] = b1;
+        if (t == 0) s_total = tot;
+    }
+    __syncthreads();
+    int redo = 0;
+#pragma unroll
+    for (int u = 0; u < GCL_ITEMS; ++u) {
+        if (slot[u] == -2) continue;
+        const int e = u * GCL_THREADS + t;
+        RowVal q;
+        q.row = s_row[pad32(e)];
+        q.pad = c[u] % GRP_COLS;
+        q.v = v[u];
+        const long long g = c[u] / GRP_COLS;
+        if (slot[u] >= 0) {
+            const int sp = s_hcnt[slot[u]] + local[u];
+            const int gp = s_hbase[slot[u]] + local[u];
+            s_rec[sp] = q;
+            s_dst[sp] = gp < GRP_CAP ? g * GRP_CAP + gp : -1;
+            redo |= gp >= GRP_CAP;
+        } else {
+            const int gp = atomicAdd(gcnt + g, 1);
+            if (gp < GRP_CAP) regions[g * GRP_CAP + gp] = q;
+            else redo = 1;
+        }
+    }
+    __syncthreads();
+    for (int q = t; q < s_total; q += GCL_THREADS) {
+        const long long d = s_dst[q];
+        if (d >= 0) regions[d] = s_rec[q];
+    }
+    if (__any_sync(0xffffffffu, redo) && lane == 0) atomicOr(status, ST_REDO);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_BAD_INDEX);
+}
+
+constexpr int GFX_THREADS = 128;
+constexpr size_t GFX_SMEM = (size_t)GRP_CAP * (sizeof(RowVal) + sizeof(int2));
+
+__global__ void __launch_bounds__(GFX_THREADS) k_fixup_grp(const int32_t *__restrict__ gpos, int32_t n_cols,
+                                                            long long n_groups, const RowVal *__restrict__ regions,
+                                                            int32_t *__restrict__ cp, int32_t *__restrict__ trow,
+                                                            double *__restrict__ tval, int32_t *__restrict__ colmax,
+                                                            int32_t *__restrict__ long_list,
+                                                            int32_t *__restrict__ long_count, int *status) {
+    extern __shared__ __align__(16) unsigned char gfx_smem[];
+    RowVal *s_rec = reinterpret_cast<RowVal *>(gfx_smem);
+    int2 *s_key = reinterpret_cast<int2 *>(s_rec + GRP_CAP);  // (row, record) in column order
+    __shared__ int32_t s_ccnt[GRP_COLS], s_coff[GRP_COLS + 1], s_cur[GRP_COLS];
+    __shared__ int s_redo;
+    const int t = threadIdx.x;
+    const unsigned lane = lane_id();
+    const long long g = blockIdx.x;
+    const int gb = gpos[g];
+    const int cnt = gpos[g + 1] - gb;
+    if (cnt < 0) return;  // only after a failed scan, which the host reports
+    const long long c0 = g * GRP_COLS;
+    const int ncl = (int)min((long long)GRP_COLS, (long long)n_cols - c0);
+    if (t < GRP_COLS) { s_ccnt[t] = 0; s_cur[t] = 0; }
+    if (t == 0) s_redo = 0;
+    if (cnt > GRP_CAP) {  // the claim flagged it; nothing here is usable
+        if (t == 0) atomicOr(status, ST_REDO);
+        return;
+    }
+    __syncthreads();
+    const RowVal *reg = regions + g * GRP_CAP;
+    for (int q = t; q < cnt; q += GFX_THREADS) {
+        const int4 w4 = __ldcs(reinterpret_cast<const int4 *>(reg) + q);  // {row, column in group, value}
+        RowVal r;
+        r.row = w4.x;
+        r.pad = (unsigned)w4.y < (unsigned)ncl ? w4.y : 0;
+        r.v = __hiloint2double(w4.w, w4.z);
+        s_rec[q] = r;
+        atomicAdd(&s_ccnt[r.pad], 1);
+    }
+    __syncthreads();
+    if (t < 32) {  // exclusive scan of the 64 column counts, two per lane
+        const int a = s_ccnt[2 * t], b = s_ccnt[2 * t + 1];
+        int inc = a + b;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, inc, o);
+            if ((int)lane >= o) inc += x;
+        }
+        s_coff[2 * t] = inc - a - b;
+        s_coff[2 * t + 1] = inc - b;
+        if (t == 31) s_coff[GRP_COLS] = inc;
+        int m = max(a, b);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (t == 0 && m > 0) atomicMax(colmax, m);
+    }
+    __syncthreads();
+    if (t < ncl) {
+        cp[c0 + t] = gb + s_coff[t];
+        if (s_ccnt[t] > SLOT_CAP) long_list[atomicAdd(long_count, 1)] = (int32_t)(c0 + t);
+    }
+    if (g == n_groups - 1 && t == 0) cp[n_cols] = gb + cnt;
+    for (int q = t; q < cnt; q += GFX_THREADS) {
+        const int j = s_rec[q].pad;
+        const int p = s_coff[j] + atomicAdd(&s_cur[j], 1);
+        s_key[p] = make_int2(s_rec[q].row, q);
+    }
+    __syncthreads();
+    if (t < ncl) {
+        const int len = s_ccnt[t];
+        const int off = s_coff[t];
+        if (len >= 2 && len <= SLOT_CAP) {
+            uint32_t key[SLOT_CAP];
+#pragma unroll
+            for (int r = 0; r < SLOT_CAP; ++r)
+                key[r] = (r < len) ? (((uint32_t)s_key[off + r].x << 5) | (uint32_t)r) : 0xffffffffu;
+            if (len <= 8) net_sort<8>(key);
+            else if (len <= 16) net_sort<16>(key);
+            else net_sort<32>(key);
+            int idx[SLOT_CAP];
+            bool dup = false;
+#pragma unroll
+            for (int r = 0; r < SLOT_CAP; ++r) {
+                if (r < len) {
+                    idx[r] = s_key[off + (int)(key[r] & 31u)].y;
+                    if (r > 0 && (key[r] >> 5) == (key[r - 1] >> 5)) dup = true;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < SLOT_CAP; ++r)
+                if (r < len) s_key[off + r] = make_int2((int)(key[r] >> 5), idx[r]);
+            if (dup) s_redo = 1;
+        }
+    }
+    __syncthreads();
+    if (t == 0 && s_redo) atomicOr(status, ST_REDO);
+    for (int q = t; q < cnt; q += GFX_THREADS) {
+        const int2 k = s_key[q];
+        __stcs(trow + gb + q, k.x);
+        __stcs(tval + gb + q, s_rec[k.y].v);
+    }
+}
+
+cudaError_t launch_col_claim_grp(const int32_t *irp, int32_t n_rows, const int32_t *icol, const double *val,
+                                 int64_t nnz, int32_t n_cols, int32_t *gcnt, void *regions, int32_t *scratch,
+                                 int *status, cudaStream_t s) {
+    if (nnz <= 0) return cudaSuccess;
+    cudaError_t e = launch_tile_lines(irp, n_rows, nnz, GCL_TILE, scratch, s);
+    if (e != cudaSuccess) return e;
+    const long long n_tiles = (nnz + GCL_TILE - 1) / GCL_TILE;
+    KernelScope ks("col_claim_grp", s);
+    k_col_claim_grp<<<(unsigned)n_tiles, GCL_THREADS, 0, s>>>(irp, n_rows, icol, val, nnz, n_cols, gcnt, scratch,
+                                                               n_tiles, reinterpret_cast<RowVal *>(regions), status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_col_fixup_grp(const int32_t *gpos, int32_t n_cols, const void *regions, int32_t *cp,
+                                 int32_t *trow, double *tval, int32_t *colmax, int32_t *long_list, int *status,
+                                 cudaStream_t s) {
+    if (n_cols <= 0) return cudaSuccess;
+    const long long n_groups = col_grp_count(n_cols);
+    int32_t *long_count = long_list - 1;
+    {
+        cudaError_t e = set_smem_attr(k_fixup_grp, GFX_SMEM);
+        if (e != cudaSuccess) return e;
+        KernelScope ks("col_fixup_grp", s);
+        k_fixup_grp<<<(unsigned)n_groups, GFX_THREADS, GFX_SMEM, s>>>(gpos, n_cols, n_groups,
+                                                                     reinterpret_cast<const RowVal *>(regions), cp,
+                                                                     trow, tval, colmax, long_list, long_count, status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    KernelScope ks("col_fixup_long_rv", s);
+    k_fixup_long_rv<<<(unsigned)sm_count() * 2u, FIX_THREADS, 0, s>>>(cp, long_list, long_count, trow, tval, status);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- column locality
+// Share of sampled neighbouring entries (k, k + 1) whose columns differ by 1
+// to 8: high for banded and stencil matrices, where a row's consecutive
+// entries fill neighbouring slots of the slot-major array, near zero for
+// scattered columns. Samples are spread evenly over the entries.
+__global__ void __launch_bounds__(256) k_col_locality(const int32_t *__restrict__ icol, int64_t nnz, int samples,
+                                                       int32_t *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int local = 0;
+    if (i < samples && nnz > 1) {
+        const long long k = (long long)((double)i * (double)(nnz - 1) / (double)samples);
+        const long long d = (long long)__ldg(icol + k + 1) - (long long)__ldg(icol + k);
+        local = (d >= 1 && d <= 8) ? 1 : 0;
+    }
+    local = __reduce_add_sync(0xffffffffu, (unsigned)local);
+    if (lane_id() == 0 && local) atomicAdd(out, local);
+}
+
+cudaError_t launch_col_locality(const int32_t *icol, int64_t nnz, int samples, int32_t *out, cudaStream_t s) {
+    if (nnz <= 1 || samples <= 0) return cudaSuccess;
+    KernelScope ks("col_locality", s);
+    k_col_locality<<<ceil_div_u(samples, 256), 256, 0, s>>>(icol, nnz, samples, out);
+    return cudaGetLastError();
+}
+
 }  // namespace spmvat
 

@@ -326,7 +326,7 @@ def _claims(L, H):
         prof = L.spmv_profile_read(reset=True)
     finally:
         L.spmv_profile_enable(False)
-    return M, prof.get("col_claim_rv", (0, 0.0))[0] + prof.get("col_claim", (0, 0.0))[0]
+    return M, sum(prof.get(k, (0, 0.0))[0] for k in ("col_claim_grp", "col_claim_rv", "col_claim"))
 
 
 def shuffled_rows(H, seed=3):
@@ -359,13 +359,14 @@ def with_extra_columns(n, mean_len, seed, every):
     return synth.CRS(n, n, irp.astype(np.int32), icol, synth.normal(seed, 5, np.arange(icol.size)))
 
 
-@pytest.mark.parametrize("mode", ["scatter", "kslot", "rv"])
+@pytest.mark.parametrize("mode", ["scatter", "kslot", "rv", "grp"])
 @pytest.mark.parametrize("name", ["stencil27_24", "powerlaw_60k", "random_duplicates", "dense_column", "wide",
                                   "tall", "all_empty", "one_by_one", "laplace37x23"])
 def test_phase1_paths_bit_exact(monkeypatch, mode, name):
     """Every Phase I path (count + scatter; (k, row) slots; (row, value)
-    slots, which hands over to the (k, row) slots on repeated entries or
-    columns over 4096) gives the oracle's CCS bit for bit."""
+    slots, per column or in 64-column group regions, which hand over to the
+    (k, row) slots on repeated entries, full groups or columns over 4096)
+    gives the oracle's CCS bit for bit."""
     L = lib()
     monkeypatch.setenv("SPMVAT_PHASE1", mode)
     H = case(name)
