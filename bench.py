@@ -142,7 +142,7 @@ def kernel_bytes(name: str, bm: dict, n_rows: int, n_cols: int, nnz: int):
     }
     if name.startswith("spmv_crs_"):
         return bm["spmv_crs"]
-    if name.startswith("spmv_coo_row_rows"):
+    if name.startswith("spmv_coo_row_rows") or name == "spmv_coo_row_seg":
         return bm["spmv_coo_row"]
     if name.startswith("spmv_coo_col_cols"):
         return bm["spmv_coo_col"]
@@ -807,13 +807,27 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def csrc_digest() -> str:
-    """Hash of the device code (kernel files and device headers): DRAM traffic
-    per launch depends on nothing else."""
+# Source files whose device code decides each kernel's DRAM traffic (the
+# shared device header counts for all of them).
+KERNEL_FILES = {
+    "col_claim_rv": "kernels_colwise.cu", "col_fixup_rv": "kernels_colwise.cu",
+    "col_claim_grp": "kernels_colwise.cu", "col_fixup_grp": "kernels_colwise.cu",
+    "col_claim": "kernels_colwise.cu", "col_fixup_slots": "kernels_colwise.cu",
+    "crs_to_ell_row": "kernels_rowwise.cu", "ccs_to_ell_col": "kernels_rowwise.cu",
+    "crs_to_coo_row": "kernels_rowwise.cu", "ccs_to_coo_col": "kernels_rowwise.cu",
+    "batch_apply": "kernels_batch.cu",
+}
+
+
+def csrc_digest(kernel: str = None) -> str:
+    """Hash of the device code a kernel's DRAM traffic depends on: its own
+    kernel file (spmv_* kernels: kernels_spmv.cu) and the device headers;
+    every kernel file when the kernel is not listed."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2407_00019_gb300", "csrc")
+    own = KERNEL_FILES.get(kernel, "kernels_spmv.cu" if (kernel or "").startswith("spmv_") else None)
     for f in sorted(os.listdir(d)):
-        if f.startswith("kernels_") or f.endswith(".cuh"):
+        if f.endswith(".cuh") or (f.startswith("kernels_") and (own is None or f == own)):
             with open(os.path.join(d, f), "rb") as fh:
                 h.update(fh.read())
     return h.hexdigest()[:16]
@@ -821,7 +835,7 @@ def csrc_digest() -> str:
 
 def stored_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from a committed ncu summary, if it matches the
-    current kernel sources."""
+    current device code of that kernel."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(p) as f:
@@ -829,7 +843,7 @@ def stored_traffic(kernel: str, workload: str):
     except (OSError, ValueError):
         return None
     for r in rows:
-        if r.get("kernel") == kernel and r.get("workload") == workload and r.get("csrc") == csrc_digest():
+        if r.get("kernel") == kernel and r.get("workload") == workload and r.get("csrc") == csrc_digest(kernel):
             return r.get("bytes_per_launch")
     return None
 

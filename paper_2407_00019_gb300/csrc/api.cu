@@ -150,6 +150,9 @@ struct spmv_matrix {
     cudaStream_t home = nullptr;
     // CRS schedule
     int crs_binned = 0;
+    int crs_seg = 0;               // entry-split product (uneven rows)
+    const int32_t *seg_tl = nullptr; //    and the tile lines it needs
+    int coo_seg = 0;               // COO-Row entry-split product
     int crs_v = 1;
     int coo_rows_split = 0;        // > 0: COO over row- (column-) aligned tiles, threads per line
     int coo_rows_cap = 0;          //      shared-memory entries per tile
@@ -322,6 +325,15 @@ spmv_status crs_plan_from(const spmv_crs *A, const spmv_stats &st, uint64_t cap,
             M->status = reinterpret_cast<int *>(sw->p);
             M->bufs.push_back(sw);
         }
+    } else if (!getenv("SPMVAT_CRS_KERNEL") || strcmp(getenv("SPMVAT_CRS_KERNEL"), "binned") != 0) {
+        // uneven rows: the entry-split product (same work per thread whatever
+        // the row lengths); its tile lines are computed once, here
+        BufPtr tl;
+        CKS(alloc_buf(spmv_seg_scratch_bytes(A->nnz), s, &tl));
+        if (A->nnz > 0) CK(launch_spmv_seg_lines(A->irp, A->n_rows, A->nnz, reinterpret_cast<int32_t *>(tl->p), s));
+        M->crs_seg = 1;
+        M->seg_tl = reinterpret_cast<const int32_t *>(tl->p);
+        M->bufs.push_back(tl);
     } else {
         const uint64_t need = (uint64_t)A->n_rows * 4;
         if (cap && need > cap) return SPMV_ERR_MEMORY_CAP;
@@ -387,11 +399,14 @@ spmv_status build_coo_row(const spmv_crs *A, uint64_t cap, spmv_matrix **out, cu
         CK(cudaStreamSynchronize(s));
         CKS(status_from_dev(hirp));
         const int cap = coo_rows_cap(h[1]);
-        if (cap > 0 && !getenv("SPMVAT_COO_ENTRY_TILES")) {
+        const char *et = getenv("SPMVAT_COO_ENTRY_TILES");
+        if (cap > 0 && !et) {
             M->coo_rows_cap = cap;
             M->coo_rows_split = ((double)A->nnz / A->n_rows <= 8.0) ? 2 : 4;
             M->coo_tb = reinterpret_cast<const int32_t *>(tb->p);
             M->bufs.push_back(tb);
+        } else if (!et || !strcmp(et, "seg")) {
+            M->coo_seg = 1;  // tiles too large for shared memory: entry-split product
         }
     }
     M->ptr = A->irp;
@@ -713,7 +728,10 @@ spmv_status apply_core(const spmv_matrix *M, const double *x, double *y, cudaStr
     if (M->layout == SPMV_ROWWISE) {
         switch (M->format) {
             case SPMV_CRS:
-                if (M->crs_rows_split > 0) {
+                if (M->crs_seg) {
+                    CK(launch_spmv_seg(false, M->ptr, M->idx, M->val, M->nnz, M->n_rows, M->n_cols, M->seg_tl, x, y,
+                                       s));
+                } else if (M->crs_rows_split > 0) {
                     CK(launch_spmv_crs_rows(M->crs_rows_split, M->crs_rows_cap, M->ptr, M->idx, M->val, M->n_rows,
                                             x, y, s));
                 } else if (M->crs_tile_s > 0) {
@@ -737,6 +755,10 @@ spmv_status apply_core(const spmv_matrix *M, const double *x, double *y, cudaStr
                 if (M->coo_rows_split > 0) {
                     CK(launch_spmv_coo_row_rows(M->coo_rows_split, M->coo_rows_cap, M->idx2, M->idx, M->val, M->coo_tb,
                                                 M->n_rows, M->n_cols, x, y, s));
+                    return SPMV_OK;
+                }
+                if (M->coo_seg) {
+                    CK(launch_spmv_seg(true, M->idx2, M->idx, M->val, M->nnz, M->n_rows, M->n_cols, nullptr, x, y, s));
                     return SPMV_OK;
                 }
                 BufPtr scr;

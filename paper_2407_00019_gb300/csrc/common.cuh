@@ -269,6 +269,13 @@ cudaError_t launch_spmv_coo_row_rows(int split, int cap, const int32_t *irow, co
 cudaError_t launch_spmv_coo_col_cols(int split, int cap, const int32_t *trow, const int32_t *tcol, const double *tval,
                                      const int32_t *tb, int32_t n_rows, int32_t n_cols, const double *x, double *y,
                                      cudaStream_t s);
+// Entry-split products for uneven rows (CRS: tl from launch_spmv_seg_lines,
+// spmv_seg_scratch_bytes; COO: lines = IROW, tl unused); zero y first.
+size_t spmv_seg_scratch_bytes(int64_t nnz);
+cudaError_t launch_spmv_seg_lines(const int32_t *irp, int32_t n_rows, int64_t nnz, int32_t *tl, cudaStream_t s);
+cudaError_t launch_spmv_seg(bool coo, const int32_t *lines, const int32_t *icol, const double *val, int64_t nnz,
+                            int32_t n_rows, int32_t n_cols, const int32_t *tl, const double *x, double *y,
+                            cudaStream_t s);
 cudaError_t launch_spmv_coo_col(const int32_t *row, const int32_t *col, const double *val, int64_t nnz,
                                 int32_t n_rows, const double *x, double *y, cudaStream_t s);
 cudaError_t launch_spmv_ccs(const int32_t *cp, const int32_t *trow, const double *tval, int32_t n_rows,

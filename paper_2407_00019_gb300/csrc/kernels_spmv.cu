@@ -1135,4 +1135,150 @@ cudaError_t launch_spmv_ccs(const int32_t *cp, const int32_t *trow, const double
     return cudaGetLastError();
 }
 
+// ===================================================== entry-split products
+// For rows of very uneven length (power-law rows): every thread multiplies 8
+// consecutive entries, one FMA each in storage order, restarting at each row
+// start; it stores the sum of every row that starts and ends inside its 8
+// entries and adds the partial sums of rows that cross its edges into y with
+// atomicAdd (y is zeroed first). Every thread issues the same FMAs whatever
+// the row lengths, where lanes that own rows would wait for the longest row
+// of their warp on the narrow FP64 pipe. CRS finds each entry's row from the
+// tile's row pointers (staged in shared memory, as the expansions do); COO
+// reads IROW.
+constexpr int SEG_THREADS = 256;
+constexpr int SEG_ITEMS = 8;
+constexpr int SEG_TILE = SEG_THREADS * SEG_ITEMS;
+constexpr int SEG_WIN = 2048;
+
+size_t spmv_seg_scratch_bytes(int64_t nnz) { return tile_lines_bytes(nnz, SEG_TILE); }
+
+template <bool COO>
+__global__ void __launch_bounds__(SEG_THREADS) k_spmv_seg(const int32_t *__restrict__ lines,
+                                                           const int32_t *__restrict__ icol,
+                                                           const double *__restrict__ val, int64_t nnz,
+                                                           int32_t n_rows, int32_t n_cols,
+                                                           const int32_t *__restrict__ tl, long long n_tiles,
+                                                           const double *__restrict__ x, double *__restrict__ y) {
+    __shared__ int32_t s_ptr[COO ? 1 : SEG_WIN];
+    const long long k0 = (long long)blockIdx.x * SEG_TILE;
+    const long long k1 = min(k0 + (long long)SEG_TILE, (long long)nnz);
+    const long long k = k0 + (long long)threadIdx.x * SEG_ITEMS;
+    const int cnt = (int)max(0ll, min((long long)SEG_ITEMS, k1 - k));
+    int c[SEG_ITEMS], r[SEG_ITEMS];
+    double v[SEG_ITEMS];
+    const bool vec = cnt == SEG_ITEMS && ((reinterpret_cast<uintptr_t>(icol + k) & 15) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(val + k) & 15) == 0) &&
+                     (!COO || ((reinterpret_cast<uintptr_t>(lines + k) & 15) == 0));
+    if (vec) {
+#pragma unroll
+        for (int h = 0; h < SEG_ITEMS / 4; ++h) {
+            const int4 q = __ldcs(reinterpret_cast<const int4 *>(icol + k) + h);
+            c[4 * h] = q.x; c[4 * h + 1] = q.y; c[4 * h + 2] = q.z; c[4 * h + 3] = q.w;
+            if (COO) {
+                const int4 p = __ldcs(reinterpret_cast<const int4 *>(lines + k) + h);
+                r[4 * h] = p.x; r[4 * h + 1] = p.y; r[4 * h + 2] = p.z; r[4 * h + 3] = p.w;
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < SEG_ITEMS / 2; ++h) {
+            const double2 q = __ldcs(reinterpret_cast<const double2 *>(val + k) + h);
+            v[2 * h] = q.x; v[2 * h + 1] = q.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < SEG_ITEMS; ++j) {
+            c[j] = (j < cnt) ? icol[k + j] : 0;
+            v[j] = (j < cnt) ? val[k + j] : 0.0;
+            if (COO) r[j] = (j < cnt) ? lines[k + j] : -1;
+        }
+    }
+    bool starts, ends;  // does the first row start, the last row end, inside these entries
+    if (COO) {
+        int last = r[0];
+#pragma unroll
+        for (int j = 1; j < SEG_ITEMS; ++j)
+            if (j < cnt) last = r[j];
+        const int prev = (cnt > 0 && k > 0) ? __ldg(lines + k - 1) : -1;
+        const int next = (cnt > 0 && k + cnt < nnz) ? __ldg(lines + k + cnt) : -1;
+        starts = prev != r[0];
+        ends = next != last;
+    } else {
+        const int lo = tl[blockIdx.x];
+        const int hi = (blockIdx.x + 1 < n_tiles) ? tl[blockIdx.x + 1] : n_rows - 1;
+        const int wn = hi - lo + 2;  // lines[lo .. hi+1]
+        const bool sm = wn <= SEG_WIN;
+        if (sm)
+            for (int i = threadIdx.x; i < wn; i += SEG_THREADS) s_ptr[i] = lines[lo + i];
+        __syncthreads();
+        starts = ends = true;
+        if (cnt > 0) {
+            auto P = [&](int row) -> long long { return sm ? s_ptr[row - lo] : lines[row]; };
+            int row = sm ? lo + last_le(s_ptr, 0, wn - 1, k) : last_le(lines, lo, hi + 1, k);
+            starts = P(row) == k;
+            long long nb = (row < hi) ? P(row + 1) : LLONG_MAX;
+            int last = row;
+#pragma unroll
+            for (int j = 0; j < SEG_ITEMS; ++j) {
+                const long long kk = k + j;
+                while (kk >= nb && row < hi) {
+                    ++row;
+                    nb = (row < hi) ? P(row + 1) : LLONG_MAX;
+                }
+                r[j] = row;
+                if (j < cnt) last = row;
+            }
+            ends = (last < hi ? P(last + 1) : (long long)lines[last + 1]) <= k + cnt;
+        }
+    }
+    if (cnt == 0) return;
+    double xv[SEG_ITEMS];
+#pragma unroll
+    for (int j = 0; j < SEG_ITEMS; ++j)
+        xv[j] = (j < cnt && (unsigned)c[j] < (unsigned)n_cols) ? __ldg(x + c[j]) : 0.0;
+    auto flush = [&](int row, double a, bool whole) {
+        if ((unsigned)row >= (unsigned)n_rows) return;
+        if (whole) y[row] = a;
+        else atomicAdd(y + row, a);
+    };
+    double acc = 0.0;
+    int cur = r[0];
+    bool first = true;
+#pragma unroll
+    for (int j = 0; j < SEG_ITEMS; ++j) {
+        if (j < cnt) {
+            if (r[j] != cur) {
+                flush(cur, acc, !first || starts);
+                acc = 0.0;
+                cur = r[j];
+                first = false;
+            }
+            acc = fma(v[j], xv[j], acc);
+        }
+    }
+    flush(cur, acc, (!first || starts) && ends);
+}
+
+cudaError_t launch_spmv_seg(bool coo, const int32_t *lines, const int32_t *icol, const double *val, int64_t nnz,
+                            int32_t n_rows, int32_t n_cols, const int32_t *tl, const double *x, double *y,
+                            cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(y, 0, sizeof(double) * (size_t)n_rows, s);
+    if (e != cudaSuccess || nnz <= 0) return e;
+    const long long n_tiles = (nnz + SEG_TILE - 1) / SEG_TILE;
+    if (coo) {
+        KernelScope ks("spmv_coo_row_seg", s);
+        k_spmv_seg<true><<<(unsigned)n_tiles, SEG_THREADS, 0, s>>>(lines, icol, val, nnz, n_rows, n_cols, nullptr,
+                                                                   n_tiles, x, y);
+    } else {
+        KernelScope ks("spmv_crs_seg", s);
+        k_spmv_seg<false><<<(unsigned)n_tiles, SEG_THREADS, 0, s>>>(lines, icol, val, nnz, n_rows, n_cols, tl,
+                                                                    n_tiles, x, y);
+    }
+    return cudaGetLastError();
+}
+
+// Tile lines of the CRS entry-split product (kept in the CRS handle).
+cudaError_t launch_spmv_seg_lines(const int32_t *irp, int32_t n_rows, int64_t nnz, int32_t *tl, cudaStream_t s) {
+    return launch_tile_lines(irp, n_rows, nnz, SEG_TILE, tl, s);
+}
+
 }  // namespace spmvat

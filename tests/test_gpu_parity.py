@@ -52,6 +52,20 @@ CASES = {
 _cache = {}
 
 
+def crs_uneven(H):
+    """The CRS schedule takes the entry-split product: D_mat > 0.5 or a row of
+    2048 entries or more (the plan's rule for uneven rows)."""
+    st = oracle.analyze(H.n_rows, H.irp)
+    return st["dmat"] > 0.5 or st["W"] >= 2048
+
+
+def coo_tiles_overflow(H):
+    """The COO-Row schedule takes the entry-split product: some 128-row tile
+    holds more entries than the row-tile kernel stages (6144)."""
+    edges = H.irp[np.minimum(np.arange(0, H.n_rows + 128, 128), H.n_rows)].astype(np.int64)
+    return H.nnz > 0 and int(np.diff(edges).max()) * 16 > 96 * 1024
+
+
 def case(name):
     if name not in _cache:
         _cache[name] = CASES[name]()
@@ -160,7 +174,9 @@ def test_spmv_every_format(name):
     for fmt, M in mats.items():
         y = run_apply(M, x, H.n_rows)
         assert_spmv_close(y, H, xh, what=f"{name}/{fmt}")
-        if fmt in ("crs", "coo_row", "ell_row"):  # row-wise formats are bitwise repeatable
+        # row-wise products sum in a fixed order and repeat bit for bit, except
+        # the entry-split product of uneven rows, which adds row pieces with atomics
+        if fmt == "ell_row" or (fmt == "crs" and not crs_uneven(H)) or (fmt == "coo_row" and not coo_tiles_overflow(H)):
             assert np.array_equal(bits(run_apply(M, x, H.n_rows)), bits(y)), fmt
     for M in mats.values():
         M.close()
@@ -187,19 +203,25 @@ def test_fused_transform_and_first_spmv(name):
     M.close()
 
 
-def test_crs_schedule_binned_and_regular_agree():
-    """The binned schedule (irregular rows) and the single-kernel schedule
-    give results inside the tolerance on the same matrix family."""
+@pytest.mark.parametrize("kernel", ["seg", "binned"])
+def test_crs_schedules_for_uneven_rows(monkeypatch, kernel):
+    """Uneven rows take the entry-split product (or, forced, the row-length
+    bins): rows crossing thread and tile edges, rows of one entry, empty rows
+    and rows thousands of entries long all land inside the tolerance."""
     import torch
     L = lib()
-    H = synth.power_law(30000, kmax=8000, seed=9)
-    A = dev(H)
-    st = L.spmv_analyze(A)
-    assert st["dmat"] > 0.5  # this one takes the binned path
-    xh = xvec(H.n_cols, seed=5)
-    M = L.spmv_transform(A, L.SPMV_CRS, L.SPMV_ROWWISE)
-    assert_spmv_close(run_apply(M, torch.from_numpy(xh).cuda(), H.n_rows), H, xh, what="binned")
-    M.close()
+    if kernel == "binned":
+        monkeypatch.setenv("SPMVAT_CRS_KERNEL", "binned")
+    mats = [synth.power_law(30000, kmax=8000, seed=9), case("powerlaw_60k"), case("long_row"),
+            case("random_empty_rows"), case("dense_column"), case("random_duplicates")]
+    for i, H in enumerate(mats):
+        A = dev(H)
+        xh = xvec(H.n_cols, seed=5 + i)
+        M = L.spmv_transform(A, L.SPMV_CRS, L.SPMV_ROWWISE)
+        for rep in range(2):
+            assert_spmv_close(run_apply(M, torch.from_numpy(xh).cuda(), H.n_rows), H, xh, what=f"{kernel}/{i}/{rep}")
+        M.close()
+    assert L.spmv_analyze(dev(mats[0]))["dmat"] > 0.5  # the first one is uneven
 
 
 def test_unaligned_caller_arrays_take_the_global_path():
@@ -269,14 +291,16 @@ def test_crs_kernel_variants(monkeypatch, kernel, S):
         M.close()
 
 
-@pytest.mark.parametrize("entry_tiles", [False, True])
+@pytest.mark.parametrize("entry_tiles", ["", "1", "seg"])
 def test_coo_row_schedules(monkeypatch, entry_tiles):
-    """Row-aligned tiles and entry tiles with carries agree with the oracle."""
+    """Row-aligned tiles, entry tiles with carries and the entry-split product
+    agree with the oracle."""
     import torch
     L = lib()
     if entry_tiles:
-        monkeypatch.setenv("SPMVAT_COO_ENTRY_TILES", "1")
-    for name in ("laplace37x23", "stencil27_24", "random_empty_rows", "long_row", "all_empty"):
+        monkeypatch.setenv("SPMVAT_COO_ENTRY_TILES", entry_tiles)
+    for name in ("laplace37x23", "stencil27_24", "random_empty_rows", "long_row", "all_empty", "powerlaw_60k",
+                 "dense_column", "one_by_one"):
         H = case(name)
         xh = xvec(H.n_cols, seed=8)
         M = L.spmv_transform(dev(H), L.SPMV_COO, L.SPMV_ROWWISE)
