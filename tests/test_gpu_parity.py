@@ -410,6 +410,26 @@ def test_phase1_row_value_path_on_shuffled_rows():
     M.close()
 
 
+@pytest.mark.parametrize("name,path", [("stencil27_24", "col_claim_rv"), ("powerlaw_60k", "col_claim_grp"),
+                                       ("random12", "col_claim_grp")])
+def test_phase1_path_follows_column_locality(name, path):
+    """Neighbouring columns (a stencil) keep the per-column slots; scattered
+    columns (random columns, the power law) take the grouped path."""
+    L = lib()
+    H = synth.random_crs(3000, 3000, 12, seed=85) if name == "random12" else case(name)
+    assert 32 * H.n_cols <= 4 * H.nnz  # a slot path is taken
+    L.spmv_profile_enable(True)
+    L.spmv_profile_read(reset=True)
+    try:
+        M = L.spmv_transform(dev(H), L.SPMV_CRS, L.SPMV_COLWISE)
+        prof = L.spmv_profile_read(reset=True)
+    finally:
+        L.spmv_profile_enable(False)
+    assert path in prof and prof["col_locality"][0] == 1
+    _ccs_matches_oracle(M, H)
+    M.close()
+
+
 @pytest.mark.parametrize("kind", ["duplicates", "column_over_4096", "many_beyond_slots"])
 def test_phase1_row_value_path_hands_over(kind):
     """Matrices the row-value slot path does not cover are rebuilt on the
