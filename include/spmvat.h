@@ -195,10 +195,13 @@ spmv_status spmv_transform_from(const spmv_matrix *src, spmv_format format,
                                 spmv_stream_t stream);
 
 /* y = A x (Sec. 3) in the handle's format. x: device float64[n_cols], y:
- * device float64[n_rows], overwritten; x and y must not overlap. Row-wise
- * formats are deterministic (bitwise repeatable); column-wise formats add
- * into y with atomics, so their rounding order may vary between calls.
- * Asynchronous. */
+ * device float64[n_rows], overwritten; x and y must not overlap. ELL-Row,
+ * and CRS and COO-Row on rows of even length, sum every row in a fixed order
+ * (bitwise repeatable). Column-wise formats add into y with atomics, and so
+ * do CRS on uneven rows (D_mat > 0.5 or a row of 2048 entries or more) and
+ * COO-Row when 128 rows hold more than 6144 entries: those rows are split
+ * over threads, so their rounding order may vary between calls (every result
+ * stays within the tolerance of a reordered sum). Asynchronous. */
 spmv_status spmv_apply(const spmv_matrix *M, const double *x, double *y, spmv_stream_t stream);
 
 /* Fused CRS -> ELL-Row transformation and first SpMV: builds the same
