@@ -112,6 +112,7 @@ def kernel_bytes(name: str, bm: dict, n_rows: int, n_cols: int, nnz: int):
         "ccs_to_coo_col": bm.get("ccs_to_coo_col"),
         "analyze": bm.get("analyze"),
         "validate_idx": 4 * nnz,
+        "spmv_ccs": 12 * nnz + 4 * (n_cols + 1) + 8 * n_cols + 8 * n_rows,
         # Phase I as built here: ICOL in, rank out; rank + ICOL in, (k, row)
         # pairs out; pairs + VAL gather in, ICOL_T + VAL_T out
         "col_count": 8 * nnz + 4 * n_cols,

@@ -1,0 +1,89 @@
+"""Host-side checks of the benchmark's accounting (no GPU): the byte models
+behind every reported rate, the per-kernel byte table against the kernels the
+library times, and the CPU oracle leg under a memory cap."""
+
+import importlib.util
+import os
+import re
+
+import numpy as np
+import pytest
+
+import spmv_synth as synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_byte_model_of_the_stencil_workload(bench):
+    """The 27-point stencil on 128^3: n = 2,097,152, nnz = (3*128 - 2)^3,
+    W = 27. The models count x and y once: CRS SpMV 12 nnz + 4(n+1) + 16n,
+    ELL-Row SpMV 12 n W + 16n (n is a multiple of 32, so ld = n),
+    CRS->ELL 12 nnz + 4(n+1) + 12 n W."""
+    n, nnz, W = 128 ** 3, (3 * 128 - 2) ** 3, 27
+    bm = bench.byte_model(n, n, nnz, W, W)
+    assert nnz == 55_742_968
+    assert bm["spmv_crs"] == 12 * nnz + 4 * (n + 1) + 16 * n == 710_858_660  # 710.9 MB
+    assert bm["spmv_ell_row"] == 12 * n * W + 16 * n == 713_031_680  # 713.0 MB
+    assert bm["crs_to_ell_row"] == 12 * nnz + 4 * (n + 1) + 12 * n * W == 1_356_781_476  # 1356.8 MB
+    assert abs(bm["crs_to_ell_row"] / bm["spmv_crs"] - 1.9087) < 1e-4
+
+
+def test_ell_width_rounds_the_leading_dimension(bench):
+    """ELL keeps each slot column 32-line aligned: ld = round-up(n, 32)."""
+    bm = bench.byte_model(33, 40, 100, 5, 7)
+    assert bm["spmv_ell_row"] == 12 * 64 * 5 + 8 * 40 + 8 * 33
+    assert bm["spmv_ell_col"] == 12 * 64 * 7 + 8 * 40 + 8 * 33
+
+
+def _timed_kernel_names():
+    names = set()
+    d = os.path.join(ROOT, "paper_2407_00019_gb300", "csrc")
+    for f in os.listdir(d):
+        if not f.endswith(".cu"):
+            continue
+        src = open(os.path.join(d, f)).read()
+        names |= set(re.findall(r'KernelScope ks\("([a-z0-9_]+)"', src))
+        names |= set(re.findall(r'"((?:crs|ccs)_to_(?:coo|ell)_(?:row|col))"', src))
+        names |= set(re.findall(r'"(coo_(?:row|col)_tile_bounds)"', src))
+    return names
+
+
+def test_every_step_kernel_has_a_byte_model(bench):
+    """Each kernel the library times in the single-matrix steps has its
+    algorithmic or design bytes in the bench's table, or is one of the few
+    whose traffic depends on the data (long-column sorts, overflow placement)
+    or that belong to other workloads (batches, row bins)."""
+    names = _timed_kernel_names()
+    assert {"col_claim_rv", "col_fixup_rv", "spmv_crs_rows_p", "crs_to_coo_row"} <= names
+    bm = bench.byte_model(1000, 1000, 20000, 30, 40)
+    unmodelled = {"col_fixup_block", "col_fixup_long_rv", "col_overflow_rv", "bin_count", "bin_scatter",
+                  "spmv_coo_row_carry"}
+    for name in sorted(names):
+        if name.startswith("batch_") or name in unmodelled:
+            continue
+        probe = name + "4" if name.endswith("_p") or name.endswith("_s") or name.endswith("_v") else name
+        assert bench.kernel_bytes(probe, bm, 1000, 1000, 20000) is not None, name
+
+
+def test_oracle_leg_leaves_out_ell_beyond_the_cap(bench):
+    """As the GPU step does under the workload's cap, the oracle leg leaves out
+    ELL-Row (and its bytes) when the sample's ELL would not fit the cap."""
+    H = synth.power_law(3000, kmax=2000, seed=3)
+    xh = synth.vector_pm1(H.n_cols, seed=4)
+    t_all = bench.oracle_step(H, xh, 0)
+    assert t_all["_ell"] and "spmv_ell_row" in t_all
+    cap = 12 * H.n_rows * 10  # far below 12 n W for rows up to 2000 entries
+    t_cap = bench.oracle_step(H, xh, cap)
+    assert not t_cap["_ell"] and "spmv_ell_row" not in t_cap and "crs_to_ell_row" not in t_cap
+    b_all = bench.oracle_bytes(H, t_all["_W"], t_all["_Wc"], True)
+    b_cap = bench.oracle_bytes(H, t_cap["_W"], t_cap["_Wc"], False)
+    bm = bench.byte_model(H.n_rows, H.n_cols, H.nnz, t_all["_W"], t_all["_Wc"])
+    assert np.isclose(b_all - b_cap, bm["crs_to_ell_row"] + bm["spmv_ell_row"])
