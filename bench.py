@@ -127,12 +127,12 @@ def kernel_bytes(name: str, bm: dict, n_rows: int, n_cols: int, nnz: int):
         "tile_lines": 4 * (nnz // 2048 + 1),
         "spmv_coo_row_carry": 16 * (nnz // 2048 + 1),
         "col_fixup_block": 0,
-        # row-value slot path (the default for >= 8 entries per column): ICOL +
-        # VAL in, one 16-byte {row, value} slot out; slots in, ICOL_T + VAL_T out
-        "col_claim_rv": 28 * nnz + 4 * (n_rows + 1) + 4 * n_cols,
+        # row-position slot path (neighbouring columns): ICOL in, one 8-byte
+        # {k, row} slot out; slots in, VAL gathered by k, ICOL_T + VAL_T out
+        "col_claim_rk": 12 * nnz + 4 * (n_rows + 1) + 4 * n_cols,
         "coo_col_tile_bounds": 8 * (n_cols // 128 + 1),
-        "col_fixup_rv": 28 * nnz + 4 * (n_cols + 1),
-        "col_overflow_rv": 0,
+        "col_fixup_rk": 28 * nnz + 4 * (n_cols + 1),
+        "col_overflow_rk": 0,
         # grouped row-value path (the default): the same bytes, records in
         # 64-column group regions; the fix-up also writes IRP_T
         "col_claim_grp": 28 * nnz + 4 * (n_rows + 1),
@@ -811,7 +811,7 @@ def measured_hbm_peak():
 # Source files whose device code decides each kernel's DRAM traffic (the
 # shared device header counts for all of them).
 KERNEL_FILES = {
-    "col_claim_rv": "kernels_colwise.cu", "col_fixup_rv": "kernels_colwise.cu",
+    "col_claim_rk": "kernels_colwise.cu", "col_fixup_rk": "kernels_colwise.cu",
     "col_claim_grp": "kernels_colwise.cu", "col_fixup_grp": "kernels_colwise.cu",
     "col_claim": "kernels_colwise.cu", "col_fixup_slots": "kernels_colwise.cu",
     "crs_to_ell_row": "kernels_rowwise.cu", "ccs_to_ell_col": "kernels_rowwise.cu",

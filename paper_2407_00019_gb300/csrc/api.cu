@@ -452,16 +452,17 @@ spmv_status build_ell_row(const spmv_crs *A, const spmv_stats &st, uint64_t cap,
 
 // Phase I (CRS -> CCS). On success M holds the CCS in ccs_bufs/bufs.
 // Three ways to the same CCS, bit for bit:
-//   GRP   : as RV, with the records of each 64-column group written as
-//           coalesced runs per CTA and one atomic per (CTA, group); groups of
-//           at most 2048 entries.
-//   RV    : slots carry (row, value); no gathers, no per-entry ranks. Needs
+//   GRP   : slots carry (row, value) in regions of 64-column groups written
+//           as coalesced runs per CTA, one atomic per (CTA, group); groups of
+//           at most 2048 entries. For scattered columns.
+//   RK    : slots carry (k, row), no per-entry ranks, a register sort per
+//           column, VAL gathered by k. For neighbouring columns. Needs
 //           >= 8 entries per column on average, no repeated (i, j), columns of
 //           at most col_rv_long_cap() entries and few entries beyond the slots;
 //           the kernels report ST_REDO when one of these fails.
 //   KSLOT : slots carry (k, row); any matrix with >= 8 entries per column.
 //   COUNT : count, scan, scatter of (k, row); any matrix.
-enum class P1 { GRP, RV, KSLOT, COUNT };
+enum class P1 { GRP, RK, KSLOT, COUNT };
 constexpr int kLocalitySamples = 4096;
 constexpr spmv_status kRedo = (spmv_status)-1;  // internal: rerun on KSLOT
 
@@ -518,7 +519,7 @@ spmv_status phase1_try(const spmv_crs *A, uint64_t cap_ell_col, bool want_ell, P
     const int64_t nnz = A->nnz;
     const int32_t nc = A->n_cols;
     if (mode == P1::GRP) return phase1_grp(A, cap_ell_col, want_ell, M, s, irp_status);
-    const bool rv = mode == P1::RV, slots = mode != P1::COUNT;
+    const bool rv = mode == P1::RK, slots = mode != P1::COUNT;
     BufPtr cp, trow, tval, rank, pairs, scan_scr, words, longl, tslots, sct0, ovl;
     CKS(alloc_buf((size_t)(nc + 1) * 4, s, &cp));
     if (!rv) CKS(alloc_buf((size_t)nnz * 4, s, &rank));
@@ -536,10 +537,10 @@ spmv_status phase1_try(const spmv_crs *A, uint64_t cap_ell_col, bool want_ell, P
     CK(cudaMemsetAsync(d_long, 0, 4, s));
     const int64_t ov_cap = nnz / 8 + 1024;
     if (rv) {
-        CKS(alloc_buf(col_rv_slot_bytes(nc), s, &tslots));
+        CKS(alloc_buf(col_rk_slot_bytes(nc), s, &tslots));
         CKS(alloc_buf(col_scatter_scratch_bytes(nnz), s, &sct0));
         CKS(alloc_buf((size_t)ov_cap * sizeof(int4), s, &ovl));
-        CK(launch_col_claim_rv(A->irp, A->n_rows, A->icol, A->val, nnz, nc, d_cp, tslots->p,
+        CK(launch_col_claim_rk(A->irp, A->n_rows, A->icol, nnz, nc, d_cp, tslots->p,
                                reinterpret_cast<int4 *>(ovl->p), ov_cap, d_over,
                                reinterpret_cast<int32_t *>(sct0->p), d_status, s));
     } else if (slots) {
@@ -567,7 +568,7 @@ spmv_status phase1_try(const spmv_crs *A, uint64_t cap_ell_col, bool want_ell, P
     CKS(alloc_buf((size_t)nnz * 4, s, &trow));
     CKS(alloc_buf((size_t)nnz * 8, s, &tval));
     if (rv) {
-        CK(launch_col_fixup_rv(d_cp, nc, A->n_rows, A->val, tslots->p, reinterpret_cast<const int4 *>(ovl->p),
+        CK(launch_col_fixup_rk(d_cp, nc, A->n_rows, A->val, tslots->p, reinterpret_cast<const int4 *>(ovl->p),
                                ov_cap,
                                d_over, d_long + 1, reinterpret_cast<int32_t *>(trow->p),
                                reinterpret_cast<double *>(tval->p), d_status, s));
@@ -618,20 +619,21 @@ spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bo
     const uint64_t own = (uint64_t)(nc + 1) * 4 + (uint64_t)nnz * 12;
     if (!want_ell && cap_ccs && own > cap_ccs) return SPMV_ERR_MEMORY_CAP;
     // The slot paths need >= 8 entries per column on average (slot array at
-    // most 4x the pairs array); SPMVAT_PHASE1 = "scatter" | "kslot" | "rv" | "grp"
+    // most 4x the pairs array); SPMVAT_PHASE1 = "scatter" | "kslot" | "rk" | "grp"
     // forces a path (tests and measurements).
     const char *force = getenv("SPMVAT_PHASE1");
     const bool dense_cols = (int64_t)col_slot_cap() * nc <= 4 * nnz && nnz > 0;
     // the row-value fix-ups pack (row << 5 | slot) into 32 bits
     const bool rv_ok = A->n_rows < (1 << 27) - 1;
-    P1 mode = dense_cols ? (rv_ok ? P1::RV : P1::KSLOT) : P1::COUNT;
-    if (mode == P1::RV && !force) {
+    P1 mode = dense_cols ? (rv_ok ? P1::RK : P1::KSLOT) : P1::COUNT;
+    if (mode == P1::RK && !force) {
         // Where a row's neighbouring entries have neighbouring columns (banded
-        // and stencil matrices), the per-column slots of the row-value path
-        // receive their stores in shared sectors; where columns are scattered,
-        // the grouped path's compact group regions and coalesced runs win
-        // (measured: 27-point stencil 1.03 vs 1.16 ms, power law with random
-        // columns 3.29 vs 2.73 ms). A sample of 4096 neighbouring pairs decides.
+        // and stencil matrices), the per-column slots of the row-position path
+        // receive their stores in shared sectors and its VAL gathers stay
+        // local; where columns are scattered, the grouped path's compact group
+        // regions and coalesced runs win (measured: 27-point stencil 0.92 vs
+        // 1.16 ms, power law with random columns 3.29 (row-value slots) vs
+        // 2.73 ms). A sample of 4096 neighbouring pairs decides.
         BufPtr lw;
         CKS(alloc_buf(16, s, &lw));
         CK(cudaMemsetAsync(lw->p, 0, 16, s));
@@ -643,7 +645,7 @@ spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bo
     }
     if (force && !strcmp(force, "scatter")) mode = P1::COUNT;
     if (force && !strcmp(force, "kslot") && nnz > 0) mode = P1::KSLOT;
-    if (force && !strcmp(force, "rv") && nnz > 0 && rv_ok) mode = P1::RV;
+    if (force && !strcmp(force, "rk") && nnz > 0 && rv_ok) mode = P1::RK;
     if (force && !strcmp(force, "grp") && nnz > 0 && rv_ok) mode = P1::GRP;
     spmv_status st = phase1_try(A, cap_ell_col, want_ell, mode, M, s, irp_status);
     if (st == kRedo) st = phase1_try(A, cap_ell_col, want_ell, P1::KSLOT, M, s, irp_status);

@@ -196,15 +196,16 @@ cudaError_t launch_col_claim(const int32_t *irp, int32_t n_rows, const int32_t *
 cudaError_t launch_col_fixup_slots(const int32_t *cp, int32_t n_cols, const int32_t *irp, int32_t n_rows,
                                    const double *val, const int2 *T, int2 *pairs, const int32_t *long_list,
                                    int32_t *keys_tmp, int32_t *trow, double *tval, cudaStream_t s);
-// Row-value slot path of Phase I (no repeated (i, j) entries, columns of at
-// most col_rv_long_cap() entries, at most `ov_cap` entries beyond the slots;
-// otherwise ST_REDO; rows below 2^27 - 1). `slots`: col_rv_slot_bytes(n_cols) bytes.
-size_t col_rv_slot_bytes(int32_t n_cols);
+// Row-position slot path of Phase I (no repeated (i, j) entries, columns of
+// at most col_rv_long_cap() entries, at most `ov_cap` entries beyond the
+// slots; otherwise ST_REDO; rows below 2^27 - 1). `slots`:
+// col_rk_slot_bytes(n_cols) bytes of {k, row} records.
+size_t col_rk_slot_bytes(int32_t n_cols);
 int col_rv_long_cap();
-cudaError_t launch_col_claim_rv(const int32_t *irp, int32_t n_rows, const int32_t *icol, const double *val,
-                                int64_t nnz, int32_t n_cols, int32_t *nc, void *slots, int4 *ov,
-                                int64_t ov_cap, int32_t *n_ov, int32_t *scratch, int *status, cudaStream_t s);
-cudaError_t launch_col_fixup_rv(const int32_t *cp, int32_t n_cols, int32_t n_rows, const double *val,
+cudaError_t launch_col_claim_rk(const int32_t *irp, int32_t n_rows, const int32_t *icol, int64_t nnz, int32_t n_cols,
+                                int32_t *nc, void *slots, int4 *ov, int64_t ov_cap, int32_t *n_ov, int32_t *scratch,
+                                int *status, cudaStream_t s);
+cudaError_t launch_col_fixup_rk(const int32_t *cp, int32_t n_cols, int32_t n_rows, const double *val,
                                 const void *slots, const int4 *ov, int64_t ov_cap, const int32_t *n_ov,
                                 const int32_t *long_list, int32_t *trow, double *tval, int *status, cudaStream_t s);
 // Grouped row-value path of Phase I: records in regions of 64-column groups

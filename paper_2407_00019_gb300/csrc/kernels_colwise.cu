@@ -777,48 +777,38 @@ cudaError_t launch_col_fixup(const int32_t *cp, int32_t n_cols, const int32_t *i
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------- row-value slot path
-// The slot path above carries (k, row) through the slot array, so its fix-up
-// gathers VAL[k] at scattered addresses. When no (i, j) pair repeats, the row
-// alone orders a column (the serial scatter lists a column's rows in
-// ascending order), so the slots can carry the row and the value instead:
-//   k_col_claim_rv  : r = atomicAdd(NC[j], 1); slot (r, j) = (i, VAL[k]) for
-//                     r < SLOT_CAP (VAL read once, coalesced); entries with
-//                     r >= SLOT_CAP become records {k, i, j, r} in a compact list.
+// ---------------------------------------------------- row-position slot path
+// The slot path above keeps a rank per entry, stores it, and sorts each
+// column of its slots with a warp-wide network. When no (i, j) pair repeats,
+// the row alone orders a column (the serial scatter lists a column's rows in
+// ascending order), so a per-thread register network over (row, slot) keys
+// does the sort, and no rank array is needed:
+//   k_col_claim_rk  : r = atomicAdd(NC[j], 1); slot (r, j) = {k, i} (8 bytes)
+//                     for r < SLOT_CAP, reading only ICOL (and IRP for the
+//                     rows); entries with r >= SLOT_CAP become records
+//                     {k, i, j, r} in a compact list.
 //   k_fixup_net     : one thread per column sorts the column's slots by row
-//                     with a register sorting network; rows and values are
-//                     written contiguously per CTA. Slots of longer columns go
-//                     straight to IRP_T[j] + r.
+//                     with a register sorting network; rows and VAL[k] are
+//                     written contiguously per CTA. The gathers of VAL stay
+//                     local where this path is chosen (neighbouring columns:
+//                     a tile's columns take their entries from the same rows).
+//                     Slots of longer columns go straight to IRP_T[j] + r.
 //   k_ov_place_rv   : list records to IRP_T[j] + r (value gathered from VAL[k]).
-//   k_fixup_long_rv : columns of 33..RV_LONG_CAP entries sorted in place by row
-//                     (CTA bitonic network on (row, position) keys).
+//   k_fixup_long_rv : columns of 33..RV_LONG_CAP entries sorted in place by
+//                     row (CTA bitonic network on (row, position) keys).
 // A repeated row within a column, a longer column or a full record list sets
 // ST_REDO; the host then rebuilds the CCS on the (k, row) slot path.
-// Slot (r, j) is one 16-byte record {row, value} at r * n_cols + j, so an
-// entry costs one store in the claim and one load in the fix-up.
 constexpr int RV_LONG_CAP = 4096;
 
+// {row, value} records of the grouped path below (pad: column within the group)
 struct __align__(16) RowVal {
     int32_t row;
     int32_t pad;
     double v;
 };
 
-size_t col_rv_slot_bytes(int32_t n_cols) { return (size_t)SLOT_CAP * (size_t)n_cols * sizeof(RowVal); }
+size_t col_rk_slot_bytes(int32_t n_cols) { return (size_t)SLOT_CAP * (size_t)n_cols * sizeof(int2); }
 int col_rv_long_cap() { return RV_LONG_CAP; }
-
-__device__ __forceinline__ void slot_put(RowVal *slots, long long at, int row, double v) {
-    RowVal q;
-    q.row = row;
-    q.pad = 0;
-    q.v = v;
-    slots[at] = q;
-}
-__device__ __forceinline__ void slot_get(const RowVal *slots, long long at, int &row, double &v) {
-    const int4 q = __ldcs(reinterpret_cast<const int4 *>(slots) + at);
-    row = q.x;
-    v = __hiloint2double(q.w, q.z);
-}
 
 // Thread-striped items (item u of thread t is entry k0 + 256 u + t): one
 // warp instruction covers 32 consecutive entries, so a row's neighbouring
@@ -830,12 +820,11 @@ __device__ __forceinline__ void slot_get(const RowVal *slots, long long at, int 
 // the same time, so the fix-up sorts every column.
 __device__ __forceinline__ int pad32(int e) { return e + (e >> 5); }
 
-__global__ void __launch_bounds__(SCT_THREADS) k_col_claim_rv(const int32_t *__restrict__ irp, int32_t n_rows,
+__global__ void __launch_bounds__(SCT_THREADS) k_col_claim_rk(const int32_t *__restrict__ irp, int32_t n_rows,
                                                                const int32_t *__restrict__ icol,
-                                                               const double *__restrict__ val, int64_t nnz,
-                                                               int32_t n_cols, int32_t *__restrict__ nc,
+                                                               int64_t nnz, int32_t n_cols, int32_t *__restrict__ nc,
                                                                const int32_t *__restrict__ tl, long long n_tiles,
-                                                               RowVal *__restrict__ slots, int4 *__restrict__ ov,
+                                                               int2 *__restrict__ slots, int4 *__restrict__ ov,
                                                                long long ov_cap, int32_t *__restrict__ n_ov,
                                                                int *status) {
     __shared__ int32_t s_ptr[SCT_WIN];
@@ -845,16 +834,10 @@ __global__ void __launch_bounds__(SCT_THREADS) k_col_claim_rv(const int32_t *__r
     const int wbase = (int)threadIdx.x;
     constexpr int USTEP = SCT_THREADS;
     int c[SCT_ITEMS];
-    double v[SCT_ITEMS];
 #pragma unroll
     for (int u = 0; u < SCT_ITEMS; ++u) {
         const long long k = k0 + wbase + USTEP * u;
         c[u] = (k < k1) ? __ldcs(icol + k) : -1;
-    }
-#pragma unroll
-    for (int u = 0; u < SCT_ITEMS; ++u) {
-        const long long k = k0 + wbase + USTEP * u;
-        v[u] = (k < k1) ? __ldcs(val + k) : 0.0;
     }
     int r[SCT_ITEMS];
     int bad = 0;
@@ -893,7 +876,7 @@ __global__ void __launch_bounds__(SCT_THREADS) k_col_claim_rv(const int32_t *__r
         if (r[u] < 0) continue;
         const int row = s_row[pad32(e)];
         if (r[u] < SLOT_CAP) {
-            slot_put(slots, (long long)r[u] * n_cols + c[u], row, v[u]);
+            slots[(long long)r[u] * n_cols + c[u]] = make_int2((int)(k0 + e), row);
         } else {
             const int q = atomicAdd(n_ov, 1);
             if (q < ov_cap) ov[q] = make_int4((int)(k0 + e), row, c[u], r[u]);
@@ -904,17 +887,16 @@ __global__ void __launch_bounds__(SCT_THREADS) k_col_claim_rv(const int32_t *__r
     if (__any_sync(0xffffffffu, bad) && lane_id() == 0) atomicOr(status, ST_BAD_INDEX);
 }
 
-cudaError_t launch_col_claim_rv(const int32_t *irp, int32_t n_rows, const int32_t *icol, const double *val,
-                                int64_t nnz, int32_t n_cols, int32_t *nc, void *slots, int4 *ov,
+cudaError_t launch_col_claim_rk(const int32_t *irp, int32_t n_rows, const int32_t *icol, int64_t nnz, int32_t n_cols,
+                                int32_t *nc, void *slots, int4 *ov,
                                 int64_t ov_cap, int32_t *n_ov, int32_t *scratch, int *status, cudaStream_t s) {
     if (nnz <= 0) return cudaSuccess;
     cudaError_t e = launch_tile_lines(irp, n_rows, nnz, SCT_TILE, scratch, s);
     if (e != cudaSuccess) return e;
     const long long n_tiles = (nnz + SCT_TILE - 1) / SCT_TILE;
-    KernelScope ks("col_claim_rv", s);
-    k_col_claim_rv<<<(unsigned)n_tiles, SCT_THREADS, 0, s>>>(irp, n_rows, icol, val, nnz, n_cols, nc, scratch, n_tiles,
-                                                              reinterpret_cast<RowVal *>(slots), ov, ov_cap, n_ov,
-                                                              status);
+    KernelScope ks("col_claim_rk", s);
+    k_col_claim_rk<<<(unsigned)n_tiles, SCT_THREADS, 0, s>>>(irp, n_rows, icol, nnz, n_cols, nc, scratch, n_tiles,
+                                                              reinterpret_cast<int2 *>(slots), ov, ov_cap, n_ov, status);
     return cudaGetLastError();
 }
 
@@ -963,9 +945,10 @@ __device__ __forceinline__ void net_sort(uint32_t (&key)[SLOT_CAP]) {
 constexpr int FN_COLS = 128;
 
 __global__ void __launch_bounds__(FN_COLS) k_fixup_net(const int32_t *__restrict__ cp, int32_t n_cols,
-                                                        const RowVal *__restrict__ slots, int32_t *__restrict__ trow,
+                                                        const int2 *__restrict__ slots, const double *__restrict__ val,
+                                                        int32_t *__restrict__ trow,
                                                         double *__restrict__ tval, int *status) {
-    __shared__ double s_val[SLOT_CAP][FN_COLS + 1];
+    __shared__ int32_t s_k[SLOT_CAP][FN_COLS + 1];  // the slots' CRS positions
     __shared__ uint32_t s_key[FN_COLS * SLOT_CAP];
     __shared__ uint8_t s_col[FN_COLS * SLOT_CAP];
     __shared__ int32_t s_cp[FN_COLS + 1];
@@ -1009,11 +992,9 @@ __global__ void __launch_bounds__(FN_COLS) k_fixup_net(const int32_t *__restrict
     if (!shortc) {
         // slots of a long column go to its place in the CCS; k_fixup_long_rv sorts it
         for (int r = 0; r < SLOT_CAP; ++r) {
-            int row;
-            double v;
-            slot_get(slots, (long long)r * n_cols + at0, row, v);
-            trow[(long long)s_cp[t] + r] = row;
-            tval[(long long)s_cp[t] + r] = v;
+            const int2 q = __ldcs(slots + (long long)r * n_cols + at0);
+            trow[(long long)s_cp[t] + r] = q.y;
+            tval[(long long)s_cp[t] + r] = __ldg(val + q.x);
         }
     }
     uint32_t key[SLOT_CAP];
@@ -1022,11 +1003,9 @@ __global__ void __launch_bounds__(FN_COLS) k_fixup_net(const int32_t *__restrict
     for (int r = 0; r < SLOT_CAP; ++r) {
         key[r] = 0xffffffffu;
         if (r < lim) {
-            int row;
-            double v;
-            slot_get(slots, (long long)r * n_cols + at0, row, v);
-            key[r] = ((uint32_t)row << 5) | (uint32_t)r;
-            s_val[r][t] = v;
+            const int2 q = __ldcs(slots + (long long)r * n_cols + at0);
+            s_k[r][t] = q.x;
+            key[r] = ((uint32_t)q.y << 5) | (uint32_t)r;
         }
     }
     if (maxl <= 8) net_sort<8>(key);
@@ -1050,7 +1029,7 @@ __global__ void __launch_bounds__(FN_COLS) k_fixup_net(const int32_t *__restrict
         const int cc = s_col[q];
         const long long pos = (long long)s_cp[cc] + (q - s_off[cc]);
         __stcs(trow + pos, (int32_t)(k >> 5));
-        __stcs(tval + pos, s_val[k & 31u][cc]);
+        __stcs(tval + pos, __ldg(val + s_k[k & 31u][cc]));
     }
 }
 
@@ -1119,19 +1098,19 @@ __global__ void __launch_bounds__(FIX_THREADS) k_fixup_long_rv(const int32_t *__
     }
 }
 
-cudaError_t launch_col_fixup_rv(const int32_t *cp, int32_t n_cols, int32_t n_rows, const double *val,
+cudaError_t launch_col_fixup_rk(const int32_t *cp, int32_t n_cols, int32_t n_rows, const double *val,
                                 const void *slots, const int4 *ov, int64_t ov_cap, const int32_t *n_ov,
                                 const int32_t *long_list, int32_t *trow, double *tval, int *status, cudaStream_t s) {
     if (n_cols <= 0) return cudaSuccess;
     {
-        KernelScope ks("col_fixup_rv", s);
-        k_fixup_net<<<ceil_div_u(n_cols, FN_COLS), FN_COLS, 0, s>>>(cp, n_cols, reinterpret_cast<const RowVal *>(slots),
-                                                                    trow, tval, status);
+        KernelScope ks("col_fixup_rk", s);
+        k_fixup_net<<<ceil_div_u(n_cols, FN_COLS), FN_COLS, 0, s>>>(cp, n_cols, reinterpret_cast<const int2 *>(slots),
+                                                                    val, trow, tval, status);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     {
-        KernelScope ks("col_overflow_rv", s);
+        KernelScope ks("col_overflow_rk", s);
         k_ov_place_rv<<<(unsigned)sm_count() * 2u, 256, 0, s>>>(cp, n_cols, val, ov, ov_cap, n_ov, trow, tval);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -341,8 +341,8 @@ def _ccs_matches_oracle(M, H):
 
 def _claims(L, H):
     """Builds the CCS of H with the kernel profile on; returns the handle and
-    how many claim passes ran (2 = the row-value path handed over to the
-    (k, row) slot path)."""
+    how many claim passes ran (2 = the row-position or grouped path handed
+    over to the (k, row) slot path)."""
     L.spmv_profile_enable(True)
     L.spmv_profile_read(reset=True)
     try:
@@ -350,7 +350,7 @@ def _claims(L, H):
         prof = L.spmv_profile_read(reset=True)
     finally:
         L.spmv_profile_enable(False)
-    return M, sum(prof.get(k, (0, 0.0))[0] for k in ("col_claim_grp", "col_claim_rv", "col_claim"))
+    return M, sum(prof.get(k, (0, 0.0))[0] for k in ("col_claim_grp", "col_claim_rk", "col_claim"))
 
 
 def shuffled_rows(H, seed=3):
@@ -383,14 +383,15 @@ def with_extra_columns(n, mean_len, seed, every):
     return synth.CRS(n, n, irp.astype(np.int32), icol, synth.normal(seed, 5, np.arange(icol.size)))
 
 
-@pytest.mark.parametrize("mode", ["scatter", "kslot", "rv", "grp"])
+@pytest.mark.parametrize("mode", ["scatter", "kslot", "rk", "grp"])
 @pytest.mark.parametrize("name", ["stencil27_24", "powerlaw_60k", "random_duplicates", "dense_column", "wide",
                                   "tall", "all_empty", "one_by_one", "laplace37x23"])
 def test_phase1_paths_bit_exact(monkeypatch, mode, name):
-    """Every Phase I path (count + scatter; (k, row) slots; (row, value)
-    slots, per column or in 64-column group regions, which hand over to the
-    (k, row) slots on repeated entries, full groups or columns over 4096)
-    gives the oracle's CCS bit for bit."""
+    """Every Phase I path (count + scatter; (k, row) slots with ranks;
+    (k, row) slots sorted by row per column; (row, value) records in 64-column
+    group regions; the last two hand over to the first slot path on repeated
+    entries, full groups or columns over 4096) gives the oracle's CCS bit for
+    bit."""
     L = lib()
     monkeypatch.setenv("SPMVAT_PHASE1", mode)
     H = case(name)
@@ -399,10 +400,13 @@ def test_phase1_paths_bit_exact(monkeypatch, mode, name):
     M.close()
 
 
-def test_phase1_row_value_path_on_shuffled_rows():
-    """Columns in arbitrary order within rows: the row-value path orders every
-    column by row (warp networks and the long-column sort both run)."""
+@pytest.mark.parametrize("mode", ["rk", "grp"])
+def test_phase1_register_sort_paths_on_shuffled_rows(monkeypatch, mode):
+    """Columns in arbitrary order within rows: the row-position and grouped
+    paths order every column by row (register networks, overflow records and
+    the long-column sort all run)."""
     L = lib()
+    monkeypatch.setenv("SPMVAT_PHASE1", mode)
     H = shuffled_rows(with_extra_columns(3000, 12, 81, [(5, 3), (9, 40)]))
     M, claims = _claims(L, H)
     assert claims == 1
@@ -410,7 +414,7 @@ def test_phase1_row_value_path_on_shuffled_rows():
     M.close()
 
 
-@pytest.mark.parametrize("name,path", [("stencil27_24", "col_claim_rv"), ("powerlaw_60k", "col_claim_grp"),
+@pytest.mark.parametrize("name,path", [("stencil27_24", "col_claim_rk"), ("powerlaw_60k", "col_claim_grp"),
                                        ("random12", "col_claim_grp")])
 def test_phase1_path_follows_column_locality(name, path):
     """Neighbouring columns (a stencil) keep the per-column slots; scattered
@@ -431,9 +435,9 @@ def test_phase1_path_follows_column_locality(name, path):
 
 
 @pytest.mark.parametrize("kind", ["duplicates", "column_over_4096", "many_beyond_slots"])
-def test_phase1_row_value_path_hands_over(kind):
-    """Matrices the row-value slot path does not cover are rebuilt on the
-    (k, row) slot path, and the result is still the serial CCS."""
+def test_phase1_register_sort_paths_hand_over(kind):
+    """Matrices the grouped and row-position paths do not cover are rebuilt on
+    the (k, row) slot path, and the result is still the serial CCS."""
     L = lib()
     if kind == "duplicates":
         H = synth.random_crs(3001, 2999, 12, seed=82, dup=True)
@@ -456,6 +460,6 @@ def test_phase1_slot_path_with_long_columns():
     H = with_extra_columns(n, 12, 71, [(5, 3), (9, 40)])  # column 5: 1000 entries, column 9: 75
     assert 32 * n <= 4 * H.nnz  # the slot path is taken
     M, claims = _claims(L, H)
-    assert claims == 1  # the row-value path covers columns of up to 4096 entries
+    assert claims == 1  # the register-sort paths cover columns of up to 4096 entries
     _ccs_matches_oracle(M, H)
     M.close()
