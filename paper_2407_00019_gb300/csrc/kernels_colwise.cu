@@ -943,6 +943,7 @@ __device__ __forceinline__ void net_sort(uint32_t (&key)[SLOT_CAP]) {
 // instructions where a warp-wide network would spend 15 shuffle stages on one
 // column. Needs n_rows < 2^27 - 1 (the host checks); repeated rows set ST_REDO.
 constexpr int FN_COLS = 128;
+constexpr int FN_WB = 8;
 
 __global__ void __launch_bounds__(FN_COLS) k_fixup_net(const int32_t *__restrict__ cp, int32_t n_cols,
                                                         const int2 *__restrict__ slots, const double *__restrict__ val,
@@ -1023,13 +1024,34 @@ __global__ void __launch_bounds__(FN_COLS) k_fixup_net(const int32_t *__restrict
     if (dup) s_redo = 1;
     __syncthreads();
     if (t == 0 && s_redo) atomicOr(status, ST_REDO);
+    // write-out: FN_WB entries per thread per round, their VAL gathers issued
+    // together before any store
     const int ns = s_off[FN_COLS];
-    for (int q = t; q < ns; q += FN_COLS) {
-        const uint32_t k = s_key[q];
-        const int cc = s_col[q];
-        const long long pos = (long long)s_cp[cc] + (q - s_off[cc]);
-        __stcs(trow + pos, (int32_t)(k >> 5));
-        __stcs(tval + pos, __ldg(val + s_k[k & 31u][cc]));
+    for (int q0 = t; q0 < ns; q0 += FN_COLS * FN_WB) {
+        long long pos[FN_WB];
+        int32_t rw[FN_WB];
+        double v[FN_WB];
+#pragma unroll
+        for (int u = 0; u < FN_WB; ++u) {
+            const int q = q0 + u * FN_COLS;
+            pos[u] = -1;
+            rw[u] = 0;
+            v[u] = 0.0;
+            if (q < ns) {
+                const uint32_t k = s_key[q];
+                const int cc = s_col[q];
+                pos[u] = (long long)s_cp[cc] + (q - s_off[cc]);
+                rw[u] = (int32_t)(k >> 5);
+                v[u] = __ldg(val + s_k[k & 31u][cc]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < FN_WB; ++u) {
+            if (pos[u] >= 0) {
+                __stcs(trow + pos[u], rw[u]);
+                __stcs(tval + pos[u], v[u]);
+            }
+        }
     }
 }
 
