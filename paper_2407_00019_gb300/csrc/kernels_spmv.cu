@@ -296,6 +296,30 @@ cudaError_t launch_spmv_crs_tile(int S, const int32_t *irp, const int32_t *icol,
 // fixed order.
 constexpr int CRS_ROWS_R = 128;
 
+// One thread's share of a staged row: entries k0, k0 + SPLIT, ... below e,
+// FMA chain in that order; the x gathers of up to eight entries are issued
+// together before their FMAs (a 27-entry row at SPLIT = 4 waits for one
+// gather latency instead of four).
+template <int SPLIT>
+__device__ __forceinline__ double staged_row_dot(const double *s_v, const int32_t *s_c, int k0, int e,
+                                                 const double *__restrict__ x) {
+    double acc = 0.0;
+    for (; k0 < e; k0 += 8 * SPLIT) {
+        double xv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + u * SPLIT;
+            xv[u] = (k < e) ? __ldg(x + s_c[k]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + u * SPLIT;
+            if (k < e) acc = fma(s_v[k], xv[u], acc);
+        }
+    }
+    return acc;
+}
+
 template <int SPLIT>
 __global__ void __launch_bounds__(CRS_ROWS_R *SPLIT) k_spmv_crs_rows(const int32_t *__restrict__ irp,
                                                                      const int32_t *__restrict__ icol,
@@ -341,16 +365,7 @@ __global__ void __launch_bounds__(CRS_ROWS_R *SPLIT) k_spmv_crs_rows(const int32
     if (r < nr) {
         const int s = s_ptr[r] - e0, e = s_ptr[r + 1] - e0;
         if (staged) {
-            int k = s + part;
-            for (; k + 3 * SPLIT < e; k += 4 * SPLIT) {
-                const int c0 = s_c[k], c1 = s_c[k + SPLIT], c2 = s_c[k + 2 * SPLIT], c3 = s_c[k + 3 * SPLIT];
-                const double x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
-                acc = fma(s_v[k], x0, acc);
-                acc = fma(s_v[k + SPLIT], x1, acc);
-                acc = fma(s_v[k + 2 * SPLIT], x2, acc);
-                acc = fma(s_v[k + 3 * SPLIT], x3, acc);
-            }
-            for (; k < e; k += SPLIT) acc = fma(s_v[k], __ldg(x + s_c[k]), acc);
+            acc = staged_row_dot<SPLIT>(s_v, s_c, s + part, e, x);
         } else {
             for (int k = e0 + s + part; k < e0 + e; k += SPLIT)
                 acc = fma(__ldcs(val + k), __ldg(x + __ldcs(icol + k)), acc);
@@ -881,16 +896,7 @@ __global__ void __launch_bounds__(COO_ROWS_R *SPLIT) k_coo_row_rows(const int32_
     double acc = 0.0;
     if (r < nr) {
         const int s = s_ptr[r], e = s_ptr[r + 1];
-        int k = s + part;
-        for (; k + 3 * SPLIT < e; k += 4 * SPLIT) {
-            const int c0 = s_c[k], c1 = s_c[k + SPLIT], c2 = s_c[k + 2 * SPLIT], c3 = s_c[k + 3 * SPLIT];
-            const double x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
-            acc = fma(s_v[k], x0, acc);
-            acc = fma(s_v[k + SPLIT], x1, acc);
-            acc = fma(s_v[k + 2 * SPLIT], x2, acc);
-            acc = fma(s_v[k + 3 * SPLIT], x3, acc);
-        }
-        for (; k < e; k += SPLIT) acc = fma(s_v[k], __ldg(x + s_c[k]), acc);
+        acc = staged_row_dot<SPLIT>(s_v, s_c, s + part, e, x);
     }
     if (SPLIT > 1) {
         if (part > 0) s_part[(part - 1) * R + r] = acc;
