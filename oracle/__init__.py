@@ -42,8 +42,10 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = ctypes.CDLL(_LIB)
+            # SPMVAT_ORACLE_LIB: another build of this file's C source (the
+            # planted-mistake tests point it at a mutated copy)
+            path = os.environ.get("SPMVAT_ORACLE_LIB") or build()
+            L = ctypes.CDLL(path)
             L.orc_analyze.argtypes = [ctypes.c_int32, _i32p, _dptr, _dptr, _dptr, _iptr]
             L.orc_crs_to_coo_row.argtypes = [ctypes.c_int32, _i32p, _i32p]
             L.orc_lines_to_ell.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, ctypes.c_int32, _f64p, _i32p]

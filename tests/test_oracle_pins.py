@@ -360,6 +360,8 @@ def test_dstar_rules_on_hand_built_points():
     assert oracle.dstar_from_points(d, [2.0] * 5, 1.0, 0) == math.inf
     assert oracle.dstar_from_points(d, [0.5, 2, 2, 2, 2], 1.0, 0) == 0.0
     assert oracle.dstar_from_points(d, [0.5] * 5, 1.0, 1) == 0.0
-    # c is the threshold: R exactly c passes
+    # c is the threshold: R exactly c passes (R_ell >= c is advantageous, Sec. 2.2), under both rules
     assert oracle.dstar_from_points([0.1, 0.2], [1.0, 0.999], 1.0, 0) == 0.2
+    assert oracle.dstar_from_points([0.1, 0.2], [1.0, 0.999], 1.0, 1) == 0.1
+    assert oracle.dstar_from_points([0.1, 0.2], [1.5, 1.0], 1.0, 1) == 0.2
     assert oracle.dstar_from_points([], [], 1.0, 0) == math.inf
