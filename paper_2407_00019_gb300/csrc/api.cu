@@ -519,10 +519,10 @@ spmv_status phase1_try(const spmv_crs *A, uint64_t cap_ell_col, bool want_ell, P
     const int64_t nnz = A->nnz;
     const int32_t nc = A->n_cols;
     if (mode == P1::GRP) return phase1_grp(A, cap_ell_col, want_ell, M, s, irp_status);
-    const bool rv = mode == P1::RK, slots = mode != P1::COUNT;
+    const bool rk = mode == P1::RK, slots = mode != P1::COUNT;
     BufPtr cp, trow, tval, rank, pairs, scan_scr, words, longl, tslots, sct0, ovl;
     CKS(alloc_buf((size_t)(nc + 1) * 4, s, &cp));
-    if (!rv) CKS(alloc_buf((size_t)nnz * 4, s, &rank));
+    if (!rk) CKS(alloc_buf((size_t)nnz * 4, s, &rank));
     CKS(alloc_buf(scan_scratch_bytes(nc), s, &scan_scr));
     CKS(alloc_buf(64, s, &words));  // [0] status [1] colmax [2] entries beyond the slots
     const int64_t max_long = std::min<int64_t>(nc, nnz / 33 + 1);
@@ -536,7 +536,7 @@ spmv_status phase1_try(const spmv_crs *A, uint64_t cap_ell_col, bool want_ell, P
     CK(cudaMemsetAsync(words->p, 0, 64, s));
     CK(cudaMemsetAsync(d_long, 0, 4, s));
     const int64_t ov_cap = nnz / 8 + 1024;
-    if (rv) {
+    if (rk) {
         CKS(alloc_buf(col_rk_slot_bytes(nc), s, &tslots));
         CKS(alloc_buf(col_scatter_scratch_bytes(nnz), s, &sct0));
         CKS(alloc_buf((size_t)ov_cap * sizeof(int4), s, &ovl));
@@ -567,7 +567,7 @@ spmv_status phase1_try(const spmv_crs *A, uint64_t cap_ell_col, bool want_ell, P
     }
     CKS(alloc_buf((size_t)nnz * 4, s, &trow));
     CKS(alloc_buf((size_t)nnz * 8, s, &tval));
-    if (rv) {
+    if (rk) {
         CK(launch_col_fixup_rk(d_cp, nc, A->n_rows, A->val, tslots->p, reinterpret_cast<const int4 *>(ovl->p),
                                ov_cap,
                                d_over, d_long + 1, reinterpret_cast<int32_t *>(trow->p),
@@ -623,15 +623,16 @@ spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bo
     // forces a path (tests and measurements).
     const char *force = getenv("SPMVAT_PHASE1");
     const bool dense_cols = (int64_t)col_slot_cap() * nc <= 4 * nnz && nnz > 0;
-    // the row-value fix-ups pack (row << 5 | slot) into 32 bits
-    const bool rv_ok = A->n_rows < (1 << 27) - 1;
-    P1 mode = dense_cols ? (rv_ok ? P1::RK : P1::KSLOT) : P1::COUNT;
+    // the register-sort fix-ups (row-position and grouped paths) pack
+    // (row << 5 | slot) into 32 bits
+    const bool key_ok = A->n_rows < (1 << 27) - 1;
+    P1 mode = dense_cols ? (key_ok ? P1::RK : P1::KSLOT) : P1::COUNT;
     if (mode == P1::RK && !force) {
         // Where a row's neighbouring entries have neighbouring columns (banded
         // and stencil matrices), the per-column slots of the row-position path
         // receive their stores in shared sectors and its VAL gathers stay
         // local; where columns are scattered, the grouped path's compact group
-        // regions and coalesced runs win (measured: 27-point stencil 0.92 vs
+        // regions and coalesced runs win (measured: 27-point stencil 0.74 vs
         // 1.16 ms, power law with random columns 3.29 (row-value slots) vs
         // 2.73 ms). A sample of 4096 neighbouring pairs decides.
         BufPtr lw;
@@ -645,8 +646,8 @@ spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bo
     }
     if (force && !strcmp(force, "scatter")) mode = P1::COUNT;
     if (force && !strcmp(force, "kslot") && nnz > 0) mode = P1::KSLOT;
-    if (force && !strcmp(force, "rk") && nnz > 0 && rv_ok) mode = P1::RK;
-    if (force && !strcmp(force, "grp") && nnz > 0 && rv_ok) mode = P1::GRP;
+    if (force && !strcmp(force, "rk") && nnz > 0 && key_ok) mode = P1::RK;
+    if (force && !strcmp(force, "grp") && nnz > 0 && key_ok) mode = P1::GRP;
     spmv_status st = phase1_try(A, cap_ell_col, want_ell, mode, M, s, irp_status);
     if (st == kRedo) st = phase1_try(A, cap_ell_col, want_ell, P1::KSLOT, M, s, irp_status);
     return st;

@@ -41,7 +41,7 @@ def _worker(rank, world, port, out):
 def test_two_rank_timing_reduction_and_replicas():
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()  # no fork of a multi-threaded process
     out = mgr.dict()
     mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
     t0, b0, v0, n0, x0 = out[0]
