@@ -393,6 +393,19 @@ def oracle_bytes(H, W, Wc, ell: bool = True) -> float:
     return float(sum(bm[k] for k in keys))
 
 
+def workload_config(name: str, w: dict, H, W: int, Wc: int, dmat: float, world: int) -> dict:
+    """The workload keys of the JSON line, the same for the native and the
+    reference arm: the matrix, its ELL widths, D_mat and the step's
+    algorithmic bytes (ELL-Row left out when its bytes exceed the cap, as the
+    step does)."""
+    bm = byte_model(H.n_rows, H.n_cols, H.nnz, W, Wc)
+    if w["cap"] and 12 * round32(H.n_rows) * W > w["cap"]:
+        bm.pop("crs_to_ell_row")
+        bm.pop("spmv_ell_row")
+    return {"workload": name, "desc": w["desc"], "n": H.n_rows, "nnz": H.nnz, "W": W, "W_col": Wc,
+            "D_mat": dmat, "step_bytes": float(sum(bm.values())), "parallelism": f"replicas x{world}"}
+
+
 def cpu_baseline(H, xh, budget_s: float = 12.0, cap: int = 0) -> dict:
     """Times the oracle on a bounded row sample of the workload."""
     frac = 4
@@ -412,6 +425,8 @@ def cpu_baseline(H, xh, budget_s: float = 12.0, cap: int = 0) -> dict:
 
 # -------------------------------------------------------------- reference
 def run_reference(args, w: dict) -> None:
+    import numpy as np
+    import oracle
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -431,8 +446,11 @@ def run_reference(args, w: dict) -> None:
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "sample_rows": rows, "sample_nnz": S.nnz, "n": H.n_rows,
-                   "nnz": H.nnz},
+        "config": {**workload_config(args.workload, w, H, int(np.diff(H.irp).max(initial=0)),
+                                     int(np.bincount(H.icol, minlength=H.n_cols).max(initial=0)),
+                                     oracle.analyze(H.n_rows, H.irp)["dmat"], world),
+                   "sample_rows": rows, "sample_nnz": S.nnz,
+                   "l2": "CPU oracle on the host cores (no GPU, no L2 flush)"},
         "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
                          "sample": f"rows 0..{rows} of {H.n_rows} per step, single-thread FP64 oracle"},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -1087,14 +1105,14 @@ def main():
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": w["desc"], "n": H.n_rows, "nnz": H.nnz, "W": W,
-                       "W_col": Wc, "D_mat": stats["dmat"], "step_bytes": step_bytes,
+            "config": {**workload_config(args.workload, w, H, W, Wc, stats["dmat"], world),
+                       "step_bytes": step_bytes,
                        "l2": ("inputs larger than L2 (CRS %.0f MB vs 129 MB L2); no flush" % (
                            (12 * H.nnz + 4 * H.n_rows) / 1e6)) if flush is None else
                              ("inputs smaller than L2 (step %.2f MB): L2 flushed by a %d MB write before each "
                               "timed step, outside its events; 'warm' has back-to-back steps" % (
                                   step_bytes / 1e6, 2 * L2_BYTES // 2 ** 20)),
-                       "parallelism": f"replicas x{world}", "launches_before_timed": int(launches0),
+                       "launches_before_timed": int(launches0),
                        "step_schedule": "sequential" if args.sequential else
                        "independent pipelines (AT+CRS+ELL-Row, COO-Row, Phase I then Phase II | CCS->ELL-Col) on four streams",
                        "per_kernel": f"{PROFILE_STEPS} sequential steps after the timed region"},

@@ -87,3 +87,36 @@ def test_oracle_leg_leaves_out_ell_beyond_the_cap(bench):
     b_cap = bench.oracle_bytes(H, t_cap["_W"], t_cap["_Wc"], False)
     bm = bench.byte_model(H.n_rows, H.n_cols, H.nnz, t_all["_W"], t_all["_Wc"])
     assert np.isclose(b_all - b_cap, bm["crs_to_ell_row"] + bm["spmv_ell_row"])
+
+
+def test_reference_arm_runs_the_oracle_on_the_native_workload_keys():
+    """`bench.py --impl reference` (the oracle on the host cores) prints one
+    line whose workload keys are those of the native arm, here with the 64x64
+    Laplacian's closed forms (n 4096, nnz 20224, W 5, D_mat 0.0498355)."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "laplace2d_64", "--steps", "2", "--warmup", "3"], capture_output=True, text=True,
+                       timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    c = d["config"]
+    assert d["impl"] == "reference" and d["value"] > 0 and d["gpu_launches"] == 0
+    assert (c["workload"], c["n"], c["nnz"], c["W"], c["W_col"]) == ("laplace2d_64", 4096, 20224, 5, 5)
+    assert abs(c["D_mat"] - 0.0498355) < 1e-7
+    assert c["step_bytes"] == 3675168.0
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_workload_config_leaves_out_ell_beyond_the_cap(bench):
+    """Under a cap the step builds no ELL-Row, and its step bytes say so."""
+    H = synth.power_law(3000, kmax=2000, seed=3)
+    W = int(np.diff(H.irp).max())
+    Wc = int(np.bincount(H.icol, minlength=H.n_cols).max())
+    bm = bench.byte_model(H.n_rows, H.n_cols, H.nnz, W, Wc)
+    free = bench.workload_config("t", {"cap": 0, "desc": ""}, H, W, Wc, 1.0, 1)
+    capped = bench.workload_config("t", {"cap": 12 * H.n_rows * 10, "desc": ""}, H, W, Wc, 1.0, 1)
+    assert free["step_bytes"] == float(sum(bm.values()))
+    assert free["step_bytes"] - capped["step_bytes"] == bm["crs_to_ell_row"] + bm["spmv_ell_row"]
