@@ -120,3 +120,22 @@ def test_workload_config_leaves_out_ell_beyond_the_cap(bench):
     capped = bench.workload_config("t", {"cap": 12 * H.n_rows * 10, "desc": ""}, H, W, Wc, 1.0, 1)
     assert free["step_bytes"] == float(sum(bm.values()))
     assert free["step_bytes"] - capped["step_bytes"] == bm["crs_to_ell_row"] + bm["spmv_ell_row"]
+
+
+def test_stored_traffic_entries_cite_committed_profiles(bench):
+    """Every stored DRAM figure names the ncu summary it comes from, that
+    summary is committed, and the figure is within a factor of two of the
+    kernel's byte model at the workload's size (far above would mean re-reads,
+    far below a capture of the wrong launch)."""
+    import json
+    with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+        entries = json.load(f)
+    sizes = {"stencil27_128": (128 ** 3, 128 ** 3, (3 * 128 - 2) ** 3, 27, 27)}
+    assert entries
+    for e in entries:
+        assert os.path.exists(os.path.join(ROOT, "profiles", e["source"])), e
+        assert len(e["csrc"]) == 16 and e["bytes_per_launch"] > 0
+        if e["workload"] in sizes:
+            n, m, nnz, W, Wc = sizes[e["workload"]]
+            model = bench.kernel_bytes(e["kernel"], bench.byte_model(n, m, nnz, W, Wc), n, m, nnz)
+            assert model and 0.5 < e["bytes_per_launch"] / model < 2.0, (e["kernel"], e["bytes_per_launch"], model)
