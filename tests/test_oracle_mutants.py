@@ -56,7 +56,15 @@ MUTANTS = [
     ("neumaier_sign", "*c += (*sum - s2) + t;", "*c += (*sum - s2) - t;"),
     ("reference_drops_product_error", "            neumaier_add(&s, &c, e);\n", ""),
     ("abs_sum_signed", "neumaier_add(&a, &ca, fabs(p));", "neumaier_add(&a, &ca, p);"),
+    ("reference_drops_compensation", "y_ref[i] = s + c;", "y_ref[i] = s;"),
+    # more Phase I / analysis / ELL slips
+    ("count_sets_instead_of_adds", "cnt[icol[k]] += 1;", "cnt[icol[k]] = 1;"),
+    ("analyze_skips_last_row", "    for (int32_t i = 0; i < n_rows; ++i) {\n        int32_t len = irp[i + 1] - irp[i];",
+     "    for (int32_t i = 0; i < n_rows - 1; ++i) {\n        int32_t len = irp[i + 1] - irp[i];"),
+    ("ell_row_skips_last_slot", "    for (int32_t k = 0; k < width; ++k) {\n        int64_t base = (int64_t)k * n_rows;",
+     "    for (int32_t k = 0; k < width - 1; ++k) {\n        int64_t base = (int64_t)k * n_rows;"),
     # Eqs. (1)-(3) and the D* rule
+    ("sp_inverted", "double sp = t_crs / t_ell;", "double sp = t_ell / t_crs;"),
     ("tt_as_printed", "double tt = t_trans / t_crs;", "double tt = t_crs / t_trans;"),
     ("dstar_fail_inclusive", "if (rell[ord[t]] < c) {", "if (rell[ord[t]] <= c) {"),
     ("dstar_last_passing", "d = (t == 0) ? 0.0 : dmat[ord[t]];", "d = (t == 0) ? 0.0 : dmat[ord[t - 1]];"),
