@@ -88,3 +88,22 @@ def test_argument_errors_need_no_device(lib):
     assert L.spmv_set_allocator(ctypes.c_void_p(1), None, None) == 1
     assert L.spmv_dstar_from_points(-1, None, None, 1.0, 0, None) == 1
     assert L.spmv_debug_scan_timeout(0, 1, None, None) == 1
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """A copy of the Python binding without libspmvat.so raises at load: the
+    product has no CPU path to fall back on."""
+    import shutil
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = tmp_path / "paper_2407_00019_gb300"
+    pkg.mkdir()
+    shutil.copy(os.path.join(root, "paper_2407_00019_gb300", "__init__.py"), pkg / "__init__.py")
+    code = ("import paper_2407_00019_gb300 as L\n"
+            "try:\n    L.load_library()\nexcept ImportError as e:\n    print('raised', e)\n"
+            "else:\n    print('loaded')\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=str(tmp_path), capture_output=True, text=True,
+                       timeout=300, env=dict(os.environ, PYTHONPATH=str(tmp_path)))
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.startswith("raised") and "libspmvat.so is missing" in r.stdout
