@@ -283,7 +283,9 @@ spmv_status spmv_autotune_choose(const spmv_crs *A, const spmv_at_params *p, int
  * array: calls whose work overlaps on one device (several streams or host
  * threads) race on it and must be ordered by the caller. The first call on a
  * device looks up the array's device address (a CUDA runtime query, no
- * allocation); make that first call before any stream capture. */
+ * allocation) and keeps it for the life of the process; make that first call
+ * before any stream capture. A cudaDeviceReset makes the kept address stale:
+ * do not call this entry point on a device after resetting it. */
 #define SPMV_NOALLOC_SCRATCH_BYTES ((1u << 20) + 256u)
 #define SPMV_NOALLOC_COO_MAX_NNZ 134217728ll /* 65536 tiles of 2048 entries, 16 bytes of scratch each */
 spmv_status spmv_apply_coo_row_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *irow,
@@ -442,6 +444,35 @@ spmv_status spmv_server_stats_get(spmv_server *S, spmv_server_stats *out, int32_
 
 /* Drains, stops the worker and frees the cache and the streams. */
 void spmv_server_destroy(spmv_server *S);
+
+/* ---- Schedule hints --------------------------------------------------------
+ * The library chooses every schedule itself from the matrix (row lengths,
+ * column locality, tile sizes). A hint overrides one of those choices for the
+ * whole process, so that a test can run every path on the same matrix and a
+ * measurement can compare paths; every path gives the same transformation
+ * bits and products within the tolerance of a reordered sum. Value 0 restores
+ * the library's own choice; a value a matrix cannot take (for example a slot
+ * path of Phase I on a matrix with no entries) is ignored for that matrix.
+ * Hints are read when a handle or batch is built, not when it is applied.
+ * Not synchronised with calls in flight on other host threads. */
+#define SPMV_HINT_PHASE1 0     /* Phase I path (Sec. 2.1): SPMV_PHASE1_* below */
+#define SPMV_HINT_CRS_SPLIT 1  /* CRS on regular rows: 1, 2, 4 or 8 threads per row of a staged
+                                  128-row tile; -1: V lanes per row without staging */
+#define SPMV_HINT_COO_FLAT 2   /* 1: COO-Row as the entry-split product, COO-Column as one
+                                  atomic add per entry (the paths taken when a tile does not fit) */
+#define SPMV_HINT_BATCH_TPR 3  /* batches: lanes per row of every CRS member, 1, 8 or 32 */
+#define SPMV_HINT_COUNT 4
+#define SPMV_PHASE1_COUNT 1    /* count, prefix sum, scatter of (k, row), per-column sort */
+#define SPMV_PHASE1_KSLOT 2    /* (k, row) slots with ranks */
+#define SPMV_PHASE1_ROWPOS 3   /* {k, row} slots sorted by row in registers */
+#define SPMV_PHASE1_GROUPED 4  /* {row, value} records per 64-column group */
+
+/* Set hint `hint` (SPMV_HINT_*) to `value`; SPMV_ERR_INVALID_ARG for an
+ * unknown hint. */
+spmv_status spmv_set_hint(int32_t hint, int32_t value);
+
+/* Current value of a hint (0 for an unknown one). */
+int32_t spmv_get_hint(int32_t hint);
 
 /* Instrumentation: number of kernels this library has launched so far. */
 uint64_t spmv_launch_count(void);

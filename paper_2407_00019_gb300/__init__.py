@@ -25,6 +25,9 @@ __all__ = [
     "spmv_calibrate", "spmv_autotune", "spmv_autotune_choose", "spmv_apply_coo_row_noalloc", "spmv_launch_count", "spmv_profile_enable", "spmv_profile_read",
     "spmv_debug_scan_timeout", "spmv_batch_create", "spmv_batch_apply", "spmv_batch_info_get",
     "spmv_batch_plan_get", "spmv_batch_destroy", "Batch", "spmv_batch_apply_multi", "Server", "spmv_server_create",
+    "spmv_set_hint", "spmv_get_hint", "hint",
+    "SPMV_HINT_PHASE1", "SPMV_HINT_CRS_SPLIT", "SPMV_HINT_COO_FLAT", "SPMV_HINT_BATCH_TPR",
+    "SPMV_PHASE1_COUNT", "SPMV_PHASE1_KSLOT", "SPMV_PHASE1_ROWPOS", "SPMV_PHASE1_GROUPED",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -34,6 +37,8 @@ SPMV_CRS, SPMV_COO, SPMV_ELL = 0, 1, 2
 SPMV_ROWWISE, SPMV_COLWISE = 0, 1
 SPMV_DSTAR_PREFIX, SPMV_DSTAR_MAXPASS = 0, 1
 SPMV_AT_TRY_COO = 1
+SPMV_HINT_PHASE1, SPMV_HINT_CRS_SPLIT, SPMV_HINT_COO_FLAT, SPMV_HINT_BATCH_TPR = 0, 1, 2, 3
+SPMV_PHASE1_COUNT, SPMV_PHASE1_KSLOT, SPMV_PHASE1_ROWPOS, SPMV_PHASE1_GROUPED = 1, 2, 3, 4
 STATUS_NAMES = {0: "SPMV_OK", 1: "SPMV_ERR_INVALID_ARG", 2: "SPMV_ERR_INVALID_MATRIX", 3: "SPMV_ERR_OOM",
                 4: "SPMV_ERR_MEMORY_CAP", 5: "SPMV_ERR_TIMEOUT", 6: "SPMV_ERR_CUDA", 7: "SPMV_ERR_UNSUPPORTED"}
 
@@ -150,6 +155,8 @@ def load_library():
         "spmv_autotune_choose": (ctypes.c_int, [P(_CrsT), P(_AtParamsT), P(i32), P(i32), P(_StatsT), vp]),
         "spmv_apply_coo_row_noalloc": (ctypes.c_int, [i32, i32, i64, vp, vp, vp, vp, vp, vp]),
         "spmv_launch_count": (u64, []),
+        "spmv_set_hint": (ctypes.c_int, [i32, i32]),
+        "spmv_get_hint": (i32, [i32]),
         "spmv_profile_enable": (ctypes.c_int, [i32]),
         "spmv_profile_read": (i32, [P(_KernelTimeT), i32, i32]),
         "spmv_debug_scan_timeout": (ctypes.c_int, [i32, i32, P(i32), vp]),
@@ -483,12 +490,63 @@ SPMV_NOALLOC_SCRATCH_BYTES = (1 << 20) + 256
 SPMV_NOALLOC_COO_MAX_NNZ = 134217728
 
 
+def _noalloc_check(n_rows: int, n_cols: int, irow, icol, val, x, y) -> int:
+    """Checks the caller's tensors before their raw pointers reach the
+    kernels (which trust sizes and dtypes): returns nnz."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    want = (("irow", irow, torch.int32), ("icol", icol, torch.int32), ("val", val, torch.float64),
+            ("x", x, torch.float64), ("y", y, torch.float64))
+    for name, t, dt in want:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+        if t.dtype != dt:
+            raise TypeError(f"{name} must be {dt}, got {t.dtype}")
+        if t.device != dev:
+            raise ValueError(f"{name} must be on the current CUDA device {dev}, got {t.device}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    nnz = icol.numel()
+    if irow.numel() != nnz or val.numel() != nnz:
+        raise ValueError(f"irow, icol and val must have the same length ({irow.numel()}, {nnz}, {val.numel()})")
+    if x.numel() < n_cols or y.numel() < n_rows:
+        raise ValueError(f"x needs {n_cols} and y {n_rows} elements, got {x.numel()} and {y.numel()}")
+    return nnz
+
+
 def spmv_apply_coo_row_noalloc(n_rows: int, n_cols: int, irow, icol, val, x, y, stream=None) -> None:
     """COO-Row SpMV from caller-owned device tensors, with no device allocation
-    (temporaries in a fixed device array shared by all calls)."""
-    _check(load_library().spmv_apply_coo_row_noalloc(int(n_rows), int(n_cols), int(icol.numel()), _ptr(irow),
+    (temporaries in a fixed device array shared by all calls). The tensors are
+    checked (dtype, device, contiguity, lengths) before the call."""
+    nnz = _noalloc_check(int(n_rows), int(n_cols), irow, icol, val, x, y)
+    _check(load_library().spmv_apply_coo_row_noalloc(int(n_rows), int(n_cols), int(nnz), _ptr(irow),
                                                      _ptr(icol), _ptr(val), _ptr(x), _ptr(y), _stream(stream)),
            "spmv_apply_coo_row_noalloc")
+
+
+def spmv_set_hint(hint: int, value: int) -> None:
+    _check(load_library().spmv_set_hint(int(hint), int(value)), "spmv_set_hint")
+
+
+def spmv_get_hint(hint: int) -> int:
+    return int(load_library().spmv_get_hint(int(hint)))
+
+
+class hint:
+    """Context manager: `with hint(SPMV_HINT_PHASE1, SPMV_PHASE1_GROUPED): ...`
+    forces one schedule choice and restores the previous value on exit."""
+
+    def __init__(self, which: int, value: int):
+        self.which, self.value = int(which), int(value)
+
+    def __enter__(self):
+        self.prev = spmv_get_hint(self.which)
+        spmv_set_hint(self.which, self.value)
+        return self
+
+    def __exit__(self, *exc):
+        spmv_set_hint(self.which, self.prev)
+        return False
 
 
 def spmv_launch_count() -> int:

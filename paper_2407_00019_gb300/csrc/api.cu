@@ -89,6 +89,10 @@ spmv_status status_from_dev(int st) {
     return SPMV_OK;
 }
 
+// Schedule hints (spmv_set_hint): process-wide, 0 = the library's choice.
+static std::atomic<int> g_hints[SPMV_HINT_COUNT];
+int hint_value(int hint) { return (hint >= 0 && hint < SPMV_HINT_COUNT) ? g_hints[hint].load() : 0; }
+
 }  // namespace spmvat
 
 namespace {
@@ -149,7 +153,6 @@ struct spmv_matrix {
     int32_t colmax = 0;            // longest column (handles holding a CCS)
     cudaStream_t home = nullptr;
     // CRS schedule
-    int crs_binned = 0;
     int crs_seg = 0;               // entry-split product (uneven rows)
     const int32_t *seg_tl = nullptr; //    and the tile lines it needs
     int coo_seg = 0;               // COO-Row entry-split product
@@ -159,12 +162,7 @@ struct spmv_matrix {
     const int32_t *coo_tb = nullptr; //    tile bounds
     int crs_rows_split = 0;        // > 0: ELL-order row-tile kernel, threads per row
     int crs_rows_cap = 0;          //      and its shared-memory capacity (entries)
-    int crs_tile_s = 0;            // > 0: row-tile kernel with S lanes per row
-    int crs_stream_s = 0;          // > 0: TMA-staged stream kernel with S lanes per row
-    int crs_stream_r = 0;          //      and R rows per tile
     int *status = nullptr;         // device status word of bounded waits in apply
-    int64_t bin_off[kNumBins + 1] = {};
-    const int32_t *rowlist = nullptr;
     uint64_t owned() const {
         uint64_t t = 0;
         for (auto &b : bufs) t += b->bytes;
@@ -252,17 +250,13 @@ spmv_matrix *new_handle(const spmv_crs *A, int format, int layout, cudaStream_t 
     return M;
 }
 
-// Bins of the CRS schedule from the class histogram (class c: [2^(c-1), 2^c)).
-void bin_counts_from_hist(const spmv_stats &st, int64_t cnt[kNumBins]) {
-    for (int b = 0; b < kNumBins; ++b) cnt[b] = 0;
-    cnt[0] += st.row_len_hist[0];
-    for (int c = 1; c < 32; ++c) {
-        const long long lo = 1ll << (c - 1);
-        cnt[bin_of_len_host((int)std::min<long long>(lo, INT_MAX))] += st.row_len_hist[c];
-    }
+// Lanes per row of the vector CRS kernel (rows too long for a staged tile):
+// half the largest power of two at or below the longest row, 1..32.
+int vector_lanes(int max_len) {
+    int v = 1;
+    while (v < 32 && 2 * (v * 2) <= max_len) v *= 2;
+    return v;
 }
-
-const int kBinV[kNumBins] = {1, 2, 4, 8, 16, 32, 0};
 
 // The column-index check of a CRS whose IRP analyze_core has already checked.
 spmv_status validate_icol(const spmv_crs *A, cudaStream_t s) {
@@ -294,38 +288,20 @@ spmv_status crs_plan_from(const spmv_crs *A, const spmv_stats &st, uint64_t cap,
     M->val = A->val;
     const bool regular = st.dmat <= 0.5 && st.max_row_len < 2048;
     if (regular) {
-        M->crs_binned = 0;
-        M->crs_v = kBinV[std::min(bin_of_len_host(st.max_row_len), 5)];
-        if (M->crs_v < 1) M->crs_v = 1;
-        // Regular rows: the tile kernel, S lanes per row chosen so that a tile
-        // of 256/S rows always fits shared memory. SPMVAT_CRS_KERNEL
-        // (tile | stream | vector) and SPMVAT_CRS_S override the choice for
-        // schedule sweeps.
-        const char *kv = getenv("SPMVAT_CRS_KERNEL");
-        const std::string kind = kv ? kv : "rows";
-        int S = crs_tile_lanes(st.max_row_len);
-        if (const char *ev = getenv("SPMVAT_CRS_S")) S = atoi(ev);
-        const bool s_ok = S == 1 || S == 2 || S == 4 || S == 8;
-        if (kind == "rows" && crs_rows_cap(st.max_row_len) > 0) {
-            int split = st.mu <= 8.0 ? 2 : 4;
-            if (const char *ev = getenv("SPMVAT_CRS_S")) split = atoi(ev);
-            if (split == 1 || split == 2 || split == 4 || split == 8) {
-                M->crs_rows_split = split;
-                M->crs_rows_cap = crs_rows_cap(st.max_row_len);
-            }
-        } else if (kind == "tile" && s_ok && crs_tile_lanes(st.max_row_len) > 0) {
-            M->crs_tile_s = S;
-        } else if (kind == "stream" && s_ok && crs_stream_rows(S, st.max_row_len) > 0) {
-            BufPtr sw;
-            CKS(alloc_buf(16, s, &sw));
-            CK(cudaMemsetAsync(sw->p, 0, 16, s));
-            M->crs_stream_s = S;
-            M->crs_stream_r = crs_stream_rows(S, st.max_row_len);
-            if (const char *rv = getenv("SPMVAT_CRS_R")) M->crs_stream_r = std::min(M->crs_stream_r, atoi(rv));
-            M->status = reinterpret_cast<int *>(sw->p);
-            M->bufs.push_back(sw);
+        // Regular rows: 128-row tiles staged in shared memory with SPLIT
+        // threads per row, or, when a tile of the longest rows would not fit,
+        // V lanes per row. SPMV_HINT_CRS_SPLIT forces SPLIT (or, -1, the
+        // vector kernel) for tests and measurements.
+        const int hint = hint_value(SPMV_HINT_CRS_SPLIT);
+        const int cap = crs_rows_cap(st.max_row_len);
+        int split = st.mu <= 8.0 ? 2 : 4;
+        if (hint == 1 || hint == 2 || hint == 4 || hint == 8) split = hint;
+        M->crs_v = vector_lanes(st.max_row_len);
+        if (cap > 0 && hint >= 0) {
+            M->crs_rows_split = split;
+            M->crs_rows_cap = cap;
         }
-    } else if (!getenv("SPMVAT_CRS_KERNEL") || strcmp(getenv("SPMVAT_CRS_KERNEL"), "binned") != 0) {
+    } else {
         // uneven rows: the entry-split product (same work per thread whatever
         // the row lengths); its tile lines are computed once, here
         BufPtr tl;
@@ -334,27 +310,6 @@ spmv_status crs_plan_from(const spmv_crs *A, const spmv_stats &st, uint64_t cap,
         M->crs_seg = 1;
         M->seg_tl = reinterpret_cast<const int32_t *>(tl->p);
         M->bufs.push_back(tl);
-    } else {
-        const uint64_t need = (uint64_t)A->n_rows * 4;
-        if (cap && need > cap) return SPMV_ERR_MEMORY_CAP;
-        int64_t cnt[kNumBins];
-        bin_counts_from_hist(st, cnt);
-        M->bin_off[0] = 0;
-        for (int b = 0; b < kNumBins; ++b) M->bin_off[b + 1] = M->bin_off[b] + cnt[b];
-        BufPtr rl, scr, stw;
-        CKS(alloc_buf(need, s, &rl));
-        CKS(alloc_buf(bin_scratch_bytes(A->n_rows), s, &scr));
-        CKS(alloc_buf(16, s, &stw));
-        CK(cudaMemsetAsync(stw->p, 0, 16, s));
-        CK(launch_bin_rows(A->irp, A->n_rows, scr->p, reinterpret_cast<int32_t *>(rl->p),
-                           reinterpret_cast<int *>(stw->p), s));
-        int hst = 0;
-        CK(cudaMemcpyAsync(&hst, stw->p, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        CKS(status_from_dev(hst));
-        M->crs_binned = 1;
-        M->rowlist = reinterpret_cast<const int32_t *>(rl->p);
-        M->bufs.push_back(rl);
     }
     *out = M.release();
     return SPMV_OK;
@@ -399,13 +354,12 @@ spmv_status build_coo_row(const spmv_crs *A, uint64_t cap, spmv_matrix **out, cu
         CK(cudaStreamSynchronize(s));
         CKS(status_from_dev(hirp));
         const int cap = coo_rows_cap(h[1]);
-        const char *et = getenv("SPMVAT_COO_ENTRY_TILES");
-        if (cap > 0 && !et) {
+        if (cap > 0 && hint_value(SPMV_HINT_COO_FLAT) != 1) {
             M->coo_rows_cap = cap;
             M->coo_rows_split = ((double)A->nnz / A->n_rows <= 8.0) ? 2 : 4;
             M->coo_tb = reinterpret_cast<const int32_t *>(tb->p);
             M->bufs.push_back(tb);
-        } else if (!et || !strcmp(et, "seg")) {
+        } else {
             M->coo_seg = 1;  // tiles too large for shared memory: entry-split product
         }
     }
@@ -619,9 +573,9 @@ spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bo
     const uint64_t own = (uint64_t)(nc + 1) * 4 + (uint64_t)nnz * 12;
     if (!want_ell && cap_ccs && own > cap_ccs) return SPMV_ERR_MEMORY_CAP;
     // The slot paths need >= 8 entries per column on average (slot array at
-    // most 4x the pairs array); SPMVAT_PHASE1 = "scatter" | "kslot" | "rk" | "grp"
-    // forces a path (tests and measurements).
-    const char *force = getenv("SPMVAT_PHASE1");
+    // most 4x the pairs array); SPMV_HINT_PHASE1 forces a path (tests and
+    // measurements).
+    const int force = hint_value(SPMV_HINT_PHASE1);
     const bool dense_cols = (int64_t)col_slot_cap() * nc <= 4 * nnz && nnz > 0;
     // the register-sort fix-ups (row-position and grouped paths) pack
     // (row << 5 | slot) into 32 bits
@@ -644,10 +598,10 @@ spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bo
         CK(cudaStreamSynchronize(s));
         if (hl < kLocalitySamples / 4) mode = P1::GRP;
     }
-    if (force && !strcmp(force, "scatter")) mode = P1::COUNT;
-    if (force && !strcmp(force, "kslot") && nnz > 0) mode = P1::KSLOT;
-    if (force && !strcmp(force, "rk") && nnz > 0 && key_ok) mode = P1::RK;
-    if (force && !strcmp(force, "grp") && nnz > 0 && key_ok) mode = P1::GRP;
+    if (force == SPMV_PHASE1_COUNT) mode = P1::COUNT;
+    if (force == SPMV_PHASE1_KSLOT && nnz > 0) mode = P1::KSLOT;
+    if (force == SPMV_PHASE1_ROWPOS && nnz > 0 && key_ok) mode = P1::RK;
+    if (force == SPMV_PHASE1_GROUPED && nnz > 0 && key_ok) mode = P1::GRP;
     spmv_status st = phase1_try(A, cap_ell_col, want_ell, mode, M, s, irp_status);
     if (st == kRedo) st = phase1_try(A, cap_ell_col, want_ell, P1::KSLOT, M, s, irp_status);
     return st;
@@ -712,7 +666,7 @@ spmv_status coo_col_from_ccs(const spmv_matrix *src, uint64_t cap, spmv_matrix *
     // SpMV schedule: 128-column tiles when a tile of the longest columns fits
     // shared memory (bounded by the longest column, known here: no sync)
     const int tcap = coo_rows_cap((int)std::min<int64_t>((int64_t)128 * src->colmax, (int64_t)(INT_MAX / 32)));
-    if (src->nnz > 0 && tcap > 0 && !getenv("SPMVAT_COO_ENTRY_TILES")) {
+    if (src->nnz > 0 && tcap > 0 && hint_value(SPMV_HINT_COO_FLAT) != 1) {
         const int64_t tiles = ((int64_t)src->n_cols + 127) / 128;
         BufPtr tb;
         CKS(alloc_buf((size_t)(tiles + 1) * 4, s, &tb));
@@ -737,21 +691,8 @@ spmv_status apply_core(const spmv_matrix *M, const double *x, double *y, cudaStr
                 } else if (M->crs_rows_split > 0) {
                     CK(launch_spmv_crs_rows(M->crs_rows_split, M->crs_rows_cap, M->ptr, M->idx, M->val, M->n_rows,
                                             x, y, s));
-                } else if (M->crs_tile_s > 0) {
-                    CK(launch_spmv_crs_tile(M->crs_tile_s, M->ptr, M->idx, M->val, M->n_rows, x, y, s));
-                } else if (M->crs_stream_s > 0) {
-                    CK(launch_spmv_crs_stream(M->crs_stream_s, M->crs_stream_r, M->ptr, M->idx, M->val, M->n_rows, x,
-                                              y, M->status, s));
-                } else if (!M->crs_binned) {
+                } else if (M->n_rows > 0) {
                     CK(launch_spmv_crs_vector(M->crs_v, M->ptr, M->idx, M->val, nullptr, M->n_rows, x, y, s));
-                } else {
-                    for (int b = 0; b < kNumBins; ++b) {
-                        const int64_t cnt = M->bin_off[b + 1] - M->bin_off[b];
-                        if (cnt <= 0) continue;
-                        const int32_t *rows = M->rowlist + M->bin_off[b];
-                        if (kBinV[b] > 0) CK(launch_spmv_crs_vector(kBinV[b], M->ptr, M->idx, M->val, rows, cnt, x, y, s));
-                        else CK(launch_spmv_crs_block(M->ptr, M->idx, M->val, rows, cnt, x, y, s));
-                    }
                 }
                 return SPMV_OK;
             case SPMV_COO: {
@@ -764,10 +705,8 @@ spmv_status apply_core(const spmv_matrix *M, const double *x, double *y, cudaStr
                     CK(launch_spmv_seg(true, M->idx2, M->idx, M->val, M->nnz, M->n_rows, M->n_cols, nullptr, x, y, s));
                     return SPMV_OK;
                 }
-                BufPtr scr;
-                CKS(alloc_buf(coo_row_scratch_bytes(M->nnz), s, &scr));
-                CK(launch_spmv_coo_row(M->idx2, M->idx, M->val, M->nnz, M->n_rows, M->n_cols, x, y, scr->p,
-                                       M->status, s));
+                // no entries: y = 0
+                CK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)M->n_rows, s));
                 return SPMV_OK;
             }
             case SPMV_ELL:
@@ -1163,6 +1102,14 @@ spmv_status spmv_matrix_status(const spmv_matrix *M, spmv_stream_t stream) {
 }
 
 uint64_t spmv_launch_count(void) { return g_launches.load(); }
+
+spmv_status spmv_set_hint(int32_t hint, int32_t value) {
+    if (hint < 0 || hint >= SPMV_HINT_COUNT) return SPMV_ERR_INVALID_ARG;
+    g_hints[hint].store(value);
+    return SPMV_OK;
+}
+
+int32_t spmv_get_hint(int32_t hint) { return hint_value(hint); }
 
 spmv_status spmv_profile_enable(int32_t on) {
     g_profile_on.store(on ? 1 : 0);

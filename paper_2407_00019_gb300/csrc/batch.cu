@@ -43,10 +43,8 @@ inline int32_t round_up32(int64_t n) { return (int32_t)((n + 31) / 32 * 32); }
 // and 32-row tiles staged through shared memory; rows long enough that one
 // lane would run through hundreds of entries get 8 lanes, or a whole warp.
 int threads_per_row(double mu, int max_len) {
-    if (const char *e = std::getenv("SPMVAT_BATCH_TPR")) {
-        const int v = std::atoi(e);
-        if (v == 1 || v == 8 || v == 32) return v;
-    }
+    const int v = hint_value(SPMV_HINT_BATCH_TPR);
+    if (v == 1 || v == 8 || v == 32) return v;
     if (max_len <= 256 || mu <= 16.0) return 1;
     return mu <= 128.0 ? 8 : 32;
 }

@@ -42,6 +42,7 @@ struct KernelScope {
     cudaStream_t stream;
 };
 int sm_count();  // SMs of the current device (cached)
+int hint_value(int hint);  // spmv_set_hint value (0: the library's choice)
 
 inline unsigned ceil_div_u(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
@@ -238,23 +239,14 @@ cudaError_t launch_spmv_crs_vector(int v, const int32_t *irp, const int32_t *ico
 int crs_rows_cap(int max_row_len);
 cudaError_t launch_spmv_crs_rows(int split, int cap, const int32_t *irp, const int32_t *icol, const double *val,
                                  int32_t n_rows, const double *x, double *y, cudaStream_t s);
-int crs_tile_lanes(int max_row_len);
-cudaError_t launch_spmv_crs_tile(int S, const int32_t *irp, const int32_t *icol, const double *val,
-                                 int32_t n_rows, const double *x, double *y, cudaStream_t s);
-size_t crs_stream_smem_bytes();
-int crs_stream_rows(int S, int max_row_len);
-cudaError_t launch_spmv_crs_stream(int S, int R, const int32_t *irp, const int32_t *icol, const double *val,
-                                   int32_t n_rows, const double *x, double *y, int *status, cudaStream_t s);
-cudaError_t launch_spmv_crs_block(const int32_t *irp, const int32_t *icol, const double *val,
-                                  const int32_t *rows, int64_t count, const double *x, double *y,
-                                  cudaStream_t s);
 cudaError_t launch_spmv_ell_row(const double *eval, const int32_t *eidx, int32_t n_rows, int32_t width,
                                 int32_t ld, const double *x, double *y, cudaStream_t s);
 cudaError_t launch_spmv_ell_col(const double *eval, const int32_t *eidx, int32_t n_rows, int32_t n_cols,
                                 int32_t width, int32_t ld, const double *x, double *y, cudaStream_t s);
+// COO-Row over 2048-entry tiles with a carry pass (the allocation-free entry
+// point). `scratch`: coo_row_scratch_bytes(nnz); `status` may be NULL (then a
+// word inside the scratch is used).
 size_t coo_row_scratch_bytes(int64_t nnz);
-// `scratch`: coo_row_scratch_bytes(nnz); `status` may be NULL (then a word
-// inside the scratch is used).
 cudaError_t launch_spmv_coo_row(const int32_t *irow, const int32_t *icol, const double *val, int64_t nnz,
                                 int32_t n_rows, int32_t n_cols, const double *x, double *y, void *scratch,
                                 int *status, cudaStream_t s);
@@ -281,13 +273,6 @@ cudaError_t launch_spmv_coo_col(const int32_t *row, const int32_t *col, const do
                                 int32_t n_rows, const double *x, double *y, cudaStream_t s);
 cudaError_t launch_spmv_ccs(const int32_t *cp, const int32_t *trow, const double *tval, int32_t n_rows,
                             int32_t n_cols, const double *x, double *y, cudaStream_t s);
-
-// CRS row-bin partition (kernels_spmv.cu): stable lists of rows per bin.
-constexpr int kNumBins = 7;
-int bin_of_len_host(int len);
-size_t bin_scratch_bytes(int32_t n_rows);
-cudaError_t launch_bin_rows(const int32_t *irp, int32_t n_rows, void *scratch, int32_t *rowlist,
-                            int *status, cudaStream_t s);
 
 // Batches of independent matrices (kernels_batch.cu). One descriptor per
 // matrix; work items ("tiles") are records {matrix and row count, first

@@ -1,24 +1,23 @@
 // SpMV y = A x in each format of Sec. 2.1 (Sec. 3 gives the paper's OpenMP
 // loops; these are GB300 designs of the same products).
 //
-//  CRS      : V lanes per row, V from the row-length class (1..32), or a CTA
-//             per row for rows of >= 2048 entries; lanes sum strided entries
-//             in order and reduce with a fixed shuffle tree (deterministic).
-//             Irregular matrices run one launch per length bin over stable
-//             row lists built once per handle.
+//  CRS      : regular rows: 128-row tiles staged in shared memory, SPLIT
+//             threads per row with lanes on consecutive rows (coalesced x
+//             gathers on banded matrices), fixed-order partial sums; rows too
+//             long for a staged tile: V lanes per row with a fixed shuffle
+//             tree; uneven rows: the entry-split product (below).
 //  ELL-Row  : one thread per two rows, 128-bit loads of the column-major
 //             slots (values and indices), FMA in slot order (Fig. 3 order).
-//  COO-Row  : 2048-entry tiles in shared memory; row segments found with
-//             integer work, FMA chains per segment with lanes on consecutive
-//             segments; partial sums of rows that cross tile edges are
-//             finished by a second, per-tile kernel in tile order
-//             (deterministic).
+//  COO-Row  : row-aligned 128-row tiles staged in shared memory (bounds
+//             from the row pointers), as CRS; tiles too large for shared
+//             memory: the entry-split product. The allocation-free entry
+//             point uses 2048-entry tiles whose rows crossing tile edges are
+//             finished by a second, per-tile kernel in tile order.
 //  COO-Col, ELL-Col, CCS : the column-major products of Fig. 1: each entry
 //             adds val * x[col] into y[row] with FP64 atomics.
 #include <climits>
 
 #include "common.cuh"
-#include "stage_pipe.cuh"
 
 namespace spmvat {
 
@@ -77,210 +76,6 @@ cudaError_t launch_spmv_crs_vector(int v, const int32_t *irp, const int32_t *ico
         SPMV_CASE(16)
         SPMV_CASE(32)
 #undef SPMV_CASE
-        default:
-            return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
-// Rows staged by TMA: persistent CTAs take tiles of R consecutive rows; the
-// tile's VAL / ICOL range arrives in shared memory through the two-stage
-// bulk-copy pipeline (stage_pipe.cuh) while the previous tile is multiplied,
-// with no load instructions spent on it. Then all threads gather x for the
-// tile's entries into shared memory, eight independent gathers in flight per
-// thread, and S lanes per row run the FMA chains (storage order, strided by
-// lane) and a fixed shuffle tree combines them. R * (longest row) fits a
-// stage, so every row of a tile is resident.
-constexpr int CRS_STAGE_CAP = 2048;
-using CrsPipe = StagePipe<CRS_STAGE_CAP, 1>;
-constexpr size_t kCrsStreamSmem = CrsPipe::kSmem + (size_t)CRS_STAGE_CAP * 8;
-
-template <int S>
-__global__ void __launch_bounds__(256) k_spmv_crs_stream(const int32_t *__restrict__ irp,
-                                                          const int32_t *__restrict__ icol,
-                                                          const double *__restrict__ val, int32_t n_rows, int R,
-                                                          int n_tiles, int can_stage, const double *__restrict__ x,
-                                                          double *__restrict__ y, int *status) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    CrsPipe P;
-    P.setup(smem);
-    double *s_x = reinterpret_cast<double *>(smem + CrsPipe::kSmem);
-    const int lt = threadIdx.x / S, sub = threadIdx.x % S;
-    auto range = [&](int tile, long long *e0, long long *e1) {
-        const long long r0 = (long long)tile * R;
-        const long long r1 = min(r0 + R, (long long)n_rows);
-        *e0 = irp[r0];
-        *e1 = irp[r1];
-    };
-    auto body = [&](int tile, int st, const StageMeta &m) {
-        const long long r = (long long)tile * R + lt;
-        const bool own = lt < R && r < n_rows;
-        // row bounds first: their latency overlaps the gathers below
-        const int rs = own ? __ldg(irp + r) : 0;
-        const int re = own ? __ldg(irp + r + 1) : 0;
-        const int e0 = (int)m.e0;
-        const int n = (int)(m.e1 - m.e0);
-        const bool fits = n <= CRS_STAGE_CAP;
-        if (fits) {
-            for (int q0 = threadIdx.x; q0 < n; q0 += 8 * 256) {
-                int c[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int q = q0 + u * 256;
-                    c[u] = (q < n) ? P.idx_at(m, st, icol, e0 + q) : 0;
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int q = q0 + u * 256;
-                    if (q < n) s_x[q] = __ldg(x + c[u]);
-                }
-            }
-        }
-        __syncthreads();
-        double acc = 0.0;
-        if (own) {
-            if (fits && m.staged && rs >= m.a0v && re <= m.b0v) {
-                const double *sv = P.sval(st) + (rs - m.a0v);
-                const double *sx = s_x + (rs - e0);
-                const int len = re - rs;
-                for (int k = sub; k < len; k += S) acc = fma(sv[k], sx[k], acc);
-            } else if (fits) {
-                for (int k = rs + sub; k < re; k += S) acc = fma(P.val_at(m, st, val, k), s_x[k - e0], acc);
-            } else {
-                for (int k = rs + sub; k < re; k += S)
-                    acc = fma(P.val_at(m, st, val, k), __ldg(x + P.idx_at(m, st, icol, k)), acc);
-            }
-        }
-#pragma unroll
-        for (int o = S / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, S);
-        if (sub == 0 && own) y[r] = acc;
-    };
-    pipe_tiles(P, n_tiles, val, icol, can_stage != 0, status, range, body);
-}
-
-size_t crs_stream_smem_bytes() { return kCrsStreamSmem; }
-
-// Rows per tile for S lanes per row: the largest power of two with
-// R * S <= 256 and R * max_row_len <= the stage capacity (0: no fit).
-int crs_stream_rows(int S, int max_row_len) {
-    for (int R = 256 / S; R >= 1; R >>= 1)
-        if ((long long)R * max_row_len <= CRS_STAGE_CAP) return R;
-    return 0;
-}
-
-cudaError_t launch_spmv_crs_stream(int S, int R, const int32_t *irp, const int32_t *icol, const double *val,
-                                   int32_t n_rows, const double *x, double *y, int *status, cudaStream_t s) {
-    if (n_rows <= 0) return cudaSuccess;
-    if (R <= 0 || R * S > 256) return cudaErrorInvalidValue;
-    const int n_tiles = (int)ceil_div_u(n_rows, R);
-    const int can_stage = ((reinterpret_cast<uintptr_t>(val) & 15) == 0) &&
-                          ((reinterpret_cast<uintptr_t>(icol) & 15) == 0);
-    int grid = sm_count() * 3;
-    if (grid > n_tiles) grid = n_tiles;
-    switch (S) {
-#define STREAM_CASE(SS)                                                                                  \
-    case SS: {                                                                                           \
-        cudaError_t e = set_smem_attr(k_spmv_crs_stream<SS>, kCrsStreamSmem);                            \
-        if (e != cudaSuccess) return e;                                                                  \
-        KernelScope ks("spmv_crs_stream_s" #SS, s);                                                      \
-        k_spmv_crs_stream<SS><<<grid, 256, kCrsStreamSmem, s>>>(irp, icol, val, n_rows, R, n_tiles, can_stage, \
-                                                                 x, y, status);                         \
-        break;                                                                                           \
-    }
-        STREAM_CASE(1)
-        STREAM_CASE(2)
-        STREAM_CASE(4)
-        STREAM_CASE(8)
-#undef STREAM_CASE
-        default:
-            return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
-// Rows in tiles, many CTAs per SM: a CTA takes 256/S consecutive rows. Phase
-// A: all threads stride over the tile's entries with coalesced loads of VAL
-// and ICOL and gather x, eight entries in flight per thread, into shared
-// memory. Phase B: S lanes per row accumulate VAL * x with FMA in storage
-// order (lane-strided), and a fixed shuffle tree combines them. The product
-// needs one FP64 FMA per entry, as the row-wise loop does.
-constexpr int CRS_TILE_CAP = 2048;
-
-template <int S>
-__global__ void __launch_bounds__(256) k_spmv_crs_tile(const int32_t *__restrict__ irp,
-                                                        const int32_t *__restrict__ icol,
-                                                        const double *__restrict__ val, int32_t n_rows,
-                                                        const double *__restrict__ x, double *__restrict__ y) {
-    constexpr int ROWS = 256 / S;
-    __shared__ double s_v[CRS_TILE_CAP];
-    __shared__ double s_x[CRS_TILE_CAP];
-    __shared__ int32_t s_ptr[ROWS + 1];
-    const long long r0 = (long long)blockIdx.x * ROWS;
-    const int nr = (int)min((long long)ROWS, (long long)n_rows - r0);
-    // the tile's entry range, read by every thread (broadcast), so the entry
-    // loads start without waiting for the row window below
-    const int e0 = __ldg(irp + r0), e1 = __ldg(irp + r0 + nr);
-    const int n = e1 - e0;
-    const bool staged = n <= CRS_TILE_CAP;
-    for (int i = threadIdx.x; i <= nr; i += 256) s_ptr[i] = irp[r0 + i];
-    if (staged) {
-        for (int q0 = threadIdx.x; q0 < n; q0 += 8 * 256) {
-            double v[8];
-            int c[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int q = q0 + u * 256;
-                v[u] = (q < n) ? __ldcs(val + e0 + q) : 0.0;
-                c[u] = (q < n) ? __ldcs(icol + e0 + q) : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int q = q0 + u * 256;
-                if (q < n) {
-                    s_v[q] = v[u];
-                    s_x[q] = __ldg(x + c[u]);
-                }
-            }
-        }
-    }
-    __syncthreads();
-    const int lt = threadIdx.x / S, sub = threadIdx.x % S;
-    double acc = 0.0;
-    if (lt < nr) {
-        const int s = s_ptr[lt] - e0, e = s_ptr[lt + 1] - e0;
-        if (staged) {
-            for (int q = s + sub; q < e; q += S) acc = fma(s_v[q], s_x[q], acc);
-        } else {
-            for (int k = e0 + s + sub; k < e0 + e; k += S) acc = fma(__ldcs(val + k), __ldg(x + __ldcs(icol + k)), acc);
-        }
-    }
-#pragma unroll
-    for (int o = S / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, S);
-    if (sub == 0 && lt < nr) y[r0 + lt] = acc;
-}
-
-int crs_tile_lanes(int max_row_len) {
-    for (int S = 1; S <= 8; S <<= 1)
-        if ((long long)(256 / S) * max_row_len <= CRS_TILE_CAP) return S;
-    return 0;  // a tile of 32 rows would not fit: use another schedule
-}
-
-cudaError_t launch_spmv_crs_tile(int S, const int32_t *irp, const int32_t *icol, const double *val,
-                                 int32_t n_rows, const double *x, double *y, cudaStream_t s) {
-    if (n_rows <= 0) return cudaSuccess;
-    const unsigned grid = ceil_div_u(n_rows, 256 / S);
-    switch (S) {
-#define TILE_CASE(SS)                                                                \
-    case SS: {                                                                       \
-        KernelScope ks("spmv_crs_tile_s" #SS, s);                                    \
-        k_spmv_crs_tile<SS><<<grid, 256, 0, s>>>(irp, icol, val, n_rows, x, y);      \
-        break;                                                                       \
-    }
-        TILE_CASE(1)
-        TILE_CASE(2)
-        TILE_CASE(4)
-        TILE_CASE(8)
-#undef TILE_CASE
         default:
             return cudaErrorInvalidValue;
     }
@@ -410,157 +205,6 @@ cudaError_t launch_spmv_crs_rows(int split, int cap, const int32_t *irp, const i
         default:
             return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
-}
-
-// One CTA per (long) row; fixed-order block reduction.
-__global__ void __launch_bounds__(256) k_spmv_crs_block(const int32_t *__restrict__ irp,
-                                                         const int32_t *__restrict__ icol,
-                                                         const double *__restrict__ val,
-                                                         const int32_t *__restrict__ rows, int64_t count,
-                                                         const double *__restrict__ x, double *__restrict__ y) {
-    __shared__ double s_part[8];
-    for (long long g = blockIdx.x; g < count; g += gridDim.x) {
-        const int r = rows ? __ldg(rows + g) : (int)g;
-        const int s = __ldg(irp + r), e = __ldg(irp + r + 1);
-        double acc = 0.0;
-        for (int k = s + (int)threadIdx.x; k < e; k += 256) acc = fma(__ldcs(val + k), __ldg(x + __ldcs(icol + k)), acc);
-        acc = warp_sum(acc);
-        if (lane_id() == 0) s_part[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) t += s_part[j];
-            y[r] = t;
-        }
-        __syncthreads();
-    }
-}
-
-cudaError_t launch_spmv_crs_block(const int32_t *irp, const int32_t *icol, const double *val,
-                                  const int32_t *rows, int64_t count, const double *x, double *y,
-                                  cudaStream_t s) {
-    if (count <= 0) return cudaSuccess;
-    unsigned grid = (unsigned)(count < (long long)sm_count() * 8 ? count : (long long)sm_count() * 8);
-    KernelScope ks("spmv_crs_block", s);
-    k_spmv_crs_block<<<grid, 256, 0, s>>>(irp, icol, val, rows, count, x, y);
-    return cudaGetLastError();
-}
-
-// ------------------------------------------------------- row-bin partition
-// Bins by row length: 0: 0-3 (V=1), 1: 4-7 (2), 2: 8-15 (4), 3: 16-31 (8),
-// 4: 32-63 (16), 5: 64-2047 (32), 6: >= 2048 (one CTA per row).
-__host__ __device__ __forceinline__ int bin_of_len(int len) {
-    if (len < 4) return 0;
-    if (len < 8) return 1;
-    if (len < 16) return 2;
-    if (len < 32) return 3;
-    if (len < 64) return 4;
-    if (len < 2048) return 5;
-    return 6;
-}
-int bin_of_len_host(int len) { return bin_of_len(len); }
-
-constexpr int BIN_THREADS = 256;
-constexpr int BIN_ITEMS = 8;
-constexpr int BIN_CHUNK = BIN_THREADS * BIN_ITEMS;
-
-size_t bin_scratch_bytes(int32_t n_rows) {
-    const long long chunks = ((long long)n_rows + BIN_CHUNK - 1) / BIN_CHUNK;
-    const long long ncnt = chunks * kNumBins;
-    return (size_t)(ncnt + 1) * 4 + 16 + scan_scratch_bytes(ncnt);
-}
-
-// Per-thread bin counts of its BIN_ITEMS consecutive rows, then a block-wide
-// exclusive scan per bin (rows keep their order inside every bin).
-__device__ __forceinline__ void bin_thread_counts(const int32_t *irp, int32_t n_rows, long long r0, int *b,
-                                                  int cnt[kNumBins]) {
-#pragma unroll
-    for (int q = 0; q < kNumBins; ++q) cnt[q] = 0;
-#pragma unroll
-    for (int j = 0; j < BIN_ITEMS; ++j) {
-        const long long r = r0 + j;
-        b[j] = -1;
-        if (r < n_rows) {
-            b[j] = bin_of_len(irp[r + 1] - irp[r]);
-#pragma unroll
-            for (int q = 0; q < kNumBins; ++q) cnt[q] += (b[j] == q);
-        }
-    }
-}
-
-__global__ void __launch_bounds__(BIN_THREADS) k_bin_count(const int32_t *__restrict__ irp, int32_t n_rows,
-                                                            int32_t *__restrict__ counts, long long n_chunks) {
-    __shared__ int s_tot[kNumBins];
-    if (threadIdx.x < kNumBins) s_tot[threadIdx.x] = 0;
-    __syncthreads();
-    int b[BIN_ITEMS], cnt[kNumBins];
-    bin_thread_counts(irp, n_rows, (long long)blockIdx.x * BIN_CHUNK + (long long)threadIdx.x * BIN_ITEMS, b, cnt);
-#pragma unroll
-    for (int q = 0; q < kNumBins; ++q) {
-        const int t = warp_sum(cnt[q]);
-        if (lane_id() == 0 && t) atomicAdd(&s_tot[q], t);
-    }
-    __syncthreads();
-    if (threadIdx.x < kNumBins) counts[(long long)threadIdx.x * n_chunks + blockIdx.x] = s_tot[threadIdx.x];
-}
-
-__global__ void __launch_bounds__(BIN_THREADS) k_bin_scatter(const int32_t *__restrict__ irp, int32_t n_rows,
-                                                              const int32_t *__restrict__ offs, long long n_chunks,
-                                                              int32_t *__restrict__ rowlist) {
-    __shared__ int s_w[BIN_THREADS / 32][kNumBins];
-    const long long r0 = (long long)blockIdx.x * BIN_CHUNK + (long long)threadIdx.x * BIN_ITEMS;
-    int b[BIN_ITEMS], cnt[kNumBins];
-    bin_thread_counts(irp, n_rows, r0, b, cnt);
-    const unsigned lane = lane_id();
-    const int w = threadIdx.x >> 5;
-    int excl[kNumBins];
-#pragma unroll
-    for (int q = 0; q < kNumBins; ++q) {
-        int inc = cnt[q];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, inc, o);
-            if ((int)lane >= o) inc += t;
-        }
-        excl[q] = inc - cnt[q];
-        if (lane == 31) s_w[w][q] = inc;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kNumBins; ++q) {
-        int add = offs[(long long)q * n_chunks + blockIdx.x];
-        for (int j = 0; j < w; ++j) add += s_w[j][q];
-        excl[q] += add;
-    }
-#pragma unroll
-    for (int j = 0; j < BIN_ITEMS; ++j) {
-        if (b[j] >= 0) {
-#pragma unroll
-            for (int q = 0; q < kNumBins; ++q)
-                if (b[j] == q) rowlist[excl[q]++] = (int32_t)(r0 + j);
-        }
-    }
-}
-
-cudaError_t launch_bin_rows(const int32_t *irp, int32_t n_rows, void *scratch, int32_t *rowlist, int *status,
-                            cudaStream_t s) {
-    if (n_rows <= 0) return cudaSuccess;
-    const long long chunks = ((long long)n_rows + BIN_CHUNK - 1) / BIN_CHUNK;
-    const long long ncnt = chunks * kNumBins;
-    int32_t *counts = reinterpret_cast<int32_t *>(scratch);
-    void *scan_scr = reinterpret_cast<char *>(scratch) + (((size_t)(ncnt + 1) * 4 + 15) & ~(size_t)15);
-    {
-        KernelScope ks("bin_count", s);
-        k_bin_count<<<(unsigned)chunks, BIN_THREADS, 0, s>>>(irp, n_rows, counts, chunks);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    cudaError_t e = launch_scan(counts, ncnt, scan_scr, nullptr, INT_MAX, nullptr, nullptr, status, kSpinLimit, 0, s);
-    if (e != cudaSuccess) return e;
-    KernelScope ks("bin_scatter", s);
-    k_bin_scatter<<<(unsigned)chunks, BIN_THREADS, 0, s>>>(irp, n_rows, counts, chunks, rowlist);
     return cudaGetLastError();
 }
 

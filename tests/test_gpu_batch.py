@@ -116,12 +116,12 @@ def test_fused_build_equals_apply_and_rerun_is_deterministic(host_set):
 
 
 @pytest.mark.parametrize("tpr", ["1", "8", "32"])
-def test_every_threads_per_row_schedule(host_set, tpr, monkeypatch):
+def test_every_threads_per_row_schedule(host_set, tpr):
     import torch
     L = lib()
-    monkeypatch.setenv("SPMVAT_BATCH_TPR", tpr)
     dev = L.Crs.batch_from_host(host_set)
-    B = L.spmv_batch_create(dev, dstar=0.0)
+    with L.hint(L.SPMV_HINT_BATCH_TPR, int(tpr)):
+        B = L.spmv_batch_create(dev, dstar=0.0)
     assert all(P["threads_per_row"] == int(tpr) for P in B.plans())
     xh, x, y = _xy(host_set, seed=13)
     B.apply(x, y)

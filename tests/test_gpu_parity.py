@@ -203,15 +203,12 @@ def test_fused_transform_and_first_spmv(name):
     M.close()
 
 
-@pytest.mark.parametrize("kernel", ["seg", "binned"])
-def test_crs_schedules_for_uneven_rows(monkeypatch, kernel):
-    """Uneven rows take the entry-split product (or, forced, the row-length
-    bins): rows crossing thread and tile edges, rows of one entry, empty rows
-    and rows thousands of entries long all land inside the tolerance."""
+def test_crs_schedule_for_uneven_rows():
+    """Uneven rows take the entry-split product: rows crossing thread and
+    tile edges, rows of one entry, empty rows and rows thousands of entries
+    long all land inside the tolerance."""
     import torch
     L = lib()
-    if kernel == "binned":
-        monkeypatch.setenv("SPMVAT_CRS_KERNEL", "binned")
     mats = [synth.power_law(30000, kmax=8000, seed=9), case("powerlaw_60k"), case("long_row"),
             case("random_empty_rows"), case("dense_column"), case("random_duplicates")]
     for i, H in enumerate(mats):
@@ -219,7 +216,7 @@ def test_crs_schedules_for_uneven_rows(monkeypatch, kernel):
         xh = xvec(H.n_cols, seed=5 + i)
         M = L.spmv_transform(A, L.SPMV_CRS, L.SPMV_ROWWISE)
         for rep in range(2):
-            assert_spmv_close(run_apply(M, torch.from_numpy(xh).cuda(), H.n_rows), H, xh, what=f"{kernel}/{i}/{rep}")
+            assert_spmv_close(run_apply(M, torch.from_numpy(xh).cuda(), H.n_rows), H, xh, what=f"seg/{i}/{rep}")
         M.close()
     assert L.spmv_analyze(dev(mats[0]))["dmat"] > 0.5  # the first one is uneven
 
@@ -272,62 +269,81 @@ def test_outputs_at_any_8_byte_offset():
         M.close()
 
 
-@pytest.mark.parametrize("kernel,S", [("rows", 1), ("rows", 2), ("rows", 4), ("rows", 8), ("tile", 1), ("tile", 2), ("tile", 4), ("tile", 8), ("stream", 1),
-                                      ("stream", 2), ("stream", 4), ("stream", 8), ("vector", 0)])
-def test_crs_kernel_variants(monkeypatch, kernel, S):
-    """Every CRS schedule the plan can pick gives results inside the tolerance,
-    on cases of one to several hundred row tiles with ragged last tiles."""
+@pytest.mark.parametrize("split", [1, 2, 4, 8, -1])
+def test_crs_kernel_variants(split):
+    """Every CRS schedule for regular rows (1, 2, 4 or 8 threads per row of a
+    staged tile; -1: V lanes per row without staging) gives results inside
+    the tolerance, on cases of one to several hundred row tiles with ragged
+    last tiles."""
     import torch
     L = lib()
-    monkeypatch.setenv("SPMVAT_CRS_KERNEL", kernel)
-    if S:
-        monkeypatch.setenv("SPMVAT_CRS_S", str(S))
     for name in ("laplace37x23", "stencil27_24", "laplace300x221", "stencil27_37"):
         H = case(name)
         xh = xvec(H.n_cols, seed=7)
-        M = L.spmv_transform(dev(H), L.SPMV_CRS, L.SPMV_ROWWISE)
-        assert_spmv_close(run_apply(M, torch.from_numpy(xh).cuda(), H.n_rows), H, xh, what=f"{name}/{kernel}{S}")
-        L.spmv_matrix_status(M)
+        with L.hint(L.SPMV_HINT_CRS_SPLIT, split):
+            M = L.spmv_transform(dev(H), L.SPMV_CRS, L.SPMV_ROWWISE)
+        y = run_apply(M, torch.from_numpy(xh).cuda(), H.n_rows)
+        assert_spmv_close(y, H, xh, what=f"{name}/split={split}")
+        assert np.array_equal(bits(run_apply(M, torch.from_numpy(xh).cuda(), H.n_rows)), bits(y))
         M.close()
 
 
-@pytest.mark.parametrize("entry_tiles", ["", "1", "seg"])
-def test_coo_row_schedules(monkeypatch, entry_tiles):
-    """Row-aligned tiles, entry tiles with carries and the entry-split product
-    agree with the oracle."""
+def test_crs_vector_kernel_on_rows_too_long_for_a_staged_tile():
+    """Regular rows longer than 64 entries (a 128-row tile would not fit
+    shared memory) take the V-lanes-per-row kernel without any hint."""
     import torch
     L = lib()
-    if entry_tiles:
-        monkeypatch.setenv("SPMVAT_COO_ENTRY_TILES", entry_tiles)
+    H = synth.banded_random_crs(3000, 300000, 10.0, seed=31)  # mean 100, D_mat 0.10, W 146
+    st = oracle.analyze(H.n_rows, H.irp)
+    assert st["dmat"] <= 0.5 and st["W"] > 64
+    xh = xvec(H.n_cols, seed=32)
+    M = L.spmv_transform(dev(H), L.SPMV_CRS, L.SPMV_ROWWISE)
+    L.spmv_profile_enable(True)
+    L.spmv_profile_read(reset=True)
+    try:
+        y = run_apply(M, torch.from_numpy(xh).cuda(), H.n_rows)
+        prof = L.spmv_profile_read(reset=True)
+    finally:
+        L.spmv_profile_enable(False)
+    assert any(k.startswith("spmv_crs_v") for k in prof), prof
+    assert_spmv_close(y, H, xh, what="vector kernel")
+    M.close()
+
+
+@pytest.mark.parametrize("flat", [0, 1])
+def test_coo_row_schedules(flat):
+    """Row-aligned tiles and the entry-split product agree with the oracle."""
+    import torch
+    L = lib()
     for name in ("laplace37x23", "stencil27_24", "random_empty_rows", "long_row", "all_empty", "powerlaw_60k",
                  "dense_column", "one_by_one"):
         H = case(name)
         xh = xvec(H.n_cols, seed=8)
-        M = L.spmv_transform(dev(H), L.SPMV_COO, L.SPMV_ROWWISE)
+        with L.hint(L.SPMV_HINT_COO_FLAT, flat):
+            M = L.spmv_transform(dev(H), L.SPMV_COO, L.SPMV_ROWWISE)
         assert_spmv_close(run_apply(M, torch.from_numpy(xh).cuda(), H.n_rows), H, xh,
-                          what=f"{name}/entry_tiles={entry_tiles}")
+                          what=f"{name}/flat={flat}")
         M.close()
 
 
-@pytest.mark.parametrize("entry_tiles", [False, True])
-def test_coo_col_schedules(monkeypatch, entry_tiles):
+@pytest.mark.parametrize("flat", [0, 1])
+def test_coo_col_schedules(flat):
     """Column-aligned tiles (lanes on consecutive columns) and the flat entry
     kernel agree with the oracle; a 9000-entry column exceeds the tile
     capacity and takes the flat kernel either way."""
     import torch
     L = lib()
-    if entry_tiles:
-        monkeypatch.setenv("SPMVAT_COO_ENTRY_TILES", "1")
     for name in ("laplace37x23", "stencil27_24", "random_empty_rows", "wide", "tall", "dense_column", "all_empty",
                  "powerlaw_60k"):
         H = case(name)
         xh = xvec(H.n_cols, seed=9)
         C = L.spmv_transform(dev(H), L.SPMV_CRS, L.SPMV_COLWISE)
-        M = L.spmv_transform_from(C, L.SPMV_COO)
+        with L.hint(L.SPMV_HINT_COO_FLAT, flat):
+            M = L.spmv_transform_from(C, L.SPMV_COO)
         C.close()
         for rep in range(2):
             assert_spmv_close(run_apply(M, torch.from_numpy(xh).cuda(), H.n_rows), H, xh,
-                              what=f"{name}/entry_tiles={entry_tiles}/{rep}")
+                              what=f"{name}/flat={flat}/{rep}")
         M.close()
 
 
@@ -383,32 +399,35 @@ def with_extra_columns(n, mean_len, seed, every):
     return synth.CRS(n, n, irp.astype(np.int32), icol, synth.normal(seed, 5, np.arange(icol.size)))
 
 
-@pytest.mark.parametrize("mode", ["scatter", "kslot", "rk", "grp"])
+PHASE1_MODES = {"scatter": 1, "kslot": 2, "rk": 3, "grp": 4}  # SPMV_PHASE1_*
+
+
+@pytest.mark.parametrize("mode", list(PHASE1_MODES))
 @pytest.mark.parametrize("name", ["stencil27_24", "powerlaw_60k", "random_duplicates", "dense_column", "wide",
                                   "tall", "all_empty", "one_by_one", "laplace37x23"])
-def test_phase1_paths_bit_exact(monkeypatch, mode, name):
+def test_phase1_paths_bit_exact(mode, name):
     """Every Phase I path (count + scatter; (k, row) slots with ranks;
     (k, row) slots sorted by row per column; (row, value) records in 64-column
     group regions; the last two hand over to the first slot path on repeated
     entries, full groups or columns over 4096) gives the oracle's CCS bit for
     bit."""
     L = lib()
-    monkeypatch.setenv("SPMVAT_PHASE1", mode)
     H = case(name)
-    M = L.spmv_transform(dev(H), L.SPMV_CRS, L.SPMV_COLWISE)
+    with L.hint(L.SPMV_HINT_PHASE1, PHASE1_MODES[mode]):
+        M = L.spmv_transform(dev(H), L.SPMV_CRS, L.SPMV_COLWISE)
     _ccs_matches_oracle(M, H)
     M.close()
 
 
 @pytest.mark.parametrize("mode", ["rk", "grp"])
-def test_phase1_register_sort_paths_on_shuffled_rows(monkeypatch, mode):
+def test_phase1_register_sort_paths_on_shuffled_rows(mode):
     """Columns in arbitrary order within rows: the row-position and grouped
     paths order every column by row (register networks, overflow records and
     the long-column sort all run)."""
     L = lib()
-    monkeypatch.setenv("SPMVAT_PHASE1", mode)
     H = shuffled_rows(with_extra_columns(3000, 12, 81, [(5, 3), (9, 40)]))
-    M, claims = _claims(L, H)
+    with L.hint(L.SPMV_HINT_PHASE1, PHASE1_MODES[mode]):
+        M, claims = _claims(L, H)
     assert claims == 1
     _ccs_matches_oracle(M, H)
     M.close()
