@@ -32,7 +32,10 @@ void *g_scratch_addr[64] = {};  // device address of the array, per device
 
 // Host code may not use g_coo_carry_scratch as a device pointer (on the host
 // it names a stand-in object). Its device address is looked up once per
-// device, with that device current.
+// device, with that device current, and kept: it stays valid as long as the
+// device's primary context lives, so a cudaDeviceReset (which destroys that
+// context) makes it stale, and the header tells callers not to call this
+// entry point after one.
 spmv_status scratch_for_current_device(void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return SPMV_ERR_CUDA; }
