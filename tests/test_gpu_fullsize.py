@@ -102,8 +102,15 @@ def test_power_law_4m_phase1_and_products():
     assert np.array_equal(arr["idx"].cpu().numpy(), icol_t)
     assert np.array_equal(bits(arr["val"].cpu().numpy()), bits(val_t))
     assert np.diff(irp_t).max() > 32  # long columns: the overflow placement ran
+    # every other product at full size: COO-Row (the entry-split product,
+    # since 128-row tiles of this matrix exceed shared memory), COO-Column and
+    # ELL-Column from the CCS
+    coo_row = L.spmv_transform(A, L.SPMV_COO, L.SPMV_ROWWISE, 40 * 10 ** 9)
+    coo_col = L.spmv_transform_from(ccs, L.SPMV_COO, 40 * 10 ** 9)
+    ell_col = L.spmv_transform_from(ccs, L.SPMV_ELL, 40 * 10 ** 9)
+    assert ell_col.describe()["width"] == int(np.diff(irp_t).max())
     ys = {}
-    for name, h in (("crs", M), ("ccs", ccs)):
+    for name, h in (("crs", M), ("ccs", ccs), ("coo_row", coo_row), ("coo_col", coo_col), ("ell_col", ell_col)):
         y = torch.full((H.n_rows,), float("nan"), dtype=torch.float64, device="cuda")
         L.spmv_apply(h, x, y)
         ys[name] = y
@@ -113,5 +120,11 @@ def test_power_law_4m_phase1_and_products():
         S = H.row_slice(r0, r0 + span)
         for name, y in ys.items():
             assert_spmv_close(y[r0:r0 + span].cpu().numpy(), S, xh, what=f"power law {name} rows {r0}")
-    M.close()
-    ccs.close()
+    # the longest rows (thousands of entries, split over many threads) on their own
+    lens = np.diff(H.irp)
+    for r in np.argsort(lens)[-4:]:
+        S = H.row_slice(int(r), int(r) + 1)
+        for name, y in ys.items():
+            assert_spmv_close(y[int(r):int(r) + 1].cpu().numpy(), S, xh, what=f"power law {name} long row {r}")
+    for h in (M, ccs, coo_row, coo_col, ell_col):
+        h.close()
