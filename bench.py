@@ -356,10 +356,14 @@ def barrier_sync(torch):
 
 
 # ------------------------------------------------------------ CPU oracle
-def oracle_step(H, xh, cap: int = 0) -> dict:
+def oracle_step(H, xh, cap: int = 0, omp: bool = False) -> dict:
     """The same rows on the CPU oracle; returns {row: seconds}. ELL-Row is
-    left out, as in the GPU step, when its bytes exceed the workload's cap."""
+    left out, as in the GPU step, when its bytes exceed the workload's cap.
+    omp: the CRS and ELL-Row products and Phase I's count and pointers run on
+    all host cores (the multi-core oracle build, same bits), the rest serial."""
     import oracle
+    spmv_crs = oracle.spmv_crs_omp if omp else oracle.spmv_crs
+    spmv_ell_row = oracle.spmv_ell_row_omp if omp else oracle.spmv_ell_row
     t = {}
     c = time.perf_counter
     t0 = c(); st = oracle.analyze(H.n_rows, H.irp); t["analyze"] = c() - t0
@@ -368,18 +372,45 @@ def oracle_step(H, xh, cap: int = 0) -> dict:
     W = int(st["W"])
     if ell:
         t0 = c(); ev, ec, W = oracle.crs_to_ell_row(H.n_rows, H.irp, H.icol, H.val); t["crs_to_ell_row"] = c() - t0
-    t0 = c(); irp_t, icol_t, val_t, nc = oracle.crs_to_ccs(H.n_rows, H.n_cols, H.irp, H.icol, H.val)
+    t0 = c()
+    if omp:
+        irp_t, icol_t, val_t = oracle.crs_to_ccs_omp(H.n_rows, H.n_cols, H.irp, H.icol, H.val)
+    else:
+        irp_t, icol_t, val_t, nc = oracle.crs_to_ccs(H.n_rows, H.n_cols, H.irp, H.icol, H.val)
     t["phase1_ccs"] = c() - t0
     t0 = c(); jcol = oracle.ccs_to_coo_col(H.n_cols, irp_t); t["ccs_to_coo_col"] = c() - t0
     t0 = c(); ev2, er2, W2 = oracle.ccs_to_ell_col(H.n_cols, irp_t, icol_t, val_t); t["ccs_to_ell_col"] = c() - t0
-    t0 = c(); oracle.spmv_crs(H.n_rows, H.irp, H.icol, H.val, xh); t["spmv_crs"] = c() - t0
+    t0 = c(); spmv_crs(H.n_rows, H.irp, H.icol, H.val, xh); t["spmv_crs"] = c() - t0
     t0 = c(); oracle.spmv_coo(H.n_rows, irow, H.icol, H.val, xh); t["spmv_coo_row"] = c() - t0
     if ell:
-        t0 = c(); oracle.spmv_ell_row(H.n_rows, W, ev, ec, xh); t["spmv_ell_row"] = c() - t0
+        t0 = c(); spmv_ell_row(H.n_rows, W, ev, ec, xh); t["spmv_ell_row"] = c() - t0
     t0 = c(); oracle.spmv_coo(H.n_rows, icol_t, jcol, val_t, xh); t["spmv_coo_col"] = c() - t0
     t0 = c(); oracle.spmv_ell_col(H.n_rows, H.n_cols, W2, ev2, er2, xh); t["spmv_ell_col"] = c() - t0
     t["_W"], t["_Wc"], t["_ell"] = W, W2, ell
     return t
+
+
+def host_cpu() -> dict:
+    """The host's logical CPUs (nproc) and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith(("model name", "cpu model")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count() or 1, "model": model or "unknown"}
 
 
 def oracle_bytes(H, W, Wc, ell: bool = True) -> float:
@@ -406,25 +437,49 @@ def workload_config(name: str, w: dict, H, W: int, Wc: int, dmat: float, world: 
             "D_mat": dmat, "step_bytes": float(sum(bm.values())), "parallelism": f"replicas x{world}"}
 
 
-def cpu_baseline(H, xh, budget_s: float = 12.0, cap: int = 0) -> dict:
-    """Times the oracle on a bounded row sample of the workload."""
-    frac = 4
-    rows = max(1, H.n_rows // frac)
-    S = H.row_slice(0, rows)
-    xs = xh  # the slice keeps all columns
+CPU_SAMPLE_FRAC = 4  # the CPU legs run rows 0 .. n/4 of the workload
+
+
+def _oracle_leg(S, xs, cap: int, omp: bool, budget_s: float):
     tot_t, tot_b, runs = 0.0, 0.0, 0
     while tot_t < budget_s and runs < 20:
-        t = oracle_step(S, xs, cap)
+        t = oracle_step(S, xs, cap, omp=omp)
         tot_t += sum(v for k, v in t.items() if not k.startswith("_"))
         tot_b += oracle_bytes(S, t["_W"], t["_Wc"], t["_ell"])
         runs += 1
-    return {"value": tot_b / tot_t / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"rows 0..{rows} of {H.n_rows} ({S.nnz} nnz), {runs} oracle step(s), {tot_t:.1f} s, "
-                      f"single thread, FP64 serial loops"}
+    return tot_b / tot_t / 1e9, runs, tot_t
+
+
+def cpu_baseline(H, xh, budget_s: float = 10.0, cap: int = 0) -> dict:
+    """Times the oracle on a bounded row sample of the workload, on one thread
+    and with the multi-core build on every host core. `value` and `cores` are
+    the multi-core figures; the single-thread figure sits beside them."""
+    import oracle
+    rows = max(1, H.n_rows // CPU_SAMPLE_FRAC)
+    S = H.row_slice(0, rows)
+    xs = xh  # the slice keeps all columns
+    host = host_cpu()
+    v1, r1, t1 = _oracle_leg(S, xs, cap, False, budget_s)
+    try:
+        threads = oracle.omp_threads()
+        vm, rm, tm = _oracle_leg(S, xs, cap, True, budget_s)
+    except Exception as e:  # no OpenMP toolchain on the host: single thread only
+        return {"value": v1, "unit": "GB/s", "cores": 1, "kind": "oracle", "cpu_model": host["model"],
+                "nproc": host["nproc"],
+                "sample": f"rows 0..{rows} of {H.n_rows} ({S.nnz} nnz), {r1} oracle step(s), {t1:.1f} s, single "
+                          f"thread (multi-core build unavailable: {type(e).__name__})"}
+    return {"value": vm, "unit": "GB/s", "cores": threads, "kind": "oracle", "cpu_model": host["model"],
+            "nproc": host["nproc"],
+            "single_thread": {"value": v1, "unit": "GB/s", "cores": 1, "steps": r1, "seconds": round(t1, 2)},
+            "sample": f"rows 0..{rows} of {H.n_rows} ({S.nnz} nnz), {rm} oracle step(s), {tm:.1f} s on {threads} "
+                      f"threads: CRS and ELL-Row products and the Phase I count and pointers in parallel, every "
+                      f"other row and the Phase I scatter serial, FP64"}
 
 
 # -------------------------------------------------------------- reference
 def run_reference(args, w: dict) -> None:
+    """The reference arm: the oracle as it stands (multi-core build where it
+    has one, on every host core), on a row sample of the same workload."""
     import numpy as np
     import oracle
     rank, world, _ = dist_env()
@@ -433,15 +488,22 @@ def run_reference(args, w: dict) -> None:
     H, xh = make_matrix(w)
     rows = max(1, H.n_rows // 16)
     S = H.row_slice(0, rows)
+    try:
+        threads, omp = oracle.omp_threads(), True
+    except Exception:
+        threads, omp = 1, False
     for _ in range(args.warmup):
-        oracle_step(S, xh, w.get("cap", 0))
+        oracle_step(S, xh, w.get("cap", 0), omp=omp)
     ts, bs = [], []
     for _ in range(args.steps):
-        t = oracle_step(S, xh, w.get("cap", 0))
+        t = oracle_step(S, xh, w.get("cap", 0), omp=omp)
         ts.append(sum(v for k, v in t.items() if not k.startswith("_")))
         bs.append(oracle_bytes(S, t["_W"], t["_Wc"], t["_ell"]))
     total = sum(ts)
     value = sum(bs) / total / 1e9
+    host = host_cpu()
+    what = (f"{threads} threads (CRS, ELL-Row and the Phase I count in parallel, the rest serial)" if omp
+            else "single thread")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
@@ -451,8 +513,9 @@ def run_reference(args, w: dict) -> None:
                                      oracle.analyze(H.n_rows, H.irp)["dmat"], world),
                    "sample_rows": rows, "sample_nnz": S.nnz,
                    "l2": "CPU oracle on the host cores (no GPU, no L2 flush)"},
-        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"rows 0..{rows} of {H.n_rows} per step, single-thread FP64 oracle"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads, "kind": "oracle",
+                         "cpu_model": host["model"], "nproc": host["nproc"],
+                         "sample": f"rows 0..{rows} of {H.n_rows} per step, FP64 oracle on {what}"},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }

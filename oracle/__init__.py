@@ -4,7 +4,10 @@ TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
 CPU-baseline leg use this package; the CUDA library and its Python binding
 never import it. The arithmetic lives in ``spmv_oracle.c`` (plain C, built
 with ``-O2 -ffp-contract=off``); this file only builds that shared object and
-passes numpy arrays to it.
+passes numpy arrays to it. ``spmv_oracle_omp.c`` is a multi-core build of the
+CRS and ELL-Row products and the Phase I count and pointers, for timing the
+oracle on all host cores; the tests check it bit for bit against the serial
+functions.
 """
 
 from __future__ import annotations
@@ -19,8 +22,11 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "spmv_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_SRC_OMP = os.path.join(_HERE, "spmv_oracle_omp.c")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -36,6 +42,32 @@ def build(force: bool = False) -> str:
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_omp(force: bool = False) -> str:
+    """Compile liboracle_omp.so (gcc -fopenmp) if missing or stale."""
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC_OMP):
+        tmp = _LIB_OMP + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                               "-o", tmp, _SRC_OMP])
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
+def _load_omp():
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            L = ctypes.CDLL(build_omp())
+            L.orc_omp_threads.restype = ctypes.c_int32
+            L.orc_omp_spmv_crs.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.c_int32]
+            L.orc_omp_spmv_ell_row.argtypes = [ctypes.c_int32, ctypes.c_int32, _f64p, _i32p, _f64p, _f64p,
+                                               ctypes.c_int32]
+            L.orc_omp_crs_to_ccs.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _f64p, _i32p, _i32p,
+                                             _f64p, ctypes.c_int32]
+            L.orc_omp_crs_to_ccs.restype = ctypes.c_int32
+            _lib_omp = L
+    return _lib_omp
 
 
 def _load():
@@ -179,3 +211,34 @@ def dstar_from_points(dmat, rell, c=1.0, rule=0):
     """Off-line step (4) of Sec. 2.2; rule 0 = prefix, 1 = max-pass."""
     d, r = _f64(dmat), _f64(rell)
     return _load().orc_dstar_from_points(int(d.size), d, r, float(c), int(rule))
+
+
+# ---- multi-core builds (same bits as the serial functions above) ----------
+def omp_threads() -> int:
+    """Threads the multi-core oracle uses by default (OpenMP's maximum)."""
+    return int(_load_omp().orc_omp_threads())
+
+
+def spmv_crs_omp(n_rows, irp, icol, val, x, nthreads=0):
+    y = np.empty(int(n_rows), dtype=np.float64)
+    _load_omp().orc_omp_spmv_crs(int(n_rows), _i32(irp), _i32(icol), _f64(val), _f64(x), y, int(nthreads))
+    return y
+
+
+def spmv_ell_row_omp(n_rows, width, eval_, ecol, x, nthreads=0):
+    y = np.empty(int(n_rows), dtype=np.float64)
+    _load_omp().orc_omp_spmv_ell_row(int(n_rows), int(width), _f64(eval_), _i32(ecol), _f64(x), y, int(nthreads))
+    return y
+
+
+def crs_to_ccs_omp(n_rows, n_cols, irp, icol, val, nthreads=0):
+    """Phase I with the count and pointers on all cores: (irp_t, icol_t, val_t)."""
+    irp = _i32(irp)
+    nnz = int(irp[-1])
+    irp_t = np.empty(int(n_cols) + 1, dtype=np.int32)
+    icol_t = np.empty(nnz, dtype=np.int32)
+    val_t = np.empty(nnz, dtype=np.float64)
+    if _load_omp().orc_omp_crs_to_ccs(int(n_rows), int(n_cols), irp, _i32(icol), _f64(val), irp_t, icol_t, val_t,
+                                      int(nthreads)) != 0:
+        raise MemoryError("per-thread column counts")
+    return irp_t, icol_t, val_t

@@ -139,3 +139,18 @@ def test_stored_traffic_entries_cite_committed_profiles(bench):
             n, m, nnz, W, Wc = sizes[e["workload"]]
             model = bench.kernel_bytes(e["kernel"], bench.byte_model(n, m, nnz, W, Wc), n, m, nnz)
             assert model and 0.5 < e["bytes_per_launch"] / model < 2.0, (e["kernel"], e["bytes_per_launch"], model)
+
+
+def test_cpu_baseline_times_one_thread_and_every_host_core():
+    """The CPU baseline reports the multi-core oracle (cores = its threads)
+    with the single-thread figure beside it, and names the host CPU."""
+    import bench
+    import oracle
+    import spmv_synth as synth
+    H = synth.laplacian_2d_5pt(64)
+    xh = synth.vector_pm1(H.n_cols, seed=0)
+    cb = bench.cpu_baseline(H, xh, budget_s=0.2)
+    assert cb["kind"] == "oracle" and cb["unit"] == "GB/s" and cb["value"] > 0
+    assert cb["cores"] == oracle.omp_threads() and cb["nproc"] >= 1 and cb["cpu_model"]
+    assert cb["single_thread"]["cores"] == 1 and cb["single_thread"]["value"] > 0
+    assert "rows 0..1024 of 4096" in cb["sample"]
