@@ -51,11 +51,13 @@ WORKLOADS = {
                            "ceil(sqrt(n)) grid cut to n, odd: Poisson(8) row lengths, unique random columns"),
     "batch_1k": dict(kind="batch", count=1000, seed=5, n_lo=100, n_hi=20000, cap=60 * 10 ** 9,
                      desc="first 1,000 matrices of batch_10k (374 MB per product, > L2; profiling size)"),
-    "serve_300": dict(kind="serve", count=300, seed=6, n_lo=1000, n_hi=200000, rate=2000.0, kmax=64,
-                      requests=4000, warm_requests=300, budget=60 * 10 ** 9, streams=8, amortize=2,
-                      desc="serving: pool of 300 matrices, n log-uniform in [1e3, 2e5], half cut 2-D 5-point "
-                           "stencils, half power law (mean 16); Poisson arrivals at 2000/s, 1-64 products per "
-                           "request with fresh seeded x; 60 GB format-cache budget"),
+    "serve_300": dict(kind="serve", count=300, seed=6, n_lo=1000, n_hi=2000000, rate=2000.0, kmax=64,
+                      requests=1500, warm_requests=200, budget=60 * 10 ** 9, streams=8, amortize=2,
+                      rates=(250.0, 500.0, 750.0, 1000.0, 1500.0, 2000.0), p99_bound_ms=50.0,
+                      desc="serving: pool of 300 matrices, n log-uniform in [1e3, 2e6], half cut 2-D 5-point "
+                           "stencils, half power law (mean 16); Poisson arrivals (2000/s nominal, swept), 1-64 "
+                           "products per request with fresh seeded x; 60 GB format-cache budget; the same "
+                           "request stream through the serving runtime and through the per-matrix form"),
 }
 DEFAULT_WORKLOAD = "stencil27_128"
 
@@ -139,6 +141,10 @@ def kernel_bytes(name: str, bm: dict, n_rows: int, n_cols: int, nnz: int):
         "col_locality": 8 * 4096,
         "col_fixup_grp": 28 * nnz + 4 * (n_cols + 1),
         "col_fixup_long_rv": 0,
+        # structurally symmetric path: ICOL and IRP in, VAL gathered from the
+        # mirror entries, ICOL_T (= ICOL) and VAL_T out (IRP_T is a copy of IRP)
+        "ccs_sym": 24 * nnz + 8 * (n_rows + 1),
+        "sym_sample": 16 * 4096,
         "crs_to_ell_row_fused_spmv": (bm["crs_to_ell_row"] + 8 * n_cols + 8 * n_rows) if "crs_to_ell_row" in bm else None,
     }
     if name.startswith("spmv_crs_"):
@@ -645,10 +651,20 @@ def run_batch(args, w: dict) -> None:
     x = torch.from_numpy(xh).to(device)
     y = torch.empty(nr, dtype=torch.float64, device=device)
     if args.dstar is None:
-        dstar, _, _ = calibrate_dstar(L, torch)
+        # the max-pass rule of the committed calibration: members with small
+        # D_mat (the stencils) take ELL-Row, the rest CRS
+        dstar, dstar_src = committed_dstar(L, torch, "maxpass")
     else:
-        dstar = args.dstar
+        dstar, dstar_src = args.dstar, "--dstar"
     stream = torch.cuda.current_stream()
+    # the committed off-line schedule table of this device (lanes per row by
+    # mean row length), else the library's default
+    from paper_2407_00019_gb300 import calibrate as cal
+    try:
+        L.spmv_batch_schedule_set(cal.load_schedule(cal.committed_schedule_path(), torch.cuda.get_device_name()))
+        sched_src = "committed schedule calibration"
+    except (OSError, ValueError, KeyError):
+        sched_src = "library default (no committed schedule for this device)"
     # build: analysis + on-line rule + ELL build fused with the first product
     create_ms = []
     for _ in range(3):
@@ -661,6 +677,30 @@ def run_batch(args, w: dict) -> None:
     B = L.spmv_batch_create(dev, dstar=dstar, mem_cap_bytes=w["cap"])
     info, plans = B.info(), B.plans()
     step_bytes = batch_bytes(mats, plans)
+    # the same build planned on the device and captured, with its first
+    # product, in one CUDA graph (pool sized to the host plan's ELL bytes)
+    D = L.spmv_batch_prepare(dev, dstar=dstar, mem_cap_bytes=max(info["ell_bytes"], 1 << 20))
+    gs = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph, stream=gs):
+        D.build(x, y)
+    gms = []
+    for _ in range(4):
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        graph.replay()
+        g1.record(stream)
+        g1.synchronize()
+        gms.append(g0.elapsed_time(g1))
+    D.status()
+    dinfo = D.info()
+    graph_build = {"ms": statistics.median(gms[1:]), "n_ell": dinfo["n_ell"], "n_tiles": dinfo["n_tiles"],
+                   "same_plan_as_host": dinfo["n_ell"] == info["n_ell"] and dinfo["n_tiles"] == info["n_tiles"],
+                   "what": "analysis, on-line rule, tile records, ELL build and first product: one CUDA graph "
+                           "replayed (device time)"}
+    del graph
+    D.close()
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -751,8 +791,10 @@ def run_batch(args, w: dict) -> None:
                       "per_matrix_graph_ms": graph_ms,
                       "speedup_vs_loop": loop_ms / (t_max / args.steps) if loop_ms else None,
                       "speedup_vs_graph": graph_ms / (t_max / args.steps) if graph_ms else None,
-                      "dstar": dstar if math.isfinite(dstar) else "inf", "formats": fmt_count,
-                      "crs_threads_per_row": tpr},
+                      "dstar": dstar if math.isfinite(dstar) else "inf", "dstar_source": dstar_src,
+                      "formats": fmt_count,
+                      "crs_threads_per_row": tpr, "schedule_table": L.spmv_batch_schedule_get(),
+                      "schedule_source": sched_src, "graph_build": graph_build},
         }
         print(json.dumps(line), flush=True)
     B.close()
@@ -767,15 +809,91 @@ def _serve_part(args):
     return [synth.serve_matrix(i, seed, n_lo, n_hi) for i in range(lo, hi)]
 
 
+def committed_dstar(L, torch, rule: str):
+    """D* of the committed off-line calibration of this device (the
+    Table-1-shaped set, Sec. 2.2, 30 timed repetitions) under `rule`, else a
+    quick calibration here; returns (D*, source)."""
+    from paper_2407_00019_gb300 import calibrate as cal
+    try:
+        return cal.load_dstar(cal.committed_path(rule), torch.cuda.get_device_name()), f"committed {rule} calibration"
+    except (OSError, ValueError, KeyError):
+        return calibrate_dstar(L, torch)[0], "quick calibration (no committed file for this device)"
+
+
+def serve_dstar(L, torch):
+    """D* for serving: the max-pass rule, under which matrices with small D_mat
+    target ELL-Row and the break-even rule decides when to build it."""
+    return committed_dstar(L, torch, "maxpass")
+
+
+def serve_arm(L, torch, S, ids, dev, reqs, rate, seed, device, warm, cap_bytes=16 * 10 ** 9):
+    """Offers the request list `reqs` [(matrix, k)] at `rate` per second
+    (Poisson gaps) to server S; the first `warm` requests are not measured.
+    Each request's x is drawn on the device from its own seed just before
+    submission; latency runs from its planned arrival to its completion, so
+    time a request spends waiting behind the client (which keeps at most
+    cap_bytes of x and y outstanding) counts too."""
+    import numpy as np
+    rng = np.random.default_rng(seed + int(rate))
+    gaps = rng.exponential(1.0 / rate, size=len(reqs))
+    pending, lat = [], []  # pending: [handle, planned arrival, submit time, bytes, x, y]
+    held = 0
+
+    def finish_oldest():
+        nonlocal held
+        h, t_arr, t_sub, nb, _, _ = pending.pop(0)
+        ms, _ = S.wait(h, 600000)
+        lat.append((t_sub - t_arr) * 1e3 + ms)
+        held -= nb
+
+    t_next = t0 = time.perf_counter()
+    launches0 = L.spmv_launch_count()
+    for r, (i, k) in enumerate(reqs):
+        if r == warm:
+            while pending:
+                finish_oldest()
+            lat.clear()
+            S.stats(reset=True)
+            t_next = t0 = time.perf_counter()
+            launches0 = L.spmv_launch_count()
+        t_next += gaps[r]
+        while time.perf_counter() < t_next:
+            pass
+        A = dev[i]
+        nb = 8 * k * (A.n_cols + A.n_rows)
+        while pending and held + nb > cap_bytes:
+            finish_oldest()
+        g = torch.Generator(device=device)
+        g.manual_seed(seed * 1000003 + r)
+        x = torch.rand(k * A.n_cols, generator=g, dtype=torch.float64, device=device)
+        y = torch.empty(k * A.n_rows, dtype=torch.float64, device=device)
+        t_sub = time.perf_counter()
+        pending.append([S.submit(ids[i], k, x, y), t_next, t_sub, nb, x, y])
+        held += nb
+    while pending:
+        finish_oldest()
+    t1 = time.perf_counter()
+    st = S.stats()
+    lat = np.array(lat)
+    return {"offered_req_per_s": rate, "served_req_per_s": len(lat) / (t1 - t0),
+            "GB/s": st["bytes"] / (t1 - t0) / 1e9, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()), "requests": int(len(lat)),
+            "products": int(st["products"]), "launches": int(L.spmv_launch_count() - launches0),
+            "cache": {k: st[k] for k in ("cache_hits", "cache_misses", "transforms", "evictions", "cache_bytes",
+                                         "peak_cache_bytes")}, "seconds": t1 - t0}
+
+
 def run_serve(args, w: dict) -> None:
-    """Requests arrive as a Poisson process; each asks for k products with one
-    matrix of the pool. The client (this process) makes each request's x on
-    the device from a per-request seed, submits it and moves on; a waiter
-    thread collects completions. Reported: aggregate algorithmic GB/s over
-    the served interval and submit-to-completion latency percentiles."""
+    """One request stream (Poisson arrivals, each request k products with one
+    matrix of the pool) served twice: by the serving runtime (continuous
+    batching over stream slots, resident formats chosen by the on-line rule
+    and built at their break-even point, a request's k products in one
+    launch) and by the per-matrix form (requests one after the other, one
+    spmv_apply per product on CRS). Each arm is swept over offered rates;
+    reported: GB/s and latency percentiles per rate, and each arm's highest
+    served rate with p99 latency within the stated bound."""
     import concurrent.futures as cf
     import multiprocessing as mp
-    import threading
     rank, world, local = dist_env()
     if args.impl == "reference":
         if rank == 0:
@@ -783,10 +901,13 @@ def run_serve(args, w: dict) -> None:
                               "computes products, it does not schedule requests"}), flush=True)
         return
     seed = w["seed"] + 100000 * rank
-    parts = [(lo, min(w["count"], lo + 20), seed, w["n_lo"], w["n_hi"]) for lo in range(0, w["count"], 20)]
+    parts = [(lo, min(w["count"], lo + 4), seed, w["n_lo"], w["n_hi"]) for lo in range(0, w["count"], 4)]
     workers = max(1, min(16, (os.cpu_count() or 2) - 1))
+    t_gen = time.perf_counter()
     with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
         pool = [H for part in ex.map(_serve_part, parts) for H in part]
+    t_gen = time.perf_counter() - t_gen
+    import numpy as np
     import torch
     import torch.distributed as dist
     if world > 1:
@@ -796,83 +917,71 @@ def run_serve(args, w: dict) -> None:
     import paper_2407_00019_gb300 as L
     L.load_library()
     dev = L.Crs.batch_from_host(pool, device=device)
-    dstar = args.dstar if args.dstar is not None else calibrate_dstar(L, torch)[0]
-    S = L.Server(mem_budget_bytes=w["budget"], dstar=dstar, n_streams=w["streams"],
-                 amortize_products=w["amortize"])
-    ids = [S.add_matrix(A) for A in dev]
-    rng = __import__("numpy").random.default_rng(seed)
+    if args.dstar is not None:
+        dstar, dsrc = args.dstar, "--dstar"
+    else:
+        dstar, dsrc = serve_dstar(L, torch)
+    rng = np.random.default_rng(seed)
     n_req = w["warm_requests"] + w["requests"]
-    gaps = rng.exponential(1.0 / w["rate"], size=n_req)
-    mats = rng.integers(0, len(pool), size=n_req)
-    ks = rng.integers(1, w["kmax"] + 1, size=n_req)
-    done_q, lock = [], threading.Lock()
-
-    def waiter():
-        while True:
-            with lock:
-                item = done_q.pop(0) if done_q else None
-            if item is None:
-                time.sleep(0.0002)
-                continue
-            if item == "stop":
-                return
-            S.wait(item[0], 600000)
-
-    th = threading.Thread(target=waiter, daemon=True)
-    th.start()
+    reqs = list(zip(rng.integers(0, len(pool), size=n_req).tolist(), rng.integers(1, w["kmax"] + 1, size=n_req).tolist()))
+    rates = [args.rate] if args.rate else list(w["rates"])
+    if w["rate"] not in rates:
+        rates.append(w["rate"])
+    rates = sorted(rates)
     clocks = ClockSampler(local)
     clocks.start()
-    launches0 = None
-    t0 = time.perf_counter()
-    t_next = t0
-    for r in range(n_req):
-        if r == w["warm_requests"]:
-            S.drain(600000)
-            S.stats(reset=True)
-            launches0 = L.spmv_launch_count()
-            h0 = time.perf_counter()
-            t_next = h0
-        t_next += gaps[r]
-        while time.perf_counter() < t_next:
-            pass
-        i, k = int(mats[r]), int(ks[r])
-        A = dev[i]
-        g = torch.Generator(device=device)
-        g.manual_seed(seed * 1000003 + r)
-        x = torch.rand(k * A.n_cols, generator=g, dtype=torch.float64, device=device)
-        y = torch.empty(k * A.n_rows, dtype=torch.float64, device=device)
-        h = S.submit(ids[i], k, x, y)
-        with lock:
-            done_q.append((h, x, y))
-    S.drain(600000)
+    h0 = time.perf_counter()
+    arms = {}
+    for arm, flags, streams in (("serve", 0, w["streams"]), ("plain", L.Server.PLAIN, 1)):
+        S = L.Server(mem_budget_bytes=w["budget"], dstar=dstar, n_streams=streams, amortize_products=w["amortize"],
+                     flags=flags)
+        ids = [S.add_matrix(A) for A in dev]
+        arms[arm] = []
+        for rate in rates:
+            res = serve_arm(L, torch, S, ids, dev, reqs, rate, seed, device, w["warm_requests"])
+            arms[arm].append(res)
+            if res["p99_ms"] > 20 * w["p99_bound_ms"]:
+                break  # far past saturation: higher rates only queue longer
+        S.close()
+        torch.cuda.empty_cache()
     h1 = time.perf_counter()
-    with lock:
-        done_q.append("stop")
-    th.join()
     clocks.mark(h0, h1)
     clk = clocks.stop()
-    launches = L.spmv_launch_count() - launches0
-    st = S.stats()
-    S.close()
-    value = st["bytes"] / st["busy_s"] / 1e9 if st["busy_s"] > 0 else 0.0
     peak, peak_kind = measured_hbm_peak()
-    t_max, b_all = reduce_max_sum(torch, st["busy_s"] * 1e3, st["bytes"], device)
+    bound = w["p99_bound_ms"]
+
+    def best(rows):
+        ok = [r for r in rows if r["p99_ms"] <= bound]
+        if not ok:
+            return None
+        r = max(ok, key=lambda r: r["served_req_per_s"])
+        return {"offered_req_per_s": r["offered_req_per_s"], "served_req_per_s": r["served_req_per_s"],
+                "GB/s": r["GB/s"], "p99_ms": r["p99_ms"]}
+    nominal = {a: next(r for r in rows if r["offered_req_per_s"] == w["rate"]) if any(
+        r["offered_req_per_s"] == w["rate"] for r in rows) else None for a, rows in arms.items()}
+    nom = nominal["serve"] or arms["serve"][0]
+    t_max, b_all = reduce_max_sum(torch, nom["seconds"] * 1e3, nom["GB/s"] * nom["seconds"] * 1e9, device)
+    at_bound = {a: best(rows) for a, rows in arms.items()}
     if rank == 0:
         line = {
             "metric": METRIC, "value": b_all / (t_max * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": world,
-            "steps": w["requests"], "warmup": w["warm_requests"], "ms_per_step": st["busy_s"] * 1e3 / w["requests"],
+            "steps": w["requests"], "warmup": w["warm_requests"], "ms_per_step": nom["seconds"] * 1e3 / w["requests"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "pool_nnz": int(sum(H.nnz for H in pool)),
-                       "pool_rows": int(sum(H.n_rows for H in pool)), "streams": w["streams"],
+                       "pool_rows": int(sum(H.n_rows for H in pool)), "pool_max_n": int(max(H.n_rows for H in pool)),
+                       "pool_generation_s": round(t_gen, 1), "streams": w["streams"],
                        "amortize_products": w["amortize"], "dstar": dstar if math.isfinite(dstar) else "inf",
-                       "offered_req_per_s": w["rate"], "parallelism": f"replicas x{world}"},
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
-            "served_req_per_s": st["completed"] / st["busy_s"] if st["busy_s"] > 0 else None,
-            "products": st["products"], "frac_of_hbm_peak": value / peak, "peak": peak, "peak_source": peak_kind,
-            "cache": {k: st[k] for k in ("cache_hits", "cache_misses", "transforms", "evictions", "cache_bytes",
-                                         "peak_cache_bytes")},
-            "gpu_launches": int(launches), "clocks": clk,
-            "e2e": None, "cpu_baseline": None,
+                       "dstar_source": dsrc, "nominal_req_per_s": w["rate"], "p99_bound_ms": bound,
+                       "parallelism": f"replicas x{world}",
+                       "value": "serving runtime at the nominal rate: algorithmic bytes of the products served "
+                                "(each format's byte model) over the measured interval"},
+            "p50_ms": nom["p50_ms"], "p99_ms": nom["p99_ms"], "served_req_per_s": nom["served_req_per_s"],
+            "frac_of_hbm_peak": nom["GB/s"] / peak, "peak": peak, "peak_source": peak_kind,
+            "cache": nom["cache"], "arms": arms, "at_p99_bound": at_bound,
+            "serving_beats_plain_at_p99_bound": (at_bound["serve"] is not None and (
+                at_bound["plain"] is None or at_bound["serve"]["served_req_per_s"] >
+                at_bound["plain"]["served_req_per_s"])),
+            "gpu_launches": nom["launches"], "clocks": clk, "e2e": None, "cpu_baseline": None,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -892,7 +1001,7 @@ def measured_hbm_peak():
 # Source files whose device code decides each kernel's DRAM traffic (the
 # shared device header counts for all of them).
 KERNEL_FILES = {
-    "col_claim_rk": "kernels_colwise.cu", "col_fixup_rk": "kernels_colwise.cu",
+    "col_claim_rk": "kernels_colwise.cu", "col_fixup_rk": "kernels_colwise.cu", "ccs_sym": "kernels_colwise.cu",
     "col_claim_grp": "kernels_colwise.cu", "col_fixup_grp": "kernels_colwise.cu",
     "col_claim": "kernels_colwise.cu", "col_fixup_slots": "kernels_colwise.cu",
     "crs_to_ell_row": "kernels_rowwise.cu", "ccs_to_ell_col": "kernels_rowwise.cu",
@@ -976,9 +1085,9 @@ def main():
     fmts = ["crs", "coo_row", "ell_row", "coo_col", "ell_col"]
     ys = {f: torch.empty(H.n_rows, dtype=torch.float64, device=device) for f in fmts}
     if args.dstar is None:
-        dstar, d_pts, r_pts = calibrate_dstar(L, torch)
+        dstar, dstar_src = committed_dstar(L, torch, "prefix")
     else:
-        dstar, d_pts, r_pts = args.dstar, [], []
+        dstar, dstar_src = args.dstar, "--dstar"
     step = Step(L, A, x, ys, dstar, w["cap"], concurrent=not args.sequential)
     seq_step = Step(L, A, x, ys, dstar, w["cap"])
     stats = L.spmv_analyze(A)
@@ -1190,7 +1299,7 @@ def main():
             "per_format": per_format,
             "crs_to_ell_cost": cost,
             "at": {"dstar": dstar if math.isfinite(dstar) else "inf", "chosen": step.chosen,
-                   "calib_dmat": d_pts, "calib_rell": r_pts},
+                   "dstar_source": dstar_src},
             "per_kernel": per_kernel,
         }
         print(json.dumps(line), flush=True)

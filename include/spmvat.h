@@ -370,6 +370,48 @@ spmv_status spmv_batch_plan_get(const spmv_batch *B, int32_t first, int32_t coun
 /* Frees the batch's device memory (stream-ordered on the creating stream). */
 void spmv_batch_destroy(spmv_batch *B);
 
+/* A batch whose whole build runs on the device, so that it can be captured
+ * in one CUDA graph together with its products. spmv_batch_prepare does the
+ * host part only: it checks the descriptors, picks each CRS member's lanes
+ * per row from the schedule table (from the member's mean row length, which
+ * the descriptor gives), and allocates the descriptors, an upper bound of the
+ * tile records and, when p->dstar > 0, an ELL pool of p->mem_cap_bytes bytes
+ * (required then: SPMV_ERR_INVALID_ARG if 0). It launches nothing. SYNC.
+ * spmv_batch_build then enqueues, with no allocation, no host work between
+ * launches and no synchronisation: the analysis (Eq. (4)), the on-line rule
+ * of Sec. 2.2 per matrix (ELL-Row iff D_mat < D* and the ELL arrays of the
+ * members chosen before it, in matrix order, and its own fit the cap; the
+ * same rule as spmv_batch_create), the tile records, the ELL build and, if x
+ * and y are given (both or neither), the first product y = A x. It may be
+ * called again (the same plan is rebuilt). Afterwards spmv_batch_apply and
+ * spmv_batch_apply_multi run as for any batch, also inside a graph. A
+ * malformed member makes the build do no product work; spmv_batch_status
+ * (SYNC) then reports SPMV_ERR_INVALID_MATRIX. spmv_batch_info_get and
+ * spmv_batch_plan_get on such a batch first wait for its stream (SYNC). */
+spmv_status spmv_batch_prepare(const spmv_crs *mats, int32_t m, const spmv_at_params *p, spmv_batch **out,
+                               spmv_stream_t stream);
+spmv_status spmv_batch_build(spmv_batch *B, const double *x, double *y, spmv_stream_t stream);
+/* SYNC (device-planned batches). Status of the last build. */
+spmv_status spmv_batch_status(spmv_batch *B);
+
+/* Schedule table of batches, an extension of the paper's on-line rule to the
+ * product schedule: lanes per row (1, 8 or 32) of a CRS member by the class of
+ * its mean row length mu = nnz / n_rows (class 0: mu < 1, class c >= 1: mu in
+ * [2^(c-1), 2^c), the last class open-ended). The off-line phase measures the
+ * batch product of each class under each choice and installs the fastest
+ * (paper_2407_00019_gb300.calibrate --schedule). Process-wide; read when a
+ * batch is created or prepared. The default: 1 below a mean of 32, 8 below
+ * 256, 32 above. */
+#define SPMV_BATCH_SCHED_CLASSES 10
+spmv_status spmv_batch_schedule_set(const int32_t *tpr_by_class, int32_t n);
+spmv_status spmv_batch_schedule_get(int32_t *tpr_by_class, int32_t n);
+
+/* SYNC. Median device time (ms, CUDA events on `stream`) of `reps` batch
+ * products y = A x after `warm` untimed ones: the measurement of the
+ * off-line schedule calibration. */
+spmv_status spmv_batch_time(const spmv_batch *B, const double *x, double *y, int32_t warm, int32_t reps,
+                            double *ms, spmv_stream_t stream);
+
 /* ---- Serving: continuous batching over a pool of matrices ----------------
  * A server owns N CUDA streams ("slots") and a worker thread. Clients
  * register matrices (the pool) and submit requests; a request asks for k
@@ -391,6 +433,9 @@ typedef struct spmv_server spmv_server;
 
 #define SPMV_SERVER_FIXED_THRESHOLD 1 /* flag: build after amortize_products products, without the
                                           break-even model (only the budget limits the cache) */
+#define SPMV_SERVER_PLAIN 2           /* flag: the per-matrix form, for comparison: one slot, requests
+                                          one after the other in arrival order, each product one
+                                          spmv_apply on the matrix's CRS handle, no format cache */
 typedef struct spmv_server_params {
     uint64_t mem_budget_bytes;   /* device bytes the format cache may hold; 0 = no limit */
     double dstar;                /* D*: target format ELL-Row iff D_mat < dstar */
@@ -466,6 +511,8 @@ void spmv_server_destroy(spmv_server *S);
 #define SPMV_PHASE1_KSLOT 2    /* (k, row) slots with ranks */
 #define SPMV_PHASE1_ROWPOS 3   /* {k, row} slots sorted by row in registers */
 #define SPMV_PHASE1_GROUPED 4  /* {row, value} records per 64-column group */
+#define SPMV_PHASE1_SYMMETRIC 5 /* structurally symmetric matrices: IRP_T = IRP, ICOL_T = ICOL, values
+                                  gathered from the mirror entries (other matrices: the library's choice) */
 
 /* Set hint `hint` (SPMV_HINT_*) to `value`; SPMV_ERR_INVALID_ARG for an
  * unknown hint. */

@@ -26,8 +26,10 @@ __all__ = [
     "spmv_debug_scan_timeout", "spmv_batch_create", "spmv_batch_apply", "spmv_batch_info_get",
     "spmv_batch_plan_get", "spmv_batch_destroy", "Batch", "spmv_batch_apply_multi", "Server", "spmv_server_create",
     "spmv_set_hint", "spmv_get_hint", "hint",
+    "spmv_batch_prepare", "spmv_batch_build", "spmv_batch_status", "spmv_batch_schedule_set",
+    "spmv_batch_schedule_get", "spmv_batch_time", "SPMV_BATCH_SCHED_CLASSES",
     "SPMV_HINT_PHASE1", "SPMV_HINT_CRS_SPLIT", "SPMV_HINT_COO_FLAT", "SPMV_HINT_BATCH_TPR",
-    "SPMV_PHASE1_COUNT", "SPMV_PHASE1_KSLOT", "SPMV_PHASE1_ROWPOS", "SPMV_PHASE1_GROUPED",
+    "SPMV_PHASE1_COUNT", "SPMV_PHASE1_KSLOT", "SPMV_PHASE1_ROWPOS", "SPMV_PHASE1_GROUPED", "SPMV_PHASE1_SYMMETRIC",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -38,7 +40,7 @@ SPMV_ROWWISE, SPMV_COLWISE = 0, 1
 SPMV_DSTAR_PREFIX, SPMV_DSTAR_MAXPASS = 0, 1
 SPMV_AT_TRY_COO = 1
 SPMV_HINT_PHASE1, SPMV_HINT_CRS_SPLIT, SPMV_HINT_COO_FLAT, SPMV_HINT_BATCH_TPR = 0, 1, 2, 3
-SPMV_PHASE1_COUNT, SPMV_PHASE1_KSLOT, SPMV_PHASE1_ROWPOS, SPMV_PHASE1_GROUPED = 1, 2, 3, 4
+SPMV_PHASE1_COUNT, SPMV_PHASE1_KSLOT, SPMV_PHASE1_ROWPOS, SPMV_PHASE1_GROUPED, SPMV_PHASE1_SYMMETRIC = 1, 2, 3, 4, 5
 STATUS_NAMES = {0: "SPMV_OK", 1: "SPMV_ERR_INVALID_ARG", 2: "SPMV_ERR_INVALID_MATRIX", 3: "SPMV_ERR_OOM",
                 4: "SPMV_ERR_MEMORY_CAP", 5: "SPMV_ERR_TIMEOUT", 6: "SPMV_ERR_CUDA", 7: "SPMV_ERR_UNSUPPORTED"}
 
@@ -166,6 +168,12 @@ def load_library():
         "spmv_batch_info_get": (ctypes.c_int, [vp, P(_BatchInfoT)]),
         "spmv_batch_plan_get": (ctypes.c_int, [vp, i32, i32, P(_BatchPlanT)]),
         "spmv_batch_destroy": (None, [vp]),
+        "spmv_batch_prepare": (ctypes.c_int, [P(_CrsT), i32, P(_AtParamsT), P(vp), vp]),
+        "spmv_batch_build": (ctypes.c_int, [vp, vp, vp, vp]),
+        "spmv_batch_status": (ctypes.c_int, [vp]),
+        "spmv_batch_schedule_set": (ctypes.c_int, [P(i32), i32]),
+        "spmv_batch_schedule_get": (ctypes.c_int, [P(i32), i32]),
+        "spmv_batch_time": (ctypes.c_int, [vp, vp, vp, i32, i32, P(dbl), vp]),
         "spmv_server_create": (ctypes.c_int, [P(_ServerParamsT), P(vp)]),
         "spmv_server_add_matrix": (ctypes.c_int, [vp, P(_CrsT), P(i32)]),
         "spmv_server_submit": (ctypes.c_int, [vp, i32, i32, vp, vp, vp, P(u64)]),
@@ -246,6 +254,10 @@ class Matrix:
     def __init__(self, handle, keep=()):
         self.handle = ctypes.c_void_p(handle)
         self._keep = tuple(keep)
+        # vector lengths, known from the descriptors (no device query, so that
+        # products can be captured in a CUDA graph)
+        self.total_rows = sum(int(A.n_rows) for A in self._keep)
+        self.total_cols = sum(int(A.n_cols) for A in self._keep)
 
     def close(self):
         if self.handle and self.handle.value:
@@ -289,6 +301,10 @@ class Batch:
     def __init__(self, handle, keep=()):
         self.handle = ctypes.c_void_p(handle)
         self._keep = tuple(keep)
+        # vector lengths, known from the descriptors (no device query, so that
+        # products can be captured in a CUDA graph)
+        self.total_rows = sum(int(A.n_rows) for A in self._keep)
+        self.total_cols = sum(int(A.n_cols) for A in self._keep)
 
     def close(self):
         if self.handle and self.handle.value:
@@ -307,14 +323,24 @@ class Batch:
 
     def apply_multi(self, x, y, nvec, ldx=None, ldy=None, stream=None):
         """nvec products: vector j of x at j * ldx, of y at j * ldy."""
-        i = self.info()
-        ldx = i["total_cols"] if ldx is None else ldx
-        ldy = i["total_rows"] if ldy is None else ldy
+        ldx = self.total_cols if ldx is None else ldx
+        ldy = self.total_rows if ldy is None else ldy
         _check(load_library().spmv_batch_apply_multi(self.handle, _ptr(x), int(ldx), _ptr(y), int(ldy), int(nvec),
                                                      _stream(stream)), "spmv_batch_apply_multi")
 
     def info(self) -> dict:
         return spmv_batch_info_get(self)
+
+    def build(self, x=None, y=None, stream=None):
+        """Device-planned batch: enqueue the whole build (and with x, y the
+        first product); no synchronisation, capturable in a CUDA graph."""
+        spmv_batch_build(self, x, y, stream)
+
+    def status(self) -> None:
+        _check(load_library().spmv_batch_status(self.handle), "spmv_batch_status")
+
+    def time(self, x, y, warm=3, reps=20, stream=None) -> float:
+        return spmv_batch_time(self, x, y, warm, reps, stream)
 
     def plans(self, first=0, count=None) -> list:
         return spmv_batch_plan_get(self, first, count)
@@ -610,6 +636,7 @@ class Server:
     pool); keeps the registered matrices alive."""
 
     FIXED_THRESHOLD = 1
+    PLAIN = 2
 
     def __init__(self, mem_budget_bytes=0, dstar=0.0, n_streams=4, amortize_products=2, flags=0):
         p = _ServerParamsT(int(mem_budget_bytes), float(dstar), int(n_streams), int(amortize_products), int(flags), 0)
@@ -672,3 +699,44 @@ def spmv_server_create(**kw) -> Server:
 
 def spmv_batch_apply_multi(B: Batch, x, y, nvec: int, ldx=None, ldy=None, stream=None) -> None:
     B.apply_multi(x, y, nvec, ldx, ldy, stream)
+
+
+SPMV_BATCH_SCHED_CLASSES = 10
+
+
+def spmv_batch_prepare(mats, stream=None, **params) -> Batch:
+    """Host part of a device-planned batch over the Crs list `mats` (no
+    launches); then Batch.build() enqueues the rest."""
+    m = len(mats)
+    arr = (_CrsT * max(m, 1))(*[A.c for A in mats])
+    h = ctypes.c_void_p()
+    p = _params(**params)
+    _check(load_library().spmv_batch_prepare(arr, m, ctypes.byref(p), ctypes.byref(h), _stream(stream)),
+           "spmv_batch_prepare")
+    return Batch(h.value, keep=tuple(mats))
+
+
+def spmv_batch_build(B: Batch, x=None, y=None, stream=None) -> None:
+    _check(load_library().spmv_batch_build(B.handle, _ptr(x), _ptr(y), _stream(stream)), "spmv_batch_build")
+
+
+def spmv_batch_status(B: Batch) -> None:
+    B.status()
+
+
+def spmv_batch_schedule_set(tpr_by_class) -> None:
+    t = (ctypes.c_int32 * max(len(tpr_by_class), 1))(*[int(v) for v in tpr_by_class])
+    _check(load_library().spmv_batch_schedule_set(t, len(tpr_by_class)), "spmv_batch_schedule_set")
+
+
+def spmv_batch_schedule_get() -> list:
+    t = (ctypes.c_int32 * SPMV_BATCH_SCHED_CLASSES)()
+    _check(load_library().spmv_batch_schedule_get(t, SPMV_BATCH_SCHED_CLASSES), "spmv_batch_schedule_get")
+    return list(t)
+
+
+def spmv_batch_time(B: Batch, x, y, warm=3, reps=20, stream=None) -> float:
+    ms = ctypes.c_double()
+    _check(load_library().spmv_batch_time(B.handle, _ptr(x), _ptr(y), int(warm), int(reps), ctypes.byref(ms),
+                                          _stream(stream)), "spmv_batch_time")
+    return ms.value

@@ -418,6 +418,7 @@ spmv_status build_ell_row(const spmv_crs *A, const spmv_stats &st, uint64_t cap,
 //   COUNT : count, scan, scatter of (k, row); any matrix.
 enum class P1 { GRP, RK, KSLOT, COUNT };
 constexpr int kLocalitySamples = 4096;
+constexpr int kSymSamples = 4096;
 constexpr spmv_status kRedo = (spmv_status)-1;  // internal: rerun on KSLOT
 
 // The grouped row-value path: claim, scan of the group counts, fix-up (which
@@ -465,6 +466,45 @@ spmv_status phase1_grp(const spmv_crs *A, uint64_t cap_ell_col, bool want_ell, s
     M->val = reinterpret_cast<const double *>(tval->p);
     M->ccs_bufs = {cp, trow, tval};
     M->colmax = hw[1];
+    return SPMV_OK;
+}
+
+// The structurally symmetric path (square matrices whose pattern equals its
+// transpose's, rows strictly ascending): IRP_T = IRP, ICOL_T = ICOL, VAL_T by
+// mirror gathers, one kernel. kRedo when the kernel finds the conditions
+// broken (the general paths then run).
+spmv_status phase1_sym(const spmv_crs *A, uint64_t cap_ell_col, bool want_ell, std::unique_ptr<spmv_matrix> &M,
+                       cudaStream_t s, const int *irp_status) {
+    const int64_t nnz = A->nnz;
+    const int32_t n = A->n_rows;
+    BufPtr cp, trow, tval, words, sct;
+    CKS(alloc_buf((size_t)(n + 1) * 4, s, &cp));
+    CKS(alloc_buf((size_t)nnz * 4, s, &trow));
+    CKS(alloc_buf((size_t)nnz * 8, s, &tval));
+    CKS(alloc_buf(64, s, &words));  // [0] status, [1..3] u64: (unused, unused, longest row)
+    CKS(alloc_buf(ccs_sym_scratch_bytes(nnz), s, &sct));
+    CK(cudaMemsetAsync(words->p, 0, 64, s));
+    CK(cudaMemcpyAsync(cp->p, A->irp, (size_t)(n + 1) * 4, cudaMemcpyDeviceToDevice, s));
+    int *d_status = reinterpret_cast<int *>(words->p);
+    unsigned long long *d_cnt = reinterpret_cast<unsigned long long *>(words->p) + 1;
+    CK(launch_ccs_sym(A->irp, n, A->icol, A->val, nnz, reinterpret_cast<int32_t *>(sct->p),
+                      reinterpret_cast<int32_t *>(trow->p), reinterpret_cast<double *>(tval->p), d_cnt, d_status, s));
+    unsigned long long hw[4] = {0, 0, 0, 0};
+    int hirp = 0;
+    CK(cudaMemcpyAsync(hw, words->p, sizeof(hw), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&hirp, irp_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CKS(status_from_dev(hirp));
+    const int dst = (int)(hw[0] & 0xffffffffu);
+    CKS(status_from_dev(dst));
+    if (dst & ST_REDO) return kRedo;  // not symmetric, or a row out of order
+    const int32_t colmax = (int32_t)hw[3];
+    if (want_ell && cap_ell_col && ell_bytes(A->n_cols, colmax) > cap_ell_col) return SPMV_ERR_MEMORY_CAP;
+    M->ptr = reinterpret_cast<const int32_t *>(cp->p);
+    M->idx = reinterpret_cast<const int32_t *>(trow->p);
+    M->val = reinterpret_cast<const double *>(tval->p);
+    M->ccs_bufs = {cp, trow, tval};
+    M->colmax = colmax;
     return SPMV_OK;
 }
 
@@ -576,6 +616,26 @@ spmv_status phase1(const spmv_crs *A, uint64_t cap_ccs, uint64_t cap_ell_col, bo
     // most 4x the pairs array); SPMV_HINT_PHASE1 forces a path (tests and
     // measurements).
     const int force = hint_value(SPMV_HINT_PHASE1);
+    // A square matrix whose sampled entries all have their mirror (and rows
+    // in ascending order) first tries the structurally symmetric path.
+    if (A->n_rows == A->n_cols && nnz > 0 && (force == 0 || force == SPMV_PHASE1_SYMMETRIC)) {
+        bool try_sym = force == SPMV_PHASE1_SYMMETRIC;
+        if (!try_sym) {
+            BufPtr fw;
+            CKS(alloc_buf(16, s, &fw));
+            CK(cudaMemsetAsync(fw->p, 0, 16, s));
+            CK(launch_sym_sample(A->irp, A->n_rows, A->icol, nnz, kSymSamples, reinterpret_cast<int32_t *>(fw->p),
+                                 s));
+            int32_t hf = 0;
+            CK(cudaMemcpyAsync(&hf, fw->p, sizeof(hf), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            try_sym = hf == 0;
+        }
+        if (try_sym) {
+            spmv_status st = phase1_sym(A, cap_ell_col, want_ell, M, s, irp_status);
+            if (st != kRedo) return st;
+        }
+    }
     const bool dense_cols = (int64_t)col_slot_cap() * nc <= 4 * nnz && nnz > 0;
     // the register-sort fix-ups (row-position and grouped paths) pack
     // (row << 5 | slot) into 32 bits

@@ -226,6 +226,18 @@ cudaError_t launch_col_claim_grp(const int32_t *irp, int32_t n_rows, const int32
 cudaError_t launch_col_fixup_grp(const int32_t *gpos, int32_t n_cols, const void *regions, int32_t *cp,
                                  int32_t *trow, double *tval, int32_t *colmax, int32_t *long_list, int *status,
                                  cudaStream_t s);
+// Structurally symmetric path of Phase I (square matrices): ICOL_T = ICOL and
+// VAL_T[p] = VAL[mirror of p]; ST_REDO when an entry has no mirror or a row is
+// not strictly ascending. cnt (zeroed u64[3]): [2] receives the longest row.
+// `scratch`: ccs_sym_scratch_bytes(nnz).
+size_t ccs_sym_scratch_bytes(int64_t nnz);
+cudaError_t launch_ccs_sym(const int32_t *irp, int32_t n, const int32_t *icol, const double *val, int64_t nnz,
+                           int32_t *scratch, int32_t *trow, double *tval, unsigned long long *cnt, int *status,
+                           cudaStream_t s);
+// failures among `samples` evenly spread entries of the symmetric path's
+// conditions, added into *fails
+cudaError_t launch_sym_sample(const int32_t *irp, int32_t n, const int32_t *icol, int64_t nnz, int samples,
+                              int32_t *fails, cudaStream_t s);
 // `pairs` must have 16 bytes of slack after its nnz elements.
 // `long_list` is preceded by its device-side count.
 cudaError_t launch_col_fixup(const int32_t *cp, int32_t n_cols, const int32_t *irp, int32_t n_rows,
@@ -310,13 +322,33 @@ cudaError_t launch_batch_analyze(const BatchMat *mats, const int2 *chunks, long 
 // every tile given.
 // Tile records of every matrix: with tiles == NULL the count per matrix
 // into cnt[m]; otherwise the records, matrix i's from tiles[cnt[i]] on.
-cudaError_t launch_batch_tiles(const BatchMat *mats, int m, long long *cnt, int4 *tiles, cudaStream_t s);
+cudaError_t launch_batch_tiles(const BatchMat *mats, int m, long long *cnt, int4 *tiles, cudaStream_t s,
+                               const long long *d_nt = nullptr);
+// d_nt (optional): the tile count in device memory (a batch planned on the
+// device); `n_tiles` then bounds it and only sizes the grid.
 cudaError_t launch_batch_build(const BatchMat *mats, const int4 *tiles, long long n_tiles, const double *x,
-                               double *y, cudaStream_t s);
+                               double *y, cudaStream_t s, const long long *d_nt = nullptr);
 cudaError_t launch_batch_apply(const BatchMat *mats, const int4 *tiles, long long n_tiles, const double *x,
-                               double *y, cudaStream_t s);
+                               double *y, cudaStream_t s, const long long *d_nt = nullptr);
 // nvec products y_j = A x_j (vector j at x + j * ldx, y + j * ldy), one launch.
 cudaError_t launch_batch_apply_multi(const BatchMat *mats, const int4 *tiles, long long n_tiles, const double *x,
-                                     long long ldx, double *y, long long ldy, int nvec, cudaStream_t s);
+                                     long long ldx, double *y, long long ldy, int nvec, cudaStream_t s,
+                                     const long long *d_nt = nullptr);
+// The plan of a batch on the device (graph-capturable build): per matrix the
+// statistics of Eq. (4) into plans, the on-line rule with the cap in matrix
+// order, ELL pointers into `pool`; bytes: scratch u64[2m]; tot (zeroed u64[2]):
+// number of ELL members and their bytes. Errors of the analysis go to *status.
+struct BatchPlanOut {
+    double mu, sigma, dmat;
+    int max_row_len;
+    int pad;
+};
+cudaError_t launch_batch_plan(BatchMat *mats, const BatchAcc *acc, int m, double dstar, unsigned long long cap,
+                              unsigned char *pool, unsigned long long *bytes, BatchPlanOut *plans,
+                              unsigned long long *tot, int *status, cudaStream_t s);
+// Exclusive scan of the tile counts in place, total into *n_tiles (0 and
+// ST_REDO when it exceeds cap).
+cudaError_t launch_batch_tile_offsets(long long *cnt, int m, long long cap, long long *n_tiles, int *status,
+                                      cudaStream_t s);
 
 }  // namespace spmvat

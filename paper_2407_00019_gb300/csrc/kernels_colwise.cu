@@ -1482,5 +1482,195 @@ cudaError_t launch_col_locality(const int32_t *icol, int64_t nnz, int samples, i
     return cudaGetLastError();
 }
 
+
+// ------------------------------------------------ structurally symmetric path
+// A special case of Phase I (Sec. 2.1) that needs no count, no prefix sum
+// and no sort. When the pattern of A equals the pattern of its transpose and
+// every row lists its columns in strictly ascending order, the serial Phase
+// I gives column c exactly the rows that row c lists as columns, in the same
+// ascending order. Then IRP_T = IRP and ICOL_T = ICOL, and the CCS value at
+// position p (row c, column i) is the value of the mirror entry (i, c):
+// VAL_T[p] = VAL[q], q the position of column c in row i.
+// k_ccs_sym does that in one pass: each entry p reads its column i, the
+// bounds of row i, and ICOL at a first guess for q reflected through the
+// row, q = IRP[i+1] - 1 - (p - IRP[c]) (exact for shift-invariant symmetric
+// stencils), else binary-searches row i; then it gathers VAL[q] and writes
+// ICOL_T[p] and VAL_T[p] coalesced. The kernel is bound by the latency of
+// these dependent gathers, so it keeps many warps in flight rather than many
+// items per thread: four items per thread, thread-striped (one warp
+// instruction = 32 consecutive entries), measured best among 2, 4, 8 and 16
+// (and faster than handling each mirror pair once, which turns half of the
+// value stores into scattered ones); rows come from the tile's staged
+// pointers as in the claim above. Every entry must find its mirror: since
+// the mirror map is then one-to-one on a finite set of distinct entries, the
+// pattern is symmetric. A missing mirror or a row out of order sets ST_REDO
+// (the host then builds the CCS on a general path), a column out of range
+// ST_BAD_INDEX; cnt[2] receives the longest row (= the longest column).
+constexpr int SYM_THREADS = 256;
+constexpr int SYM_ITEMS = 4;
+constexpr int SYM_TILE = SYM_THREADS * SYM_ITEMS;
+
+__global__ void __launch_bounds__(SYM_THREADS) k_ccs_sym(const int32_t *__restrict__ irp, int32_t n,
+                                                          const int32_t *__restrict__ icol,
+                                                          const double *__restrict__ val, int64_t nnz,
+                                                          const int32_t *__restrict__ tl, long long n_tiles,
+                                                          int32_t *__restrict__ trow, double *__restrict__ tval,
+                                                          unsigned long long *__restrict__ cnt, int *status) {
+    __shared__ int32_t s_ptr[SCT_WIN];
+    __shared__ int32_t s_row[SYM_TILE + SYM_TILE / 32];
+    const long long k0 = (long long)blockIdx.x * SYM_TILE;
+    const long long k1 = min(k0 + (long long)SYM_TILE, (long long)nnz);
+    const int t = (int)threadIdx.x;
+    const unsigned lane = lane_id();
+    int ci[SYM_ITEMS], nx[SYM_ITEMS];
+#pragma unroll
+    for (int u = 0; u < SYM_ITEMS; ++u) {
+        const long long p = k0 + t + SYM_THREADS * u;
+        ci[u] = (p < k1) ? __ldcs(icol + p) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < SYM_ITEMS; ++u) {
+        const long long p = k0 + t + SYM_THREADS * u;
+        nx[u] = __shfl_down_sync(0xffffffffu, ci[u], 1);
+        if (lane == 31) nx[u] = (p + 1 < nnz) ? __ldg(icol + p + 1) : INT_MAX;
+    }
+    const int lo = tl[blockIdx.x];
+    const int hi = (blockIdx.x + 1 < n_tiles) ? tl[blockIdx.x + 1] : n - 1;
+    const int wn = hi - lo + 2;
+    const bool sm = wn <= SCT_WIN;
+    if (sm)
+        for (int i = t; i < wn; i += SYM_THREADS) s_ptr[i] = irp[lo + i];
+    __syncthreads();
+    {
+        const long long kb = k0 + (long long)t * SYM_ITEMS;  // this thread's block of entries
+        if (kb < k1) {
+            int row = sm ? lo + last_le(s_ptr, 0, wn - 1, kb) : last_le(irp, lo, hi + 1, kb);
+#pragma unroll
+            for (int j = 0; j < SYM_ITEMS; ++j) {
+                const long long kk = kb + j;
+                while (row < hi && (long long)(sm ? s_ptr[row + 1 - lo] : irp[row + 1]) <= kk) ++row;
+                s_row[pad32(t * SYM_ITEMS + j)] = row;
+            }
+        }
+    }
+    __syncthreads();
+    int bad = 0, redo = 0, wmax = 0;
+    int c[SYM_ITEMS], jj[SYM_ITEMS], a[SYM_ITEMS], b[SYM_ITEMS];
+#pragma unroll
+    for (int u = 0; u < SYM_ITEMS; ++u) {
+        const long long p = k0 + t + SYM_THREADS * u;
+        c[u] = -1;
+        a[u] = b[u] = 0;
+        jj[u] = 0;
+        if (p >= k1) continue;
+        const int row = s_row[pad32(t + SYM_THREADS * u)];
+        const int rs = sm ? s_ptr[row - lo] : __ldg(irp + row);
+        const int re = sm ? s_ptr[row + 1 - lo] : __ldg(irp + row + 1);
+        if ((unsigned)ci[u] >= (unsigned)n) { bad = 1; continue; }
+        if (p + 1 < re && nx[u] <= ci[u]) redo = 1;
+        if (p == rs) wmax = max(wmax, re - rs);
+        c[u] = row;
+        jj[u] = (int)(p - rs);
+        const long long ra = min(max((long long)__ldg(irp + ci[u]), 0ll), (long long)nnz);
+        const long long rb = min(max((long long)__ldg(irp + ci[u] + 1), ra), (long long)nnz);
+        a[u] = (int)ra;
+        b[u] = (int)rb;
+    }
+    int q[SYM_ITEMS], g[SYM_ITEMS];
+#pragma unroll
+    for (int u = 0; u < SYM_ITEMS; ++u) {
+        q[u] = -1;
+        g[u] = -1;
+        if (c[u] < 0) continue;
+        const int guess = b[u] - 1 - jj[u];
+        if (guess >= a[u] && guess < b[u]) {
+            q[u] = guess;
+            g[u] = __ldg(icol + guess);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < SYM_ITEMS; ++u) {
+        if (c[u] < 0 || g[u] == c[u]) continue;
+        int l = a[u], h = b[u];
+        while (h - l > 1) {
+            const int m = l + ((h - l) >> 1);
+            if (__ldg(icol + m) <= c[u]) l = m; else h = m;
+        }
+        q[u] = (l < b[u] && __ldg(icol + l) == c[u]) ? l : -1;
+        if (q[u] < 0) redo = 1;
+    }
+    double v[SYM_ITEMS];
+#pragma unroll
+    for (int u = 0; u < SYM_ITEMS; ++u) v[u] = (c[u] >= 0 && q[u] >= 0) ? __ldg(val + q[u]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < SYM_ITEMS; ++u) {
+        const long long p = k0 + t + SYM_THREADS * u;
+        if (c[u] >= 0 && q[u] >= 0) {
+            __stcs(trow + p, ci[u]);
+            __stcs(tval + p, v[u]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+    if (lane == 0 && wmax > 0) atomicMax(cnt + 2, (unsigned long long)wmax);
+    if (__any_sync(0xffffffffu, redo) && lane == 0) atomicOr(status, ST_REDO);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_BAD_INDEX);
+}
+
+size_t ccs_sym_scratch_bytes(int64_t nnz) { return tile_lines_bytes(nnz, SYM_TILE); }
+
+cudaError_t launch_ccs_sym(const int32_t *irp, int32_t n, const int32_t *icol, const double *val, int64_t nnz,
+                           int32_t *scratch, int32_t *trow, double *tval, unsigned long long *cnt, int *status,
+                           cudaStream_t s) {
+    if (nnz <= 0) return cudaSuccess;
+    cudaError_t e = launch_tile_lines(irp, n, nnz, SYM_TILE, scratch, s);
+    if (e != cudaSuccess) return e;
+    const long long n_tiles = (nnz + SYM_TILE - 1) / SYM_TILE;
+    KernelScope ks("ccs_sym", s);
+    k_ccs_sym<<<(unsigned)n_tiles, SYM_THREADS, 0, s>>>(irp, n, icol, val, nnz, scratch, n_tiles, trow, tval, cnt,
+                                                          status);
+    return cudaGetLastError();
+}
+
+// Sample for the symmetric path: `samples` evenly spread entries; an entry
+// counts as a failure when its column is out of range, the next entry of its
+// row does not have a larger column, or its mirror (i, c) is missing. The
+// count goes to *fails.
+__global__ void __launch_bounds__(256) k_sym_sample(const int32_t *__restrict__ irp, int32_t n,
+                                                     const int32_t *__restrict__ icol, int64_t nnz, int samples,
+                                                     int32_t *__restrict__ fails) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    int fail = 0;
+    if (s < samples) {
+        const long long p = (long long)((double)s * (double)(nnz - 1) / (double)samples);
+        const int c = last_le(irp, 0, n, p);
+        const int i = __ldg(icol + p);
+        if ((unsigned)i >= (unsigned)n) {
+            fail = 1;
+        } else {
+            if (p + 1 < nnz && p + 1 < __ldg(irp + c + 1) && __ldg(icol + p + 1) <= i) fail = 1;
+            const long long ra = min(max((long long)__ldg(irp + i), 0ll), (long long)nnz);
+            const long long rb = min(max((long long)__ldg(irp + i + 1), ra), (long long)nnz);
+            int l = (int)ra, h = (int)rb;
+            const int e = h;
+            while (h - l > 1) {
+                const int m = l + ((h - l) >> 1);
+                if (__ldg(icol + m) <= c) l = m; else h = m;
+            }
+            if (!(l < e && __ldg(icol + l) == c)) fail = 1;
+        }
+    }
+    fail = (int)__reduce_add_sync(0xffffffffu, (unsigned)fail);
+    if (lane_id() == 0 && fail) atomicAdd(fails, fail);
+}
+
+cudaError_t launch_sym_sample(const int32_t *irp, int32_t n, const int32_t *icol, int64_t nnz, int samples,
+                              int32_t *fails, cudaStream_t s) {
+    if (nnz <= 0 || samples <= 0) return cudaSuccess;
+    KernelScope ks("sym_sample", s);
+    k_sym_sample<<<ceil_div_u(samples, 256), 256, 0, s>>>(irp, n, icol, nnz, samples, fails);
+    return cudaGetLastError();
+}
+
 }  // namespace spmvat
 

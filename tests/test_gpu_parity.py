@@ -399,7 +399,7 @@ def with_extra_columns(n, mean_len, seed, every):
     return synth.CRS(n, n, irp.astype(np.int32), icol, synth.normal(seed, 5, np.arange(icol.size)))
 
 
-PHASE1_MODES = {"scatter": 1, "kslot": 2, "rk": 3, "grp": 4}  # SPMV_PHASE1_*
+PHASE1_MODES = {"scatter": 1, "kslot": 2, "rk": 3, "grp": 4, "sym": 5}  # SPMV_PHASE1_*
 
 
 @pytest.mark.parametrize("mode", list(PHASE1_MODES))
@@ -433,13 +433,26 @@ def test_phase1_register_sort_paths_on_shuffled_rows(mode):
     M.close()
 
 
-@pytest.mark.parametrize("name,path", [("stencil27_24", "col_claim_rk"), ("powerlaw_60k", "col_claim_grp"),
+def upper_stencil():
+    """The 27-point stencil's upper triangle (columns >= row): neighbouring
+    columns, but not a symmetric pattern."""
+    H = case("stencil27_24")
+    rows = np.repeat(np.arange(H.n_rows), np.diff(H.irp))
+    keep = H.icol >= rows
+    irp = np.zeros(H.n_rows + 1, np.int64)
+    irp[1:] = np.cumsum(np.bincount(rows[keep], minlength=H.n_rows))
+    return synth.CRS(H.n_rows, H.n_cols, irp.astype(np.int32), H.icol[keep], H.val[keep])
+
+
+@pytest.mark.parametrize("name,path", [("upper_stencil", "col_claim_rk"), ("powerlaw_60k", "col_claim_grp"),
                                        ("random12", "col_claim_grp")])
 def test_phase1_path_follows_column_locality(name, path):
-    """Neighbouring columns (a stencil) keep the per-column slots; scattered
-    columns (random columns, the power law) take the grouped path."""
+    """Neighbouring columns (a stencil's upper triangle) keep the per-column
+    slots; scattered columns (random columns, the power law) take the grouped
+    path."""
     L = lib()
-    H = synth.random_crs(3000, 3000, 12, seed=85) if name == "random12" else case(name)
+    H = {"random12": lambda: synth.random_crs(3000, 3000, 12, seed=85), "upper_stencil": upper_stencil}.get(
+        name, lambda: case(name))()
     assert 32 * H.n_cols <= 4 * H.nnz  # a slot path is taken
     L.spmv_profile_enable(True)
     L.spmv_profile_read(reset=True)
@@ -480,5 +493,78 @@ def test_phase1_slot_path_with_long_columns():
     assert 32 * n <= 4 * H.nnz  # the slot path is taken
     M, claims = _claims(L, H)
     assert claims == 1  # the register-sort paths cover columns of up to 4096 entries
+    _ccs_matches_oracle(M, H)
+    M.close()
+
+
+def _drop_entry(H, r, c):
+    """H without entry (r, c) (its mirror (c, r) stays): no longer symmetric."""
+    a, b = int(H.irp[r]), int(H.irp[r + 1])
+    k = a + int(np.nonzero(H.icol[a:b] == c)[0][0])
+    keep = np.ones(H.nnz, bool)
+    keep[k] = False
+    irp = H.irp.copy()
+    irp[r + 1:] -= 1
+    return synth.CRS(H.n_rows, H.n_cols, irp, H.icol[keep], H.val[keep])
+
+
+def _reverse_row(H, r):
+    icol, val = H.icol.copy(), H.val.copy()
+    a, b = int(H.irp[r]), int(H.irp[r + 1])
+    icol[a:b], val[a:b] = H.icol[a:b][::-1], H.val[a:b][::-1]
+    return synth.CRS(H.n_rows, H.n_cols, H.irp.copy(), icol, val)
+
+
+def _phase1_kernels(L, H):
+    L.spmv_profile_enable(True)
+    L.spmv_profile_read(reset=True)
+    try:
+        M = L.spmv_transform(dev(H), L.SPMV_CRS, L.SPMV_COLWISE)
+        prof = L.spmv_profile_read(reset=True)
+    finally:
+        L.spmv_profile_enable(False)
+    return M, prof
+
+
+@pytest.mark.parametrize("name", ["laplace64", "laplace37x23", "stencil27_24", "stencil27_37", "laplace300x221",
+                                  "one_by_one"])
+def test_symmetric_patterns_take_the_mirror_path(name):
+    """Structurally symmetric matrices (stencils, Laplacians) build the CCS in
+    one mirror-gather pass: IRP_T = IRP, rows = ICOL, values of the mirror
+    entries, bit for bit the serial Phase I."""
+    L = lib()
+    H = case(name)
+    M, prof = _phase1_kernels(L, H)
+    assert "ccs_sym" in prof and not any(k.startswith("col_claim") or k == "col_count" for k in prof), prof
+    _ccs_matches_oracle(M, H)
+    arr = M.arrays()
+    assert np.array_equal(arr["ptr"].cpu().numpy(), H.irp) and np.array_equal(arr["idx"].cpu().numpy(), H.icol)
+    # the longest column feeds ELL-Column
+    E = L.spmv_transform_from(M, L.SPMV_ELL)
+    assert E.describe()["width"] == int(np.diff(H.irp).max())
+    E.close()
+    M.close()
+
+
+@pytest.mark.parametrize("kind", ["one_mirror_missing", "one_row_reversed"])
+def test_symmetric_path_hands_over_when_a_condition_fails(kind):
+    """A matrix that passes the sample but breaks the conditions in one row
+    (one entry without its mirror, or one row in descending order) is rebuilt
+    on a general path, and the CCS is still the serial one."""
+    L = lib()
+    H = synth.stencil_3d_27pt(24)
+    r = 7001
+    H = _drop_entry(H, r, int(H.icol[H.irp[r] + 3])) if kind == "one_mirror_missing" else _reverse_row(H, r)
+    M, prof = _phase1_kernels(L, H)
+    assert "ccs_sym" in prof and any(k.startswith("col_claim") or k == "col_count" for k in prof), prof
+    _ccs_matches_oracle(M, H)
+    M.close()
+
+
+def test_symmetric_path_not_taken_for_scattered_columns():
+    L = lib()
+    H = synth.random_crs(3000, 3000, 12, seed=85)
+    M, prof = _phase1_kernels(L, H)
+    assert "ccs_sym" not in prof and "sym_sample" in prof
     _ccs_matches_oracle(M, H)
     M.close()

@@ -114,7 +114,7 @@ def test_fused_build_keeps_special_bits(name):
     M.close()
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3, 4])  # SPMV_PHASE1_COUNT, _KSLOT, _ROWPOS, _GROUPED
+@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5])  # SPMV_PHASE1_COUNT, _KSLOT, _ROWPOS, _GROUPED, _SYMMETRIC
 @pytest.mark.parametrize("name", list(CASES))
 def test_column_wise_transforms_keep_special_bits(mode, name):
     L = lib()
