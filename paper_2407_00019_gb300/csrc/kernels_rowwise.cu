@@ -161,51 +161,93 @@ cudaError_t launch_tile_lines(const int32_t *ptr, int32_t n_lines, int64_t nnz, 
 }
 
 // ------------------------------------------------------------------ expand
-// Tile of EXP_TILE consecutive entries; each thread writes EXP_ITEMS of them
-// with 16-byte stores. The pointers of the lines that cover the tile are
-// staged in shared memory when they fit; each thread finds its first line by
-// binary search there and walks forward.
+// Tile of EXP_TILE consecutive entries [k0, k1). The line of entry k is the
+// largest line i with ptr[i] <= k, so: every line that starts inside the
+// tile marks its first entry (s_out[ptr[i] - k0] = i, the largest i when
+// empty lines share a start), entry k0 is marked with the tile's first line,
+// and an inclusive max-scan over the tile (8 consecutive entries per thread,
+// then warp shuffles, then the warps' totals) fills in every entry: a few
+// integer instructions per entry instead of a search per thread and a walk.
+// The tile leaves with 16-byte streaming stores. Tiles whose lines do not
+// fit the marking budget (very many empty lines) take one binary search per
+// thread in global memory and a walk instead.
 constexpr int EXP_THREADS = 256;
 constexpr int EXP_ITEMS = 8;
 constexpr int EXP_TILE = EXP_THREADS * EXP_ITEMS;
-constexpr int EXP_WIN = 2048;
+constexpr int EXP_MARK_MAX = 8192;  // lines a tile marks at most
 
 __global__ void __launch_bounds__(EXP_THREADS) k_expand(const int32_t *__restrict__ ptr, int32_t n_lines, int64_t nnz,
                                                          const int32_t *__restrict__ tl, long long n_tiles,
                                                          int32_t *__restrict__ out) {
-    __shared__ int32_t s_ptr[EXP_WIN];
+    __shared__ __align__(16) int32_t s_out[EXP_TILE];
+    __shared__ int32_t s_wmax[EXP_THREADS / 32];
     const long long k0 = (long long)blockIdx.x * EXP_TILE;
     const long long k1 = min(k0 + (long long)EXP_TILE, (long long)nnz);
+    const int n = (int)(k1 - k0);
+    const int t = (int)threadIdx.x;
+    const unsigned lane = lane_id();
     const int lo = tl[blockIdx.x];
     const int hi = (blockIdx.x + 1 < n_tiles) ? tl[blockIdx.x + 1] : n_lines - 1;
-    const int wn = hi - lo + 2;  // ptr[lo .. hi+1]
-    const bool sm = wn <= EXP_WIN;
-    if (sm)
-        for (int i = threadIdx.x; i < wn; i += EXP_THREADS) s_ptr[i] = ptr[lo + i];
-    __syncthreads();
-    const long long k = k0 + (long long)threadIdx.x * EXP_ITEMS;
-    if (k >= k1) return;
-    int line = sm ? lo + last_le(s_ptr, 0, wn - 1, k) : last_le(ptr, lo, hi + 1, k);
-    // the next line's first entry stays in a register: one compare per entry
-    long long nb = (line < hi) ? (long long)(sm ? s_ptr[line + 1 - lo] : ptr[line + 1]) : LLONG_MAX;
+    const int e = t * EXP_ITEMS;  // this thread's first entry within the tile
     int v[EXP_ITEMS];
-#pragma unroll
-    for (int j = 0; j < EXP_ITEMS; ++j) {
-        const long long kk = k + j;
-        while (kk >= nb) {
-            ++line;
-            nb = (line < hi) ? (long long)(sm ? s_ptr[line + 1 - lo] : ptr[line + 1]) : LLONG_MAX;
-        }
-        v[j] = line;
-    }
-    if (k + EXP_ITEMS <= k1 && ((reinterpret_cast<uintptr_t>(out + k) & 15) == 0)) {
+    if (hi - lo <= EXP_MARK_MAX) {
 #pragma unroll
         for (int h = 0; h < EXP_ITEMS / 4; ++h)
-            __stcs(reinterpret_cast<int4 *>(out + k) + h, make_int4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]));
+            *reinterpret_cast<int4 *>(s_out + e + 4 * h) = make_int4(-1, -1, -1, -1);
+        __syncthreads();
+        if (t == 0) atomicMax(&s_out[0], lo);
+        for (int i = lo + 1 + t; i <= hi; i += EXP_THREADS) {
+            const long long a = (long long)__ldg(ptr + i) - k0;  // first entry of line i
+            if (a >= 0 && a < n) atomicMax(&s_out[a], i);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < EXP_ITEMS / 4; ++h) {
+            const int4 q = *reinterpret_cast<const int4 *>(s_out + e + 4 * h);
+            v[4 * h] = q.x;
+            v[4 * h + 1] = q.y;
+            v[4 * h + 2] = q.z;
+            v[4 * h + 3] = q.w;
+        }
+#pragma unroll
+        for (int j = 1; j < EXP_ITEMS; ++j) v[j] = max(v[j], v[j - 1]);
+        int inc = v[EXP_ITEMS - 1];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, inc, o);
+            if ((int)lane >= o) inc = max(inc, x);
+        }
+        int pre = __shfl_up_sync(0xffffffffu, inc, 1);
+        if (lane == 0) pre = -1;
+        if (lane == 31) s_wmax[t >> 5] = inc;
+        __syncthreads();
+        for (int w = 0; w < (t >> 5); ++w) pre = max(pre, s_wmax[w]);
+#pragma unroll
+        for (int j = 0; j < EXP_ITEMS; ++j) v[j] = max(v[j], pre);
+    } else {
+        if (e >= n) return;
+        const long long k = k0 + e;
+        int line = last_le(ptr, lo, hi + 1, k);
+        long long nb = (line < hi) ? (long long)ptr[line + 1] : LLONG_MAX;
+#pragma unroll
+        for (int j = 0; j < EXP_ITEMS; ++j) {
+            while (k + j >= nb) {
+                ++line;
+                nb = (line < hi) ? (long long)ptr[line + 1] : LLONG_MAX;
+            }
+            v[j] = line;
+        }
+    }
+    if (e >= n) return;
+    if (e + EXP_ITEMS <= n && ((reinterpret_cast<uintptr_t>(out + k0 + e) & 15) == 0)) {
+#pragma unroll
+        for (int h = 0; h < EXP_ITEMS / 4; ++h)
+            __stcs(reinterpret_cast<int4 *>(out + k0 + e) + h,
+                   make_int4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]));
     } else {
 #pragma unroll
         for (int j = 0; j < EXP_ITEMS; ++j)
-            if (k + j < k1) out[k + j] = v[j];
+            if (e + j < n) out[k0 + e + j] = v[j];
     }
 }
 
@@ -227,22 +269,27 @@ cudaError_t launch_expand(const int32_t *ptr, int32_t n_lines, int64_t nnz, int3
 // two-stage TMA pipeline (stage_pipe.cuh): the tile's values and indices
 // arrive in shared memory while the previous tile is written out. Slot k of
 // line i goes to k*ld + i: for a fixed k a warp writes 32 consecutive lines
-// (coalesced, streaming stores). Two threads per line take alternate slots.
+// (coalesced, streaming stores). SPLIT threads per line take slots
+// part, part + SPLIT, ...: two for the build alone, four when the build also
+// multiplies (the x gathers then need twice the warps in flight to hide
+// their latency, and a 27-slot row is one batch of gathers per thread).
 constexpr int ELL_LINES = 128;
-constexpr int ELL_SPLIT = 2;
-constexpr int ELL_THREADS = ELL_LINES * ELL_SPLIT;
+constexpr int ELL_SPLIT_BUILD = 2;
+constexpr int ELL_SPLIT_FUSED = 4;
 constexpr int ELL_STAGE_CAP = 4096;  // entries per stage (48 KB)
-constexpr int ELL_KB = 8;            // slots a thread handles at once
+constexpr int ELL_KB_BUILD = 8;      // slots a thread handles at once
+constexpr int ELL_KB_FUSED = 4;      // (fused: two CTAs of 512 threads per SM leave 64 registers)
 using EllPipe = StagePipe<ELL_STAGE_CAP, 1>;
 
-template <bool FUSED>
-__global__ void __launch_bounds__(ELL_THREADS) k_lines_to_ell(
+template <bool FUSED, int ELL_SPLIT>
+__global__ void __launch_bounds__(ELL_LINES *ELL_SPLIT, FUSED ? 2 : 4) k_lines_to_ell(
     const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx, const double *__restrict__ val,
     int32_t n_lines, int32_t idx_bound, int32_t width, int32_t ld, int32_t n_tiles, int can_stage,
     double *__restrict__ eval, int32_t *__restrict__ eidx, const double *__restrict__ x, double *__restrict__ y,
     int *status) {
+    constexpr int ELL_KB = FUSED ? ELL_KB_FUSED : ELL_KB_BUILD;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ double s_acc[ELL_LINES];
+    __shared__ double s_acc[(ELL_SPLIT - 1) * ELL_LINES];
     EllPipe P;
     P.setup(smem);
     const int lt = threadIdx.x % ELL_LINES;
@@ -308,9 +355,13 @@ __global__ void __launch_bounds__(ELL_THREADS) k_lines_to_ell(
             }
         }
         if (FUSED) {
-            if (part == 1) s_acc[lt] = acc;
+            if (part > 0) s_acc[(part - 1) * ELL_LINES + lt] = acc;
             __syncthreads();
-            if (part == 0 && l < n_lines) y[l] = acc + s_acc[lt];
+            if (part == 0 && l < n_lines) {
+#pragma unroll
+                for (int q = 1; q < ELL_SPLIT; ++q) acc += s_acc[(q - 1) * ELL_LINES + lt];
+                y[l] = acc;
+            }
         }
     };
     pipe_tiles(P, n_tiles, val, idx, can_stage != 0, status, range, body);
@@ -325,18 +376,18 @@ cudaError_t launch_lines_to_ell(const int32_t *ptr, const int32_t *idx, const do
     const int can_stage = ((reinterpret_cast<uintptr_t>(val) & 15) == 0) &&
                           ((reinterpret_cast<uintptr_t>(idx) & 15) == 0);
     const bool fused = (y != nullptr);
-    cudaError_t e = fused ? set_smem_attr(k_lines_to_ell<true>, EllPipe::kSmem)
-                          : set_smem_attr(k_lines_to_ell<false>, EllPipe::kSmem);
+    cudaError_t e = fused ? set_smem_attr(k_lines_to_ell<true, ELL_SPLIT_FUSED>, EllPipe::kSmem)
+                          : set_smem_attr(k_lines_to_ell<false, ELL_SPLIT_BUILD>, EllPipe::kSmem);
     if (e != cudaSuccess) return e;
     int grid = sm_count() * 2;
     if (grid > n_tiles) grid = n_tiles;
     if (fused) {
         KernelScope ks("crs_to_ell_row_fused_spmv", s);
-        k_lines_to_ell<true><<<grid, ELL_THREADS, EllPipe::kSmem, s>>>(
+        k_lines_to_ell<true, ELL_SPLIT_FUSED><<<grid, ELL_LINES * ELL_SPLIT_FUSED, EllPipe::kSmem, s>>>(
             ptr, idx, val, n_lines, idx_bound, width, ld, n_tiles, can_stage, eval, eidx, x, y, status);
     } else {
         KernelScope ks(name, s);
-        k_lines_to_ell<false><<<grid, ELL_THREADS, EllPipe::kSmem, s>>>(
+        k_lines_to_ell<false, ELL_SPLIT_BUILD><<<grid, ELL_LINES * ELL_SPLIT_BUILD, EllPipe::kSmem, s>>>(
             ptr, idx, val, n_lines, idx_bound, width, ld, n_tiles, can_stage, eval, eidx, nullptr, nullptr, status);
     }
     return cudaGetLastError();
