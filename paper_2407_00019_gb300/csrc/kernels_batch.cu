@@ -425,7 +425,9 @@ __device__ __forceinline__ int tile_rows(int key) { return (int)((unsigned)key >
 // {matrix, first row, first entry, entries} from tiles[cnt[i]] on.
 template <bool FILL>
 __global__ void __launch_bounds__(T) k_batch_tiles(const BatchMat *__restrict__ mats, int m,
-                                                   long long *__restrict__ cnt, int4 *__restrict__ tiles) {
+                                                   long long *__restrict__ cnt, int4 *__restrict__ tiles,
+                                                   const long long *__restrict__ d_nt) {
+    if (FILL && d_nt && *d_nt == 0) return;  // planned on the device: no records, or more than allocated
     const int lane = (int)lane_id();
     const int nwarps = (int)(gridDim.x * (T / 32));
     for (int i = (int)(blockIdx.x * (T / 32) + (threadIdx.x >> 5)); i < m; i += nwarps) {
@@ -464,8 +466,9 @@ __global__ void __launch_bounds__(T) k_batch_tiles(const BatchMat *__restrict__ 
 
 template <bool MUL>
 __global__ void __launch_bounds__(T) k_batch_build(const BatchMat *__restrict__ mats, const int4 *__restrict__ tiles,
-                                                   long long n_tiles, const double *__restrict__ x,
-                                                   double *__restrict__ y) {
+                                                   long long n_tiles, const long long *__restrict__ d_nt,
+                                                   const double *__restrict__ x, double *__restrict__ y) {
+    if (d_nt) n_tiles = *d_nt;  // a batch planned on the device
     __shared__ BuildSmem sm_all[T / 32];  // a warp uses one member per tile
     WarpSmem &ws = sm_all[threadIdx.x >> 5].ws;
     RowSmem &rs = sm_all[threadIdx.x >> 5].rs;
@@ -509,8 +512,9 @@ __device__ __forceinline__ void stage_issue(PipeSmem &ps, int st, const BatchMat
 // into the other stage while it works on the current one, so only the x
 // gathers (and the row bounds, loaded alongside) wait on memory.
 __global__ void __launch_bounds__(AT) k_batch_apply(const BatchMat *__restrict__ mats, const int4 *__restrict__ tiles,
-                                                    long long n_tiles, const double *__restrict__ x,
-                                                    double *__restrict__ y) {
+                                                    long long n_tiles, const long long *__restrict__ d_nt,
+                                                    const double *__restrict__ x, double *__restrict__ y) {
+    if (d_nt) n_tiles = *d_nt;  // a batch planned on the device
     __shared__ PipeSmem ps_all[AT / 32];
     PipeSmem &ps = ps_all[threadIdx.x >> 5];
     const int lane = (int)lane_id();
@@ -572,8 +576,10 @@ __global__ void __launch_bounds__(AT) k_batch_apply(const BatchMat *__restrict__
 // x + j * ldx, of y at y + j * ldy.
 __global__ void __launch_bounds__(AT) k_batch_apply_multi(const BatchMat *__restrict__ mats,
                                                           const int4 *__restrict__ tiles, long long n_tiles,
+                                                          const long long *__restrict__ d_nt,
                                                           const double *__restrict__ x, long long ldx,
                                                           double *__restrict__ y, long long ldy, int nvec) {
+    if (d_nt) n_tiles = *d_nt;  // a batch planned on the device
     __shared__ RowSmem rs_all[AT / 32];
     RowSmem &rs = rs_all[threadIdx.x >> 5];
     const long long nw = (long long)gridDim.x * (AT / 32);
@@ -627,40 +633,41 @@ cudaError_t launch_batch_analyze(const BatchMat *mats, const int2 *chunks, long 
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_tiles(const BatchMat *mats, int m, long long *cnt, int4 *tiles, cudaStream_t s) {
+cudaError_t launch_batch_tiles(const BatchMat *mats, int m, long long *cnt, int4 *tiles, cudaStream_t s,
+                               const long long *d_nt) {
     if (m <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)std::min<long long>((m + T / 32 - 1) / (T / 32), (long long)sm_count() * 8);
     if (tiles) {
         KernelScope ks("batch_tiles", s);
-        k_batch_tiles<true><<<grid, T, 0, s>>>(mats, m, cnt, tiles);
+        k_batch_tiles<true><<<grid, T, 0, s>>>(mats, m, cnt, tiles, d_nt);
     } else {
         KernelScope ks("batch_tile_count", s);
-        k_batch_tiles<false><<<grid, T, 0, s>>>(mats, m, cnt, nullptr);
+        k_batch_tiles<false><<<grid, T, 0, s>>>(mats, m, cnt, nullptr, nullptr);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch_build(const BatchMat *mats, const int4 *tiles, long long n_tiles, const double *x,
-                               double *y, cudaStream_t s) {
+                               double *y, cudaStream_t s, const long long *d_nt) {
     if (n_tiles <= 0) return cudaSuccess;
     if (x) {
         const unsigned grid = (unsigned)std::min<long long>(n_tiles, batch_grid(2));
         KernelScope ks("batch_build_apply", s);
-        k_batch_build<true><<<grid, T, 0, s>>>(mats, tiles, n_tiles, x, y);
+        k_batch_build<true><<<grid, T, 0, s>>>(mats, tiles, n_tiles, d_nt, x, y);
     } else {
         const unsigned grid = (unsigned)std::min<long long>(n_tiles, batch_grid(1));
         KernelScope ks("batch_build", s);
-        k_batch_build<false><<<grid, T, 0, s>>>(mats, tiles, n_tiles, nullptr, nullptr);
+        k_batch_build<false><<<grid, T, 0, s>>>(mats, tiles, n_tiles, d_nt, nullptr, nullptr);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch_apply(const BatchMat *mats, const int4 *tiles, long long n_tiles, const double *x,
-                               double *y, cudaStream_t s) {
+                               double *y, cudaStream_t s, const long long *d_nt) {
     if (n_tiles <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)std::min<long long>((n_tiles + AT / 32 - 1) / (AT / 32), batch_grid(3));
     KernelScope ks("batch_apply", s);
-    k_batch_apply<<<grid, AT, 0, s>>>(mats, tiles, n_tiles, x, y);
+    k_batch_apply<<<grid, AT, 0, s>>>(mats, tiles, n_tiles, d_nt, x, y);
     return cudaGetLastError();
 }
 
@@ -669,12 +676,180 @@ cudaError_t launch_batch_apply(const BatchMat *mats, const int4 *tiles, long lon
 namespace spmvat {
 
 cudaError_t launch_batch_apply_multi(const BatchMat *mats, const int4 *tiles, long long n_tiles, const double *x,
-                                     long long ldx, double *y, long long ldy, int nvec, cudaStream_t s) {
+                                     long long ldx, double *y, long long ldy, int nvec, cudaStream_t s,
+                                     const long long *d_nt) {
     if (n_tiles <= 0 || nvec <= 0) return cudaSuccess;
-    if (nvec == 1) return launch_batch_apply(mats, tiles, n_tiles, x, y, s);
+    if (nvec == 1) return launch_batch_apply(mats, tiles, n_tiles, x, y, s, d_nt);
     const unsigned grid = (unsigned)std::min<long long>((n_tiles + AT / 32 - 1) / (AT / 32), batch_grid(4));
     KernelScope ks("batch_apply_multi", s);
-    k_batch_apply_multi<<<grid, AT, 0, s>>>(mats, tiles, n_tiles, x, ldx, y, ldy, nvec);
+    k_batch_apply_multi<<<grid, AT, 0, s>>>(mats, tiles, n_tiles, d_nt, x, ldx, y, ldy, nvec);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------- plan on the device
+// The build of a batch without host work between its launches (so that one
+// CUDA graph can hold it): the on-line rule of Sec. 2.2 per matrix, the ELL
+// arrays placed in a pool allocated beforehand, and the tile records counted,
+// offset and written by kernels.
+//
+// k_batch_plan (one CTA): Eq. (4) per matrix from the analysis sums (the
+// numerator of sigma^2 exact in 128-bit integers, as on the host); ELL-Row
+// iff D_mat < D* and the ELL arrays of the matrices chosen before it, in
+// matrix order, plus its own fit the cap (a block-wide scan of the
+// candidates' bytes; only if they do not all fit, one thread takes them in
+// order and skips those that do not fit); then the descriptors (format,
+// width, leading dimension, ELL pointers into the pool, and for ELL members
+// one lane per row in 32-row tiles; CRS members keep the lanes per row the
+// host set from the schedule table) and the plan records for the host.
+constexpr int PLAN_T = 1024;
+constexpr unsigned long long kCand = 1ull << 63;  // flag: the rule picks ELL-Row (bytes below it)
+
+__device__ unsigned long long block_excl_scan_u64(unsigned long long v, unsigned long long *s_w,
+                                                  unsigned long long *total) {
+    const int lane = (int)lane_id(), w = (int)(threadIdx.x >> 5);
+    unsigned long long inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) s_w[w] = inc;
+    __syncthreads();
+    unsigned long long pre = 0, tot = 0;
+    for (int j = 0; j < PLAN_T / 32; ++j) {
+        if (j < w) pre += s_w[j];
+        tot += s_w[j];
+    }
+    __syncthreads();
+    *total = tot;
+    return pre + inc - v;
+}
+
+__global__ void __launch_bounds__(PLAN_T) k_batch_plan(BatchMat *__restrict__ mats, const BatchAcc *__restrict__ acc,
+                                                       int m, double dstar, unsigned long long cap,
+                                                       unsigned char *__restrict__ pool,
+                                                       unsigned long long *__restrict__ bytes,
+                                                       BatchPlanOut *__restrict__ plans,
+                                                       unsigned long long *__restrict__ tot, int *status) {
+    __shared__ unsigned long long s_w[PLAN_T / 32];
+    __shared__ int s_greedy;
+    int bad = 0;
+    // statistics and the candidates' ELL bytes
+    for (int i = threadIdx.x; i < m; i += PLAN_T) {
+        const BatchAcc a = acc[i];
+        const BatchMat &D = mats[i];
+        BatchPlanOut P;
+        const int st = a.status;
+        if (st) bad |= st;
+        if ((long long)a.sum_len != D.nnz) bad |= ST_BAD_PTR;
+        const double n = (double)D.n_rows;
+        const unsigned __int128 num = (unsigned __int128)(unsigned long long)D.n_rows * a.sum_len2 -
+                                      (unsigned __int128)a.sum_len * a.sum_len;
+        P.mu = (double)a.sum_len / n;
+        P.sigma = sqrt((double)num) / n;
+        P.dmat = a.sum_len == 0 ? 0.0 : P.sigma / P.mu;
+        P.max_row_len = a.max_len;
+        plans[i] = P;
+        const unsigned long long eb = (unsigned long long)((D.n_rows + 31) / 32 * 32) * (unsigned long long)a.max_len * 12ull;
+        bytes[i] = (P.dmat < dstar) ? (kCand | eb) : 0ull;  // a candidate may need 0 bytes (no entries)
+    }
+    if (bad) atomicOr(status, bad);
+    __syncthreads();
+    // matrix-order offsets of the candidates
+    unsigned long long carry = 0;
+    for (int base = 0; base < m; base += PLAN_T) {
+        const int i = base + (int)threadIdx.x;
+        const unsigned long long v = i < m ? (bytes[i] & ~kCand) : 0ull;
+        unsigned long long t = 0;
+        const unsigned long long ex = block_excl_scan_u64(v, s_w, &t);
+        if (i < m) bytes[m + i] = carry + ex;  // offset if every candidate before it is taken
+        carry += t;
+    }
+    if (threadIdx.x == 0) s_greedy = carry > cap;
+    __syncthreads();
+    if (s_greedy && threadIdx.x == 0) {
+        // the cap binds: candidates in matrix order, each taken if it still fits
+        unsigned long long used = 0;
+        for (int i = 0; i < m; ++i) {
+            const unsigned long long eb = bytes[i] & ~kCand;
+            if ((bytes[i] & kCand) && used + eb <= cap) {
+                bytes[m + i] = used;
+                used += eb;
+            } else {
+                bytes[i] = 0;
+            }
+        }
+    }
+    __syncthreads();
+    unsigned long long n_ell = 0, ell_bytes = 0;
+    for (int i = threadIdx.x; i < m; i += PLAN_T) {
+        BatchMat &D = mats[i];
+        const BatchPlanOut &P = plans[i];
+        const unsigned long long eb = bytes[i] & ~kCand;
+        if (bytes[i] & kCand) {
+            D.fmt = BATCH_ELL;
+            D.width = P.max_row_len;
+            D.ld = (D.n_rows + 31) / 32 * 32;
+            D.tpr = 1;
+            D.rpt = 32;
+            unsigned char *b = pool + bytes[m + i];
+            D.eval = reinterpret_cast<double *>(b);
+            D.ecol = reinterpret_cast<int32_t *>(b + (unsigned long long)D.ld * D.width * 8ull);
+            n_ell += 1;
+            ell_bytes += eb;
+        } else {
+            D.fmt = BATCH_CRS;
+            D.width = D.ld = 0;
+            D.eval = nullptr;
+            D.ecol = nullptr;
+        }
+    }
+    n_ell = warp_sum(n_ell);
+    ell_bytes = warp_sum(ell_bytes);
+    if (lane_id() == 0 && n_ell) {
+        atomicAdd(tot, n_ell);
+        atomicAdd(tot + 1, ell_bytes);
+    }
+}
+
+// Exclusive scan of the per-matrix tile counts in place; the total into
+// *n_tiles. A total above `cap` (the records allocated) sets ST_REDO and
+// leaves *n_tiles = 0, so that no later launch writes or reads past them; so
+// does a malformed member.
+__global__ void __launch_bounds__(PLAN_T) k_batch_tile_offsets(long long *__restrict__ cnt, int m, long long cap,
+                                                               long long *__restrict__ n_tiles, int *status) {
+    __shared__ unsigned long long s_w[PLAN_T / 32];
+    unsigned long long carry = 0;
+    for (int base = 0; base < m; base += PLAN_T) {
+        const int i = base + (int)threadIdx.x;
+        const unsigned long long v = i < m ? (unsigned long long)cnt[i] : 0ull;
+        unsigned long long t = 0;
+        const unsigned long long ex = block_excl_scan_u64(v, s_w, &t);
+        if (i < m) cnt[i] = (long long)(carry + ex);
+        carry += t;
+    }
+    if (threadIdx.x == 0) {
+        // a malformed member (reported by the plan) or more records than
+        // allocated: no records, so the later launches do nothing
+        const bool malformed = (*status & (ST_BAD_PTR | ST_BAD_INDEX)) != 0;
+        const bool over = (long long)carry > cap;
+        *n_tiles = (over || malformed) ? 0 : (long long)carry;
+        if (over) atomicOr(status, ST_REDO);
+    }
+}
+
+cudaError_t launch_batch_plan(BatchMat *mats, const BatchAcc *acc, int m, double dstar, unsigned long long cap,
+                              unsigned char *pool, unsigned long long *bytes, BatchPlanOut *plans,
+                              unsigned long long *tot, int *status, cudaStream_t s) {
+    KernelScope ks("batch_plan", s);
+    k_batch_plan<<<1, PLAN_T, 0, s>>>(mats, acc, m, dstar, cap, pool, bytes, plans, tot, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_tile_offsets(long long *cnt, int m, long long cap, long long *n_tiles, int *status,
+                                      cudaStream_t s) {
+    KernelScope ks("batch_tile_offsets", s);
+    k_batch_tile_offsets<<<1, PLAN_T, 0, s>>>(cnt, m, cap, n_tiles, status);
     return cudaGetLastError();
 }
 

@@ -262,3 +262,122 @@ def test_allocation_failure_is_reported_and_nothing_leaks(host_set):
     torch.cuda.synchronize()
     assert live == {}
     L.spmv_batch_create(dev, dstar=math.inf).close()
+
+
+# ---- batches planned on the device (one CUDA graph for build and products) ----
+def _cap_for(host_set, dstar):
+    """A cap that fits every candidate of the host-planned batch."""
+    L = lib()
+    B = L.spmv_batch_create(L.Crs.batch_from_host(host_set), dstar=dstar)
+    eb = B.info()["ell_bytes"]
+    B.close()
+    return max(eb, 1 << 20)
+
+
+@pytest.mark.parametrize("dstar", [0.0, math.inf, 0.2])
+def test_device_planned_batch_equals_the_host_planned_one(host_set, dstar):
+    """prepare + build gives the host path's plan (format, lanes, widths,
+    statistics) and its products bit for bit, and ELL arrays equal to the
+    oracle's."""
+    import torch
+    L = lib()
+    dev = L.Crs.batch_from_host(host_set)
+    kw = dict(dstar=dstar, mem_cap_bytes=_cap_for(host_set, dstar) if dstar > 0 else 0)
+    H = L.spmv_batch_create(dev, **kw)
+    D = L.spmv_batch_prepare(dev, **kw)
+    xh, x, y0 = _xy(host_set, seed=21)
+    y1 = torch.full_like(y0, float("nan"))
+    D.build(x, y1)  # the first product fused with the build
+    D.status()
+    ph, pd = H.plans(), D.plans()
+    for i, (a, b) in enumerate(zip(ph, pd)):
+        for k in ("format", "threads_per_row", "rows_per_tile", "width", "ld", "max_row_len", "x_offset",
+                  "y_offset"):
+            assert a[k] == b[k], (i, k, a[k], b[k])
+        for k in ("mu", "sigma", "dmat"):
+            assert a[k] == b[k] or math.isclose(a[k], b[k], rel_tol=2 ** -52), (i, k, a[k], b[k])
+        if b["format"] == L.SPMV_ELL and b["width"] > 0:
+            Hm = host_set[i]
+            ev, ei, W = oracle.crs_to_ell_row(Hm.n_rows, Hm.irp, Hm.icol, Hm.val)
+            gv, gi = _ell_arrays(b, Hm.n_rows)
+            assert np.array_equal(bits(gv), bits(ev.reshape(W, Hm.n_rows)))
+            assert np.array_equal(gi, ei.reshape(W, Hm.n_rows))
+    hi, di = H.info(), D.info()
+    assert hi["n_tiles"] == di["n_tiles"] and hi["n_ell"] == di["n_ell"] and hi["ell_bytes"] == di["ell_bytes"]
+    H.apply(x, y0)
+    y2 = torch.full_like(y0, float("nan"))
+    D.apply(x, y2)
+    torch.cuda.synchronize()
+    assert np.array_equal(bits(y0.cpu().numpy()), bits(y2.cpu().numpy()))
+    _check_products(host_set, pd, xh, y1.cpu().numpy(), f"device plan, fused, D*={dstar}")
+    H.close()
+    D.close()
+
+
+def test_device_planned_build_and_products_in_one_cuda_graph(host_set):
+    """The whole build (analysis, rule, tiles, ELL build, first product) and
+    two more products captured in one CUDA graph and replayed: every product
+    equals the oracle within the tolerance, and replays repeat their bits."""
+    import torch
+    L = lib()
+    dev = L.Crs.batch_from_host(host_set)
+    D = L.spmv_batch_prepare(dev, dstar=0.2, mem_cap_bytes=_cap_for(host_set, 0.2))
+    xh, x, y0 = _xy(host_set, seed=22)
+    y1 = torch.full_like(y0, float("nan"))
+    xx = torch.cat([x, x])
+    yy = torch.full((2 * y0.numel(),), float("nan"), dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        D.build(x, y0)
+        D.apply(x, y1)
+        D.apply_multi(xx, yy, 2)
+    launches0 = L.spmv_launch_count()
+    for rep in range(3):
+        y0.fill_(float("nan"))
+        y1.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        a, b = y0.cpu().numpy(), y1.cpu().numpy()
+        if rep == 0:
+            first = bits(b).copy()
+        assert np.array_equal(bits(b), first)
+    assert L.spmv_launch_count() == launches0  # replays launch nothing through the host library
+    D.status()
+    plans = D.plans()
+    assert sum(P["format"] == L.SPMV_ELL for P in plans) > 0
+    _check_products(host_set, plans, xh, a, "graph build + first product")
+    _check_products(host_set, plans, xh, b, "graph product")
+    yyh = yy.cpu().numpy()
+    assert np.array_equal(bits(yyh[:y0.numel()]), bits(b)) and np.array_equal(bits(yyh[y0.numel():]), bits(b))
+    D.close()
+
+
+def test_device_planned_batch_reports_a_malformed_member(host_set):
+    L = lib()
+    bad = synth.CRS(4, 4, np.array([0, 2, 1, 3, 4], np.int32), np.array([0, 1, 2, 3], np.int32), np.ones(4))
+    D = L.spmv_batch_prepare(L.Crs.batch_from_host(host_set[:5] + [bad]), dstar=0.0)
+    D.build()
+    with pytest.raises(L.SpmvError) as e:
+        D.status()
+    assert e.value.status == 2  # SPMV_ERR_INVALID_MATRIX
+    D.close()
+
+
+def test_schedule_table_sets_lanes_per_row(host_set):
+    L = lib()
+    old = L.spmv_batch_schedule_get()
+    try:
+        L.spmv_batch_schedule_set([8] * L.SPMV_BATCH_SCHED_CLASSES)
+        B = L.spmv_batch_create(L.Crs.batch_from_host(host_set), dstar=0.0)
+        assert all(P["threads_per_row"] == 8 for P in B.plans())
+        xh, x, y = _xy(host_set, seed=23)
+        B.apply(x, y)
+        _check_products(host_set, B.plans(), xh, y.cpu().numpy(), "table of 8 lanes")
+        assert B.time(x, y, warm=1, reps=3) > 0
+        B.close()
+        with pytest.raises(L.SpmvError):
+            L.spmv_batch_schedule_set([3])
+    finally:
+        L.spmv_batch_schedule_set(old)
