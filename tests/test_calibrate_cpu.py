@@ -80,3 +80,33 @@ def test_dstar_save_load(tmp_path):
         C.load_dstar(p, device="GPU Y")
     C.save_dstar(p, dict(res, dstar=math.inf))
     assert C.load_dstar(p) == math.inf
+
+
+def test_schedule_files_round_trip_and_refuse_another_device(tmp_path):
+    from paper_2407_00019_gb300 import calibrate as cal
+    res = {"table": [1, 1, 1, 1, 1, 8, 8, 8, 32, 32], "times_ms": {}, "device": "NVIDIA GB300"}
+    p = tmp_path / "s.json"
+    cal.save_schedule(str(p), res)
+    assert cal.load_schedule(str(p), "NVIDIA GB300") == res["table"]
+    with pytest.raises(ValueError):
+        cal.load_schedule(str(p), "another GPU")
+    bad = dict(res, table=[3] * 10)
+    cal.save_schedule(str(p), bad)
+    with pytest.raises(ValueError):
+        cal.load_schedule(str(p))
+
+
+def test_schedule_calibration_sets_cover_every_class():
+    from paper_2407_00019_gb300 import calibrate as cal
+    for c in (0, 3, 9):
+        mats = cal.schedule_set_for_class(c, entries=200_000, rows=512)
+        mu = sum(H.nnz for H in mats) / sum(H.n_rows for H in mats)
+        lo, hi = (0.0, 1.0) if c == 0 else (2.0 ** (c - 1), 2.0 ** c)
+        assert lo * 0.8 <= mu < hi * 1.2, (c, mu)
+
+
+def test_committed_calibrations_are_for_the_gpu_and_readable():
+    from paper_2407_00019_gb300 import calibrate as cal
+    for rule in ("prefix", "maxpass"):
+        d = cal.load_dstar(cal.committed_path(rule), "NVIDIA GB300")
+        assert d >= 0.0
