@@ -59,6 +59,10 @@ struct MatEntry {
     int32_t target = SPMV_CRS;
     uint64_t target_bytes = 0;       // device bytes of the target transformation
     spmv_batch *crs = nullptr;       // the matrix alone as a batch, in CRS (always present)
+    spmv_matrix *plain = nullptr;    // CRS handle of spmv_transform: SPMV_SERVER_PLAIN, and uneven rows
+    bool uneven = false;             // D_mat > 0.5 or a row of 2048 entries or more: products in CRS
+                                     // run as spmv_apply on `plain` (the entry-split product), which on
+                                     // such rows beats the batch product even with k vectors at once
     spmv_batch *fast = nullptr;      // the same in its target format (cached), or NULL
     cudaEvent_t built = nullptr;     // recorded after the transformation's kernels
     uint64_t fast_bytes = 0;
@@ -155,6 +159,24 @@ void admit(spmv_server *S, Request *r, int slot) {
     MatEntry *E = entry(S, r->mat);
     if (r->ready) cudaStreamWaitEvent(s, r->ready, 0);
     E->products += r->k;
+    if ((S->p.flags & SPMV_SERVER_PLAIN) || (E->uneven && !E->fast && E->target == SPMV_CRS)) {
+        // the per-matrix form (one spmv_apply per product, CRS, in arrival
+        // order), and CRS products of uneven rows
+        r->status = SPMV_OK;
+        for (int32_t j = 0; j < r->k && r->status == SPMV_OK; ++j)
+            r->status = spmv_apply(E->plain, r->x + (size_t)j * E->A.n_cols, r->y + (size_t)j * E->A.n_rows, s);
+        r->format = SPMV_CRS;
+        r->cached = false;
+        r->state.store(R_RUNNING);
+        S->slot_req[slot] = r;
+        if (cudaLaunchHostFunc(s, on_done, r) != cudaSuccess) {
+            cudaGetLastError();
+            cudaStreamSynchronize(s);
+            r->status = r->status == SPMV_OK ? SPMV_ERR_CUDA : r->status;
+            on_done(r);
+        }
+        return;
+    }
     spmv_batch *H = E->crs;
     bool miss = false;
     if (E->target != SPMV_CRS) {
@@ -296,6 +318,7 @@ spmv_status spmv_server_create(const spmv_server_params *p, spmv_server **out) {
     if (!S) return SPMV_ERR_OOM;
     if (p) S->p = *p;
     if (S->p.n_streams <= 0) S->p.n_streams = 4;
+    if (S->p.flags & SPMV_SERVER_PLAIN) S->p.n_streams = 1;  // serial, one request at a time
     if (S->p.n_streams > 64) return SPMV_ERR_INVALID_ARG;
     if (S->p.amortize_products <= 0) S->p.amortize_products = 2;
     if (cudaGetDevice(&S->device) != cudaSuccess) { cudaGetLastError(); return SPMV_ERR_CUDA; }
@@ -340,11 +363,26 @@ spmv_status spmv_server_add_matrix(spmv_server *S, const spmv_crs *A, int32_t *i
     if (rc != SPMV_OK) return rc;
     spmv_at_params crs;
     memset(&crs, 0, sizeof(crs));  // D* = 0: CRS
-    rc = spmv_batch_create(A, 1, &crs, nullptr, nullptr, &E->crs, S->ctrl);
-    if (rc != SPMV_OK) return rc;
+    E->uneven = st.dmat > 0.5 || st.max_row_len >= 2048;
+    if (S->p.flags & SPMV_SERVER_PLAIN) {
+        rc = spmv_transform(A, SPMV_CRS, SPMV_ROWWISE, 0, &E->plain, S->ctrl);
+        if (rc != SPMV_OK) return rc;
+        fmt = SPMV_CRS;  // no format cache in the per-matrix form
+    } else {
+        rc = spmv_batch_create(A, 1, &crs, nullptr, nullptr, &E->crs, S->ctrl);
+        if (rc != SPMV_OK) return rc;
+        if (E->uneven && fmt == SPMV_CRS) {
+            rc = spmv_transform(A, SPMV_CRS, SPMV_ROWWISE, 0, &E->plain, S->ctrl);
+            if (rc != SPMV_OK) {
+                spmv_batch_destroy(E->crs);
+                return rc;
+            }
+        }
+    }
     if (cudaStreamSynchronize(S->ctrl) != cudaSuccess) {
         cudaGetLastError();
-        spmv_batch_destroy(E->crs);
+        if (E->crs) spmv_batch_destroy(E->crs);
+        if (E->plain) spmv_destroy(E->plain);
         return SPMV_ERR_CUDA;
     }
     E->target = fmt;
@@ -483,6 +521,7 @@ void spmv_server_destroy(spmv_server *S) {
     for (auto &e : S->mats) {
         if (e->fast) spmv_batch_destroy(e->fast);
         if (e->crs) spmv_batch_destroy(e->crs);
+        if (e->plain) spmv_destroy(e->plain);
         if (e->built) cudaEventDestroy(e->built);
     }
     for (auto &s : S->streams) {

@@ -275,3 +275,47 @@ def test_failed_transformation_falls_back_to_crs():
     assert fmt == L.SPMV_ELL
     assert_spmv_close(y.cpu().numpy(), H, xs, what="after fallback")
     S.close()
+
+
+def test_plain_form_serves_every_request_on_crs():
+    """The per-matrix form the serving benchmark compares against: one slot,
+    one spmv_apply per product on CRS, no format cache; results within the
+    tolerance and in CRS whatever D* says."""
+    L = lib()
+    pool = _pool()
+    dev = [L.Crs.from_host(H) for H in pool]
+    reqs = _requests(pool, 24, seed=3)
+    S = L.Server(dstar=math.inf, n_streams=6, amortize_products=1, flags=L.Server.PLAIN)
+    ids = [S.add_matrix(A) for A in dev]
+    launches0 = L.spmv_launch_count()
+    ys, fmts = _run(S, dev, ids, reqs, concurrent=True)
+    st = S.stats()
+    S.close()
+    assert all(f == L.SPMV_CRS for f in fmts)
+    assert st["transforms"] == 0 and st["cache_hits"] == 0 and st["completed"] == len(reqs)
+    assert st["products"] == sum(k for _, k, _ in reqs)
+    assert L.spmv_launch_count() - launches0 >= st["products"]  # at least one launch per product
+    _check_oracle(pool, reqs, ys, "plain")
+
+
+def test_uneven_rows_run_per_product_in_the_mix():
+    """Matrices with uneven rows (D_mat > 0.5 or a row of 2048 entries) that
+    stay in CRS run each product as spmv_apply's entry-split product: results
+    alone and in the mix agree within the tolerance, and both with the
+    oracle."""
+    L = lib()
+    pool = [synth.power_law(20000, kmax=5000, seed=15), synth.laplacian_2d_5pt(40)]
+    assert L.spmv_analyze(L.Crs.from_host(pool[0]))["dmat"] > 0.5
+    dev = [L.Crs.from_host(H) for H in pool]
+    reqs = _requests(pool, 16, seed=5)
+    outs = []
+    for streams, conc in ((1, False), (4, True)):
+        S = L.Server(dstar=0.0, n_streams=streams)
+        ids = [S.add_matrix(A) for A in dev]
+        launches0 = L.spmv_launch_count()
+        ys, fmts = _run(S, dev, ids, reqs, concurrent=conc)
+        S.close()
+        outs.append(ys)
+        _check_oracle(pool, reqs, ys, f"uneven, {streams} slots")
+    # the power-law requests took one launch (or more) per product
+    assert L.spmv_launch_count() - launches0 >= sum(k for i, k, _ in reqs if i == 0)
