@@ -1052,6 +1052,8 @@ def main():
     ap.add_argument("--no-loop", action="store_true", help="batches: skip the per-matrix loop comparison")
     ap.add_argument("--sequential", action="store_true",
                     help="run the row-wise and column-wise pipelines of a step one after the other on one stream")
+    ap.add_argument("--phase1", choices=["auto", "scatter", "kslot", "rk", "grp", "sym"], default="auto",
+                    help="force one Phase I path through the library's schedule hint (profiling)")
     ap.add_argument("--dstar", type=float, default=None,
                     help="use this D* instead of the off-line calibration (profiling runs)")
     args = ap.parse_args()
@@ -1078,6 +1080,10 @@ def main():
     device = torch.device("cuda", local)
     import paper_2407_00019_gb300 as L
     L.load_library()
+    if args.phase1 != "auto":
+        L.spmv_set_hint(L.SPMV_HINT_PHASE1, {"scatter": L.SPMV_PHASE1_COUNT, "kslot": L.SPMV_PHASE1_KSLOT,
+                                             "rk": L.SPMV_PHASE1_ROWPOS, "grp": L.SPMV_PHASE1_GROUPED,
+                                             "sym": L.SPMV_PHASE1_SYMMETRIC}[args.phase1])
 
     H, xh = make_matrix(w, rank)
     A = L.Crs.from_host(H)
@@ -1195,6 +1201,14 @@ def main():
                   "ell_row": fmt_rate([k for k in per_kernel if k == "spmv_ell_row"], "spmv_ell_row"),
                   "coo_col": fmt_rate(cooc_k, "spmv_coo_col"),
                   "ell_col": fmt_rate([k for k in per_kernel if k == "spmv_ell_col"], "spmv_ell_col")}
+    # the ceiling of the column-wise products: their FP64 atomic adds alone
+    # (coalesced, the best case on banded matrices), one per entry (COO-Column)
+    # or per slot (ELL-Column)
+    for fmt, adds in (("coo_col", H.nnz), ("ell_col", round32(H.n_cols) * Wc)):
+        if per_format.get(fmt) and adds > 0:
+            t_at = L.spmv_measure_atomics(H.n_rows, adds, reps=10)
+            per_format[fmt]["atomics_ceiling_ms"] = t_at
+            per_format[fmt]["frac_of_atomics_ceiling"] = t_at / per_format[fmt]["ms"]
     # CRS -> ELL cost in CRS-SpMV units: standalone build, and the fused
     # build + first SpMV counted beyond the SpMV it replaces
     t_crs = per_format["crs"]["ms"] if per_format["crs"] else None

@@ -243,6 +243,14 @@ spmv_status spmv_dstar_from_points(int32_t m, const double *dmat, const double *
 spmv_status spmv_measure(const spmv_crs *A, const spmv_at_params *p, spmv_timing *out,
                          spmv_stream_t stream);
 
+/* SYNC. Measurement of the ceiling that binds the column-wise products
+ * (Sec. 2.1 column-wise formats add every product into y with an FP64 atomic,
+ * Fig. 1): the median device time (ms) of `reps` launches that do n_adds
+ * FP64 atomic adds into n_targets doubles, lanes on consecutive elements
+ * (their best case on banded matrices), and nothing else. */
+spmv_status spmv_measure_atomics(int64_t n_targets, int64_t n_adds, int32_t reps, double *ms,
+                                 spmv_stream_t stream);
+
 /* SYNC. Off-line phase (Sec. 2.2 steps (1)-(4)): spmv_measure on each of the
  * m matrices, then D* by p->dstar_rule and p->c. dmat_out / rell_out (host
  * double[m], may be NULL) receive the D_mat-R_ell graph; a matrix whose ELL

@@ -27,7 +27,7 @@ __all__ = [
     "spmv_batch_plan_get", "spmv_batch_destroy", "Batch", "spmv_batch_apply_multi", "Server", "spmv_server_create",
     "spmv_set_hint", "spmv_get_hint", "hint",
     "spmv_batch_prepare", "spmv_batch_build", "spmv_batch_status", "spmv_batch_schedule_set",
-    "spmv_batch_schedule_get", "spmv_batch_time", "SPMV_BATCH_SCHED_CLASSES",
+    "spmv_batch_schedule_get", "spmv_batch_time", "SPMV_BATCH_SCHED_CLASSES", "spmv_measure_atomics",
     "SPMV_HINT_PHASE1", "SPMV_HINT_CRS_SPLIT", "SPMV_HINT_COO_FLAT", "SPMV_HINT_BATCH_TPR",
     "SPMV_PHASE1_COUNT", "SPMV_PHASE1_KSLOT", "SPMV_PHASE1_ROWPOS", "SPMV_PHASE1_GROUPED", "SPMV_PHASE1_SYMMETRIC",
 ]
@@ -174,6 +174,7 @@ def load_library():
         "spmv_batch_schedule_set": (ctypes.c_int, [P(i32), i32]),
         "spmv_batch_schedule_get": (ctypes.c_int, [P(i32), i32]),
         "spmv_batch_time": (ctypes.c_int, [vp, vp, vp, i32, i32, P(dbl), vp]),
+        "spmv_measure_atomics": (ctypes.c_int, [i64, i64, i32, P(dbl), vp]),
         "spmv_server_create": (ctypes.c_int, [P(_ServerParamsT), P(vp)]),
         "spmv_server_add_matrix": (ctypes.c_int, [vp, P(_CrsT), P(i32)]),
         "spmv_server_submit": (ctypes.c_int, [vp, i32, i32, vp, vp, vp, P(u64)]),
@@ -739,4 +740,12 @@ def spmv_batch_time(B: Batch, x, y, warm=3, reps=20, stream=None) -> float:
     ms = ctypes.c_double()
     _check(load_library().spmv_batch_time(B.handle, _ptr(x), _ptr(y), int(warm), int(reps), ctypes.byref(ms),
                                           _stream(stream)), "spmv_batch_time")
+    return ms.value
+
+
+def spmv_measure_atomics(n_targets: int, n_adds: int, reps: int = 10, stream=None) -> float:
+    """Median ms of n_adds coalesced FP64 atomic adds into n_targets doubles."""
+    ms = ctypes.c_double()
+    _check(load_library().spmv_measure_atomics(int(n_targets), int(n_adds), int(reps), ctypes.byref(ms),
+                                               _stream(stream)), "spmv_measure_atomics")
     return ms.value

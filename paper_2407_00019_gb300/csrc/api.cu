@@ -1077,6 +1077,19 @@ spmv_status spmv_measure(const spmv_crs *A, const spmv_at_params *p, spmv_timing
     return SPMV_OK;
 }
 
+spmv_status spmv_measure_atomics(int64_t n_targets, int64_t n_adds, int32_t reps, double *ms, spmv_stream_t stream) {
+    if (n_targets <= 0 || n_adds <= 0 || reps <= 0 || !ms) return SPMV_ERR_INVALID_ARG;
+    cudaStream_t s = S(stream);
+    BufPtr yb;
+    CKS(alloc_buf(sizeof(double) * (size_t)n_targets, s, &yb));
+    double *y = reinterpret_cast<double *>(yb->p);
+    CK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)n_targets, s));
+    return time_median([&]() -> spmv_status {
+        CK(launch_atomic_ceiling(y, n_targets, n_adds, s));
+        return SPMV_OK;
+    }, 3, reps, s, ms);
+}
+
 spmv_status spmv_calibrate(const spmv_crs *const *set, int32_t m, const spmv_at_params *p, double *dmat_out,
                            double *rell_out, double *dstar_out, spmv_stream_t stream) {
     if (!set || m < 0 || !p || !dstar_out) return SPMV_ERR_INVALID_ARG;

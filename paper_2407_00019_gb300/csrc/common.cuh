@@ -281,6 +281,9 @@ cudaError_t launch_spmv_seg_lines(const int32_t *irp, int32_t n_rows, int64_t nn
 cudaError_t launch_spmv_seg(bool coo, const int32_t *lines, const int32_t *icol, const double *val, int64_t nnz,
                             int32_t n_rows, int32_t n_cols, const int32_t *tl, const double *x, double *y,
                             cudaStream_t s);
+// n_adds coalesced FP64 atomic adds into y[0..n) (measurement of the
+// column-wise products' ceiling)
+cudaError_t launch_atomic_ceiling(double *y, long long n, long long n_adds, cudaStream_t s);
 cudaError_t launch_spmv_coo_col(const int32_t *row, const int32_t *col, const double *val, int64_t nnz,
                                 int32_t n_rows, const double *x, double *y, cudaStream_t s);
 cudaError_t launch_spmv_ccs(const int32_t *cp, const int32_t *trow, const double *tval, int32_t n_rows,

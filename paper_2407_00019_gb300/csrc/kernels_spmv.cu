@@ -297,6 +297,25 @@ cudaError_t launch_spmv_ell_col(const double *eval, const int32_t *eidx, int32_t
     return cudaGetLastError();
 }
 
+// ---- the ceiling of the column-wise products: FP64 atomic adds alone -------
+// n_adds adds of 1.0 into y[0..n), lanes on consecutive elements and each
+// pass over y shifted by a fixed offset: the best case of the atomic adds of
+// COO-Column and ELL-Column on banded matrices, with no other memory traffic.
+__global__ void __launch_bounds__(256) k_atomic_ceiling(double *__restrict__ y, long long n, long long n_adds) {
+    const long long nt = (long long)gridDim.x * blockDim.x;
+    for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < n_adds; a += nt) {
+        const long long pass = a / n;
+        atomicAdd(y + (a + pass * 16384) % n, 1.0);
+    }
+}
+
+cudaError_t launch_atomic_ceiling(double *y, long long n, long long n_adds, cudaStream_t s) {
+    if (n <= 0 || n_adds <= 0) return cudaSuccess;
+    KernelScope ks("atomic_ceiling", s);
+    k_atomic_ceiling<<<(unsigned)sm_count() * 8u, 256, 0, s>>>(y, n, n_adds);
+    return cudaGetLastError();
+}
+
 // ================================================================= COO-Row
 constexpr int COO_ROWS_R = 128;  // rows per tile of the row-aligned COO-Row kernel
 constexpr int COO_THREADS = 256;
