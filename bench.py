@@ -145,6 +145,8 @@ def kernel_bytes(name: str, bm: dict, n_rows: int, n_cols: int, nnz: int):
         # mirror entries, ICOL_T (= ICOL) and VAL_T out (IRP_T is a copy of IRP)
         "ccs_sym": 24 * nnz + 8 * (n_rows + 1),
         "sym_sample": 16 * 4096,
+        # the measuring stick of the column-wise products: atomics into y only
+        "atomic_ceiling": 8 * n_rows,
         "crs_to_ell_row_fused_spmv": (bm["crs_to_ell_row"] + 8 * n_cols + 8 * n_rows) if "crs_to_ell_row" in bm else None,
     }
     if name.startswith("spmv_crs_"):

@@ -60,12 +60,11 @@ def test_every_step_kernel_has_a_byte_model(bench):
     """Each kernel the library times in the single-matrix steps has its
     algorithmic or design bytes in the bench's table, or is one of the few
     whose traffic depends on the data (long-column sorts, overflow placement)
-    or that belong to other workloads (batches, row bins)."""
+    or that belong to other workloads (batches)."""
     names = _timed_kernel_names()
     assert {"col_claim_rk", "col_fixup_rk", "spmv_crs_rows_p", "crs_to_coo_row"} <= names
     bm = bench.byte_model(1000, 1000, 20000, 30, 40)
-    unmodelled = {"col_fixup_block", "col_fixup_long_rv", "col_overflow_rk", "bin_count", "bin_scatter",
-                  "spmv_coo_row_carry"}
+    unmodelled = {"col_fixup_block", "col_fixup_long_rv", "col_overflow_rk", "spmv_coo_row_carry"}
     for name in sorted(names):
         if name.startswith("batch_") or name in unmodelled:
             continue
