@@ -545,7 +545,8 @@ __global__ void __launch_bounds__(COO_ROWS_R *SPLIT) k_coo_row_rows(const int32_
         }
     }
     __syncthreads();
-    if (threadIdx.x <= (unsigned)nr) {  // first entry of row r0 + i: lower bound in s_r
+    if (threadIdx.x == 0) s_ptr[nr] = n;  // every staged entry belongs to a row below r0 + nr
+    if (threadIdx.x < (unsigned)nr) {  // first entry of row r0 + i: lower bound in s_r
         const long long key = r0 + threadIdx.x;
         int lo = 0, hi = n;
         while (lo < hi) {
@@ -593,7 +594,6 @@ cudaError_t launch_spmv_coo_row_rows(int split, int cap, const int32_t *irow, co
         k_coo_row_rows<SP><<<grid, COO_ROWS_R * SP, smem, s>>>(irow, icol, val, tb, n_rows, n_cols, cap, x, y); \
         break;                                                                                         \
     }
-        COOR_CASE(1)
         COOR_CASE(2)
         COOR_CASE(4)
 #undef COOR_CASE
