@@ -923,11 +923,13 @@ def run_serve(args, w: dict) -> None:
         dstar, dsrc = args.dstar, "--dstar"
     else:
         dstar, dsrc = serve_dstar(L, torch)
+    if args.requests:
+        w = dict(w, requests=int(args.requests), warm_requests=max(50, int(args.requests) // 6))
     rng = np.random.default_rng(seed)
     n_req = w["warm_requests"] + w["requests"]
     reqs = list(zip(rng.integers(0, len(pool), size=n_req).tolist(), rng.integers(1, w["kmax"] + 1, size=n_req).tolist()))
     rates = [args.rate] if args.rate else list(w["rates"])
-    if w["rate"] not in rates:
+    if not args.rate and w["rate"] not in rates:
         rates.append(w["rate"])
     rates = sorted(rates)
     clocks = ClockSampler(local)
@@ -1050,6 +1052,9 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="default workload: skip the child runs of the other configurations")
+    ap.add_argument("--requests", type=int, default=None, help="serving: measured requests per rate")
     ap.add_argument("--rate", type=float, default=None, help="serving: offered requests per second")
     ap.add_argument("--no-loop", action="store_true", help="batches: skip the per-matrix loop comparison")
     ap.add_argument("--sequential", action="store_true",
@@ -1318,9 +1323,63 @@ def main():
                    "dstar_source": dstar_src},
             "per_kernel": per_kernel,
         }
+        if world == 1 and args.workload == DEFAULT_WORKLOAD and not args.no_other_configs:
+            line["other_configs"] = other_configs()
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# The other configurations of the benchmark, each as a child run of this
+# script after the headline measurement (bounded in time), so that one default
+# run also carries their figures: the 64x64 Laplacian (latency), the 4e6-row
+# power law (the AT under the 40 GB cap), the 10,000-matrix batch and a short
+# two-arm serving run.
+OTHER_CONFIGS = [
+    ("laplace2d_64", ["--steps", "20", "--warmup", "5"], 240),
+    ("powerlaw_4m", ["--steps", "5", "--warmup", "3"], 420),
+    ("batch_10k", ["--steps", "10", "--warmup", "3", "--no-loop"], 420),
+    ("serve_300", ["--rate", "750", "--requests", "600"], 420),
+]
+
+
+def _summary(name: str, d: dict) -> dict:
+    out = {"value": d.get("value"), "unit": d.get("unit"), "ms_per_step": d.get("ms_per_step")}
+    if d.get("roofline"):
+        r = d["roofline"]
+        out["roofline"] = {k: r.get(k) for k in ("kernel", "frac", "achieved", "peak")}
+    if name == "laplace2d_64":
+        out["latency_us"] = d.get("latency_us")
+    if name == "powerlaw_4m":
+        out["at"] = d.get("at")
+        out["per_format"] = {k: (v and {"GB/s": v["GB/s"], "pct_hbm": v["pct_hbm"]}) for k, v in
+                             (d.get("per_format") or {}).items()}
+    if name == "batch_10k":
+        b = d.get("batch") or {}
+        out["batch"] = {k: b.get(k) for k in ("create_ms", "formats", "schedule_table", "graph_build")}
+    if name == "serve_300":
+        out["arms"] = {a: [{k: r[k] for k in ("offered_req_per_s", "served_req_per_s", "GB/s", "p50_ms", "p99_ms")}
+                           for r in rows] for a, rows in (d.get("arms") or {}).items()}
+        out["cache"] = d.get("cache")
+    return out
+
+
+def other_configs() -> dict:
+    res = {}
+    for name, extra, limit in OTHER_CONFIGS:
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", name, "--no-e2e", "--no-cpu-baseline"] + extra
+        t0 = time.perf_counter()
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=limit)
+            lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+            if r.returncode != 0 or not lines:
+                res[name] = {"error": f"exit {r.returncode}: {r.stderr.strip().splitlines()[-1:] or ''}"}
+            else:
+                res[name] = _summary(name, json.loads(lines[-1]))
+        except subprocess.TimeoutExpired:
+            res[name] = {"error": f"did not finish within {limit} s"}
+        res[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+    return res
 
 
 if __name__ == "__main__":

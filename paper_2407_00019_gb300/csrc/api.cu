@@ -532,11 +532,9 @@ spmv_status phase1_try(const spmv_crs *A, uint64_t cap_ell_col, bool want_ell, P
     const int64_t ov_cap = nnz / 8 + 1024;
     if (rk) {
         CKS(alloc_buf(col_rk_slot_bytes(nc), s, &tslots));
-        CKS(alloc_buf(col_scatter_scratch_bytes(nnz), s, &sct0));
         CKS(alloc_buf((size_t)ov_cap * sizeof(int4), s, &ovl));
         CK(launch_col_claim_rk(A->irp, A->n_rows, A->icol, nnz, nc, d_cp, tslots->p,
-                               reinterpret_cast<int4 *>(ovl->p), ov_cap, d_over,
-                               reinterpret_cast<int32_t *>(sct0->p), d_status, s));
+                               reinterpret_cast<int4 *>(ovl->p), ov_cap, d_over, nullptr, d_status, s));
     } else if (slots) {
         CKS(alloc_buf(col_slot_bytes(nc), s, &tslots));
         CKS(alloc_buf(col_scatter_scratch_bytes(nnz), s, &sct0));

@@ -200,7 +200,8 @@ cudaError_t launch_col_fixup_slots(const int32_t *cp, int32_t n_cols, const int3
 // Row-position slot path of Phase I (no repeated (i, j) entries, columns of
 // at most col_rv_long_cap() entries, at most `ov_cap` entries beyond the
 // slots; otherwise ST_REDO; rows below 2^27 - 1). `slots`:
-// col_rk_slot_bytes(n_cols) bytes of {k, row} records.
+// col_rk_slot_bytes(n_cols) bytes of {k, row} records. The claim's `scratch`
+// is unused (its rows are owned by lanes).
 size_t col_rk_slot_bytes(int32_t n_cols);
 int col_rv_long_cap();
 cudaError_t launch_col_claim_rk(const int32_t *irp, int32_t n_rows, const int32_t *icol, int64_t nnz, int32_t n_cols,
@@ -234,8 +235,8 @@ size_t ccs_sym_scratch_bytes(int64_t nnz);
 cudaError_t launch_ccs_sym(const int32_t *irp, int32_t n, const int32_t *icol, const double *val, int64_t nnz,
                            int32_t *scratch, int32_t *trow, double *tval, unsigned long long *cnt, int *status,
                            cudaStream_t s);
-// failures among `samples` evenly spread entries of the symmetric path's
-// conditions, added into *fails
+// failures of the symmetric path's conditions among one entry of each of
+// `samples` evenly spread rows, added into *fails
 cudaError_t launch_sym_sample(const int32_t *irp, int32_t n, const int32_t *icol, int64_t nnz, int samples,
                               int32_t *fails, cudaStream_t s);
 // `pairs` must have 16 bytes of slack after its nnz elements.
