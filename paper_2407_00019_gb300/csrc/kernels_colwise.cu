@@ -827,6 +827,21 @@ __device__ __forceinline__ int pad32(int e) { return e + (e >> 5); }
 constexpr int CR_ROWS = 256;
 constexpr int CR_CAP = 8192;  // staged entries (32 KB)
 constexpr int CR_STEP = 4;
+constexpr int CR_LONG = 64;   // longest row a CTA claims row-owned
+
+// Claim of entry k (row `row`, column c): its rank, then its slot or a
+// record of the overflow list.
+__device__ __forceinline__ void claim_place(int c, int k, int row, int r, int32_t n_cols, int2 *__restrict__ slots,
+                                            int4 *__restrict__ ov, long long ov_cap, int32_t *__restrict__ n_ov,
+                                            int &redo) {
+    if (r < SLOT_CAP) {
+        slots[(long long)r * n_cols + c] = make_int2(k, row);
+    } else {
+        const int q = atomicAdd(n_ov, 1);
+        if (q < ov_cap) ov[q] = make_int4(k, row, c, r);
+        else redo = 1;
+    }
+}
 
 __global__ void __launch_bounds__(CR_ROWS) k_col_claim_rows(const int32_t *__restrict__ irp, int32_t n_rows,
                                                             const int32_t *__restrict__ icol, int64_t nnz,
@@ -835,6 +850,7 @@ __global__ void __launch_bounds__(CR_ROWS) k_col_claim_rows(const int32_t *__res
                                                             long long ov_cap, int32_t *__restrict__ n_ov,
                                                             int *status) {
     __shared__ int32_t s_c[CR_CAP];
+    __shared__ int32_t s_ptr[CR_ROWS + 1];
     const long long r0 = (long long)blockIdx.x * CR_ROWS;
     const int nr = (int)min((long long)CR_ROWS, (long long)n_rows - r0);
     const int t = (int)threadIdx.x;
@@ -857,38 +873,58 @@ __global__ void __launch_bounds__(CR_ROWS) k_col_claim_rows(const int32_t *__res
     if (t < nr) {
         a = min(max((long long)__ldg(irp + row), e0), e1);
         b = min(max((long long)__ldg(irp + row + 1), a), e1);
+        s_ptr[t] = (int)(a - e0);
     }
-    __syncthreads();
+    if (t == 0) s_ptr[nr] = n;
     const int len = (int)(b - a);
-    int wlen = len;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) wlen = max(wlen, __shfl_xor_sync(0xffffffffu, wlen, o));
+    // A CTA with a row longer than CR_LONG (or too many entries to stage)
+    // claims entry-striped instead: one lane per entry, rows found in the
+    // staged pointers, so one long row does not serialise its lane.
+    const bool striped = __syncthreads_or(len > CR_LONG) || !staged;
     int bad = 0, redo = 0;
-    for (int j0 = 0; j0 < wlen; j0 += CR_STEP) {
-        int c[CR_STEP], r[CR_STEP];
+    if (!striped) {
+        int wlen = len;
 #pragma unroll
-        for (int u = 0; u < CR_STEP; ++u) {
-            const int j = j0 + u;
-            c[u] = -1;
-            if (j < len) {
-                const long long k = a + j;
-                const int col = staged ? s_c[(int)(k - e0)] : __ldg(icol + k);
-                if ((unsigned)col < (unsigned)n_cols) c[u] = col;
-                else bad = 1;
+        for (int o = 16; o > 0; o >>= 1) wlen = max(wlen, __shfl_xor_sync(0xffffffffu, wlen, o));
+        for (int j0 = 0; j0 < wlen; j0 += CR_STEP) {
+            int c[CR_STEP], r[CR_STEP];
+#pragma unroll
+            for (int u = 0; u < CR_STEP; ++u) {
+                const int j = j0 + u;
+                c[u] = -1;
+                if (j < len) {
+                    const int col = s_c[(int)(a - e0) + j];
+                    if ((unsigned)col < (unsigned)n_cols) c[u] = col;
+                    else bad = 1;
+                }
             }
+#pragma unroll
+            for (int u = 0; u < CR_STEP; ++u) r[u] = (c[u] >= 0) ? atomicAdd(nc + c[u], 1) : -1;
+#pragma unroll
+            for (int u = 0; u < CR_STEP; ++u)
+                if (r[u] >= 0) claim_place(c[u], (int)(a + j0 + u), (int)row, r[u], n_cols, slots, ov, ov_cap, n_ov, redo);
         }
+    } else {
+        for (int q0 = t; q0 < n; q0 += CR_STEP * CR_ROWS) {
+            int c[CR_STEP], r[CR_STEP];
 #pragma unroll
-        for (int u = 0; u < CR_STEP; ++u) r[u] = (c[u] >= 0) ? atomicAdd(nc + c[u], 1) : -1;
+            for (int u = 0; u < CR_STEP; ++u) {
+                const int q = q0 + u * CR_ROWS;
+                c[u] = -1;
+                if (q < n) {
+                    const int col = staged ? s_c[q] : __ldcs(icol + e0 + q);
+                    if ((unsigned)col < (unsigned)n_cols) c[u] = col;
+                    else bad = 1;
+                }
+            }
 #pragma unroll
-        for (int u = 0; u < CR_STEP; ++u) {
-            if (r[u] < 0) continue;
-            const int k = (int)(a + j0 + u);
-            if (r[u] < SLOT_CAP) {
-                slots[(long long)r[u] * n_cols + c[u]] = make_int2(k, (int)row);
-            } else {
-                const int q = atomicAdd(n_ov, 1);
-                if (q < ov_cap) ov[q] = make_int4(k, (int)row, c[u], r[u]);
-                else redo = 1;
+            for (int u = 0; u < CR_STEP; ++u) r[u] = (c[u] >= 0) ? atomicAdd(nc + c[u], 1) : -1;
+#pragma unroll
+            for (int u = 0; u < CR_STEP; ++u) {
+                if (r[u] < 0) continue;
+                const int q = q0 + u * CR_ROWS;
+                const int rr = (int)r0 + last_le(s_ptr, 0, nr, q);  // the row holding staged entry q
+                claim_place(c[u], (int)(e0 + q), rr, r[u], n_cols, slots, ov, ov_cap, n_ov, redo);
             }
         }
     }
