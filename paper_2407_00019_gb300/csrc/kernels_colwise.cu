@@ -1534,130 +1534,176 @@ cudaError_t launch_col_locality(const int32_t *icol, int64_t nnz, int samples, i
 // ascending order. Then IRP_T = IRP and ICOL_T = ICOL, and the CCS value at
 // position p (row c, column i) is the value of the mirror entry (i, c):
 // VAL_T[p] = VAL[q], q the position of column c in row i.
-// k_ccs_sym does that in one pass: each entry p reads its column i, the
-// bounds of row i, and ICOL at a first guess for q reflected through the
-// row, q = IRP[i+1] - 1 - (p - IRP[c]) (exact for shift-invariant symmetric
-// stencils), else binary-searches row i; then it gathers VAL[q] and writes
-// ICOL_T[p] and VAL_T[p] coalesced. The kernel is bound by the latency of
-// these dependent gathers, so it keeps many warps in flight rather than many
-// items per thread: four items per thread, thread-striped (one warp
-// instruction = 32 consecutive entries), measured best among 2, 4, 8 and 16
-// (and faster than handling each mirror pair once, which turns half of the
-// value stores into scattered ones); rows come from the tile's staged
-// pointers as in the claim above. Every entry must find its mirror: since
-// the mirror map is then one-to-one on a finite set of distinct entries, the
-// pattern is symmetric. A missing mirror or a row out of order sets ST_REDO
-// (the host then builds the CCS on a general path), a column out of range
-// ST_BAD_INDEX; cnt[2] receives the longest row (= the longest column).
+// k_ccs_sym does that in one pass. A CTA takes a tile of SYM_TILE
+// consecutive entries and each thread SYM_ITEMS consecutive ones (16-byte
+// loads of ICOL and stores of ICOL_T and VAL_T when the arrays allow it):
+// the thread finds the row of its first entry by a binary search of the
+// tile's row pointers (staged in shared memory) and walks on from there, so
+// every entry knows its row c, its place in the row and whether it is the
+// row's last. Then entry p (row c, column i) reads the bounds of row i and
+// ICOL at a first guess for q reflected through the row,
+// q = IRP[i+1] - 1 - (p - IRP[c]) (exact for shift-invariant symmetric
+// stencils), else binary-searches row i, and gathers VAL[q]. The kernel is
+// bound by the latency of these dependent gathers and by the instructions
+// around them, so positions are 32-bit (IRP is int32, so nnz <= 2^31 - 1)
+// and the items of a thread run their gathers side by side. Every entry must
+// find its mirror: since the mirror map is then one-to-one on a finite set
+// of distinct entries, the pattern is symmetric. A missing mirror or a row
+// out of order sets ST_REDO (the host then builds the CCS on a general path
+// and drops what this kernel wrote), a column out of range ST_BAD_INDEX;
+// cnt[2] receives the longest row (= the longest column).
 constexpr int SYM_THREADS = 256;
 constexpr int SYM_ITEMS = 4;
 constexpr int SYM_TILE = SYM_THREADS * SYM_ITEMS;
 
+static_assert(SYM_ITEMS % 4 == 0, "16-byte accesses cover a thread's items");
+
+// rows of a thread's entries [kb, kb + m) from the tile's row pointers
+// rp[r - lo] = IRP[r], rows lo..hi: c[j] the row, jj[j] the place in it
+// (unsigned: a malformed IRP gives a huge value, never a negative one), last
+// bit j set when entry j ends its row; wmax = longest row started here.
+template <int ITEMS>
+__device__ __forceinline__ void sym_rows(const int32_t *rp, int lo, int hi, int kb, int m, int (&c)[ITEMS],
+                                         unsigned (&jj)[ITEMS], unsigned &last, int &wmax) {
+    int l = 0, h = hi - lo + 1;  // largest r - lo in [0, hi - lo] with IRP[r] <= kb
+    while (h - l > 1) {
+        const int mid = (l + h) >> 1;
+        if (rp[mid] <= kb) l = mid; else h = mid;
+    }
+    int r = lo + l, rs = rp[l], re = rp[l + 1];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const int p = kb + j;
+        c[j] = -1;
+        jj[j] = 0;
+        if (j < m) {
+            while (p >= re && r < hi) {
+                ++r;
+                rs = re;
+                re = rp[r + 1 - lo];
+            }
+            c[j] = r;
+            jj[j] = (unsigned)p - (unsigned)rs;
+            if (p + 1 >= re) last |= 1u << j;
+            if (p == rs) wmax = max(wmax, re - rs);
+        }
+    }
+}
+
+template <bool VEC>
 __global__ void __launch_bounds__(SYM_THREADS) k_ccs_sym(const int32_t *__restrict__ irp, int32_t n,
                                                           const int32_t *__restrict__ icol,
-                                                          const double *__restrict__ val, int64_t nnz,
-                                                          const int32_t *__restrict__ tl, long long n_tiles,
+                                                          const double *__restrict__ val, int32_t nnz,
+                                                          const int32_t *__restrict__ tl, int n_tiles,
                                                           int32_t *__restrict__ trow, double *__restrict__ tval,
                                                           unsigned long long *__restrict__ cnt, int *status) {
     __shared__ int32_t s_ptr[SCT_WIN];
-    __shared__ int32_t s_row[SYM_TILE + SYM_TILE / 32];
-    const long long k0 = (long long)blockIdx.x * SYM_TILE;
-    const long long k1 = min(k0 + (long long)SYM_TILE, (long long)nnz);
-    const int t = (int)threadIdx.x;
+    __shared__ int s_wmax;
+    if (threadIdx.x == 0) s_wmax = 0;
+    const long long kbl = (long long)blockIdx.x * SYM_TILE + (long long)threadIdx.x * SYM_ITEMS;
+    const int m = (int)max(min((long long)SYM_ITEMS, (long long)nnz - kbl), 0ll);
+    const int kb = m > 0 ? (int)kbl : 0;
     const unsigned lane = lane_id();
-    int ci[SYM_ITEMS], nx[SYM_ITEMS];
+    int ci[SYM_ITEMS];
+    if (VEC && m == SYM_ITEMS) {
 #pragma unroll
-    for (int u = 0; u < SYM_ITEMS; ++u) {
-        const long long p = k0 + t + SYM_THREADS * u;
-        ci[u] = (p < k1) ? __ldcs(icol + p) : 0;
-    }
+        for (int h = 0; h < SYM_ITEMS / 4; ++h) {
+            const int4 w = __ldcs(reinterpret_cast<const int4 *>(icol + kb) + h);
+            ci[4 * h] = w.x;
+            ci[4 * h + 1] = w.y;
+            ci[4 * h + 2] = w.z;
+            ci[4 * h + 3] = w.w;
+        }
+    } else {
 #pragma unroll
-    for (int u = 0; u < SYM_ITEMS; ++u) {
-        const long long p = k0 + t + SYM_THREADS * u;
-        nx[u] = __shfl_down_sync(0xffffffffu, ci[u], 1);
-        if (lane == 31) nx[u] = (p + 1 < nnz) ? __ldg(icol + p + 1) : INT_MAX;
+        for (int j = 0; j < SYM_ITEMS; ++j) ci[j] = (j < m) ? __ldcs(icol + kb + j) : 0;
     }
+    // column of the entry after this thread's last one
+    int nxt = __shfl_down_sync(0xffffffffu, ci[0], 1);
+    if (lane == 31 || m < SYM_ITEMS) nxt = (m == SYM_ITEMS && kbl + SYM_ITEMS < nnz) ? __ldg(icol + kb + SYM_ITEMS) : INT_MAX;
     const int lo = tl[blockIdx.x];
     const int hi = (blockIdx.x + 1 < n_tiles) ? tl[blockIdx.x + 1] : n - 1;
     const int wn = hi - lo + 2;
     const bool sm = wn <= SCT_WIN;
     if (sm)
-        for (int i = t; i < wn; i += SYM_THREADS) s_ptr[i] = irp[lo + i];
+        for (int i = threadIdx.x; i < wn; i += SYM_THREADS) s_ptr[i] = irp[lo + i];
     __syncthreads();
-    {
-        const long long kb = k0 + (long long)t * SYM_ITEMS;  // this thread's block of entries
-        if (kb < k1) {
-            int row = sm ? lo + last_le(s_ptr, 0, wn - 1, kb) : last_le(irp, lo, hi + 1, kb);
+    int c[SYM_ITEMS];
+    unsigned jj[SYM_ITEMS], last = 0;
+    int wmax = 0;
+    if (m > 0) {
+        if (sm) sym_rows<SYM_ITEMS>(s_ptr, lo, hi, kb, m, c, jj, last, wmax);
+        else sym_rows<SYM_ITEMS>(irp + lo, lo, hi, kb, m, c, jj, last, wmax);
+    } else {
 #pragma unroll
-            for (int j = 0; j < SYM_ITEMS; ++j) {
-                const long long kk = kb + j;
-                while (row < hi && (long long)(sm ? s_ptr[row + 1 - lo] : irp[row + 1]) <= kk) ++row;
-                s_row[pad32(t * SYM_ITEMS + j)] = row;
-            }
-        }
+        for (int j = 0; j < SYM_ITEMS; ++j) c[j] = -1, jj[j] = 0;
     }
-    __syncthreads();
-    int bad = 0, redo = 0, wmax = 0;
-    int c[SYM_ITEMS], jj[SYM_ITEMS], a[SYM_ITEMS], b[SYM_ITEMS];
+    int bad = 0, redo = 0;
+    int a[SYM_ITEMS], b[SYM_ITEMS];
 #pragma unroll
-    for (int u = 0; u < SYM_ITEMS; ++u) {
-        const long long p = k0 + t + SYM_THREADS * u;
-        c[u] = -1;
-        a[u] = b[u] = 0;
-        jj[u] = 0;
-        if (p >= k1) continue;
-        const int row = s_row[pad32(t + SYM_THREADS * u)];
-        const int rs = sm ? s_ptr[row - lo] : __ldg(irp + row);
-        const int re = sm ? s_ptr[row + 1 - lo] : __ldg(irp + row + 1);
-        if ((unsigned)ci[u] >= (unsigned)n) { bad = 1; continue; }
-        if (p + 1 < re && nx[u] <= ci[u]) redo = 1;
-        if (p == rs) wmax = max(wmax, re - rs);
-        c[u] = row;
-        jj[u] = (int)(p - rs);
-        const long long ra = min(max((long long)__ldg(irp + ci[u]), 0ll), (long long)nnz);
-        const long long rb = min(max((long long)__ldg(irp + ci[u] + 1), ra), (long long)nnz);
-        a[u] = (int)ra;
-        b[u] = (int)rb;
+    for (int j = 0; j < SYM_ITEMS; ++j) {
+        a[j] = b[j] = 0;
+        if (c[j] < 0) continue;
+        const int i = ci[j];
+        if ((unsigned)i >= (unsigned)n) {
+            bad = 1;
+            c[j] = -1;
+            continue;
+        }
+        const int after = (j + 1 < SYM_ITEMS) ? ci[j + 1] : nxt;
+        if (!((last >> j) & 1u) && after <= i) redo = 1;
+        a[j] = min(max(__ldg(irp + i), 0), nnz);
+        b[j] = min(max(__ldg(irp + i + 1), a[j]), nnz);
     }
     int q[SYM_ITEMS], g[SYM_ITEMS];
 #pragma unroll
-    for (int u = 0; u < SYM_ITEMS; ++u) {
-        q[u] = -1;
-        g[u] = -1;
-        if (c[u] < 0) continue;
-        const int guess = b[u] - 1 - jj[u];
-        if (guess >= a[u] && guess < b[u]) {
-            q[u] = guess;
-            g[u] = __ldg(icol + guess);
+    for (int j = 0; j < SYM_ITEMS; ++j) {
+        q[j] = 0;
+        g[j] = -1;
+        if (c[j] >= 0 && jj[j] < (unsigned)(b[j] - a[j])) {
+            q[j] = b[j] - 1 - (int)jj[j];
+            g[j] = __ldg(icol + q[j]);
         }
     }
 #pragma unroll
-    for (int u = 0; u < SYM_ITEMS; ++u) {
-        if (c[u] < 0 || g[u] == c[u]) continue;
-        int l = a[u], h = b[u];
+    for (int j = 0; j < SYM_ITEMS; ++j) {
+        if (c[j] < 0 || g[j] == c[j]) continue;
+        int l = a[j], h = b[j];
         while (h - l > 1) {
-            const int m = l + ((h - l) >> 1);
-            if (__ldg(icol + m) <= c[u]) l = m; else h = m;
+            const int mid = l + ((h - l) >> 1);
+            if (__ldg(icol + mid) <= c[j]) l = mid; else h = mid;
         }
-        q[u] = (l < b[u] && __ldg(icol + l) == c[u]) ? l : -1;
-        if (q[u] < 0) redo = 1;
+        if (l < b[j] && __ldg(icol + l) == c[j]) q[j] = l;
+        else redo = 1, c[j] = -1;
     }
     double v[SYM_ITEMS];
 #pragma unroll
-    for (int u = 0; u < SYM_ITEMS; ++u) v[u] = (c[u] >= 0 && q[u] >= 0) ? __ldg(val + q[u]) : 0.0;
+    for (int j = 0; j < SYM_ITEMS; ++j) v[j] = (c[j] >= 0) ? __ldg(val + q[j]) : 0.0;
+    // every entry is stored: a failed one leaves ST_REDO or ST_BAD_INDEX set,
+    // and the host then discards both arrays
+    if (VEC && m == SYM_ITEMS) {
 #pragma unroll
-    for (int u = 0; u < SYM_ITEMS; ++u) {
-        const long long p = k0 + t + SYM_THREADS * u;
-        if (c[u] >= 0 && q[u] >= 0) {
-            __stcs(trow + p, ci[u]);
-            __stcs(tval + p, v[u]);
-        }
+        for (int h = 0; h < SYM_ITEMS / 4; ++h)
+            __stcs(reinterpret_cast<int4 *>(trow + kb) + h, make_int4(ci[4 * h], ci[4 * h + 1], ci[4 * h + 2], ci[4 * h + 3]));
+#pragma unroll
+        for (int h = 0; h < SYM_ITEMS / 2; ++h)
+            __stcs(reinterpret_cast<double2 *>(tval + kb) + h, make_double2(v[2 * h], v[2 * h + 1]));
+    } else {
+#pragma unroll
+        for (int j = 0; j < SYM_ITEMS; ++j)
+            if (j < m) {
+                __stcs(trow + kb + j, ci[j]);
+                __stcs(tval + kb + j, v[j]);
+            }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-    if (lane == 0 && wmax > 0) atomicMax(cnt + 2, (unsigned long long)wmax);
+    // the longest row: one global atomic per CTA (one per warp on a single
+    // address kept its L2 slice busy enough to slow the whole kernel)
+    wmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(wmax, 0));
+    if (lane == 0 && wmax > 0) atomicMax(&s_wmax, wmax);
     if (__any_sync(0xffffffffu, redo) && lane == 0) atomicOr(status, ST_REDO);
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_BAD_INDEX);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_wmax > 0) atomicMax(cnt + 2, (unsigned long long)s_wmax);
 }
 
 size_t ccs_sym_scratch_bytes(int64_t nnz) { return tile_lines_bytes(nnz, SYM_TILE); }
@@ -1666,12 +1712,19 @@ cudaError_t launch_ccs_sym(const int32_t *irp, int32_t n, const int32_t *icol, c
                            int32_t *scratch, int32_t *trow, double *tval, unsigned long long *cnt, int *status,
                            cudaStream_t s) {
     if (nnz <= 0) return cudaSuccess;
+    if (nnz > INT_MAX) return cudaErrorInvalidValue;  // int32 row pointers bound nnz
     cudaError_t e = launch_tile_lines(irp, n, nnz, SYM_TILE, scratch, s);
     if (e != cudaSuccess) return e;
-    const long long n_tiles = (nnz + SYM_TILE - 1) / SYM_TILE;
+    const int n_tiles = (int)((nnz + SYM_TILE - 1) / SYM_TILE);
+    const bool vec = ((reinterpret_cast<uintptr_t>(icol) | reinterpret_cast<uintptr_t>(trow) |
+                       reinterpret_cast<uintptr_t>(tval)) & 15u) == 0;
     KernelScope ks("ccs_sym", s);
-    k_ccs_sym<<<(unsigned)n_tiles, SYM_THREADS, 0, s>>>(irp, n, icol, val, nnz, scratch, n_tiles, trow, tval, cnt,
-                                                          status);
+    if (vec)
+        k_ccs_sym<true><<<(unsigned)n_tiles, SYM_THREADS, 0, s>>>(irp, n, icol, val, (int32_t)nnz, scratch, n_tiles,
+                                                                  trow, tval, cnt, status);
+    else
+        k_ccs_sym<false><<<(unsigned)n_tiles, SYM_THREADS, 0, s>>>(irp, n, icol, val, (int32_t)nnz, scratch, n_tiles,
+                                                                   trow, tval, cnt, status);
     return cudaGetLastError();
 }
 
@@ -1701,12 +1754,16 @@ __global__ void __launch_bounds__(256) k_sym_sample(const int32_t *__restrict__ 
                 if (p + 1 < rb && __ldg(icol + p + 1) <= i) fail = 1;
                 const long long ma = min(max((long long)__ldg(irp + i), 0ll), (long long)nnz);
                 const long long mb = min(max((long long)__ldg(irp + i + 1), ma), (long long)nnz);
-                int l = (int)ma, h = (int)mb;
-                while (h - l > 1) {
-                    const int m = l + ((h - l) >> 1);
-                    if (__ldg(icol + m) <= c) l = m; else h = m;
+                // the reflected guess first (as in k_ccs_sym), a search only if it misses
+                const long long gq = mb - 1 - (p - ra);
+                if (!(gq >= ma && __ldg(icol + gq) == c)) {
+                    int l = (int)ma, h = (int)mb;
+                    while (h - l > 1) {
+                        const int m = l + ((h - l) >> 1);
+                        if (__ldg(icol + m) <= c) l = m; else h = m;
+                    }
+                    if (!(l < (int)mb && __ldg(icol + l) == c)) fail = 1;
                 }
-                if (!(l < (int)mb && __ldg(icol + l) == c)) fail = 1;
             }
         }
     }

@@ -476,18 +476,26 @@ __global__ void __launch_bounds__(COO_THREADS) k_coo_row_tiles(const int32_t *__
 // ptr[min(128 t, n_lines)], the first entry of line 128 t in the line-sorted
 // COO (ptr: the pointers of the compressed format the COO is made from), and
 // the largest tile's entry count into *maxn when given. Bounds are clamped to
-// [0, nnz], so the products stay in bounds even on malformed pointers.
+// [0, nnz], so the products stay in bounds even on malformed pointers. The
+// largest count is reduced per warp first (one atomic per warp, not per tile).
 __global__ void __launch_bounds__(256) k_line_tile_bounds(const int32_t *__restrict__ ptr, int32_t n_lines,
                                                            int64_t nnz, long long n_tiles, int32_t *__restrict__ tb,
                                                            int32_t *__restrict__ maxn) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t > n_tiles) return;
     const auto bound = [&](long long u) {
         return (int32_t)min(max((long long)__ldg(ptr + min(u * COO_ROWS_R, (long long)n_lines)), 0ll), (long long)nnz);
     };
-    const int32_t a = bound(t);
-    tb[t] = a;
-    if (maxn && t < n_tiles) atomicMax(maxn, bound(t + 1) - a);
+    int32_t m = 0;
+    if (t <= n_tiles) {
+        const int32_t a = bound(t);
+        tb[t] = a;
+        if (t < n_tiles) m = bound(t + 1) - a;
+    }
+    if (maxn) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane_id() == 0 && m > 0) atomicMax(maxn, m);
+    }
 }
 
 cudaError_t launch_line_tile_bounds(const int32_t *ptr, int32_t n_lines, int64_t nnz, int32_t *tb, int32_t *maxn,

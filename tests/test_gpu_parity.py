@@ -568,3 +568,30 @@ def test_symmetric_path_not_taken_for_scattered_columns():
     assert "ccs_sym" not in prof and "sym_sample" in prof
     _ccs_matches_oracle(M, H)
     M.close()
+
+
+@pytest.mark.parametrize("name", ["stencil27_24", "laplace37x23"])
+def test_symmetric_path_with_unaligned_arrays(name):
+    """ICOL and VAL at addresses that are not 16-byte aligned (views one
+    element into larger buffers): the mirror pass takes its scalar loads and
+    stores, and the CCS is still the serial one bit for bit."""
+    import torch
+    L = lib()
+    H = case(name)
+    icol = torch.empty(H.nnz + 1, dtype=torch.int32, device="cuda")[1:]
+    val = torch.empty(H.nnz + 1, dtype=torch.float64, device="cuda")[1:]
+    icol.copy_(torch.from_numpy(H.icol))
+    val.copy_(torch.from_numpy(H.val))
+    assert icol.data_ptr() % 16 and val.data_ptr() % 16
+    A = L.Crs(H.n_rows, H.n_cols, torch.from_numpy(H.irp).cuda(), icol, val)
+    L.spmv_profile_enable(True)
+    L.spmv_profile_read(reset=True)
+    try:
+        M = L.spmv_transform(A, L.SPMV_CRS, L.SPMV_COLWISE)
+        prof = L.spmv_profile_read(reset=True)
+    finally:
+        L.spmv_profile_enable(False)
+    assert "ccs_sym" in prof, prof
+    _ccs_matches_oracle(M, H)
+    M.close()
+
