@@ -507,59 +507,63 @@ cudaError_t launch_line_tile_bounds(const int32_t *ptr, int32_t n_lines, int64_t
 }
 
 // A CTA takes 128 consecutive rows: their entries [tb[t], tb[t+1]) are
-// loaded into shared memory with coalesced loads, each row finds its first
-// entry by binary search over the staged IROW, then SPLIT threads per row run
-// the FMA chains with lanes on consecutive rows (as k_spmv_crs_rows). Rows
-// never cross tiles, so no partial sums are carried.
+// loaded into shared memory with coalesced loads (VAL, ICOL, and IROW as a
+// one-byte offset from the tile's first row: 13 bytes an entry, so four CTAs
+// of 512 threads fit an SM), each row finds its first entry by binary search
+// over the staged offsets, then SPLIT threads per row run the FMA chains with
+// lanes on consecutive rows (as k_spmv_crs_rows). Rows never cross tiles, so
+// no partial sums are carried.
+constexpr int COO_STAGE_U = 4;  // entries a thread loads at once while staging
+
+__host__ __device__ constexpr size_t coo_tile_smem(int cap) { return ((size_t)cap * 13 + 15) & ~(size_t)15; }
+
 template <int SPLIT>
-__global__ void __launch_bounds__(COO_ROWS_R *SPLIT) k_coo_row_rows(const int32_t *__restrict__ irow,
-                                                                     const int32_t *__restrict__ icol,
-                                                                     const double *__restrict__ val,
-                                                                     const int32_t *__restrict__ tb, int32_t n_rows,
-                                                                     int32_t n_cols, int cap,
-                                                                     const double *__restrict__ x,
-                                                                     double *__restrict__ y) {
+__global__ void __launch_bounds__(COO_ROWS_R *SPLIT, 2048 / (COO_ROWS_R * SPLIT)) k_coo_row_rows(
+    const int32_t *__restrict__ irow, const int32_t *__restrict__ icol, const double *__restrict__ val,
+    const int32_t *__restrict__ tb, int32_t n_rows, int32_t n_cols, int cap, const double *__restrict__ x,
+    double *__restrict__ y) {
     constexpr int R = COO_ROWS_R;
     constexpr int T = R * SPLIT;
+    constexpr int U = COO_STAGE_U;
     extern __shared__ __align__(16) unsigned char smem[];
     double *s_v = reinterpret_cast<double *>(smem);
     int32_t *s_c = reinterpret_cast<int32_t *>(s_v + cap);
-    int32_t *s_r = s_c + cap;
+    uint8_t *s_r = reinterpret_cast<uint8_t *>(s_c + cap);  // row - r0, clamped to [0, R]
     __shared__ int32_t s_ptr[R + 1];
     __shared__ double s_part[SPLIT > 1 ? (SPLIT - 1) * R : 1];
     const long long r0 = (long long)blockIdx.x * R;
     const int nr = (int)min((long long)R, (long long)n_rows - r0);
     const int e0 = __ldg(tb + blockIdx.x), e1 = __ldg(tb + blockIdx.x + 1);
     const int n = e1 - e0;  // <= cap by construction of the schedule
-    for (int q0 = threadIdx.x; q0 < n; q0 += 8 * T) {
-        double v[8];
-        int c[8], r[8];
+    for (int q0 = threadIdx.x; q0 < n; q0 += U * T) {
+        double v[U];
+        int c[U], r[U];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int q = q0 + u * T;
             v[u] = (q < n) ? __ldcs(val + e0 + q) : 0.0;
             c[u] = (q < n) ? __ldcs(icol + e0 + q) : 0;
             r[u] = (q < n) ? __ldcs(irow + e0 + q) : 0;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int q = q0 + u * T;
             if (q < n) {
                 const bool ok = (unsigned)c[u] < (unsigned)n_cols;
                 s_v[q] = ok ? v[u] : 0.0;
                 s_c[q] = ok ? c[u] : 0;
-                s_r[q] = r[u];
+                s_r[q] = (uint8_t)min(max((long long)r[u] - r0, 0ll), (long long)R);
             }
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) s_ptr[nr] = n;  // every staged entry belongs to a row below r0 + nr
     if (threadIdx.x < (unsigned)nr) {  // first entry of row r0 + i: lower bound in s_r
-        const long long key = r0 + threadIdx.x;
+        const int key = (int)threadIdx.x;
         int lo = 0, hi = n;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            if ((long long)s_r[mid] < key) lo = mid + 1; else hi = mid;
+            if ((int)s_r[mid] < key) lo = mid + 1; else hi = mid;
         }
         s_ptr[threadIdx.x] = lo;
     }
@@ -592,7 +596,7 @@ cudaError_t launch_spmv_coo_row_rows(int split, int cap, const int32_t *irow, co
     if (n_rows <= 0) return cudaSuccess;
     if (cap <= 0) return cudaErrorInvalidValue;
     const unsigned grid = ceil_div_u(n_rows, COO_ROWS_R);
-    const size_t smem = (size_t)cap * 16;
+    const size_t smem = coo_tile_smem(cap);
     switch (split) {
 #define COOR_CASE(SP)                                                                                  \
     case SP: {                                                                                         \
@@ -678,61 +682,60 @@ __global__ void __launch_bounds__(256) k_spmv_coo_col(const int32_t *__restrict_
 }
 
 // COO-Column over column-aligned tiles: a CTA takes 128 consecutive columns,
-// stages their entries (TROW, TCOL, TVAL) in shared memory with coalesced
-// loads, finds each column's first entry by binary search over the staged
-// TCOL, and SPLIT threads per column add VAL * x[col] into y[row] with lanes
+// stages their entries (TVAL, TROW, and TCOL as a one-byte offset from the
+// tile's first column) in shared memory with coalesced loads, finds each
+// column's first entry by binary search over the staged offsets, and SPLIT
+// threads per column add VAL * x[col] into y[row] with lanes
 // on consecutive columns. Lanes then hold the m-th entries of neighbouring
 // columns, which in banded matrices lie in neighbouring rows, so the 32
 // atomic adds of a warp instruction fall into a few sectors of y instead of
 // 32. `tb` are the tiles' first entries (tile t starts at column 128 t).
 template <int SPLIT>
-__global__ void __launch_bounds__(COO_ROWS_R *SPLIT) k_coo_col_cols(const int32_t *__restrict__ trow,
-                                                                     const int32_t *__restrict__ tcol,
-                                                                     const double *__restrict__ tval,
-                                                                     const int32_t *__restrict__ tb,
-                                                                     int32_t n_rows, int32_t n_cols, int cap,
-                                                                     const double *__restrict__ x,
-                                                                     double *__restrict__ y) {
+__global__ void __launch_bounds__(COO_ROWS_R *SPLIT, 2048 / (COO_ROWS_R * SPLIT)) k_coo_col_cols(
+    const int32_t *__restrict__ trow, const int32_t *__restrict__ tcol, const double *__restrict__ tval,
+    const int32_t *__restrict__ tb, int32_t n_rows, int32_t n_cols, int cap, const double *__restrict__ x,
+    double *__restrict__ y) {
     constexpr int R = COO_ROWS_R;
     constexpr int T = R * SPLIT;
+    constexpr int U = COO_STAGE_U;
     extern __shared__ __align__(16) unsigned char smem[];
     double *s_v = reinterpret_cast<double *>(smem);
-    int32_t *s_c = reinterpret_cast<int32_t *>(s_v + cap);
-    int32_t *s_r = s_c + cap;
+    int32_t *s_r = reinterpret_cast<int32_t *>(s_v + cap);
+    uint8_t *s_c = reinterpret_cast<uint8_t *>(s_r + cap);  // column - c0, clamped to [0, R]
     __shared__ int32_t s_ptr[R + 1];
     const long long c0 = (long long)blockIdx.x * R;
     const int nc = (int)min((long long)R, (long long)n_cols - c0);
     const int e0 = __ldg(tb + blockIdx.x), e1 = __ldg(tb + blockIdx.x + 1);
     const int n = e1 - e0;  // <= cap by construction of the schedule
-    for (int q0 = threadIdx.x; q0 < n; q0 += 8 * T) {
-        double v[8];
-        int c[8], r[8];
+    for (int q0 = threadIdx.x; q0 < n; q0 += U * T) {
+        double v[U];
+        int c[U], r[U];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int q = q0 + u * T;
             v[u] = (q < n) ? __ldcs(tval + e0 + q) : 0.0;
             c[u] = (q < n) ? __ldcs(tcol + e0 + q) : 0;
             r[u] = (q < n) ? __ldcs(trow + e0 + q) : 0;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int q = q0 + u * T;
             if (q < n) {
                 const bool ok = (unsigned)r[u] < (unsigned)n_rows;
                 s_v[q] = ok ? v[u] : 0.0;
-                s_c[q] = c[u];
                 s_r[q] = ok ? r[u] : 0;
+                s_c[q] = (uint8_t)min(max((long long)c[u] - c0, 0ll), (long long)R);
             }
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) s_ptr[nc] = n;  // every staged entry belongs to a column below c0 + nc
-    if (threadIdx.x < (unsigned)nc) {  // first entry of column c0 + i: lower bound in the staged TCOL
-        const long long key = c0 + threadIdx.x;
+    if (threadIdx.x < (unsigned)nc) {  // first entry of column c0 + i: lower bound in the staged offsets
+        const int key = (int)threadIdx.x;
         int lo = 0, hi = n;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            if ((long long)s_c[mid] < key) lo = mid + 1; else hi = mid;
+            if ((int)s_c[mid] < key) lo = mid + 1; else hi = mid;
         }
         s_ptr[threadIdx.x] = lo;
     }
@@ -760,7 +763,7 @@ cudaError_t launch_spmv_coo_col_cols(int split, int cap, const int32_t *trow, co
     if (e != cudaSuccess || n_cols <= 0) return e;
     if (cap <= 0) return cudaErrorInvalidValue;
     const unsigned grid = ceil_div_u(n_cols, COO_ROWS_R);
-    const size_t smem = (size_t)cap * 16;
+    const size_t smem = coo_tile_smem(cap);
     switch (split) {
 #define COOC_CASE(SP)                                                                                           \
     case SP: {                                                                                                  \
