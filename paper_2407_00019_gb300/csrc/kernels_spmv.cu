@@ -264,26 +264,32 @@ cudaError_t launch_spmv_ell_row(const double *eval, const int32_t *eidx, int32_t
 }
 
 // ================================================================= ELL-Col
+// One column per thread: slot k of column j is at k*ld + j, so a warp loads
+// 32 consecutive columns (coalesced) and its atomic adds go to the k-th rows
+// of 32 consecutive columns, which in banded matrices are consecutive rows:
+// a few sectors of y per warp instruction.
 __global__ void __launch_bounds__(256) k_spmv_ell_col(const double *__restrict__ eval,
                                                        const int32_t *__restrict__ eidx, int32_t n_cols,
                                                        int32_t width, int32_t ld, const double *__restrict__ x,
                                                        double *__restrict__ y) {
-    const long long pairs = ((long long)n_cols + 1) >> 1;
-    const long long step = (long long)ld >> 1;
-    const double2 *pv = reinterpret_cast<const double2 *>(eval);
-    const int2 *pc = reinterpret_cast<const int2 *>(eidx);
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < pairs;
-         p += (long long)gridDim.x * blockDim.x) {
-        const long long j = 2 * p;
-        const bool two = j + 1 < n_cols;
-        const double x0 = __ldg(x + j), x1 = two ? __ldg(x + j + 1) : 0.0;
-#pragma unroll 4
-        for (int k = 0; k < width; ++k) {
-            const double2 v = __ldcs(pv + (long long)k * step + p);
-            const int2 r = __ldcs(pc + (long long)k * step + p);
-            atomicAdd(y + r.x, v.x * x0);
-            if (two) atomicAdd(y + r.y, v.y * x1);
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n_cols;
+         j += (long long)gridDim.x * blockDim.x) {
+        const double xj = __ldg(x + j);
+        const double *pv = eval + j;
+        const int32_t *pr = eidx + j;
+        int k = 0;
+        for (; k + 4 <= width; k += 4) {
+            double v[4];
+            int r[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                v[u] = __ldcs(pv + (long long)(k + u) * ld);
+                r[u] = __ldcs(pr + (long long)(k + u) * ld);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) atomicAdd(y + r[u], v[u] * xj);
         }
+        for (; k < width; ++k) atomicAdd(y + __ldcs(pr + (long long)k * ld), __ldcs(pv + (long long)k * ld) * xj);
     }
 }
 
@@ -291,9 +297,8 @@ cudaError_t launch_spmv_ell_col(const double *eval, const int32_t *eidx, int32_t
                                 int32_t width, int32_t ld, const double *x, double *y, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(y, 0, sizeof(double) * (size_t)n_rows, s);
     if (e != cudaSuccess || n_cols <= 0) return e;
-    const long long pairs = ((long long)n_cols + 1) >> 1;
     KernelScope ks("spmv_ell_col", s);
-    k_spmv_ell_col<<<ceil_div_u(pairs, 256), 256, 0, s>>>(eval, eidx, n_cols, width, ld, x, y);
+    k_spmv_ell_col<<<ceil_div_u(n_cols, 256), 256, 0, s>>>(eval, eidx, n_cols, width, ld, x, y);
     return cudaGetLastError();
 }
 
