@@ -161,49 +161,51 @@ cudaError_t launch_tile_lines(const int32_t *ptr, int32_t n_lines, int64_t nnz, 
 }
 
 // ------------------------------------------------------------------ expand
-// Tile of EXP_TILE consecutive entries [k0, k1). The line of entry k is the
-// largest line i with ptr[i] <= k, so: every line that starts inside the
-// tile marks its first entry (s_out[ptr[i] - k0] = i, the largest i when
-// empty lines share a start), entry k0 is marked with the tile's first line,
-// and an inclusive max-scan over the tile (8 consecutive entries per thread,
-// then warp shuffles, then the warps' totals) fills in every entry: a few
-// integer instructions per entry instead of a search per thread and a walk.
-// The tile leaves with 16-byte streaming stores. Tiles whose lines do not
-// fit the marking budget (very many empty lines) take one binary search per
-// thread in global memory and a walk instead.
+// Each warp expands a tile of EXP_TILE = 256 consecutive entries [k0, k1)
+// on its own (no CTA-wide barrier). The line of entry k is the largest line
+// i with ptr[i] <= k, so: every line that starts inside the tile marks its
+// first entry in the warp's part of shared memory (s_out[ptr[i] - k0] = i,
+// the largest i when empty lines share a start), entry k0 is marked with the
+// tile's first line (from the tile lines), and an inclusive max-scan over the
+// tile (8 consecutive entries per lane, then warp shuffles) fills in every
+// entry: a few integer instructions per entry instead of a search per thread
+// and a walk. The tile leaves with 16-byte streaming stores. Tiles whose
+// lines do not fit the marking budget (very many empty lines) take one
+// binary search per lane in global memory and a walk instead.
 constexpr int EXP_THREADS = 256;
+constexpr int EXP_WARPS = EXP_THREADS / 32;
 constexpr int EXP_ITEMS = 8;
-constexpr int EXP_TILE = EXP_THREADS * EXP_ITEMS;
-constexpr int EXP_MARK_MAX = 8192;  // lines a tile marks at most
+constexpr int EXP_TILE = 32 * EXP_ITEMS;
+constexpr int EXP_MARK_MAX = 2048;  // lines a tile marks at most
 
 __global__ void __launch_bounds__(EXP_THREADS) k_expand(const int32_t *__restrict__ ptr, int32_t n_lines, int64_t nnz,
                                                          const int32_t *__restrict__ tl, long long n_tiles,
                                                          int32_t *__restrict__ out) {
-    __shared__ __align__(16) int32_t s_out[EXP_TILE];
-    __shared__ int32_t s_wmax[EXP_THREADS / 32];
-    const long long k0 = (long long)blockIdx.x * EXP_TILE;
-    const long long k1 = min(k0 + (long long)EXP_TILE, (long long)nnz);
-    const int n = (int)(k1 - k0);
-    const int t = (int)threadIdx.x;
+    __shared__ __align__(16) int32_t s_out[EXP_WARPS][EXP_TILE];
     const unsigned lane = lane_id();
-    const int lo = tl[blockIdx.x];
-    const int hi = (blockIdx.x + 1 < n_tiles) ? tl[blockIdx.x + 1] : n_lines - 1;
-    const int e = t * EXP_ITEMS;  // this thread's first entry within the tile
+    const long long tile = (long long)blockIdx.x * EXP_WARPS + (threadIdx.x >> 5);
+    if (tile >= n_tiles) return;  // the whole warp: nothing below waits on other warps
+    const long long k0 = tile * EXP_TILE;
+    const int n = (int)min((long long)EXP_TILE, (long long)nnz - k0);
+    const int lo = tl[tile];
+    const int hi = (tile + 1 < n_tiles) ? tl[tile + 1] : n_lines - 1;
+    const int e = (int)lane * EXP_ITEMS;  // this lane's first entry within the tile
+    int32_t *so = s_out[threadIdx.x >> 5];
     int v[EXP_ITEMS];
     if (hi - lo <= EXP_MARK_MAX) {
 #pragma unroll
         for (int h = 0; h < EXP_ITEMS / 4; ++h)
-            *reinterpret_cast<int4 *>(s_out + e + 4 * h) = make_int4(-1, -1, -1, -1);
-        __syncthreads();
-        if (t == 0) atomicMax(&s_out[0], lo);
-        for (int i = lo + 1 + t; i <= hi; i += EXP_THREADS) {
+            *reinterpret_cast<int4 *>(so + e + 4 * h) = make_int4(-1, -1, -1, -1);
+        __syncwarp();
+        if (lane == 0) atomicMax(&so[0], lo);
+        for (int i = lo + 1 + (int)lane; i <= hi; i += 32) {
             const long long a = (long long)__ldg(ptr + i) - k0;  // first entry of line i
-            if (a >= 0 && a < n) atomicMax(&s_out[a], i);
+            if (a >= 0 && a < n) atomicMax(&so[a], i);
         }
-        __syncthreads();
+        __syncwarp();
 #pragma unroll
         for (int h = 0; h < EXP_ITEMS / 4; ++h) {
-            const int4 q = *reinterpret_cast<const int4 *>(s_out + e + 4 * h);
+            const int4 q = *reinterpret_cast<const int4 *>(so + e + 4 * h);
             v[4 * h] = q.x;
             v[4 * h + 1] = q.y;
             v[4 * h + 2] = q.z;
@@ -219,9 +221,6 @@ __global__ void __launch_bounds__(EXP_THREADS) k_expand(const int32_t *__restric
         }
         int pre = __shfl_up_sync(0xffffffffu, inc, 1);
         if (lane == 0) pre = -1;
-        if (lane == 31) s_wmax[t >> 5] = inc;
-        __syncthreads();
-        for (int w = 0; w < (t >> 5); ++w) pre = max(pre, s_wmax[w]);
 #pragma unroll
         for (int j = 0; j < EXP_ITEMS; ++j) v[j] = max(v[j], pre);
     } else {
@@ -260,7 +259,8 @@ cudaError_t launch_expand(const int32_t *ptr, int32_t n_lines, int64_t nnz, int3
     if (e != cudaSuccess) return e;
     const long long n_tiles = (nnz + EXP_TILE - 1) / EXP_TILE;
     KernelScope ks(name, s);
-    k_expand<<<(unsigned)n_tiles, EXP_THREADS, 0, s>>>(ptr, n_lines, nnz, scratch, n_tiles, out);
+    k_expand<<<(unsigned)((n_tiles + EXP_WARPS - 1) / EXP_WARPS), EXP_THREADS, 0, s>>>(ptr, n_lines, nnz, scratch,
+                                                                                      n_tiles, out);
     return cudaGetLastError();
 }
 
