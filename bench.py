@@ -46,6 +46,9 @@ WORKLOADS = {
     "powerlaw_4m": dict(kind="powerlaw", n=4_000_000, seed_a=3, seed_x=4, cap=40 * 10 ** 9,
                         desc="n = 4e6, truncated power-law row lengths (exponent 2, mean 16, max 20000), "
                              "sorted unique random columns"),
+    "powerlaw_1m": dict(kind="powerlaw", n=1_000_000, seed_a=3, seed_x=4, cap=40 * 10 ** 9,
+                        desc="n = 1e6, the power law above at a quarter of the rows (CRS 196 MB > L2; "
+                             "profiling size)"),
     "batch_10k": dict(kind="batch", count=10000, seed=5, n_lo=100, n_hi=20000, cap=60 * 10 ** 9,
                       desc="10,000 matrices, n log-uniform in [100, 20000]; even: 2-D 5-point stencil on a "
                            "ceil(sqrt(n)) grid cut to n, odd: Poisson(8) row lengths, unique random columns"),

@@ -808,6 +808,12 @@ struct __align__(16) RowVal {
     double v;
 };
 
+// One 16-byte store of a record (L2 only): a plain struct assignment may be
+// split into narrower stores, each a partial sector of its own.
+__device__ __forceinline__ void store_rec(RowVal *dst, const RowVal &r) {
+    __stcg(reinterpret_cast<int4 *>(dst), make_int4(r.row, r.pad, __double2loint(r.v), __double2hiint(r.v)));
+}
+
 size_t col_rk_slot_bytes(int32_t n_cols) { return (size_t)SLOT_CAP * (size_t)n_cols * sizeof(int2); }
 int col_rv_long_cap() { return RV_LONG_CAP; }
 
@@ -1243,6 +1249,7 @@ __global__ void __launch_bounds__(GCL_THREADS) k_col_claim_grp(const int32_t *__
     const long long k0 = (long long)blockIdx.x * GCL_TILE;
     const long long k1 = min(k0 + (long long)GCL_TILE, (long long)nnz);
     for (int i = t; i < GCL_HASH; i += GCL_THREADS) { s_hkey[i] = -1; s_hcnt[i] = 0; }
+    if (t == 0) s_total = 0;  // first the tile's run count, later its record count
     int c[GCL_ITEMS];
     double v[GCL_ITEMS];
 #pragma unroll
@@ -1274,19 +1281,54 @@ __global__ void __launch_bounds__(GCL_THREADS) k_col_claim_grp(const int32_t *__
             }
         }
     }
-    // runs: lanes of one instruction with the same group share one table
-    // update by their leader
-    int slot[GCL_ITEMS], local[GCL_ITEMS];
-    int bad = 0;
+    // lanes of one instruction with the same group form a run led by its
+    // first lane; a tile whose runs outnumber half the table (scattered
+    // columns: nearly one group per entry) skips the table and lets every
+    // leader reserve its run with one global atomic and store it directly
+    int grp[GCL_ITEMS];
+    unsigned peers[GCL_ITEMS];
+    int bad = 0, n_lead = 0;
 #pragma unroll
     for (int u = 0; u < GCL_ITEMS; ++u) {
         const long long k = k0 + u * GCL_THREADS + t;
         const bool has = k < k1;
         const bool ok = has && (unsigned)c[u] < (unsigned)n_cols;
         bad |= has && !ok;
-        const int g = ok ? (c[u] / GRP_COLS) : -1 - (int)lane;
-        const unsigned peers = __match_any_sync(0xffffffffu, g);
-        const int leader = __ffs(peers) - 1;
+        grp[u] = ok ? (c[u] / GRP_COLS) : -1 - (int)lane;
+        peers[u] = __match_any_sync(0xffffffffu, grp[u]);
+        n_lead += __popc(__ballot_sync(0xffffffffu, ok && (int)lane == __ffs(peers[u]) - 1));
+    }
+    if (lane == 0 && n_lead) atomicAdd(&s_total, n_lead);
+    __syncthreads();
+    if (s_total > GCL_HASH / 2) {
+        int redo = 0;
+#pragma unroll
+        for (int u = 0; u < GCL_ITEMS; ++u) {
+            const bool ok = grp[u] >= 0;
+            const int leader = __ffs(peers[u]) - 1;
+            int base = 0;
+            if (ok && (int)lane == leader) base = atomicAdd(gcnt + grp[u], __popc(peers[u]));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (!ok) continue;
+            const int gp = base + __popc(peers[u] & lanemask_lt());
+            RowVal q;
+            q.row = s_row[pad32(u * GCL_THREADS + t)];
+            q.pad = c[u] % GRP_COLS;
+            q.v = v[u];
+            if (gp < GRP_CAP) store_rec(regions + (long long)grp[u] * GRP_CAP + gp, q);
+            else redo = 1;
+        }
+        if (__any_sync(0xffffffffu, redo) && lane == 0) atomicOr(status, ST_REDO);
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_BAD_INDEX);
+        return;
+    }
+    // banded tiles: runs of the same group share one table slot
+    int slot[GCL_ITEMS], local[GCL_ITEMS];
+#pragma unroll
+    for (int u = 0; u < GCL_ITEMS; ++u) {
+        const bool ok = grp[u] >= 0;
+        const int g = grp[u];
+        const int leader = __ffs(peers[u]) - 1;
         int h = -1, base = 0;
         if (ok && (int)lane == leader) {
             h = (int)(((unsigned)g * 2654435761u) >> 23);  // 9 bits
@@ -1296,12 +1338,12 @@ __global__ void __launch_bounds__(GCL_THREADS) k_col_claim_grp(const int32_t *__
                 if (p + 1 >= GCL_PROBES) { h = -1; break; }
                 h = (h + 1) & (GCL_HASH - 1);
             }
-            if (h >= 0) base = atomicAdd(&s_hcnt[h], __popc(peers));
+            if (h >= 0) base = atomicAdd(&s_hcnt[h], __popc(peers[u]));
         }
         h = __shfl_sync(0xffffffffu, h, leader);
         base = __shfl_sync(0xffffffffu, base, leader);
         slot[u] = ok ? h : -2;  // -1: no table slot, the entry goes alone
-        local[u] = base + __popc(peers & lanemask_lt());
+        local[u] = base + __popc(peers[u] & lanemask_lt());
     }
     __syncthreads();
     {
@@ -1350,14 +1392,14 @@ __global__ void __launch_bounds__(GCL_THREADS) k_col_claim_grp(const int32_t *__
             redo |= gp >= GRP_CAP;
         } else {
             const int gp = atomicAdd(gcnt + g, 1);
-            if (gp < GRP_CAP) regions[g * GRP_CAP + gp] = q;
+            if (gp < GRP_CAP) store_rec(regions + g * GRP_CAP + gp, q);
             else redo = 1;
         }
     }
     __syncthreads();
     for (int q = t; q < s_total; q += GCL_THREADS) {
         const long long d = s_dst[q];
-        if (d >= 0) regions[d] = s_rec[q];
+        if (d >= 0) store_rec(regions + d, s_rec[q]);
     }
     if (__any_sync(0xffffffffu, redo) && lane == 0) atomicOr(status, ST_REDO);
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_BAD_INDEX);
