@@ -786,7 +786,7 @@ spmv_status apply_core(const spmv_matrix *M, const double *x, double *y, cudaStr
                 CK(launch_spmv_coo_col(M->idx, M->idx2, M->val, M->nnz, M->n_rows, x, y, s));
                 return SPMV_OK;
             case SPMV_ELL:
-                CK(launch_spmv_ell_col(M->val, M->idx, M->n_rows, M->n_cols, M->width, M->ld, x, y, s));
+                CK(launch_spmv_ell_col(M->val, M->idx, M->n_rows, M->n_cols, M->width, M->ld, M->nnz, x, y, s));
                 return SPMV_OK;
         }
     }

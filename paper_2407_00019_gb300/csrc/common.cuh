@@ -254,8 +254,10 @@ cudaError_t launch_spmv_crs_rows(int split, int cap, const int32_t *irp, const i
                                  int32_t n_rows, const double *x, double *y, cudaStream_t s);
 cudaError_t launch_spmv_ell_row(const double *eval, const int32_t *eidx, int32_t n_rows, int32_t width,
                                 int32_t ld, const double *x, double *y, cudaStream_t s);
+// nnz: the entries of the matrix (not the slots); with padding at least a
+// quarter of the slots, the adds of zero slots are left out where x_j is finite.
 cudaError_t launch_spmv_ell_col(const double *eval, const int32_t *eidx, int32_t n_rows, int32_t n_cols,
-                                int32_t width, int32_t ld, const double *x, double *y, cudaStream_t s);
+                                int32_t width, int32_t ld, int64_t nnz, const double *x, double *y, cudaStream_t s);
 // COO-Row over 2048-entry tiles with a carry pass (the allocation-free entry
 // point). `scratch`: coo_row_scratch_bytes(nnz); `status` may be NULL (then a
 // word inside the scratch is used).

@@ -268,6 +268,15 @@ cudaError_t launch_spmv_ell_row(const double *eval, const int32_t *eidx, int32_t
 // 32 consecutive columns (coalesced) and its atomic adds go to the k-th rows
 // of 32 consecutive columns, which in banded matrices are consecutive rows:
 // a few sectors of y per warp instruction.
+// SKIP (chosen when padding is at least a quarter of the slots): a slot
+// holding +-0 (the padding of a short column, Fig. 3) adds +-0 when x_j is
+// finite, which leaves y unchanged (y starts at +0, so no element is ever
+// -0), and such adds are left out; with x_j infinite or NaN every slot is
+// added, so the padding still turns y into NaN as the padded product does.
+// A warp whose four slots of a batch hold no zero adds them unconditionally.
+// Without SKIP the loop has no test at all (the test costs matrices with
+// little padding more than it saves).
+template <bool SKIP>
 __global__ void __launch_bounds__(256) k_spmv_ell_col(const double *__restrict__ eval,
                                                        const int32_t *__restrict__ eidx, int32_t n_cols,
                                                        int32_t width, int32_t ld, const double *__restrict__ x,
@@ -275,6 +284,7 @@ __global__ void __launch_bounds__(256) k_spmv_ell_col(const double *__restrict__
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n_cols;
          j += (long long)gridDim.x * blockDim.x) {
         const double xj = __ldg(x + j);
+        const bool all = !SKIP || !isfinite(xj);
         const double *pv = eval + j;
         const int32_t *pr = eidx + j;
         int k = 0;
@@ -286,19 +296,40 @@ __global__ void __launch_bounds__(256) k_spmv_ell_col(const double *__restrict__
                 v[u] = __ldcs(pv + (long long)(k + u) * ld);
                 r[u] = __ldcs(pr + (long long)(k + u) * ld);
             }
+            if (!SKIP) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) atomicAdd(y + r[u], v[u] * xj);
+                for (int u = 0; u < 4; ++u) atomicAdd(y + r[u], v[u] * xj);
+                continue;
+            }
+            bool keep[4], every = true;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) every &= keep[u] = all || v[u] != 0.0;
+            if (__all_sync(__activemask(), every)) {  // lanes past n_cols have left the loop
+#pragma unroll
+                for (int u = 0; u < 4; ++u) atomicAdd(y + r[u], v[u] * xj);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (keep[u]) atomicAdd(y + r[u], v[u] * xj);
+            }
         }
-        for (; k < width; ++k) atomicAdd(y + __ldcs(pr + (long long)k * ld), __ldcs(pv + (long long)k * ld) * xj);
+        for (; k < width; ++k) {
+            const double v = __ldcs(pv + (long long)k * ld);
+            if (all || v != 0.0) atomicAdd(y + __ldcs(pr + (long long)k * ld), v * xj);
+        }
     }
 }
 
 cudaError_t launch_spmv_ell_col(const double *eval, const int32_t *eidx, int32_t n_rows, int32_t n_cols,
-                                int32_t width, int32_t ld, const double *x, double *y, cudaStream_t s) {
+                                int32_t width, int32_t ld, int64_t nnz, const double *x, double *y, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(y, 0, sizeof(double) * (size_t)n_rows, s);
     if (e != cudaSuccess || n_cols <= 0) return e;
+    const bool skip = 4.0 * (double)nnz <= 3.0 * (double)width * (double)n_cols;  // >= 1/4 of the slots padding
     KernelScope ks("spmv_ell_col", s);
-    k_spmv_ell_col<<<ceil_div_u(n_cols, 256), 256, 0, s>>>(eval, eidx, n_cols, width, ld, x, y);
+    if (skip)
+        k_spmv_ell_col<true><<<ceil_div_u(n_cols, 256), 256, 0, s>>>(eval, eidx, n_cols, width, ld, x, y);
+    else
+        k_spmv_ell_col<false><<<ceil_div_u(n_cols, 256), 256, 0, s>>>(eval, eidx, n_cols, width, ld, x, y);
     return cudaGetLastError();
 }
 

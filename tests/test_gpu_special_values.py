@@ -202,3 +202,38 @@ def test_batch_ell_build_keeps_special_bits(fused):
         xs = xh[P["x_offset"]:P["x_offset"] + H.n_cols]
         assert_products_with_specials(yh[P["y_offset"]:P["y_offset"] + H.n_rows], H, xs, f"batch {i}")
     B.close()
+
+
+def test_ell_column_padding_with_non_finite_x():
+    """ELL-Column pads short columns with zeros (Fig. 3). The product skips
+    the adds of zero slots when x_j is finite (they leave y unchanged) and
+    keeps them when x_j is infinite or NaN, so its result equals the padded
+    product of the oracle: the same rows NaN, the same rows +-Inf with the
+    same sign, the finite rows within the tolerance."""
+    import torch
+    L = lib()
+    H = synth.random_crs(3000, 2500, 6, seed=27, empty_frac=0.2)
+    irp_t, icol_t, val_t, _ = oracle.crs_to_ccs(H.n_rows, H.n_cols, H.irp, H.icol, H.val)
+    ev, er, W = oracle.ccs_to_ell_col(H.n_cols, irp_t, icol_t, val_t)
+    ccs = L.spmv_transform(dev(H), L.SPMV_CRS, L.SPMV_COLWISE)
+    ell = L.spmv_transform_from(ccs, L.SPMV_ELL)
+    for seed in (1, 2):
+        xh = xvec(H.n_cols, seed=40 + seed)
+        pick = np.nonzero(synth.uniform01(seed, 41, np.arange(H.n_cols, dtype=np.uint64)) < 0.01)[0]
+        xh[pick[0::3]] = np.inf
+        xh[pick[1::3]] = -np.inf
+        xh[pick[2::3]] = np.nan
+        y_ref = oracle.spmv_ell_col(H.n_rows, H.n_cols, W, ev, er, xh)
+        assert np.isnan(y_ref).any() and np.isinf(y_ref).any()
+        y = torch.full((H.n_rows,), 7.0, dtype=torch.float64, device="cuda")
+        L.spmv_apply(ell, torch.from_numpy(xh).cuda(), y)
+        torch.cuda.synchronize()
+        yh = y.cpu().numpy()
+        assert np.array_equal(np.isnan(yh), np.isnan(y_ref))
+        inf = np.isinf(y_ref)
+        assert np.array_equal(np.isinf(yh), inf) and np.array_equal(np.sign(yh[inf]), np.sign(y_ref[inf]))
+        fin = np.isfinite(y_ref)
+        _, s = oracle.spmv_ref(H.n_rows, H.irp, H.icol, H.val, np.where(np.isfinite(xh), xh, 0.0))
+        assert np.all(np.abs(yh[fin] - y_ref[fin]) <= TOL * s[fin])
+    ell.close()
+    ccs.close()
