@@ -34,6 +34,7 @@ METRIC = "SpMV GB/s (% HBM peak) per format; CRS->ELL cost in CRS-SpMV units; p9
 L2_BYTES = 129 * 1024 * 1024
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_STEPS = 3  # sequential steps timed per kernel after the timed region
+PRODUCT_REPS = 20  # back-to-back products timed per format
 
 WORKLOADS = {
     "stencil27_128": dict(kind="stencil27", N=128, seed_a=1, seed_x=2, cap=0,
@@ -77,6 +78,34 @@ def make_matrix(w: dict, rank: int = 0):
         H = synth.power_law(w["n"], seed=w["seed_a"] + off)
     x = synth.vector_pm1(H.n_cols, seed=w["seed_x"] + off)
     return H, x
+
+
+def steady_products(L, torch, A, x, n_rows: int, cap: int, with_ell_row: bool) -> dict:
+    """{format: {kernel: (launches, total ms)}} over PRODUCT_REPS back-to-back
+    products of each format's handle (built once, 3 warm-up products)."""
+    hs = {"crs": L.spmv_transform(A, L.SPMV_CRS, L.SPMV_ROWWISE),
+          "coo_row": L.spmv_transform(A, L.SPMV_COO, L.SPMV_ROWWISE)}
+    if with_ell_row:
+        hs["ell_row"] = L.spmv_transform(A, L.SPMV_ELL, L.SPMV_ROWWISE, cap)
+    ccs = L.spmv_transform(A, L.SPMV_CRS, L.SPMV_COLWISE, cap)
+    hs["coo_col"] = L.spmv_transform_from(ccs, L.SPMV_COO, cap)
+    hs["ell_col"] = L.spmv_transform_from(ccs, L.SPMV_ELL, cap)
+    y = torch.empty(n_rows, dtype=torch.float64, device=x.device)
+    out = {}
+    for name, M in hs.items():
+        for _ in range(3):
+            L.spmv_apply(M, x, y)
+        torch.cuda.synchronize()
+        L.spmv_profile_read(reset=True)
+        L.spmv_profile_enable(True)
+        for _ in range(PRODUCT_REPS):
+            L.spmv_apply(M, x, y)
+        torch.cuda.synchronize()
+        L.spmv_profile_enable(False)
+        out[name] = L.spmv_profile_read(reset=True)
+    for M in list(hs.values()) + [ccs]:
+        M.close()
+    return out
 
 
 # -------------------------------------------------------------- byte model
@@ -198,13 +227,17 @@ class Step:
         fmt = chosen.describe()["format"]
         self.chosen = {0: "CRS", 1: "COO-Row", 2: "ELL-Row"}[fmt]
         mats = {}
+        # each product runs right after its own handle is built: the CRS
+        # product does not follow the ELL build, whose 680 MB of writes would
+        # still be draining from L2 during it
         mats["crs"] = chosen if fmt == L.SPMV_CRS else L.spmv_transform(A, L.SPMV_CRS, L.SPMV_ROWWISE, stream=s)
+        L.spmv_apply(mats["crs"], self.x, self.ys["crs"], stream=s)
         if fmt == L.SPMV_ELL:
             mats["ell_row"] = chosen
         elif not self.cap or stats["ell_bytes"] <= self.cap:
             mats["ell_row"] = L.spmv_transform(A, L.SPMV_ELL, L.SPMV_ROWWISE, self.cap, stream=s)
-        for name, M in mats.items():
-            L.spmv_apply(M, self.x, self.ys[name], stream=s)
+        if "ell_row" in mats:
+            L.spmv_apply(mats["ell_row"], self.x, self.ys["ell_row"], stream=s)
         self.stats = stats
         return list(mats.values())
 
@@ -1195,22 +1228,24 @@ def main():
                 "traffic": stored_traffic(top, args.workload),
                 "algorithmic_bytes_per_launch": top_b}
 
-    def fmt_rate(knames, model):
-        """One product's rate: the device time of all its kernels (a binned CRS
-        product is several launches, one per row bin) over the profiled steps,
-        each of which runs the product once."""
-        if not knames or model not in bm:
+    # Per-format product rates in the steady state of an iterative solver: each
+    # format's handle built once, its product run back to back (3 warm-up
+    # runs, PRODUCT_REPS timed), the device time of the product's kernels from
+    # the library's events (a product on uneven rows may be several launches).
+    # These are the t_crs and t_ell of Eqs. 1-2; the per-kernel table above
+    # times single launches inside the sequential steps instead.
+    prods = steady_products(L, torch, A, x, H.n_rows, w["cap"], "spmv_ell_row" in bm)
+
+    def fmt_rate(name, model):
+        if name not in prods or model not in bm:
             return None
-        ms = sum(per_kernel[k]["ms_per_launch"] * per_kernel[k]["launches"] for k in knames) / PROFILE_STEPS
+        ms = sum(t for _, t in prods[name].values()) / PRODUCT_REPS
         g = bm[model] / (ms * 1e-3) / 1e9
-        return {"GB/s": g, "pct_hbm": 100.0 * g / peak, "ms": ms, "kernels": sorted(knames)}
-    crs_k = [k for k in per_kernel if k.startswith("spmv_crs_")]
-    coo_k = [k for k in per_kernel if k.startswith("spmv_coo_row")]
-    cooc_k = [k for k in per_kernel if k.startswith("spmv_coo_col")]
-    per_format = {"crs": fmt_rate(crs_k, "spmv_crs"), "coo_row": fmt_rate(coo_k, "spmv_coo_row"),
-                  "ell_row": fmt_rate([k for k in per_kernel if k == "spmv_ell_row"], "spmv_ell_row"),
-                  "coo_col": fmt_rate(cooc_k, "spmv_coo_col"),
-                  "ell_col": fmt_rate([k for k in per_kernel if k == "spmv_ell_col"], "spmv_ell_col")}
+        return {"GB/s": g, "pct_hbm": 100.0 * g / peak, "ms": ms, "kernels": sorted(prods[name]),
+                "runs": f"mean of {PRODUCT_REPS} back-to-back products after 3 warm-up runs"}
+    per_format = {"crs": fmt_rate("crs", "spmv_crs"), "coo_row": fmt_rate("coo_row", "spmv_coo_row"),
+                  "ell_row": fmt_rate("ell_row", "spmv_ell_row"), "coo_col": fmt_rate("coo_col", "spmv_coo_col"),
+                  "ell_col": fmt_rate("ell_col", "spmv_ell_col")}
     # the ceiling of the column-wise products: their FP64 atomic adds alone
     # (coalesced, the best case on banded matrices), one per entry (COO-Column)
     # or per slot (ELL-Column)
@@ -1311,7 +1346,8 @@ def main():
                        "launches_before_timed": int(launches0),
                        "step_schedule": "sequential" if args.sequential else
                        "independent pipelines (AT+CRS+ELL-Row, COO-Row, Phase I then Phase II | CCS->ELL-Col) on four streams",
-                       "per_kernel": f"{PROFILE_STEPS} sequential steps after the timed region"},
+                       "per_kernel": f"{PROFILE_STEPS} sequential steps after the timed region",
+                       "per_format": f"each product {PRODUCT_REPS} times back to back after 3 warm-up runs"},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -277,7 +277,7 @@ constexpr int ELL_LINES = 128;
 constexpr int ELL_SPLIT_BUILD = 2;
 constexpr int ELL_SPLIT_FUSED = 4;
 constexpr int ELL_STAGE_CAP = 4096;  // entries per stage (48 KB)
-constexpr int ELL_KB_BUILD = 8;      // slots a thread handles at once
+constexpr int ELL_KB_BUILD = 6;      // slots a thread handles at once
 constexpr int ELL_KB_FUSED = 4;      // (fused: two CTAs of 512 threads per SM leave 64 registers)
 using EllPipe = StagePipe<ELL_STAGE_CAP, 1>;
 
@@ -302,12 +302,17 @@ __global__ void __launch_bounds__(ELL_LINES *ELL_SPLIT, FUSED ? 2 : 4) k_lines_t
         *e0 = ptr[l0];
         *e1 = ptr[l1];
     };
-    auto body = [&](int tile, int st, const StageMeta &m) {
+    // this thread's line pointers, loaded a tile ahead
+    auto pre = [&](int tile) {
+        const long long l = (long long)tile * ELL_LINES + lt;
+        return (l < n_lines) ? make_int2(ptr[l], ptr[l + 1]) : make_int2(0, 0);
+    };
+    auto body = [&](int tile, int st, const StageMeta &m, int2 se) {
         const long long l = (long long)tile * ELL_LINES + lt;
         double acc = 0.0;
         if (l < ld) {
             if (l < n_lines) {
-                const long long s = ptr[l], e = ptr[l + 1];
+                const long long s = se.x, e = se.y;
                 int len = (int)(e - s);
                 if (len < 0 || len > width) { bad = 1; len = len < 0 ? 0 : width; }
                 int last = len > 0 ? P.idx_at(m, st, idx, s + len - 1) : 0;
@@ -364,7 +369,7 @@ __global__ void __launch_bounds__(ELL_LINES *ELL_SPLIT, FUSED ? 2 : 4) k_lines_t
             }
         }
     };
-    pipe_tiles(P, n_tiles, val, idx, can_stage != 0, status, range, body);
+    pipe_tiles(P, n_tiles, val, idx, can_stage != 0, status, range, pre, body);
     if (bad) atomicOr(status, ST_BAD_INDEX);
 }
 

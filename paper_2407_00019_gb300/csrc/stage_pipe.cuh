@@ -95,26 +95,35 @@ struct StagePipe {
 };
 
 // Standard loop over tiles with the pipeline. `range(tile, &e0, &e1)` gives
-// a tile's entry range, `body(tile, st, meta)` consumes it; all threads call.
-// On a wait that runs out, sets ST_TIMEOUT, waits (bounded) for the copies in
-// flight and returns false.
-template <class Pipe, class RangeF, class BodyF>
+// a tile's entry range (thread 0 only); `pre(tile)` returns what every thread
+// loads for a tile before consuming it (for example its line pointers);
+// `body(tile, st, meta, pre)` consumes it; all threads call. Both loads run
+// ahead of their use: thread 0 loads the range of the tile after next while
+// the current tile is consumed, and every thread loads `pre` of the next
+// tile, so no tile waits for them. On a wait that runs out, sets ST_TIMEOUT,
+// waits (bounded) for the copies in flight and returns false.
+template <class Pipe, class RangeF, class PreF, class BodyF>
 __device__ bool pipe_tiles(Pipe &P, int n_tiles, const double *val, const int32_t *idx, bool can_stage,
-                           int *status, RangeF range, BodyF body, const int32_t *idx2 = nullptr) {
-    int it = 0;
-    if (threadIdx.x == 0 && (int)blockIdx.x < n_tiles) {
+                           int *status, RangeF range, PreF pre, BodyF body, const int32_t *idx2 = nullptr) {
+    const int G = gridDim.x;
+    int tile = blockIdx.x;
+    if (tile >= n_tiles) return true;
+    long long f0 = 0, f1 = 0;  // thread 0: the range of the next tile to issue
+    if (threadIdx.x == 0) {
         long long e0, e1;
-        range((int)blockIdx.x, &e0, &e1);
+        range(tile, &e0, &e1);
         P.issue(0, e0, e1, val, idx, can_stage, idx2);
+        if (tile + G < n_tiles) range(tile + G, &f0, &f1);
     }
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+    auto cur = pre(tile);
+    for (int it = 0; tile < n_tiles; tile += G, ++it) {
         const int st = it & 1;
-        const int next = tile + gridDim.x;
+        const int next = tile + G;
         if (threadIdx.x == 0 && next < n_tiles) {
-            long long e0, e1;
-            range(next, &e0, &e1);
-            P.issue(st ^ 1, e0, e1, val, idx, can_stage, idx2);
+            P.issue(st ^ 1, f0, f1, val, idx, can_stage, idx2);
+            if (next + G < n_tiles) range(next + G, &f0, &f1);
         }
+        const auto nxt = (next < n_tiles) ? pre(next) : cur;
         const bool ok = P.wait(st, it >> 1);
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) {
@@ -125,8 +134,9 @@ __device__ bool pipe_tiles(Pipe &P, int n_tiles, const double *val, const int32_
             return false;
         }
         const StageMeta m = P.meta[st];
-        body(tile, st, m);
+        body(tile, st, m, cur);
         __syncthreads();
+        cur = nxt;
     }
     return true;
 }
