@@ -145,6 +145,7 @@ def kernel_bytes(name: str, bm: dict, n_rows: int, n_cols: int, nnz: int):
         "crs_to_coo_row": bm.get("crs_to_coo_row"),
         "ccs_to_coo_col": bm.get("ccs_to_coo_col"),
         "analyze": bm.get("analyze"),
+        "row_width": 4 * (n_rows + 1),  # the ELL-Row builds' pointer pass
         "validate_idx": 4 * nnz,
         "spmv_ccs": 12 * nnz + 4 * (n_cols + 1) + 8 * n_cols + 8 * n_rows,
         # Phase I as built here: ICOL in, rank out; rank + ICOL in, (k, row)
@@ -1259,7 +1260,8 @@ def main():
     t_crs = per_format["crs"]["ms"] if per_format["crs"] else None
     cost = None
     if t_crs and "crs_to_ell_row" in per_kernel:
-        t_an = per_kernel["analyze"]["ms_per_launch"]
+        # the ELL-Row build's own pointer pass (the longest row), not the AT analysis
+        t_an = per_kernel.get("row_width", per_kernel["analyze"])["ms_per_launch"]
         t_tr = per_kernel["crs_to_ell_row"]["ms_per_launch"]
         L.spmv_profile_enable(True)
         yf = torch.empty(H.n_rows, dtype=torch.float64, device=device)

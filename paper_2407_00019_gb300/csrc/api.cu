@@ -238,6 +238,24 @@ spmv_status analyze_core(const spmv_crs *A, bool validate_icol, spmv_stats *out,
     return SPMV_OK;
 }
 
+// The longest row and the row-pointer checks only (an ELL-Row build needs no
+// other statistic): st->max_row_len and st->ell_bytes, the rest zero.
+spmv_status analyze_width(const spmv_crs *A, spmv_stats *out, cudaStream_t s) {
+    BufPtr acc_buf;
+    CKS(alloc_buf(sizeof(AnalyzeAcc), s, &acc_buf));
+    AnalyzeAcc *acc = reinterpret_cast<AnalyzeAcc *>(acc_buf->p);
+    CK(cudaMemsetAsync(acc, 0, sizeof(AnalyzeAcc), s));
+    CK(launch_row_width(A->irp, A->n_rows, A->nnz, acc, s));
+    AnalyzeAcc h;
+    CK(cudaMemcpyAsync(&h, acc, sizeof(AnalyzeAcc), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CKS(status_from_dev(h.status));
+    memset(out, 0, sizeof(*out));
+    out->max_row_len = h.max_len;
+    out->ell_bytes = ell_bytes(A->n_rows, h.max_len);
+    return SPMV_OK;
+}
+
 spmv_matrix *new_handle(const spmv_crs *A, int format, int layout, cudaStream_t s) {
     spmv_matrix *M = new (std::nothrow) spmv_matrix();
     if (!M) return nullptr;
@@ -908,7 +926,7 @@ spmv_status spmv_transform(const spmv_crs *A, spmv_format format, spmv_layout la
         if (format == SPMV_CRS) return build_crs_plan(A, mem_cap_bytes, out, s);
         if (format == SPMV_COO) return build_coo_row(A, mem_cap_bytes, out, s);
         spmv_stats st;
-        CKS(analyze_core(A, false, &st, s));
+        CKS(analyze_width(A, &st, s));
         return build_ell_row(A, st, mem_cap_bytes, nullptr, nullptr, out, s);
     }
     // column-wise: Phase I first
@@ -954,7 +972,7 @@ spmv_status spmv_transform_apply(const spmv_crs *A, const double *x, double *y, 
     CKS(check_crs(A));
     if (!x || !y) return SPMV_ERR_INVALID_ARG;
     spmv_stats st;
-    CKS(analyze_core(A, false, &st, S(stream)));
+    CKS(analyze_width(A, &st, S(stream)));
     return build_ell_row(A, st, mem_cap_bytes, x, y, out, S(stream));
 }
 

@@ -151,6 +151,9 @@ __device__ __forceinline__ T warp_sum(T v) {
 // All return cudaGetLastError() after enqueueing on `s`.
 
 // analyze / validate (kernels_rowwise.cu)
+// The longest row and the row-pointer checks of launch_analyze only (what
+// an ELL build needs): max_len and status of `acc` (zeroed by the caller).
+cudaError_t launch_row_width(const int32_t *irp, int32_t n_rows, int64_t nnz, AnalyzeAcc *acc, cudaStream_t s);
 cudaError_t launch_analyze(const int32_t *irp, int32_t n_rows, int64_t nnz, AnalyzeAcc *acc, cudaStream_t s);
 cudaError_t launch_validate_idx(const int32_t *idx, int64_t n, int32_t bound, int *status, cudaStream_t s);
 

@@ -107,6 +107,70 @@ cudaError_t launch_analyze(const int32_t *irp, int32_t n_rows, int64_t nnz, Anal
     return cudaGetLastError();
 }
 
+// The pass an ELL build needs of the row pointers: the longest row and the
+// same pointer checks as k_analyze (first 0, last nnz, none decreasing, all
+// in [0, nnz]), nothing else. Persistent CTAs, rows in a grid-stride loop,
+// one accumulator update per CTA.
+constexpr int RW_CTAS_PER_SM = 4;
+constexpr int RW_ITEMS = 4;  // rows a thread takes at a time (16-byte loads of IRP)
+static_assert(RW_ITEMS % 4 == 0, "whole 16-byte loads");
+
+__global__ void __launch_bounds__(AN_THREADS) k_row_width(const int32_t *__restrict__ irp, int32_t n, int64_t nnz,
+                                                           AnalyzeAcc *acc) {
+    __shared__ int s_mx[AN_THREADS / 32], s_bad[AN_THREADS / 32];
+    int mx = 0, bad = 0;
+    const long long stride = (long long)gridDim.x * AN_THREADS * RW_ITEMS;
+    for (long long i0 = ((long long)blockIdx.x * AN_THREADS + threadIdx.x) * RW_ITEMS; i0 < n; i0 += stride) {
+        int p[RW_ITEMS + 1];
+        if (i0 + RW_ITEMS <= n && ((reinterpret_cast<uintptr_t>(irp + i0) & 15) == 0)) {
+#pragma unroll
+            for (int h = 0; h < RW_ITEMS / 4; ++h) {
+                const int4 q = __ldcs(reinterpret_cast<const int4 *>(irp + i0) + h);
+                p[4 * h] = q.x; p[4 * h + 1] = q.y; p[4 * h + 2] = q.z; p[4 * h + 3] = q.w;
+            }
+            p[RW_ITEMS] = irp[i0 + RW_ITEMS];
+        } else {
+#pragma unroll
+            for (int j = 0; j <= RW_ITEMS; ++j) p[j] = (i0 + j <= n) ? irp[i0 + j] : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < RW_ITEMS; ++j) {
+            const long long i = i0 + j;
+            if (i < n) {
+                const int len = p[j + 1] - p[j];
+                if (len < 0 || p[j] < 0 || (long long)p[j + 1] > nnz) bad = 1;
+                if (i == 0 && p[0] != 0) bad = 1;
+                if (i == n - 1 && (long long)p[j + 1] != nnz) bad = 1;
+                mx = max(mx, len);
+            }
+        }
+    }
+    mx = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(mx, 0));
+    bad = (int)__reduce_or_sync(0xffffffffu, (unsigned)bad);
+    if (lane_id() == 0) {
+        s_mx[threadIdx.x >> 5] = mx;
+        s_bad[threadIdx.x >> 5] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < AN_THREADS / 32; ++w) {
+            mx = max(mx, s_mx[w]);
+            bad |= s_bad[w];
+        }
+        if (mx > 0) atomicMax(&acc->max_len, mx);
+        if (bad) atomicOr(&acc->status, ST_BAD_PTR);
+    }
+}
+
+cudaError_t launch_row_width(const int32_t *irp, int32_t n_rows, int64_t nnz, AnalyzeAcc *acc, cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    unsigned grid = ceil_div_u(n_rows, (long long)AN_THREADS * RW_ITEMS);
+    if (grid > (unsigned)sm_count() * RW_CTAS_PER_SM) grid = (unsigned)sm_count() * RW_CTAS_PER_SM;
+    KernelScope ks("row_width", s);
+    k_row_width<<<grid, AN_THREADS, 0, s>>>(irp, n_rows, nnz, acc);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- validate
 __global__ void __launch_bounds__(256) k_validate_idx(const int32_t *__restrict__ idx, int64_t n, int32_t bound,
                                                        int *status) {
