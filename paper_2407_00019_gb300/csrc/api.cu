@@ -344,7 +344,7 @@ spmv_status build_coo_row(const spmv_crs *A, uint64_t cap, spmv_matrix **out, cu
     // IRP checks (the transformation reads no column index), read at the sync below
     CKS(alloc_buf(sizeof(AnalyzeAcc), s, &acc_buf));
     CK(cudaMemsetAsync(acc_buf->p, 0, sizeof(AnalyzeAcc), s));
-    CK(launch_analyze(A->irp, A->n_rows, A->nnz, reinterpret_cast<AnalyzeAcc *>(acc_buf->p), s));
+    CK(launch_row_width(A->irp, A->n_rows, A->nnz, reinterpret_cast<AnalyzeAcc *>(acc_buf->p), s));
     CK(launch_expand(A->irp, A->n_rows, A->nnz, reinterpret_cast<int32_t *>(irow->p),
                      reinterpret_cast<int32_t *>(scr->p), s, "crs_to_coo_row"));
     BufPtr sw;
@@ -938,7 +938,7 @@ spmv_status spmv_transform(const spmv_crs *A, spmv_format format, spmv_layout la
     BufPtr acc_buf;
     CKS(alloc_buf(sizeof(AnalyzeAcc), s, &acc_buf));
     CK(cudaMemsetAsync(acc_buf->p, 0, sizeof(AnalyzeAcc), s));
-    CK(launch_analyze(A->irp, A->n_rows, A->nnz, reinterpret_cast<AnalyzeAcc *>(acc_buf->p), s));
+    CK(launch_row_width(A->irp, A->n_rows, A->nnz, reinterpret_cast<AnalyzeAcc *>(acc_buf->p), s));
     const int *irp_status = &reinterpret_cast<AnalyzeAcc *>(acc_buf->p)->status;
     CKS(phase1(A, format == SPMV_CRS ? mem_cap_bytes : 0, mem_cap_bytes, format == SPMV_ELL, M, s, irp_status));
     M->bufs = M->ccs_bufs;
@@ -1048,8 +1048,9 @@ spmv_status spmv_measure(const spmv_crs *A, const spmv_at_params *p, spmv_timing
     CKS(build_crs_plan(A, 0, &crs, s));
     std::unique_ptr<spmv_matrix> crs_h(crs);
     CKS(time_median([&] { return apply_core(crs, x, y, s); }, warm, reps, s, &out->t_crs_ms));
-    // t_trans: device work of CRS -> ELL-Row (row statistics + the ELL
-    // build) into preallocated arrays; allocation is not timed.
+    // t_trans: device work of CRS -> ELL-Row (the row-pointer pass + the ELL
+    // build, as spmv_transform runs them) into preallocated arrays;
+    // allocation is not timed.
     const int32_t W = st.max_row_len, ld = round_up32(A->n_rows);
     BufPtr ev, ei, acc, stw;
     CKS(alloc_buf((size_t)ld * W * 8, s, &ev));
@@ -1059,7 +1060,7 @@ spmv_status spmv_measure(const spmv_crs *A, const spmv_at_params *p, spmv_timing
     CK(cudaMemsetAsync(stw->p, 0, 16, s));
     auto trans = [&]() -> spmv_status {
         CK(cudaMemsetAsync(acc->p, 0, sizeof(AnalyzeAcc), s));
-        CK(launch_analyze(A->irp, A->n_rows, A->nnz, reinterpret_cast<AnalyzeAcc *>(acc->p), s));
+        CK(launch_row_width(A->irp, A->n_rows, A->nnz, reinterpret_cast<AnalyzeAcc *>(acc->p), s));
         CK(launch_lines_to_ell(A->irp, A->icol, A->val, A->n_rows, A->n_cols, W, ld,
                                reinterpret_cast<double *>(ev->p), reinterpret_cast<int32_t *>(ei->p), nullptr,
                                nullptr, reinterpret_cast<int *>(stw->p), s, "crs_to_ell_row"));
