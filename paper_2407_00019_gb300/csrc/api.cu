@@ -338,15 +338,13 @@ spmv_status build_coo_row(const spmv_crs *A, uint64_t cap, spmv_matrix **out, cu
     if (cap && need > cap) return SPMV_ERR_MEMORY_CAP;
     std::unique_ptr<spmv_matrix> M(new_handle(A, SPMV_COO, SPMV_ROWWISE, s));
     if (!M) return SPMV_ERR_OOM;
-    BufPtr irow, scr, acc_buf;
+    BufPtr irow, acc_buf;
     CKS(alloc_buf(need, s, &irow));
-    CKS(alloc_buf(expand_scratch_bytes(A->nnz), s, &scr));
     // IRP checks (the transformation reads no column index), read at the sync below
     CKS(alloc_buf(sizeof(AnalyzeAcc), s, &acc_buf));
     CK(cudaMemsetAsync(acc_buf->p, 0, sizeof(AnalyzeAcc), s));
     CK(launch_row_width(A->irp, A->n_rows, A->nnz, reinterpret_cast<AnalyzeAcc *>(acc_buf->p), s));
-    CK(launch_expand(A->irp, A->n_rows, A->nnz, reinterpret_cast<int32_t *>(irow->p),
-                     reinterpret_cast<int32_t *>(scr->p), s, "crs_to_coo_row"));
+    CK(launch_expand(A->irp, A->n_rows, A->nnz, reinterpret_cast<int32_t *>(irow->p), s, "crs_to_coo_row"));
     BufPtr sw;
     CKS(alloc_buf(16, s, &sw));
     CK(cudaMemsetAsync(sw->p, 0, 16, s));
@@ -726,11 +724,9 @@ spmv_status coo_col_from_ccs(const spmv_matrix *src, uint64_t cap, spmv_matrix *
     M->n_cols = src->n_cols;
     M->nnz = src->nnz;
     M->home = s;
-    BufPtr tcol, scr;
+    BufPtr tcol;
     CKS(alloc_buf(need, s, &tcol));
-    CKS(alloc_buf(expand_scratch_bytes(src->nnz), s, &scr));
-    CK(launch_expand(src->ptr, src->n_cols, src->nnz, reinterpret_cast<int32_t *>(tcol->p),
-                     reinterpret_cast<int32_t *>(scr->p), s, "ccs_to_coo_col"));
+    CK(launch_expand(src->ptr, src->n_cols, src->nnz, reinterpret_cast<int32_t *>(tcol->p), s, "ccs_to_coo_col"));
     M->ptr = src->ptr;
     M->idx = src->idx;
     M->idx2 = reinterpret_cast<const int32_t *>(tcol->p);

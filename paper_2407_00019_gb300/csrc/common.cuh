@@ -68,6 +68,22 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// 32-byte global stores (sm_100 and later), streaming cache policy: a thread
+// that owns 32 consecutive bytes writes them in one instruction, so a warp's
+// store covers whole 32-byte sectors. Two 16-byte stores per thread instead
+// leave every sector half-written by each instruction; on GB300 that pattern
+// wrote a 223 MB buffer at 0.6 of the rate of whole-sector stores. (Loads in
+// the same pattern lose nothing: the second half of a sector hits L1.) The
+// address must be 32-byte aligned.
+__device__ __forceinline__ void st_cs_v8(int32_t *p, const int (&v)[8]) {
+    asm volatile("st.global.cs.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                 :: "l"(p), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+__device__ __forceinline__ void st_cs_v4d(double *p, double a, double b, double c, double d) {
+    asm volatile("st.global.cs.v4.f64 [%0], {%1, %2, %3, %4};" :: "l"(p), "d"(a), "d"(b), "d"(c), "d"(d) : "memory");
+}
+
 // Largest i in [lo, hi) with a[i] <= key, given a[lo] <= key (a sorted).
 __device__ __forceinline__ int last_le(const int32_t *a, int lo, int hi, long long key) {
     while (hi - lo > 1) {
@@ -163,9 +179,8 @@ cudaError_t launch_tile_lines(const int32_t *ptr, int32_t n_lines, int64_t nnz, 
                               cudaStream_t s);
 
 // pointer expansion: out[k] = line of entry k (COO-Row IROW, Phase II column)
-size_t expand_scratch_bytes(int64_t nnz);
-cudaError_t launch_expand(const int32_t *ptr, int32_t n_lines, int64_t nnz, int32_t *out, int32_t *scratch,
-                          cudaStream_t s, const char *name = "expand");
+cudaError_t launch_expand(const int32_t *ptr, int32_t n_lines, int64_t nnz, int32_t *out, cudaStream_t s,
+                          const char *name = "expand");
 
 // compressed lines -> padded column-major ELL; optional fused y = A x
 cudaError_t launch_lines_to_ell(const int32_t *ptr, const int32_t *idx, const double *val, int32_t n_lines,

@@ -349,10 +349,9 @@ __global__ void __launch_bounds__(SCT_THREADS) k_col_claim(const int32_t *__rest
             if (r[j] < SLOT_CAP) T[(long long)r[j] * n_cols + c[j]] = make_int2((int)kk, row);
             else over = 1;
         }
-        if (k + SCT_ITEMS <= k1 && ((reinterpret_cast<uintptr_t>(rank + k) & 15) == 0)) {
-#pragma unroll
-            for (int h = 0; h < SCT_ITEMS / 4; ++h)
-                __stcs(reinterpret_cast<int4 *>(rank + k) + h, make_int4(r[4 * h], r[4 * h + 1], r[4 * h + 2], r[4 * h + 3]));
+        static_assert(SCT_ITEMS == 8, "a thread's ranks leave in one 32-byte store");
+        if (k + SCT_ITEMS <= k1 && ((reinterpret_cast<uintptr_t>(rank + k) & 31) == 0)) {
+            st_cs_v8(rank + k, r);
         } else {
 #pragma unroll
             for (int j = 0; j < SCT_ITEMS; ++j)
@@ -1584,7 +1583,8 @@ cudaError_t launch_col_locality(const int32_t *icol, int64_t nnz, int samples, i
 // VAL_T[p] = VAL[q], q the position of column c in row i.
 // k_ccs_sym does that in one pass. A CTA takes a tile of SYM_TILE
 // consecutive entries and each thread SYM_ITEMS consecutive ones (16-byte
-// loads of ICOL and stores of ICOL_T and VAL_T when the arrays allow it):
+// loads of ICOL and stores of ICOL_T, 32-byte stores of VAL_T, when the
+// arrays are aligned for them):
 // the thread finds the row of its first entry by a binary search of the
 // tile's row pointers (staged in shared memory) and walks on from there, so
 // every entry knows its row c, its place in the row and whether it is the
@@ -1738,8 +1738,8 @@ __global__ void __launch_bounds__(SYM_THREADS) k_ccs_sym(const int32_t *__restri
         for (int h = 0; h < SYM_ITEMS / 4; ++h)
             __stcs(reinterpret_cast<int4 *>(trow + kb) + h, make_int4(ci[4 * h], ci[4 * h + 1], ci[4 * h + 2], ci[4 * h + 3]));
 #pragma unroll
-        for (int h = 0; h < SYM_ITEMS / 2; ++h)
-            __stcs(reinterpret_cast<double2 *>(tval + kb) + h, make_double2(v[2 * h], v[2 * h + 1]));
+        for (int h = 0; h < SYM_ITEMS / 4; ++h)
+            st_cs_v4d(tval + kb + 4 * h, v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
     } else {
 #pragma unroll
         for (int j = 0; j < SYM_ITEMS; ++j)
@@ -1768,8 +1768,9 @@ cudaError_t launch_ccs_sym(const int32_t *irp, int32_t n, const int32_t *icol, c
     cudaError_t e = launch_tile_lines(irp, n, nnz, SYM_TILE, scratch, s);
     if (e != cudaSuccess) return e;
     const int n_tiles = (int)((nnz + SYM_TILE - 1) / SYM_TILE);
-    const bool vec = ((reinterpret_cast<uintptr_t>(icol) | reinterpret_cast<uintptr_t>(trow) |
-                       reinterpret_cast<uintptr_t>(tval)) & 15u) == 0;
+    // 16-byte loads of ICOL and stores of ICOL_T, 32-byte stores of VAL_T
+    const bool vec = ((reinterpret_cast<uintptr_t>(icol) | reinterpret_cast<uintptr_t>(trow)) & 15u) == 0 &&
+                     (reinterpret_cast<uintptr_t>(tval) & 31u) == 0;
     // the smallest shared-memory carveout that holds the resident CTAs (2 KB
     // each), so that the rest of the SM's 256 KB is L1, where the gathers of a
     // mirror row by its three neighbouring output rows meet (477 -> 449 us on

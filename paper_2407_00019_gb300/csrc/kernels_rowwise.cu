@@ -225,106 +225,110 @@ cudaError_t launch_tile_lines(const int32_t *ptr, int32_t n_lines, int64_t nnz, 
 }
 
 // ------------------------------------------------------------------ expand
-// Each warp expands a tile of EXP_TILE = 256 consecutive entries [k0, k1)
-// on its own (no CTA-wide barrier). The line of entry k is the largest line
-// i with ptr[i] <= k, so: every line that starts inside the tile marks its
-// first entry in the warp's part of shared memory (s_out[ptr[i] - k0] = i,
-// the largest i when empty lines share a start), entry k0 is marked with the
-// tile's first line (from the tile lines), and an inclusive max-scan over the
-// tile (8 consecutive entries per lane, then warp shuffles) fills in every
-// entry: a few integer instructions per entry instead of a search per thread
-// and a walk. The tile leaves with 16-byte streaming stores. Tiles whose
-// lines do not fit the marking budget (very many empty lines) take one
-// binary search per lane in global memory and a walk instead.
-constexpr int EXP_THREADS = 256;
+// Each warp expands the entries of 32·G consecutive lines [L0, L0 + 32G)
+// (lane l holds lines L0 + lG .. L0 + lG + G - 1): one coalesced load of their
+// pointers, then the warp's entry range [ptr[L0], ptr[L0 + 32G]) in passes of
+// EXP_TILE = 256 entries (8 per lane). The line of entry k is the largest
+// line i with ptr[i] <= k, i.e. the non-empty line holding k; lines grow with
+// their starts, so within a pass it is the last line whose start lies at or
+// before k, else the line of the pass's previous entry (the carry). In a
+// pass every non-empty line starting inside it writes its offset i - L0
+// (one byte) at its first entry in the warp's part of shared memory; a lane
+// reads its 8 slots in one 8-byte load and takes running maxima from the
+// carry on. Marks of earlier passes are never cleared: they hold lines at or
+// below the carry, so the maxima absorb them. A lane whose slots hold a line
+// above the carry is marked (ballot); the line before a lane's first slot is
+// the running maximum of the last marked lane below it (one shuffle), and
+// the next carry is lane 31's maximum. Passes start at the range's first
+// entry rounded down to a multiple of 8, so a lane's 8 entries leave in one
+// 32-byte streaming store (whole sectors per warp instruction); entries of
+// neighbouring warps in a pass's first and last group are left to them. No
+// global load after the pointers, no search, no CTA barrier; shared memory
+// moves a byte per entry. G (1..8, so offsets fit a byte) is picked on the
+// host so that a warp's range spans four passes or more.
+constexpr int EXP_THREADS = 128;
 constexpr int EXP_WARPS = EXP_THREADS / 32;
 constexpr int EXP_ITEMS = 8;
 constexpr int EXP_TILE = 32 * EXP_ITEMS;
-constexpr int EXP_MARK_MAX = 2048;  // lines a tile marks at most
 
-__global__ void __launch_bounds__(EXP_THREADS) k_expand(const int32_t *__restrict__ ptr, int32_t n_lines, int64_t nnz,
-                                                         const int32_t *__restrict__ tl, long long n_tiles,
+template <int G, bool VEC>
+__global__ void __launch_bounds__(EXP_THREADS) k_expand(const int32_t *__restrict__ ptr, int32_t n_lines, int32_t nnz,
                                                          int32_t *__restrict__ out) {
-    __shared__ __align__(16) int32_t s_out[EXP_WARPS][EXP_TILE];
+    static_assert(32 * G <= 256, "line offsets within a warp fit a byte");
+    __shared__ __align__(16) uint8_t s_mark[EXP_WARPS][EXP_TILE];
     const unsigned lane = lane_id();
-    const long long tile = (long long)blockIdx.x * EXP_WARPS + (threadIdx.x >> 5);
-    if (tile >= n_tiles) return;  // the whole warp: nothing below waits on other warps
-    const long long k0 = tile * EXP_TILE;
-    const int n = (int)min((long long)EXP_TILE, (long long)nnz - k0);
-    const int lo = tl[tile];
-    const int hi = (tile + 1 < n_tiles) ? tl[tile + 1] : n_lines - 1;
-    const int e = (int)lane * EXP_ITEMS;  // this lane's first entry within the tile
-    int32_t *so = s_out[threadIdx.x >> 5];
-    int v[EXP_ITEMS];
-    if (hi - lo <= EXP_MARK_MAX) {
+    const long long l0 = ((long long)blockIdx.x * EXP_WARPS + (threadIdx.x >> 5)) * 32 * G;
+    if (l0 >= n_lines) return;  // the whole warp: nothing below waits on other warps
+    const long long lf = l0 + (long long)lane * G;  // this lane's first line
+    const auto at = [&](long long i) { return min(max(__ldg(ptr + min(i, (long long)n_lines)), 0), nnz); };
+    int st[G + 1];  // starts of the lane's lines, then the end of its last one
 #pragma unroll
-        for (int h = 0; h < EXP_ITEMS / 4; ++h)
-            *reinterpret_cast<int4 *>(so + e + 4 * h) = make_int4(-1, -1, -1, -1);
-        __syncwarp();
-        if (lane == 0) atomicMax(&so[0], lo);
-        for (int i = lo + 1 + (int)lane; i <= hi; i += 32) {
-            const long long a = (long long)__ldg(ptr + i) - k0;  // first entry of line i
-            if (a >= 0 && a < n) atomicMax(&so[a], i);
+    for (int g = 0; g <= G; ++g) st[g] = at(lf + g);
+    const int k_lo = __shfl_sync(0xffffffffu, st[0], 0);
+    const int k_hi = __shfl_sync(0xffffffffu, st[G], 31);
+    uint8_t *sm = s_mark[threadIdx.x >> 5];
+    const int e = (int)lane * EXP_ITEMS;  // this lane's first entry within a pass
+    *reinterpret_cast<uint2 *>(sm + e) = make_uint2(0u, 0u);  // offset 0: at or below every entry's line
+    const unsigned below = (1u << lane) - 1u;
+    int carry = 0;
+    for (int b = k_lo & ~7; b < k_hi; b += EXP_TILE) {
+        __syncwarp();  // the slots written below were read in the pass before
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const unsigned a = (unsigned)(st[g] - b);
+            if (st[g + 1] > st[g] && a < (unsigned)EXP_TILE) sm[a] = (uint8_t)((int)lane * G + g);
         }
         __syncwarp();
+        const uint2 w = *reinterpret_cast<const uint2 *>(sm + e);
+        int v[EXP_ITEMS];
 #pragma unroll
-        for (int h = 0; h < EXP_ITEMS / 4; ++h) {
-            const int4 q = *reinterpret_cast<const int4 *>(so + e + 4 * h);
-            v[4 * h] = q.x;
-            v[4 * h + 1] = q.y;
-            v[4 * h + 2] = q.z;
-            v[4 * h + 3] = q.w;
-        }
+        for (int j = 0; j < EXP_ITEMS; ++j) v[j] = (int)(((j < 4 ? w.x : w.y) >> (8 * (j & 3))) & 0xffu);
+        v[0] = max(v[0], carry);
 #pragma unroll
         for (int j = 1; j < EXP_ITEMS; ++j) v[j] = max(v[j], v[j - 1]);
-        int inc = v[EXP_ITEMS - 1];
+        const unsigned lt = __ballot_sync(0xffffffffu, v[EXP_ITEMS - 1] > carry) & below;
+        const int x = __shfl_sync(0xffffffffu, v[EXP_ITEMS - 1], lt ? 31 - __clz(lt) : (int)lane);
+        if (lt) {
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int x = __shfl_up_sync(0xffffffffu, inc, o);
-            if ((int)lane >= o) inc = max(inc, x);
+            for (int j = 0; j < EXP_ITEMS; ++j) v[j] = max(v[j], x);
         }
-        int pre = __shfl_up_sync(0xffffffffu, inc, 1);
-        if (lane == 0) pre = -1;
+        carry = __shfl_sync(0xffffffffu, v[EXP_ITEMS - 1], 31);
+        const int k = b + e;
+        const int base = (int)l0;
 #pragma unroll
-        for (int j = 0; j < EXP_ITEMS; ++j) v[j] = max(v[j], pre);
-    } else {
-        if (e >= n) return;
-        const long long k = k0 + e;
-        int line = last_le(ptr, lo, hi + 1, k);
-        long long nb = (line < hi) ? (long long)ptr[line + 1] : LLONG_MAX;
+        for (int j = 0; j < EXP_ITEMS; ++j) v[j] += base;
+        if (VEC && k >= k_lo && k + EXP_ITEMS <= k_hi) {
+            st_cs_v8(out + k, v);
+        } else {
 #pragma unroll
-        for (int j = 0; j < EXP_ITEMS; ++j) {
-            while (k + j >= nb) {
-                ++line;
-                nb = (line < hi) ? (long long)ptr[line + 1] : LLONG_MAX;
-            }
-            v[j] = line;
+            for (int j = 0; j < EXP_ITEMS; ++j)
+                if (k + j >= k_lo && k + j < k_hi) __stcs(out + k + j, v[j]);
         }
-    }
-    if (e >= n) return;
-    if (e + EXP_ITEMS <= n && ((reinterpret_cast<uintptr_t>(out + k0 + e) & 15) == 0)) {
-#pragma unroll
-        for (int h = 0; h < EXP_ITEMS / 4; ++h)
-            __stcs(reinterpret_cast<int4 *>(out + k0 + e) + h,
-                   make_int4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]));
-    } else {
-#pragma unroll
-        for (int j = 0; j < EXP_ITEMS; ++j)
-            if (e + j < n) out[k0 + e + j] = v[j];
     }
 }
 
-size_t expand_scratch_bytes(int64_t nnz) { return tile_lines_bytes(nnz, EXP_TILE); }
-
-cudaError_t launch_expand(const int32_t *ptr, int32_t n_lines, int64_t nnz, int32_t *out, int32_t *scratch,
-                          cudaStream_t s, const char *name) {
-    if (nnz <= 0) return cudaSuccess;
-    cudaError_t e = launch_tile_lines(ptr, n_lines, nnz, EXP_TILE, scratch, s);
-    if (e != cudaSuccess) return e;
-    const long long n_tiles = (nnz + EXP_TILE - 1) / EXP_TILE;
+cudaError_t launch_expand(const int32_t *ptr, int32_t n_lines, int64_t nnz, int32_t *out, cudaStream_t s,
+                          const char *name) {
+    if (nnz <= 0 || n_lines <= 0) return cudaSuccess;
+    if (nnz > INT_MAX) return cudaErrorInvalidValue;  // int32 pointers bound nnz
+    // lines per lane: a warp's range should span about four passes or more
+    const double mean = (double)nnz / (double)n_lines;
+    int g = 1;
+    while (g < 8 && 32.0 * g * mean < 4.0 * EXP_TILE) g <<= 1;
+    const bool vec = (reinterpret_cast<uintptr_t>(out) & 31u) == 0;
+    const long long per_cta = (long long)EXP_WARPS * 32 * g;
+    const unsigned grid = (unsigned)((n_lines + per_cta - 1) / per_cta);
     KernelScope ks(name, s);
-    k_expand<<<(unsigned)((n_tiles + EXP_WARPS - 1) / EXP_WARPS), EXP_THREADS, 0, s>>>(ptr, n_lines, nnz, scratch,
-                                                                                      n_tiles, out);
+#define SPMVAT_EXPAND(G)                                                                                   \
+    if (vec) k_expand<G, true><<<grid, EXP_THREADS, 0, s>>>(ptr, n_lines, (int32_t)nnz, out);              \
+    else k_expand<G, false><<<grid, EXP_THREADS, 0, s>>>(ptr, n_lines, (int32_t)nnz, out);
+    switch (g) {
+    case 1: SPMVAT_EXPAND(1) break;
+    case 2: SPMVAT_EXPAND(2) break;
+    case 4: SPMVAT_EXPAND(4) break;
+    default: SPMVAT_EXPAND(8) break;
+    }
+#undef SPMVAT_EXPAND
     return cudaGetLastError();
 }
 
