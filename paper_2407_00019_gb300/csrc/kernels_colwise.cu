@@ -1581,7 +1581,7 @@ cudaError_t launch_col_locality(const int32_t *icol, int64_t nnz, int samples, i
 // ascending order. Then IRP_T = IRP and ICOL_T = ICOL, and the CCS value at
 // position p (row c, column i) is the value of the mirror entry (i, c):
 // VAL_T[p] = VAL[q], q the position of column c in row i.
-// k_ccs_sym does that in one pass. A CTA takes a tile of SYM_TILE
+// k_ccs_sym does that in one pass. A warp takes a tile of SYM_TILE
 // consecutive entries and each thread SYM_ITEMS consecutive ones (16-byte
 // loads of ICOL and stores of ICOL_T, 32-byte stores of VAL_T, when the
 // arrays are aligned for them):
@@ -1601,12 +1601,15 @@ cudaError_t launch_col_locality(const int32_t *icol, int64_t nnz, int samples, i
 // and drops what this kernel wrote), a column out of range ST_BAD_INDEX;
 // cnt[2] receives the longest row (= the longest column).
 constexpr int SYM_THREADS = 256;
+constexpr int SYM_WARPS = SYM_THREADS / 32;
 constexpr int SYM_ITEMS = 4;
-constexpr int SYM_TILE = SYM_THREADS * SYM_ITEMS;
-// row pointers a tile stages (more rows: read from global memory); kept small
-// so that the CTAs of an SM need little shared memory and the rest of the
-// 256 KB per SM serves as L1 for the mirror gathers (see the carveout below)
-constexpr int SYM_WIN = 512;
+constexpr int SYM_TILE = 32 * SYM_ITEMS;  // entries of a warp tile
+constexpr int SYM_CTAS_PER_SM = 6;        // resident CTAs at 40 registers a thread
+// row pointers a warp stages per tile (more rows: read from global memory);
+// small, so that the CTAs of an SM need little shared memory and the rest of
+// the 256 KB per SM serves as L1 for the mirror gathers (see the carveout
+// below)
+constexpr int SYM_WIN = 64;
 
 static_assert(SYM_ITEMS % 4 == 0, "16-byte accesses cover a thread's items");
 
@@ -1642,120 +1645,123 @@ __device__ __forceinline__ void sym_rows(const int32_t *rp, int lo, int hi, int 
     }
 }
 
+// Persistent warps: warp w takes the tiles w, w + (warps in the grid), ...;
+// a tile is SYM_TILE consecutive entries, SYM_ITEMS per lane. Nothing waits
+// on another warp: the tile's row pointers go to the warp's own slice of
+// shared memory, and the longest row, ST_REDO and ST_BAD_INDEX leave once
+// per warp, at its end.
 template <bool VEC>
-__global__ void __launch_bounds__(SYM_THREADS) k_ccs_sym(const int32_t *__restrict__ irp, int32_t n,
-                                                          const int32_t *__restrict__ icol,
-                                                          const double *__restrict__ val, int32_t nnz,
-                                                          const int32_t *__restrict__ tl, int n_tiles,
-                                                          int32_t *__restrict__ trow, double *__restrict__ tval,
-                                                          unsigned long long *__restrict__ cnt, int *status) {
-    __shared__ int32_t s_ptr[SYM_WIN];
-    __shared__ int s_wmax;
-    if (threadIdx.x == 0) s_wmax = 0;
-    const long long kbl = (long long)blockIdx.x * SYM_TILE + (long long)threadIdx.x * SYM_ITEMS;
-    const int m = (int)max(min((long long)SYM_ITEMS, (long long)nnz - kbl), 0ll);
-    const int kb = m > 0 ? (int)kbl : 0;
+__global__ void __launch_bounds__(SYM_THREADS, SYM_CTAS_PER_SM) k_ccs_sym(
+    const int32_t *__restrict__ irp, int32_t n, const int32_t *__restrict__ icol, const double *__restrict__ val,
+    int32_t nnz, const int32_t *__restrict__ tl, int n_tiles, int32_t *__restrict__ trow,
+    double *__restrict__ tval, unsigned long long *__restrict__ cnt, int *status) {
+    __shared__ int32_t s_ptr[SYM_WARPS][SYM_WIN];
     const unsigned lane = lane_id();
-    int ci[SYM_ITEMS];
-    if (VEC && m == SYM_ITEMS) {
+    int32_t *sp = s_ptr[threadIdx.x >> 5];
+    const int warps = (int)(gridDim.x * SYM_WARPS);
+    int wmax = 0, bad = 0, redo = 0;
+    for (int t = (int)(blockIdx.x * SYM_WARPS + (threadIdx.x >> 5)); t < n_tiles; t += warps) {
+        const long long kbl = (long long)t * SYM_TILE + (long long)lane * SYM_ITEMS;
+        const int m = (int)max(min((long long)SYM_ITEMS, (long long)nnz - kbl), 0ll);
+        const int kb = m > 0 ? (int)kbl : 0;
+        int ci[SYM_ITEMS];
+        if (VEC && m == SYM_ITEMS) {
 #pragma unroll
-        for (int h = 0; h < SYM_ITEMS / 4; ++h) {
-            const int4 w = __ldcs(reinterpret_cast<const int4 *>(icol + kb) + h);
-            ci[4 * h] = w.x;
-            ci[4 * h + 1] = w.y;
-            ci[4 * h + 2] = w.z;
-            ci[4 * h + 3] = w.w;
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < SYM_ITEMS; ++j) ci[j] = (j < m) ? __ldcs(icol + kb + j) : 0;
-    }
-    // column of the entry after this thread's last one
-    int nxt = __shfl_down_sync(0xffffffffu, ci[0], 1);
-    if (lane == 31 || m < SYM_ITEMS) nxt = (m == SYM_ITEMS && kbl + SYM_ITEMS < nnz) ? __ldg(icol + kb + SYM_ITEMS) : INT_MAX;
-    const int lo = tl[blockIdx.x];
-    const int hi = (blockIdx.x + 1 < n_tiles) ? tl[blockIdx.x + 1] : n - 1;
-    const int wn = hi - lo + 2;
-    const bool sm = wn <= SYM_WIN;
-    if (sm)
-        for (int i = threadIdx.x; i < wn; i += SYM_THREADS) s_ptr[i] = irp[lo + i];
-    __syncthreads();
-    int c[SYM_ITEMS];
-    unsigned jj[SYM_ITEMS], last = 0;
-    int wmax = 0;
-    if (m > 0) {
-        if (sm) sym_rows<SYM_ITEMS>(s_ptr, lo, hi, kb, m, c, jj, last, wmax);
-        else sym_rows<SYM_ITEMS>(irp + lo, lo, hi, kb, m, c, jj, last, wmax);
-    } else {
-#pragma unroll
-        for (int j = 0; j < SYM_ITEMS; ++j) c[j] = -1, jj[j] = 0;
-    }
-    int bad = 0, redo = 0;
-    int a[SYM_ITEMS], b[SYM_ITEMS];
-#pragma unroll
-    for (int j = 0; j < SYM_ITEMS; ++j) {
-        a[j] = b[j] = 0;
-        if (c[j] < 0) continue;
-        const int i = ci[j];
-        if ((unsigned)i >= (unsigned)n) {
-            bad = 1;
-            c[j] = -1;
-            continue;
-        }
-        const int after = (j + 1 < SYM_ITEMS) ? ci[j + 1] : nxt;
-        if (!((last >> j) & 1u) && after <= i) redo = 1;
-        a[j] = min(max(__ldg(irp + i), 0), nnz);
-        b[j] = min(max(__ldg(irp + i + 1), a[j]), nnz);
-    }
-    int q[SYM_ITEMS], g[SYM_ITEMS];
-#pragma unroll
-    for (int j = 0; j < SYM_ITEMS; ++j) {
-        q[j] = 0;
-        g[j] = -1;
-        if (c[j] >= 0 && jj[j] < (unsigned)(b[j] - a[j])) {
-            q[j] = b[j] - 1 - (int)jj[j];
-            g[j] = __ldg(icol + q[j]);
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < SYM_ITEMS; ++j) {
-        if (c[j] < 0 || g[j] == c[j]) continue;
-        int l = a[j], h = b[j];
-        while (h - l > 1) {
-            const int mid = l + ((h - l) >> 1);
-            if (__ldg(icol + mid) <= c[j]) l = mid; else h = mid;
-        }
-        if (l < b[j] && __ldg(icol + l) == c[j]) q[j] = l;
-        else redo = 1, c[j] = -1;
-    }
-    double v[SYM_ITEMS];
-#pragma unroll
-    for (int j = 0; j < SYM_ITEMS; ++j) v[j] = (c[j] >= 0) ? __ldg(val + q[j]) : 0.0;
-    // every entry is stored: a failed one leaves ST_REDO or ST_BAD_INDEX set,
-    // and the host then discards both arrays
-    if (VEC && m == SYM_ITEMS) {
-#pragma unroll
-        for (int h = 0; h < SYM_ITEMS / 4; ++h)
-            __stcs(reinterpret_cast<int4 *>(trow + kb) + h, make_int4(ci[4 * h], ci[4 * h + 1], ci[4 * h + 2], ci[4 * h + 3]));
-#pragma unroll
-        for (int h = 0; h < SYM_ITEMS / 4; ++h)
-            st_cs_v4d(tval + kb + 4 * h, v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
-    } else {
-#pragma unroll
-        for (int j = 0; j < SYM_ITEMS; ++j)
-            if (j < m) {
-                __stcs(trow + kb + j, ci[j]);
-                __stcs(tval + kb + j, v[j]);
+            for (int h = 0; h < SYM_ITEMS / 4; ++h) {
+                const int4 w = __ldcs(reinterpret_cast<const int4 *>(icol + kb) + h);
+                ci[4 * h] = w.x;
+                ci[4 * h + 1] = w.y;
+                ci[4 * h + 2] = w.z;
+                ci[4 * h + 3] = w.w;
             }
+        } else {
+#pragma unroll
+            for (int j = 0; j < SYM_ITEMS; ++j) ci[j] = (j < m) ? __ldcs(icol + kb + j) : 0;
+        }
+        // column of the entry after this thread's last one
+        int nxt = __shfl_down_sync(0xffffffffu, ci[0], 1);
+        if (lane == 31 || m < SYM_ITEMS)
+            nxt = (m == SYM_ITEMS && kbl + SYM_ITEMS < nnz) ? __ldg(icol + kb + SYM_ITEMS) : INT_MAX;
+        const int lo = tl[t];
+        const int hi = (t + 1 < n_tiles) ? tl[t + 1] : n - 1;
+        const int wn = hi - lo + 2;
+        const bool sm = wn <= SYM_WIN;
+        __syncwarp();  // the slice was read for the tile before
+        if (sm)
+            for (int i = (int)lane; i < wn; i += 32) sp[i] = irp[lo + i];
+        __syncwarp();
+        int c[SYM_ITEMS];
+        unsigned jj[SYM_ITEMS], last = 0;
+        if (m > 0) {
+            if (sm) sym_rows<SYM_ITEMS>(sp, lo, hi, kb, m, c, jj, last, wmax);
+            else sym_rows<SYM_ITEMS>(irp + lo, lo, hi, kb, m, c, jj, last, wmax);
+        } else {
+#pragma unroll
+            for (int j = 0; j < SYM_ITEMS; ++j) c[j] = -1, jj[j] = 0;
+        }
+        int a[SYM_ITEMS], b[SYM_ITEMS];
+#pragma unroll
+        for (int j = 0; j < SYM_ITEMS; ++j) {
+            a[j] = b[j] = 0;
+            if (c[j] < 0) continue;
+            const int i = ci[j];
+            if ((unsigned)i >= (unsigned)n) {
+                bad = 1;
+                c[j] = -1;
+                continue;
+            }
+            const int after = (j + 1 < SYM_ITEMS) ? ci[j + 1] : nxt;
+            if (!((last >> j) & 1u) && after <= i) redo = 1;
+            a[j] = min(max(__ldg(irp + i), 0), nnz);
+            b[j] = min(max(__ldg(irp + i + 1), a[j]), nnz);
+        }
+        int q[SYM_ITEMS], g[SYM_ITEMS];
+#pragma unroll
+        for (int j = 0; j < SYM_ITEMS; ++j) {
+            q[j] = 0;
+            g[j] = -1;
+            if (c[j] >= 0 && jj[j] < (unsigned)(b[j] - a[j])) {
+                q[j] = b[j] - 1 - (int)jj[j];
+                g[j] = __ldg(icol + q[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < SYM_ITEMS; ++j) {
+            if (c[j] < 0 || g[j] == c[j]) continue;
+            int l = a[j], h = b[j];
+            while (h - l > 1) {
+                const int mid = l + ((h - l) >> 1);
+                if (__ldg(icol + mid) <= c[j]) l = mid; else h = mid;
+            }
+            if (l < b[j] && __ldg(icol + l) == c[j]) q[j] = l;
+            else redo = 1, c[j] = -1;
+        }
+        double v[SYM_ITEMS];
+#pragma unroll
+        for (int j = 0; j < SYM_ITEMS; ++j) v[j] = (c[j] >= 0) ? __ldg(val + q[j]) : 0.0;
+        // every entry is stored: a failed one leaves ST_REDO or ST_BAD_INDEX set,
+        // and the host then discards both arrays
+        if (VEC && m == SYM_ITEMS) {
+#pragma unroll
+            for (int h = 0; h < SYM_ITEMS / 4; ++h)
+                __stcs(reinterpret_cast<int4 *>(trow + kb) + h, make_int4(ci[4 * h], ci[4 * h + 1], ci[4 * h + 2], ci[4 * h + 3]));
+#pragma unroll
+            for (int h = 0; h < SYM_ITEMS / 4; ++h)
+                st_cs_v4d(tval + kb + 4 * h, v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < SYM_ITEMS; ++j)
+                if (j < m) {
+                    __stcs(trow + kb + j, ci[j]);
+                    __stcs(tval + kb + j, v[j]);
+                }
+        }
     }
-    // the longest row: one global atomic per CTA (one per warp on a single
-    // address kept its L2 slice busy enough to slow the whole kernel)
+    // once per warp (a few thousand warps: no single L2 slice saturates)
     wmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(wmax, 0));
-    if (lane == 0 && wmax > 0) atomicMax(&s_wmax, wmax);
+    if (lane == 0 && wmax > 0) atomicMax(cnt + 2, (unsigned long long)wmax);
     if (__any_sync(0xffffffffu, redo) && lane == 0) atomicOr(status, ST_REDO);
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_BAD_INDEX);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_wmax > 0) atomicMax(cnt + 2, (unsigned long long)s_wmax);
 }
 
 size_t ccs_sym_scratch_bytes(int64_t nnz) { return tile_lines_bytes(nnz, SYM_TILE); }
@@ -1773,19 +1779,20 @@ cudaError_t launch_ccs_sym(const int32_t *irp, int32_t n, const int32_t *icol, c
                      (reinterpret_cast<uintptr_t>(tval) & 31u) == 0;
     // the smallest shared-memory carveout that holds the resident CTAs (2 KB
     // each), so that the rest of the SM's 256 KB is L1, where the gathers of a
-    // mirror row by its three neighbouring output rows meet (477 -> 449 us on
-    // the 128^3 stencil with this and the 512-row window); a cheap host call,
-    // made before every launch like set_smem_attr
+    // mirror row by its three neighbouring output rows meet; a cheap host
+    // call, made before every launch like set_smem_attr
     e = vec ? cudaFuncSetAttribute(k_ccs_sym<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 8)
             : cudaFuncSetAttribute(k_ccs_sym<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 8);
     if (e != cudaSuccess) return e;
+    const long long want = ((long long)n_tiles + SYM_WARPS - 1) / SYM_WARPS;
+    const unsigned grid = (unsigned)std::min<long long>(want, (long long)sm_count() * SYM_CTAS_PER_SM);
     KernelScope ks("ccs_sym", s);
     if (vec)
-        k_ccs_sym<true><<<(unsigned)n_tiles, SYM_THREADS, 0, s>>>(irp, n, icol, val, (int32_t)nnz, scratch, n_tiles,
-                                                                  trow, tval, cnt, status);
+        k_ccs_sym<true><<<grid, SYM_THREADS, 0, s>>>(irp, n, icol, val, (int32_t)nnz, scratch, n_tiles, trow, tval,
+                                                     cnt, status);
     else
-        k_ccs_sym<false><<<(unsigned)n_tiles, SYM_THREADS, 0, s>>>(irp, n, icol, val, (int32_t)nnz, scratch, n_tiles,
-                                                                   trow, tval, cnt, status);
+        k_ccs_sym<false><<<grid, SYM_THREADS, 0, s>>>(irp, n, icol, val, (int32_t)nnz, scratch, n_tiles, trow, tval,
+                                                      cnt, status);
     return cudaGetLastError();
 }
 
