@@ -1604,7 +1604,7 @@ constexpr int SYM_THREADS = 256;
 constexpr int SYM_WARPS = SYM_THREADS / 32;
 constexpr int SYM_ITEMS = 4;
 constexpr int SYM_TILE = 32 * SYM_ITEMS;  // entries of a warp tile
-constexpr int SYM_CTAS_PER_SM = 6;        // resident CTAs at 40 registers a thread
+constexpr int SYM_CTAS_PER_SM = 4;        // resident CTAs (up to 64 registers a thread)
 // row pointers a warp stages per tile (more rows: read from global memory);
 // small, so that the CTAs of an SM need little shared memory and the rest of
 // the 256 KB per SM serves as L1 for the mirror gathers (see the carveout
@@ -1649,7 +1649,10 @@ __device__ __forceinline__ void sym_rows(const int32_t *rp, int lo, int hi, int 
 // a tile is SYM_TILE consecutive entries, SYM_ITEMS per lane. Nothing waits
 // on another warp: the tile's row pointers go to the warp's own slice of
 // shared memory, and the longest row, ST_REDO and ST_BAD_INDEX leave once
-// per warp, at its end.
+// per warp, at its end. A warp loads its next tile's columns and row range
+// while it works on the current one, and that tile's row pointers (into two
+// registers a lane) at the end of it, so only the dependent gathers remain on
+// each tile's path.
 template <bool VEC>
 __global__ void __launch_bounds__(SYM_THREADS, SYM_CTAS_PER_SM) k_ccs_sym(
     const int32_t *__restrict__ irp, int32_t n, const int32_t *__restrict__ icol, const double *__restrict__ val,
@@ -1660,35 +1663,53 @@ __global__ void __launch_bounds__(SYM_THREADS, SYM_CTAS_PER_SM) k_ccs_sym(
     int32_t *sp = s_ptr[threadIdx.x >> 5];
     const int warps = (int)(gridDim.x * SYM_WARPS);
     int wmax = 0, bad = 0, redo = 0;
-    for (int t = (int)(blockIdx.x * SYM_WARPS + (threadIdx.x >> 5)); t < n_tiles; t += warps) {
+    // the next tile's columns and row range are loaded while this one is processed
+    const auto load_tile = [&](int t, int (&ci)[SYM_ITEMS], int &nxt, int &lo, int &hi) {
         const long long kbl = (long long)t * SYM_TILE + (long long)lane * SYM_ITEMS;
         const int m = (int)max(min((long long)SYM_ITEMS, (long long)nnz - kbl), 0ll);
         const int kb = m > 0 ? (int)kbl : 0;
-        int ci[SYM_ITEMS];
         if (VEC && m == SYM_ITEMS) {
-#pragma unroll
-            for (int h = 0; h < SYM_ITEMS / 4; ++h) {
-                const int4 w = __ldcs(reinterpret_cast<const int4 *>(icol + kb) + h);
-                ci[4 * h] = w.x;
-                ci[4 * h + 1] = w.y;
-                ci[4 * h + 2] = w.z;
-                ci[4 * h + 3] = w.w;
-            }
+            const int4 w = __ldcs(reinterpret_cast<const int4 *>(icol + kb));
+            ci[0] = w.x; ci[1] = w.y; ci[2] = w.z; ci[3] = w.w;
         } else {
 #pragma unroll
             for (int j = 0; j < SYM_ITEMS; ++j) ci[j] = (j < m) ? __ldcs(icol + kb + j) : 0;
         }
-        // column of the entry after this thread's last one
+        nxt = (m == SYM_ITEMS && kbl + SYM_ITEMS < nnz && lane == 31) ? __ldg(icol + kb + SYM_ITEMS) : INT_MAX;
+        lo = tl[t];
+        hi = (t + 1 < n_tiles) ? tl[t + 1] : n - 1;
+    };
+    // and the next tile's row pointers (at most SYM_WIN of them: two a lane)
+    const auto load_win = [&](int lo, int hi, int &w0, int &w1) {
+        const int wn = hi - lo + 2;
+        w0 = (wn <= SYM_WIN && (int)lane < wn) ? __ldg(irp + lo + lane) : 0;
+        w1 = (wn <= SYM_WIN && (int)lane + 32 < wn) ? __ldg(irp + lo + 32 + lane) : 0;
+    };
+    static_assert(SYM_WIN <= 64, "two row pointers a lane");
+    int t = (int)(blockIdx.x * SYM_WARPS + (threadIdx.x >> 5));
+    int ci_n[SYM_ITEMS] = {0, 0, 0, 0}, nx_n = INT_MAX, lo_n = 0, hi_n = 0, w0 = 0, w1 = 0;
+    if (t < n_tiles) {
+        load_tile(t, ci_n, nx_n, lo_n, hi_n);
+        load_win(lo_n, hi_n, w0, w1);
+    }
+    for (; t < n_tiles; t += warps) {
+        const long long kbl = (long long)t * SYM_TILE + (long long)lane * SYM_ITEMS;
+        const int m = (int)max(min((long long)SYM_ITEMS, (long long)nnz - kbl), 0ll);
+        const int kb = m > 0 ? (int)kbl : 0;
+        int ci[SYM_ITEMS];
+#pragma unroll
+        for (int j = 0; j < SYM_ITEMS; ++j) ci[j] = ci_n[j];
         int nxt = __shfl_down_sync(0xffffffffu, ci[0], 1);
-        if (lane == 31 || m < SYM_ITEMS)
-            nxt = (m == SYM_ITEMS && kbl + SYM_ITEMS < nnz) ? __ldg(icol + kb + SYM_ITEMS) : INT_MAX;
-        const int lo = tl[t];
-        const int hi = (t + 1 < n_tiles) ? tl[t + 1] : n - 1;
+        if (lane == 31 || m < SYM_ITEMS) nxt = (m == SYM_ITEMS) ? nx_n : INT_MAX;
+        const int lo = lo_n, hi = hi_n;
+        if (t + warps < n_tiles) load_tile(t + warps, ci_n, nx_n, lo_n, hi_n);
         const int wn = hi - lo + 2;
         const bool sm = wn <= SYM_WIN;
         __syncwarp();  // the slice was read for the tile before
-        if (sm)
-            for (int i = (int)lane; i < wn; i += 32) sp[i] = irp[lo + i];
+        if (sm) {
+            if ((int)lane < wn) sp[lane] = w0;
+            if ((int)lane + 32 < wn) sp[lane + 32] = w1;
+        }
         __syncwarp();
         int c[SYM_ITEMS];
         unsigned jj[SYM_ITEMS], last = 0;
@@ -1756,6 +1777,7 @@ __global__ void __launch_bounds__(SYM_THREADS, SYM_CTAS_PER_SM) k_ccs_sym(
                     __stcs(tval + kb + j, v[j]);
                 }
         }
+        if (t + warps < n_tiles) load_win(lo_n, hi_n, w0, w1);
     }
     // once per warp (a few thousand warps: no single L2 slice saturates)
     wmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(wmax, 0));
