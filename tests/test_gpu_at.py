@@ -243,3 +243,30 @@ def test_reserve_grows_the_pool_and_respects_hooks():
         L.spmv_reserve(1 << 60)
     assert e.value.status == 3  # SPMV_ERR_OOM
     torch.cuda.synchronize()
+
+
+def test_column_check_finds_every_position_at_every_alignment():
+    """The index check reads the body of ICOL in 16-byte loads and the entries
+    before the first 16-byte boundary and after the last whole vector one by
+    one: an out-of-range column must be found wherever it sits, with ICOL
+    starting 0, 4, 8 or 12 bytes past a 16-byte boundary."""
+    import torch
+    L = lib()
+    H = synth.random_crs(300, 200, 7, seed=63)
+    nnz = H.icol.size
+    irp = torch.from_numpy(H.irp).cuda()
+    val = torch.from_numpy(H.val).cuda()
+    for off in range(4):
+        base = torch.zeros(nnz + 4, dtype=torch.int32, device="cuda")
+        icol = base[off:off + nnz]
+        icol.copy_(torch.from_numpy(H.icol))
+        A = L.Crs(H.n_rows, H.n_cols, irp, icol, val)
+        L.spmv_validate(A)  # every column in range
+        for pos in (0, 1, 2, 3, 4, nnz // 2, nnz - 5, nnz - 4, nnz - 3, nnz - 2, nnz - 1):
+            keep = int(icol[pos])
+            icol[pos] = H.n_cols if pos % 2 else -1
+            with pytest.raises(L.SpmvError) as e:
+                L.spmv_validate(A)
+            assert e.value.status == 2, (off, pos)
+            icol[pos] = keep
+        L.spmv_validate(A)
