@@ -1686,6 +1686,7 @@ __global__ void __launch_bounds__(SYM_THREADS, SYM_CTAS_PER_SM) k_ccs_sym(
         w1 = (wn <= SYM_WIN && (int)lane + 32 < wn) ? __ldg(irp + lo + 32 + lane) : 0;
     };
     static_assert(SYM_WIN <= 64, "two row pointers a lane");
+    static_assert(SYM_ITEMS == 4, "a lane's columns are one 16-byte load");
     int t = (int)(blockIdx.x * SYM_WARPS + (threadIdx.x >> 5));
     int ci_n[SYM_ITEMS] = {0, 0, 0, 0}, nx_n = INT_MAX, lo_n = 0, hi_n = 0, w0 = 0, w1 = 0;
     if (t < n_tiles) {
